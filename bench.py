@@ -1,0 +1,380 @@
+"""Throughput of the batched implicit-complementarity QP solver on one GB300.
+
+One step = the whole hot path over one batch of synthetic QPs resident in HBM:
+Alg. 1 solve (predictor-corrector, Schur-complement Cholesky, eq. 7 line
+search, retraction) + Alg. 2 relax to kappa_relax + factor cache, then the
+Alg. 3 backward pass for an upstream gradient g.  Workload (default): 4096
+degenerate dense QPs, n=50, m=100 inequalities (half active at the optimum),
+p=10 equalities, FP32.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "QP solves+grads/sec on 1 GB300 at KKT res≤1e-5 (FP32); serve p50/p99 ms"
+UNIT = "QP solves+grads/s"
+L2_BYTES = 129 * 1024 * 1024
+
+# DRAM bytes per launch of the forward kernel from the ncu capture summarised in
+# profiles/forward_degenerate_n50.md (None until captured for the current kernel).
+FORWARD_TRAFFIC_BYTES = None
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="degenerate")
+    ap.add_argument("--batch", type=int, default=None)
+    ap.add_argument("--kappa-relax", type=float, default=1e-4)
+    ap.add_argument("--tol", type=float, default=1e-5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- algorithmic work
+def fma_counts(n: int, m: int, p: int):
+    """FMA of one factorisation, of one right-hand side, of one Newton iteration."""
+    factor = m * n * (n + 1) / 2 + n ** 3 / 6 + p * n * n / 2 + p * p * n / 2 + p ** 3 / 6
+    rhs = n * n + 2 * m * n + 2 * p * n + p * p
+    resid = n * n + 2 * m * n + 2 * p * n
+    it = factor + 2 * rhs + resid
+    return factor, rhs, it
+
+
+def forward_flops(n, m, p, iters: np.ndarray) -> float:
+    """2 x FMA over the batch: start (factor + 1 rhs), iters Newton iterations
+    (solve + relax), final factorisation at the relaxed point."""
+    factor, rhs, it = fma_counts(n, m, p)
+    return float(2.0 * np.sum((factor + rhs) + iters.astype(np.float64) * it + factor))
+
+
+def backward_bytes(n, m, p, B) -> float:
+    """Algorithmic HBM bytes of Alg. 3: read the cached factor, point, W, G and
+    g; write dQ, dq, dA, db, dG, dh."""
+    rd = n * (n + 1) / 2 + p * n + p * (p + 1) / 2 + m + n + p + m + m * n + n
+    wr = n * n + n + p * n + p + m * n + m
+    return 4.0 * B * (rd + wr)
+
+
+def fp32_alu_peak_tflops(sms=152, lanes=128, mhz=2070.0):
+    return sms * lanes * 2 * mhz * 1e6 / 1e12
+
+
+# ---------------------------------------------------------------- clocks sampler
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- CPU oracle baseline
+def cpu_oracle_rate(workload, n_target_s, seed=0, kappa_relax=1e-4):
+    """Time the FP64 oracle (solve + relax + gradients) on host cores over a
+    bounded sample of the workload; returns (instances/s, cores, sample)."""
+    from oracle import oracle as O
+    from qpgen import make_batch
+
+    cores = os.cpu_count() or 1
+    probe = make_batch(workload, 2 * cores, seed=seed, start=0)
+    t0 = time.perf_counter()
+    O.solve(probe.Q, probe.q, probe.A, probe.b, probe.G, probe.h, tol=1e-12,
+            kappa_relax=kappa_relax, g=probe.g, nthreads=cores)
+    dt = time.perf_counter() - t0
+    count = int(min(4096, max(2 * cores, probe.batch * n_target_s / max(dt, 1e-6))))
+    smp = make_batch(workload, count, seed=seed, start=0)
+    t0 = time.perf_counter()
+    O.solve(smp.Q, smp.q, smp.A, smp.b, smp.G, smp.h, tol=1e-12, kappa_relax=kappa_relax,
+            g=smp.g, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return count / dt, cores, f"{count} instances of '{workload}' (first {count} of the batch), " \
+                              f"solve tol 1e-12 + relax + gradients, {dt:.1f} s"
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from qpgen import CONFIGS, make_batch
+
+    cores = os.cpu_count() or 1
+    cfg = CONFIGS[args.workload]
+    B = args.batch or cfg["batch"]
+    # each step is a bounded sample of the workload sized to ~2 s of host work
+    probe = make_batch(args.workload, cores, seed=0)
+    t0 = time.perf_counter()
+    O.solve(probe.Q, probe.q, probe.A, probe.b, probe.G, probe.h, tol=1e-12,
+            kappa_relax=args.kappa_relax, g=probe.g, nthreads=cores)
+    per = (time.perf_counter() - t0) / probe.batch
+    count = int(max(cores, min(B, 2.0 / max(per, 1e-6))))
+    smp = make_batch(args.workload, count, seed=0)
+    run = lambda: O.solve(smp.Q, smp.q, smp.A, smp.b, smp.G, smp.h, tol=1e-12,  # noqa: E731
+                          kappa_relax=args.kappa_relax, g=smp.g, nthreads=cores)
+    for _ in range(args.warmup):
+        run()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        run()
+    dt = time.perf_counter() - t0
+    value = count * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "batch": B, "n": cfg["n"], "m": cfg["m"],
+                       "p": cfg["p"], "sample_per_step": count},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{count} instances per step of '{args.workload}'"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    import __graft_entry__ as ge
+    from paper_2605_17913_gb300.metrics import kkt_report, rel_err_inf
+    from paper_2605_17913_gb300.solver import QPSolver
+    from qpgen import CONFIGS, make_batch
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if rank == 0 or world == 1:
+        ge.build()
+    if world > 1:
+        torch.distributed.barrier()
+        ge.build()
+    cfg = CONFIGS[args.workload]
+    B = args.batch or cfg["batch"]
+    # weak scaling: every rank solves its own shard of B instances
+    data = make_batch(args.workload, B, seed=0, start=rank * B)
+    n, m, p = data.n, data.m, data.p
+    names = ("Q", "q", "A", "b", "G", "h", "g")
+    T = {k: torch.from_numpy(getattr(data, k)).to(dev) for k in names}
+    slv = QPSolver(B, n, p, m)
+    cache = slv.new_grad_cache()
+    st = dict(tol=args.tol, kappa_relax=args.kappa_relax)
+    out = dict(x=torch.empty(B, n, device=dev), y=torch.empty(B, p, device=dev),
+               z=torch.empty(B, m, device=dev), s=torch.empty(B, m, device=dev),
+               status=torch.empty(B, dtype=torch.int32, device=dev),
+               iters=torch.empty(B, dtype=torch.int32, device=dev), kkt=torch.empty(B, device=dev))
+    gout = dict(dQ=torch.empty(B, n, n, device=dev), dq=torch.empty(B, n, device=dev),
+                dA=torch.empty(B, p, n, device=dev), db=torch.empty(B, p, device=dev),
+                dG=torch.empty(B, m, n, device=dev), dh=torch.empty(B, m, device=dev))
+    settings = __import__("paper_2605_17913_gb300")._lib.default_settings(**st)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        slv.solve(T["Q"], T["q"], T["A"], T["b"], T["G"], T["h"], settings=settings,
+                  grad_cache=cache, out=out)
+        if ev is not None:
+            ev[1].record(stream)
+        slv.backward(cache, T["G"], T["g"], out=gout)
+        if ev is not None:
+            ev[2].record(stream)
+
+    for _ in range(max(3, args.warmup)):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    clocks = Clocks(local_rank)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()  # L2 flush between steps (outside the per-step events)
+        step(evs[k])
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    fwd_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    bwd_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    step_ms = sum(fwd_ms) + sum(bwd_ms)
+    # correctness of what was timed: every instance against the FP64 KKT bar and
+    # (degenerate workload) the known optimum; only passing instances count
+    res = {k: v.cpu().numpy() for k, v in out.items()}
+    rep = kkt_report(data.Q, data.q, data.A, data.b, data.G, data.h, res["x"], res["y"],
+                     res["z"], res["s"])
+    ok = (res["status"] == 0) & (rep["scaled"] <= 1e-5)
+    if args.workload == "degenerate":
+        ok &= rel_err_inf(res["x"], data.x0) <= 1e-4
+    for k, v in gout.items():
+        arr = v.cpu().numpy().reshape(B, -1)
+        ok &= np.all(np.isfinite(arr), axis=1)
+    passed = int(ok.sum())
+    local = {"ms": step_ms / args.steps, "passed": passed}
+    if world > 1:
+        t = torch.tensor([local["ms"], -passed], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_max = float(t[0])
+        tp = torch.tensor([passed], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(tp)
+        total_passed = int(tp.item())
+    else:
+        ms_max, total_passed = local["ms"], passed
+    value = total_passed / (ms_max / 1e3)
+    # ---- roofline of the dominant kernel (the forward launch) ----
+    iters = res["iters"]
+    flops = forward_flops(n, m, p, iters)
+    fwd_avg = sum(fwd_ms) / len(fwd_ms)
+    achieved = flops / (fwd_avg / 1e3) / 1e12
+    peak = fp32_alu_peak_tflops()
+    traffic = FORWARD_TRAFFIC_BYTES
+    bwd_avg = sum(bwd_ms) / len(bwd_ms)
+    bwd_gbs = backward_bytes(n, m, p, B) / (bwd_avg / 1e3) / 1e9
+    # ---- end to end through the public API with pinned host buffers ----
+    H = {k: torch.from_numpy(getattr(data, k)).pin_memory() for k in names}
+    Hout = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in
+            list(gout.items()) + [("x", out["x"]), ("status", out["status"])]}
+    h2d = sum(v.numel() * v.element_size() for v in H.values())
+    d2h = sum(v.numel() * v.element_size() for v in Hout.values())
+
+    def e2e_step():
+        for k in names:
+            T[k].copy_(H[k], non_blocking=True)
+        step()
+        for k, v in Hout.items():
+            v.copy_(gout[k] if k in gout else out[k], non_blocking=True)
+        torch.cuda.synchronize()
+
+    for _ in range(2):
+        e2e_step()
+    e2e_steps = max(3, args.steps // 2)
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    e2e_dt = (time.perf_counter() - t0) / e2e_steps
+    e2e_value = total_passed / e2e_dt if world == 1 else None
+    if world > 1:
+        te = torch.tensor([e2e_dt], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
+        e2e_value = total_passed / float(te.item())
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        rate, cores, sample = cpu_oracle_rate(args.workload, args.cpu_seconds,
+                                              kappa_relax=args.kappa_relax)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms_max, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "batch_per_gpu": B, "n": n, "m_ineq": m,
+                   "p_eq": p, "kappa_relax": args.kappa_relax, "tol_scaled_kkt": args.tol,
+                   "step": "solve (Alg. 1) + relax (Alg. 2) + backward (Alg. 3)",
+                   "l2": "inputs larger than L2 and L2 flushed between steps",
+                   "parallelism": f"replicas x{world}", "passed": total_passed,
+                   "instances": B * world},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "qp_forward_kernel",
+                     "peak_note": "FP32 FMA pipe: 152 SMs x 128 lanes x 2 x 2070 MHz"},
+        "kernels": {"forward_ms": fwd_avg, "backward_ms": bwd_avg,
+                    "backward_algorithmic_gbs": bwd_gbs,
+                    "mean_iters": float(np.mean(iters)), "max_iters": int(np.max(iters))},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk,
+        "wall_s_timed_region": wall,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,159 @@
+/*
+ * qp.h -- C ABI of libqpgpu: batched, differentiable FP32 interior-point QP
+ * solver with implicit complementarity, for one NVIDIA GB300 (sm_103a).
+ *
+ * Method: "A Differentiable Interior-Point Method in Single Precision".
+ *   Problem (eq. 1):  minimise 1/2 x'Qx + q'x  subject to  A x = b,  G x <= h.
+ *   Complementarity is kept on the manifold z .* s = kappa by the softplus
+ *   retraction z = b_k(v), s = b_k(-v) (eq. 9-11, App. C); each Newton step
+ *   solves eq. 14, here by eliminating dv into K = Q + G' diag(W) G with
+ *   W = B_k(v)/B_k(-v), a Cholesky factor of K and the range-space Schur
+ *   complement A K^-1 A' of the equality block (Alg. 1), then takes eq. 7's
+ *   step length and retracts.  Gradients follow Alg. 2 (relax to kappa_relax)
+ *   and Alg. 3 (implicit-function-theorem adjoint with the cached factor).
+ *
+ * Letters: n variables, n_eq equality rows (A, b), n_ineq inequality rows
+ * (G, h).  (The paper writes m for the equality count and p for the
+ * inequality count.)
+ *
+ * Conventions for every call:
+ *   - All matrix/vector arguments are FP32 DEVICE pointers owned by the caller,
+ *     batch-major and row-major per instance, packed (no padding):
+ *       Q[B][n][n] (symmetric, both triangles stored), q[B][n], A[B][n_eq][n],
+ *       b[B][n_eq], G[B][n_ineq][n], h[B][n_ineq]; x[B][n], y[B][n_eq],
+ *       z[B][n_ineq], s[B][n_ineq]; status[B], iters[B] int32; kkt_res[B].
+ *     Gradient outputs have the shapes of the data they differentiate.
+ *     Every pointer must be 4-byte aligned; pointers for empty blocks may be NULL.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *     enqueue work and return; nothing synchronises except create/destroy.
+ *   - Return value: QP_OK or a negative QP_E* code.  Argument errors are
+ *     detected on the host before anything is enqueued.  Per-instance
+ *     outcomes are written to status[] on the device.
+ *   - A handle holds only launch configuration for one problem size; it owns
+ *     no device memory, so one handle may serve several streams at once.
+ *     The factor cache that the backward pass reuses is caller-owned device
+ *     memory (qp_grad_cache_bytes), which keeps each forward/backward pair
+ *     independent of any other.
+ */
+#ifndef QPGPU_QP_H
+#define QPGPU_QP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes (API level) ------------------------------------------ */
+#define QP_OK 0
+#define QP_PENDING 1      /* serving: result not ready yet                    */
+#define QP_EINVAL (-1)    /* bad argument (sizes, NULL pointer, alignment)     */
+#define QP_ENOMEM (-2)    /* device allocation failed                          */
+#define QP_ECUDA (-3)     /* a CUDA runtime call failed                        */
+#define QP_EAGAIN (-4)    /* serving: not admissible now, retry later          */
+#define QP_ETIMEOUT (-5)  /* serving: a bounded wait ran out                   */
+#define QP_ENOTSUP (-6)   /* size or option not supported by this build        */
+#define QP_ESTATE (-7)    /* call out of order (e.g. backward before solve)    */
+
+/* ---- per-instance status ------------------------------------------------- */
+#define QP_SOLVED 0       /* residual measure below tol (and relax converged)  */
+#define QP_MAX_ITER 1     /* max_iter reached                                  */
+#define QP_STALLED 2      /* residual measure stopped decreasing               */
+#define QP_NUMERICAL 3    /* non-finite value or non-positive Cholesky pivot   */
+#define QP_BAD_INPUT 4    /* non-finite problem data                           */
+
+/* ---- options --------------------------------------------------------------- */
+#define QP_IMPLICIT 0     /* the paper's implicit complementarity (eq. 9-14)   */
+#define QP_STANDARD 1     /* explicit z .* s = kappa, Mehrotra (eq. 6, 8)      */
+#define QP_SIGMA_MEHROTRA 0 /* sigma = (mu_aff / kappa)^3 clipped to [0, 1]    */
+#define QP_SIGMA_CONSTANT 1 /* sigma = settings.sigma                          */
+#define QP_NORM_SCALED 0  /* scaled infinity-norm residual measure             */
+#define QP_NORM_ABS 1     /* absolute infinity norms (Alg. 1 as printed)       */
+#define QP_GWG_FP32 0     /* K = Q + G'WG formed in FP32                       */
+#define QP_GWG_TF32 1     /* G'WG on tensor cores, TF32 inputs, FP32 accumulate */
+#define QP_GWG_BF16 2     /* G'WG on tensor cores, BF16 inputs, FP32 accumulate */
+
+typedef struct {
+  int32_t batch;  /* number of independent QPs (>= 0)        */
+  int32_t n;      /* variables (>= 1)                        */
+  int32_t n_eq;   /* equality rows (0 <= n_eq <= n)          */
+  int32_t n_ineq; /* inequality rows (>= 0)                  */
+} qp_dims;
+
+typedef struct {
+  float tol;            /* stop when the residual measure < tol (Alg. 1)            */
+  int32_t max_iter;     /* Newton iterations of the solve (Alg. 1; paper: 100)      */
+  int32_t sigma_mode;   /* QP_SIGMA_*                                               */
+  float sigma;          /* constant sigma (QP_SIGMA_CONSTANT)                       */
+  float kappa_min;      /* floor on kappa_target (0: 1e-2 * tol)                    */
+  float kappa_relax;    /* central-path parameter of the gradients (Alg. 2); 0:
+                           gradients at the solution itself                         */
+  float relax_tol;      /* Alg. 2 stop tolerance (0: tol)                           */
+  int32_t relax_max_iter; /* Alg. 2 iteration cap (0: max_iter)                     */
+  int32_t formulation;  /* QP_IMPLICIT or QP_STANDARD                               */
+  int32_t residual_norm; /* QP_NORM_*                                               */
+  int32_t gwg_precision; /* QP_GWG_* (only QP_GWG_FP32 for n that fits on chip)      */
+  int32_t refine_steps;  /* iterative-refinement sweeps of each Newton solve        */
+  int32_t warm_start;    /* 1: start from the x, y, z, s passed in (z, s > 0)       */
+} qp_settings;
+
+typedef struct qp_handle qp_handle;
+
+/* Fill `s` with the defaults: tol 1e-5, max_iter 100, Mehrotra sigma,
+ * sigma 0.1, kappa_min 0 (-> 1e-2 tol), kappa_relax 1e-4, relax_tol 0,
+ * relax_max_iter 0, implicit, scaled norm, FP32 G'WG, no refinement, cold
+ * start.  (Defaults follow the paper's ablation settings where it states
+ * them: max_iter 100, kappa_relax 1e-4.) */
+void qp_settings_default(qp_settings* s);
+
+/* Create a solver handle for batches of the given size on the current
+ * device.  Allocates no device memory.  Returns QP_EINVAL (bad dims),
+ * QP_ENOTSUP (size too large for this build) or QP_ECUDA. */
+int qp_handle_create(const qp_dims* dims, qp_handle** out);
+
+/* Free the handle (host memory only). */
+int qp_handle_destroy(qp_handle* h);
+
+/* Bytes of device memory the gradient cache of one solve needs: per
+ * instance n(n+1)/2 floats of the Cholesky factor L of Q + G'WG, n_eq*n of
+ * U' = L^-1 A', n_eq(n_eq+1)/2 of the factor of U'U, n_ineq of W and the
+ * relaxed point (x, y, z), each block padded to 16 bytes. */
+size_t qp_grad_cache_bytes(const qp_dims* dims);
+
+/* Per-instance shared memory the solve kernel uses, in bytes (0 if the
+ * size is unsupported); for capacity planning. */
+size_t qp_smem_bytes(int32_t n, int32_t n_eq, int32_t n_ineq);
+
+/* Solve the batch (Alg. 1).  If grad_cache is not NULL (device memory of
+ * qp_grad_cache_bytes, 16-byte aligned), also relax each solution to
+ * settings->kappa_relax (Alg. 2; kappa_relax = 0 keeps the solution itself),
+ * factor the Newton matrix at that point and store the factor, W and the
+ * point in grad_cache for qp_backward_batch (Alg. 3).  x, y, z, s receive
+ * the solution of Alg. 1 (not the relaxed point); with settings->warm_start
+ * they are also read as the starting point.  status/iters/kkt_res may be
+ * NULL.  iters counts all Newton iterations (solve + relax); kkt_res is the
+ * FP32 residual measure at the returned point.  Instances whose data are
+ * not finite get status QP_BAD_INPUT and NaN outputs. */
+int qp_solve_batch(qp_handle* h, const qp_settings* settings, const float* Q, const float* q,
+                   const float* A, const float* b, const float* G, const float* h_,
+                   float* x, float* y, float* z, float* s, int32_t* status, int32_t* iters,
+                   float* kkt_res, float* grad_cache, void* stream);
+
+/* Vector-Jacobian product (Alg. 3) of the solve that filled grad_cache:
+ * given dl_dx[B][n], writes the gradients of <dl_dx, x(kappa_relax)> with
+ * respect to Q (symmetrised, (dx x' + x dx')/2), q, A, b, G and h.  G must be
+ * the data passed to that solve.  Any gradient pointer may be NULL to skip
+ * that block.  The result is undefined if grad_cache was not filled by a
+ * qp_solve_batch of the same size enqueued before this call. */
+int qp_backward_batch(qp_handle* h, const float* grad_cache, const float* G, const float* dl_dx,
+                      float* dQ, float* dq, float* dA, float* db, float* dG, float* dh,
+                      void* stream);
+
+/* Human-readable name of a return or status code. */
+const char* qp_status_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QPGPU_QP_H */

@@ -1,0 +1,191 @@
+// qp_api.cu -- C ABI of libqpgpu (declared in include/qp.h): argument
+// validation on the host, device workspace, kernel dispatch.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "../../include/qp.h"
+#include "qp_internal.h"
+
+using namespace qpgpu;
+
+struct qp_handle {
+  qp_dims dims;
+  int device;
+  int num_sms;
+  int fwd_threads, fwd_blocks_per_sm;
+  size_t fwd_smem;
+  int bwd_threads;
+  size_t bwd_smem;
+  long long cache_stride;  // floats per instance in the gradient cache
+};
+
+static bool aligned4(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 3) == 0; }
+
+static bool dims_ok(const qp_dims* d) {
+  return d && d->batch >= 0 && d->n >= 1 && d->n_eq >= 0 && d->n_eq <= d->n && d->n_ineq >= 0;
+}
+
+extern "C" {
+
+void qp_settings_default(qp_settings* s) {
+  if (!s) return;
+  memset(s, 0, sizeof(*s));
+  s->tol = 1e-5f;
+  s->max_iter = 100;
+  s->sigma_mode = QP_SIGMA_MEHROTRA;
+  s->sigma = 0.1f;
+  s->kappa_min = 0.0f;
+  s->kappa_relax = 1e-4f;
+  s->relax_tol = 0.0f;
+  s->relax_max_iter = 0;
+  s->formulation = QP_IMPLICIT;
+  s->residual_norm = QP_NORM_SCALED;
+  s->gwg_precision = QP_GWG_FP32;
+  s->refine_steps = 0;
+  s->warm_start = 0;
+}
+
+const char* qp_status_string(int code) {
+  switch (code) {
+    case QP_OK: return "QP_OK / QP_SOLVED";
+    case QP_PENDING: return "QP_PENDING / QP_MAX_ITER";
+    case QP_STALLED: return "QP_STALLED";
+    case QP_NUMERICAL: return "QP_NUMERICAL";
+    case QP_BAD_INPUT: return "QP_BAD_INPUT";
+    case QP_EINVAL: return "QP_EINVAL: invalid argument";
+    case QP_ENOMEM: return "QP_ENOMEM: device allocation failed";
+    case QP_ECUDA: return "QP_ECUDA: CUDA runtime error";
+    case QP_EAGAIN: return "QP_EAGAIN: not admissible now";
+    case QP_ETIMEOUT: return "QP_ETIMEOUT: bounded wait ran out";
+    case QP_ENOTSUP: return "QP_ENOTSUP: size or option not supported";
+    case QP_ESTATE: return "QP_ESTATE: call out of order";
+    default: return "unknown code";
+  }
+}
+
+size_t qp_smem_bytes(int32_t n, int32_t n_eq, int32_t n_ineq) {
+  if (n < 1 || n_eq < 0 || n_eq > n || n_ineq < 0) return 0;
+  return forward_smem_bytes(n, n_ineq, n_eq, nullptr);
+}
+
+int qp_handle_create(const qp_dims* dims, qp_handle** out) {
+  if (!out || !dims_ok(dims)) return QP_EINVAL;
+  *out = nullptr;
+  qp_handle* h = (qp_handle*)calloc(1, sizeof(qp_handle));
+  if (!h) return QP_ENOMEM;
+  h->dims = *dims;
+  const int n = dims->n, m = dims->n_ineq, p = dims->n_eq;
+  h->fwd_smem = forward_smem_bytes(n, m, p, &h->fwd_threads);
+  h->bwd_smem = backward_smem_bytes(n, m, p, &h->bwd_threads);
+  h->cache_stride = cache_layout(n, m, p).stride;
+  if (h->fwd_smem == 0 || h->bwd_smem == 0) {
+    free(h);
+    return QP_ENOTSUP;
+  }
+  if (cudaGetDevice(&h->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    free(h);
+    return QP_ECUDA;
+  }
+  h->fwd_blocks_per_sm = forward_blocks_per_sm(h->fwd_threads, h->fwd_smem);
+  if (h->fwd_blocks_per_sm < 1) {
+    cudaGetLastError();
+    free(h);
+    return QP_ENOTSUP;
+  }
+  *out = h;
+  return QP_OK;
+}
+
+int qp_handle_destroy(qp_handle* h) {
+  if (!h) return QP_EINVAL;
+  free(h);
+  return QP_OK;
+}
+
+size_t qp_grad_cache_bytes(const qp_dims* dims) {
+  if (!dims_ok(dims)) return 0;
+  return (size_t)dims->batch * (size_t)cache_layout(dims->n, dims->n_ineq, dims->n_eq).stride *
+         sizeof(float);
+}
+
+int qp_solve_batch(qp_handle* h, const qp_settings* st, const float* Q, const float* q,
+                   const float* A, const float* b, const float* G, const float* hv, float* x,
+                   float* y, float* z, float* s, int32_t* status, int32_t* iters, float* kkt_res,
+                   float* grad_cache, void* stream) {
+  if (!h || !st) return QP_EINVAL;
+  const int B = h->dims.batch, n = h->dims.n, m = h->dims.n_ineq, p = h->dims.n_eq;
+  if (B == 0) return QP_OK;
+  if (!Q || !q || !x || (p > 0 && (!A || !b || !y)) || (m > 0 && (!G || !hv || !z || !s)))
+    return QP_EINVAL;
+  const void* ptrs[] = {Q, q, A, b, G, hv, x, y, z, s, status, iters, kkt_res};
+  for (const void* ptr : ptrs)
+    if (ptr && !aligned4(ptr)) return QP_EINVAL;
+  if (grad_cache && (reinterpret_cast<uintptr_t>(grad_cache) & 15)) return QP_EINVAL;
+  if (!(st->tol > 0.0f) || st->max_iter < 0 || st->formulation < 0 || st->formulation > 1 ||
+      st->sigma_mode < 0 || st->sigma_mode > 1 || !(st->kappa_relax >= 0.0f) ||
+      st->residual_norm < 0 || st->residual_norm > 1 || st->refine_steps < 0)
+    return QP_EINVAL;
+  if (st->gwg_precision != QP_GWG_FP32) return QP_ENOTSUP;
+  if (st->sigma_mode == QP_SIGMA_CONSTANT && !(st->sigma >= 0.0f && st->sigma <= 1.0f))
+    return QP_EINVAL;
+  FwdParams P;
+  memset(&P, 0, sizeof(P));
+  P.batch = B; P.n = n; P.m = m; P.p = p;
+  P.Q = Q; P.q = q; P.A = A; P.b = b; P.G = G; P.h = hv;
+  P.x = x; P.y = y; P.z = z; P.s = s;
+  P.status = status; P.iters = iters; P.kkt = kkt_res;
+  P.tol = st->tol;
+  P.sigma = st->sigma;
+  P.kappa_min = st->kappa_min > 0.0f ? st->kappa_min : 1e-2f * st->tol;
+  P.kappa_relax = st->kappa_relax;
+  P.relax_tol = st->relax_tol > 0.0f ? st->relax_tol : st->tol;
+  P.step_frac = 1.0f;
+  P.max_iter = st->max_iter;
+  P.relax_max_iter = st->relax_max_iter > 0 ? st->relax_max_iter : st->max_iter;
+  P.sigma_mode = st->sigma_mode;
+  P.formulation = st->formulation;
+  P.norm_abs = st->residual_norm == QP_NORM_ABS;
+  P.warm_start = st->warm_start;
+  P.refine_steps = st->refine_steps;
+  P.cache = grad_cache;
+  P.cache_stride = h->cache_stride;
+  // one CTA per instance: the block scheduler hands a new instance to an SM
+  // as soon as one finishes, which balances uneven iteration counts
+  cudaError_t e = launch_forward(P, h->fwd_threads, h->fwd_smem, B, (cudaStream_t)stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return QP_ECUDA;
+  }
+  return QP_OK;
+}
+
+int qp_backward_batch(qp_handle* h, const float* grad_cache, const float* G, const float* dl_dx,
+                      float* dQ, float* dq, float* dA, float* db, float* dG, float* dh,
+                      void* stream) {
+  if (!h) return QP_EINVAL;
+  const int B = h->dims.batch, n = h->dims.n, m = h->dims.n_ineq, p = h->dims.n_eq;
+  if (B == 0) return QP_OK;
+  if (!grad_cache || !dl_dx || (m > 0 && !G)) return QP_EINVAL;
+  if (reinterpret_cast<uintptr_t>(grad_cache) & 15) return QP_EINVAL;
+  const void* ptrs[] = {G, dl_dx, dQ, dq, dA, db, dG, dh};
+  for (const void* ptr : ptrs)
+    if (ptr && !aligned4(ptr)) return QP_EINVAL;
+  BwdParams P;
+  P.batch = B; P.n = n; P.m = m; P.p = p;
+  P.G = G; P.g = dl_dx; P.cache = grad_cache; P.cache_stride = h->cache_stride;
+  P.dQ = dQ; P.dq = dq; P.dA = p > 0 ? dA : nullptr; P.db = p > 0 ? db : nullptr;
+  P.dG = m > 0 ? dG : nullptr; P.dh = m > 0 ? dh : nullptr;
+  cudaError_t e = launch_backward(P, h->bwd_threads, h->bwd_smem, (cudaStream_t)stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return QP_ECUDA;
+  }
+  return QP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,413 @@
+// qp_device.cuh -- shared-memory building blocks of the batched IPM kernels.
+//
+// One CTA owns one QP at a time.  Every per-instance array lives in shared
+// memory with strides chosen for the two access patterns used:
+//   * "vector" strides (ldg): a multiple of 4 floats whose quarter is odd, so
+//     thread-per-row float4 dot products and column reads are both free of
+//     bank conflicts; pad columns are zero, so float4 reads past n add 0;
+//   * "odd" strides (ldk) for the Cholesky factor, so that both a column
+//     (forward substitution) and a row (back substitution) of L are read by a
+//     warp without bank conflicts.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace qpgpu {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kRedK = 16;  // maximum quantities reduced by one block_reduce call
+
+__host__ __device__ inline int round4(int v) { return (v + 3) & ~3; }
+__host__ __device__ inline int ld_vec(int n) {
+  int l = round4(n < 1 ? 1 : n);
+  if (((l >> 2) & 1) == 0) l += 4;
+  return l;
+}
+__host__ __device__ inline int ld_odd(int n) { return n | 1; }
+
+// Shared-memory layout of one instance, in floats (all offsets multiples of 4).
+struct Layout {
+  int n, m, p;
+  int ldg, ldk, ldx, lds;
+  int nv, mv, pv;
+  int oQ, oG, oA, oK, oX, oS, oCol, oRed;
+  int o_q, o_x, o_rt, o_dinv, o_sdinv, o_tn;
+  int o_b, o_y, o_re, o_r3a, o_r3b, o_dya, o_dyb;
+  int o_h, o_z, o_s, o_ri, o_rz, o_rs, o_W, o_ibs, o_ea, o_eb, o_ta, o_tb;
+  int total;
+};
+
+__host__ __device__ inline Layout make_layout(int n, int m, int p, int nthreads) {
+  Layout L;
+  L.n = n; L.m = m; L.p = p;
+  L.ldg = ld_vec(n);
+  L.ldk = ld_odd(n);
+  L.ldx = round4(n);
+  L.lds = ld_odd(p > 0 ? p : 1);
+  L.nv = round4(n); L.mv = round4(m > 0 ? m : 1); L.pv = round4(p > 0 ? p : 1);
+  int o = 0;
+  auto take = [&](int cnt) { int r = o; o += round4(cnt); return r; };
+  L.oQ = take(n * L.ldg);
+  L.oG = take(m * L.ldg);
+  L.oA = take(p * L.ldg);
+  L.oK = take(n * L.ldk);
+  L.oX = take((p + 2) * L.ldx);
+  L.oS = take(p * L.lds);
+  L.oCol = take(2 * nthreads);
+  L.oRed = take(2 * 32 * kRedK);
+  L.o_q = take(L.nv); L.o_x = take(L.nv); L.o_rt = take(L.nv); L.o_dinv = take(L.nv);
+  L.o_tn = take(L.nv); L.o_sdinv = take(L.pv);
+  L.o_b = take(L.pv); L.o_y = take(L.pv); L.o_re = take(L.pv); L.o_r3a = take(L.pv);
+  L.o_r3b = take(L.pv); L.o_dya = take(L.pv); L.o_dyb = take(L.pv);
+  L.o_h = take(L.mv); L.o_z = take(L.mv); L.o_s = take(L.mv); L.o_ri = take(L.mv);
+  L.o_rz = take(L.mv); L.o_rs = take(L.mv); L.o_W = take(L.mv); L.o_ibs = take(L.mv);
+  L.o_ea = take(L.mv); L.o_eb = take(L.mv); L.o_ta = take(L.mv); L.o_tb = take(L.mv);
+  L.total = o;
+  return L;
+}
+
+// ---------------------------------------------------------------------------
+// Retraction (eq. 11) in the cancellation-free form of App. C, evaluated for
+// both signs at once: bz = b_k(v), bs = b_k(-v).  bz*bs = kappa, bz - bs = v,
+// bz + bs = sqrt(v^2 + 4 kappa).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void retract_pair(float v, float kappa, float& bz, float& bs) {
+  float rho = sqrtf(fmaf(v, v, 4.0f * kappa));
+  if (v >= 0.0f) {
+    bz = 0.5f * (v + rho);
+    bs = (2.0f * kappa) / (rho + v);
+  } else {
+    bz = (2.0f * kappa) / (rho - v);
+    bs = 0.5f * (rho - v);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Block-wide reductions of K values at once; every thread gets the results.
+// Two alternating buffers make back-to-back calls safe with one barrier each.
+// ---------------------------------------------------------------------------
+struct OpMax { __device__ float operator()(float a, float b) const { return fmaxf(a, b); } };
+struct OpMin { __device__ float operator()(float a, float b) const { return fminf(a, b); } };
+struct OpSum { __device__ float operator()(float a, float b) const { return a + b; } };
+
+template <int NT, int K, class Op>
+__device__ __forceinline__ void block_reduce(float (&v)[K], float* red, int& parity, Op op) {
+  static_assert(K <= kRedK, "too many reduced values");
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] = op(v[k], __shfl_xor_sync(kFull, v[k], o));
+  float* buf = red + parity * (32 * kRedK);
+  parity ^= 1;
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) buf[w * K + k] = v[k];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    float r = buf[k];
+    for (int j = 1; j < NT / 32; ++j) r = op(r, buf[j * K + k]);
+    v[k] = r;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Dot products with shared-memory matrices (row-major, stride ld, zero pads).
+// ---------------------------------------------------------------------------
+// Row r of M times vector x (length rounded up to 4, zero-padded).
+__device__ __forceinline__ float row_dot(const float* M, int ld, int r, const float* x, int nv) {
+  const float4* a = reinterpret_cast<const float4*>(M + r * ld);
+  const float4* b = reinterpret_cast<const float4*>(x);
+  float s0 = 0.f, s1 = 0.f;
+  int k = 0;
+  for (; k + 1 < (nv >> 2); k += 2) {
+    float4 u = a[k], v = b[k], u2 = a[k + 1], v2 = b[k + 1];
+    s0 = fmaf(u.x, v.x, s0); s0 = fmaf(u.y, v.y, s0); s0 = fmaf(u.z, v.z, s0); s0 = fmaf(u.w, v.w, s0);
+    s1 = fmaf(u2.x, v2.x, s1); s1 = fmaf(u2.y, v2.y, s1); s1 = fmaf(u2.z, v2.z, s1); s1 = fmaf(u2.w, v2.w, s1);
+  }
+  if (k < (nv >> 2)) {
+    float4 u = a[k], v = b[k];
+    s0 = fmaf(u.x, v.x, s0); s0 = fmaf(u.y, v.y, s0); s0 = fmaf(u.z, v.z, s0); s0 = fmaf(u.w, v.w, s0);
+  }
+  return s0 + s1;
+}
+
+// Two vectors at once.
+__device__ __forceinline__ void row_dot2(const float* M, int ld, int r, const float* x,
+                                         const float* y, int nv, float& ox, float& oy) {
+  const float4* a = reinterpret_cast<const float4*>(M + r * ld);
+  const float4* bx = reinterpret_cast<const float4*>(x);
+  const float4* by = reinterpret_cast<const float4*>(y);
+  float sx = 0.f, sy = 0.f;
+  for (int k = 0; k < (nv >> 2); ++k) {
+    float4 u = a[k], v = bx[k], w = by[k];
+    sx = fmaf(u.x, v.x, sx); sx = fmaf(u.y, v.y, sx); sx = fmaf(u.z, v.z, sx); sx = fmaf(u.w, v.w, sx);
+    sy = fmaf(u.x, w.x, sy); sy = fmaf(u.y, w.y, sy); sy = fmaf(u.z, w.z, sy); sy = fmaf(u.w, w.w, sy);
+  }
+  ox = sx;
+  oy = sy;
+}
+
+// out_k[c] = sum_r M[r][c] * v_k[r] for c < cols, K = 1 or 2 vectors; the
+// row range is split over thread groups and reduced in a fixed order
+// (deterministic).  Uses col scratch of 2*NT floats; ends with a barrier.
+template <int NT, int K>
+__device__ void col_dot(const float* M, int ld, int rows, int cols, const float* const (&v)[K],
+                        float* const (&out)[K], float* col, const float* add0 = nullptr,
+                        float scale0 = 1.0f) {
+  const int t = threadIdx.x;
+  int ns = NT / (cols > 0 ? cols : 1);
+  if (ns < 1) ns = 1;
+  if (ns > 16) ns = 16;
+  if (ns == 1) {
+    for (int c = t; c < cols; c += NT) {
+      float acc[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) acc[k] = 0.f;
+      for (int r = 0; r < rows; ++r) {
+        float g = M[r * ld + c];
+#pragma unroll
+        for (int k = 0; k < K; ++k) acc[k] = fmaf(g, v[k][r], acc[k]);
+      }
+      out[0][c] = add0 ? fmaf(scale0, add0[c], acc[0]) : acc[0];
+#pragma unroll
+      for (int k = 1; k < K; ++k) out[k][c] = acc[k];
+    }
+    __syncthreads();
+    return;
+  }
+  const int c = t % cols, sp = t / cols;
+  if (sp < ns) {
+    float acc[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = 0.f;
+    for (int r = sp; r < rows; r += ns) {
+      float g = M[r * ld + c];
+#pragma unroll
+      for (int k = 0; k < K; ++k) acc[k] = fmaf(g, v[k][r], acc[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) col[k * NT + sp * cols + c] = acc[k];
+  }
+  __syncthreads();
+  for (int cc = t; cc < cols; cc += NT) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      float s = col[k * NT + cc];
+      for (int j = 1; j < ns; ++j) s += col[k * NT + j * cols + cc];
+      if (k == 0 && add0) s = fmaf(scale0, add0[cc], s);
+      out[k][cc] = s;
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// K = Q + G' diag(W) G, lower triangle, 4x4 register tiles (eq. 14 with dv
+// eliminated).  Tiles are split over the contraction when there are fewer
+// tiles than threads; partial sums are added in a fixed order.
+// ---------------------------------------------------------------------------
+template <int NT>
+__device__ void syrk_gwg(const float* Q, int ldg, const float* G, const float* W, int m, int n,
+                         float* K, int ldk) {
+  const int nt = (n + 3) >> 2;
+  const int T = nt * (nt + 1) / 2;
+  int ns = NT / T;
+  if (ns < 1) ns = 1;
+  if (ns > 4) ns = 4;
+  const int chunk = (m + ns - 1) / ns;
+  for (int item0 = 0; item0 < T * ns; item0 += NT) {
+    const int item = item0 + (int)threadIdx.x;
+    const bool active = item < T * ns;
+    const int t = active ? item % T : 0;
+    const int sp = active ? item / T : 0;
+    // tile index -> (I, J), J <= I
+    int I = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while ((I + 1) * (I + 2) / 2 <= t) ++I;
+    while (I * (I + 1) / 2 > t) --I;
+    const int J = t - I * (I + 1) / 2;
+    float acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[a][c] = 0.f;
+    if (active) {
+      const int r0 = sp * chunk, r1 = min(m, r0 + chunk);
+#pragma unroll 2
+      for (int r = r0; r < r1; ++r) {
+        const float4 a = *reinterpret_cast<const float4*>(G + r * ldg + 4 * I);
+        const float4 c = *reinterpret_cast<const float4*>(G + r * ldg + 4 * J);
+        const float w = W[r];
+        const float aw[4] = {a.x * w, a.y * w, a.z * w, a.w * w};
+        const float cv[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+        for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) acc[ii][jj] = fmaf(aw[ii], cv[jj], acc[ii][jj]);
+      }
+    }
+    for (int phase = 0; phase < ns; ++phase) {
+      if (active && sp == phase) {
+#pragma unroll
+        for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) {
+            const int i = 4 * I + ii, j = 4 * J + jj;
+            if (i < n && j <= i) {
+              float* dst = K + i * ldk + j;
+              *dst = (phase == 0 ? Q[i * ldg + j] : *dst) + acc[ii][jj];
+            }
+          }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Right-looking Cholesky of the lower triangle of K (n x n, stride ldk, odd).
+// On exit K's lower triangle holds L (K = L L') and dinv[j] = 1 / L[j][j].
+// Returns false if a pivot is not positive and finite.  Ends with a barrier.
+// ---------------------------------------------------------------------------
+template <int NT>
+__device__ bool cholesky(float* K, int ldk, int n, float* dinv) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  constexpr int nw = NT / 32;
+  bool ok = true;
+  for (int j = 0; j < n; ++j) {
+    const float d = K[j * ldk + j];
+    if (!(d > 0.0f) || !(d < INFINITY)) ok = false;
+    const float inv = 1.0f / d;
+    for (int r = j + 1 + w; r < n; r += nw) {
+      const float lrj = K[r * ldk + j] * inv;
+      for (int c = j + 1 + l; c <= r; c += 32) K[r * ldk + c] = fmaf(-lrj, K[c * ldk + j], K[r * ldk + c]);
+    }
+    __syncthreads();
+  }
+  for (int j = threadIdx.x; j < n; j += NT) {
+    const float sd = sqrtf(K[j * ldk + j]);
+    dinv[j] = 1.0f / sd;
+  }
+  __syncthreads();
+  for (int r = w; r < n; r += nw) {
+    for (int c = l; c < r; c += 32) K[r * ldk + c] *= dinv[c];
+    if (l == 0) K[r * ldk + r] = 1.0f / dinv[r];
+  }
+  __syncthreads();
+  return ok;
+}
+
+// ---------------------------------------------------------------------------
+// Warp-level triangular solves for R right-hand sides held in registers
+// (lane owns rows lane + 32 s, s < S).  L stride ldk (odd => conflict-free).
+// ---------------------------------------------------------------------------
+template <int S, int R>
+__device__ __forceinline__ void warp_lower_solve(const float* L, int ldk, const float* dinv, int n,
+                                                 float (&x)[R][S]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int sl = 0; sl < S; ++sl) {
+    const int jend = min(32, n - 32 * sl);
+    for (int jj = 0; jj < jend; ++jj) {
+      const int j = 32 * sl + jj;
+      const float dj = dinv[j];
+      float xj[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        xj[r] = __shfl_sync(kFull, x[r][sl] * dj, jj);
+        if (lane == jj) x[r][sl] = xj[r];
+      }
+#pragma unroll
+      for (int s = sl; s < S; ++s) {
+        const int i = lane + 32 * s;
+        if (i > j && i < n) {
+          const float lij = L[i * ldk + j];
+#pragma unroll
+          for (int r = 0; r < R; ++r) x[r][s] = fmaf(-lij, xj[r], x[r][s]);
+        }
+      }
+    }
+  }
+}
+
+// Solve L' x = b (back substitution using rows of L).
+template <int S, int R>
+__device__ __forceinline__ void warp_upper_solve(const float* L, int ldk, const float* dinv, int n,
+                                                 float (&x)[R][S]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int sl = S - 1; sl >= 0; --sl) {
+    const int jend = min(32, n - 32 * sl);
+    for (int jj = jend - 1; jj >= 0; --jj) {
+      const int j = 32 * sl + jj;
+      const float dj = dinv[j];
+      float xj[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        xj[r] = __shfl_sync(kFull, x[r][sl] * dj, jj);
+        if (lane == jj) x[r][sl] = xj[r];
+      }
+#pragma unroll
+      for (int s = 0; s <= sl; ++s) {
+        const int i = lane + 32 * s;
+        if (i < j) {
+          const float lji = L[j * ldk + i];
+#pragma unroll
+          for (int r = 0; r < R; ++r) x[r][s] = fmaf(-lji, xj[r], x[r][s]);
+        }
+      }
+    }
+  }
+}
+
+// Solve rows of X in place (stride ldx): forward (lower) or backward (upper).
+// Rows are dealt to warps; each warp solves two rows at a time.
+template <int NT, int S, bool kUpper>
+__device__ void solve_rows_S(const float* L, int ldk, const float* dinv, int n, float* X, int ldx,
+                             int row0, int nrows) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int nw = NT / 32;
+  for (int base = 2 * w; base < nrows; base += 2 * nw) {
+    const int ra = row0 + base;
+    const bool two = base + 1 < nrows;
+    const int rb = two ? ra + 1 : ra;
+    float x[2][S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      const int i = lane + 32 * s;
+      x[0][s] = i < n ? X[ra * ldx + i] : 0.f;
+      x[1][s] = i < n ? X[rb * ldx + i] : 0.f;
+    }
+    if (kUpper)
+      warp_upper_solve<S, 2>(L, ldk, dinv, n, x);
+    else
+      warp_lower_solve<S, 2>(L, ldk, dinv, n, x);
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      const int i = lane + 32 * s;
+      if (i < n) {
+        X[ra * ldx + i] = x[0][s];
+        if (two) X[rb * ldx + i] = x[1][s];
+      }
+    }
+  }
+}
+
+template <int NT, bool kUpper>
+__device__ void solve_rows(const float* L, int ldk, const float* dinv, int n, float* X, int ldx,
+                           int row0, int nrows) {
+  if (n <= 32)
+    solve_rows_S<NT, 1, kUpper>(L, ldk, dinv, n, X, ldx, row0, nrows);
+  else if (n <= 64)
+    solve_rows_S<NT, 2, kUpper>(L, ldk, dinv, n, X, ldx, row0, nrows);
+  else if (n <= 96)
+    solve_rows_S<NT, 3, kUpper>(L, ldk, dinv, n, X, ldx, row0, nrows);
+  else
+    solve_rows_S<NT, 4, kUpper>(L, ldk, dinv, n, X, ldx, row0, nrows);
+  __syncthreads();
+}
+
+}  // namespace qpgpu

@@ -1,0 +1,231 @@
+"""CUDA path vs the FP64 oracle, through the C ABI (via the ctypes binding).
+
+Bars (stated by the method's accuracy targets):
+  scaled KKT residual of the returned point <= 1e-5 (FP64 evaluation of FP32 outputs),
+  |x - x*|_inf / max(1, |x*|_inf) <= 1e-4,  |f - f*| / max(1, |f*|) <= 1e-4,
+  |grad - grad*|_2 / max(|grad*|_2, 1e-6) <= 1e-3 per block (Q, q, A, b, G, h).
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2605_17913_gb300.metrics import kkt_report, rel_err_2, rel_err_inf
+from qpgen import make_batch
+
+pytestmark = pytest.mark.gpu
+
+TOL_KKT, TOL_X, TOL_F, TOL_G = 1e-5, 1e-4, 1e-4, 1e-3
+GRAD_KEYS = ("dQ", "dq", "dA", "db", "dG", "dh")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__ as g
+
+    g.build()
+    torch.cuda.set_device(0)
+
+
+def _dev(batch):
+    return {k: torch.from_numpy(np.ascontiguousarray(getattr(batch, k))).cuda()
+            for k in ("Q", "q", "A", "b", "G", "h", "g")}
+
+
+def gpu_run(batch, grad=False, **settings):
+    from paper_2605_17913_gb300.solver import QPSolver
+
+    T = _dev(batch)
+    slv = QPSolver(batch.batch, batch.n, batch.p, batch.m)
+    cache = slv.new_grad_cache() if grad else None
+    out = slv.solve(T["Q"], T["q"], T["A"], T["b"], T["G"], T["h"], grad_cache=cache, **settings)
+    res = {k: v.cpu().numpy() for k, v in out.items()}
+    if grad:
+        g = slv.backward(cache, T["G"], T["g"])
+        res.update({k: v.cpu().numpy() for k, v in g.items()})
+    torch.cuda.synchronize()
+    return res
+
+
+def oracle_run(batch, grad=False, kappa_relax=1e-4, **kw):
+    return O.solve(batch.Q, batch.q, batch.A, batch.b, batch.G, batch.h, tol=1e-12,
+                   kappa_relax=kappa_relax if grad else None, g=batch.g if grad else None,
+                   nthreads=8, **kw)
+
+
+def objective(batch, x):
+    x = x.astype(np.float64)
+    return (0.5 * np.einsum("bi,bij,bj->b", x, batch.Q.astype(np.float64), x)
+            + np.einsum("bi,bi->b", batch.q.astype(np.float64), x))
+
+
+def check_forward(batch, res, ref, tol_kkt=TOL_KKT):
+    assert np.all(res["status"] == 0), np.unique(res["status"], return_counts=True)
+    rep = kkt_report(batch.Q, batch.q, batch.A, batch.b, batch.G, batch.h, res["x"], res["y"],
+                     res["z"], res["s"])
+    assert rep["scaled"].max() <= tol_kkt, rep["scaled"].max()
+    assert rep["min_z"].min() > 0 and rep["min_s"].min() > 0
+    ex = rel_err_inf(res["x"], ref["x"])
+    assert ex.max() <= TOL_X, ex.max()
+    f, fs = objective(batch, res["x"]), objective(batch, ref["x"])
+    ef = np.abs(f - fs) / np.maximum(1.0, np.abs(fs))
+    assert ef.max() <= TOL_F, ef.max()
+    # the kernel's own FP32 measure agrees with the FP64 one on what passed
+    assert np.all(res["kkt"] < 1e-5)
+    return rep
+
+
+def check_grads(res, ref):
+    for k in GRAD_KEYS:
+        if ref[k].size == 0:
+            continue
+        e = rel_err_2(res[k], ref[k])
+        assert e.max() <= TOL_G, (k, e.max())
+
+
+# ---------------------------------------------------------------- forward parity
+def test_small_parity_full_batch():
+    batch = make_batch("small", 64, seed=0)
+    res = gpu_run(batch)
+    ref = oracle_run(batch)
+    rep = check_forward(batch, res, ref)
+    # multipliers are unique here (LICQ + strict complementarity hold generically)
+    assert rel_err_inf(res["y"], ref["y"]).max() <= 1e-3
+    assert rel_err_inf(res["z"], ref["z"]).max() <= 1e-3
+    # the absolute form of the residual also meets the bar at this size
+    assert rep["absolute"].max() <= 1e-5
+
+
+def test_small_gradients_vs_oracle():
+    batch = make_batch("small", 64, seed=1)
+    res = gpu_run(batch, grad=True)
+    ref = oracle_run(batch, grad=True)
+    check_grads(res, ref)
+
+
+def test_degenerate_subset_parity():
+    batch = make_batch("degenerate", 96, seed=0)
+    res = gpu_run(batch, grad=True)
+    ref = oracle_run(batch, grad=True)
+    # forward: x* is known exactly for this construction (up to the FP32 rounding of the data)
+    ex0 = rel_err_inf(res["x"], batch.x0)
+    assert ex0.max() <= TOL_X, ex0.max()
+    check_forward(batch, res, O.solve(batch.Q, batch.q, batch.A, batch.b, batch.G, batch.h,
+                                      tol=1e-12, nthreads=8))
+    check_grads(res, ref)
+
+
+def test_diff_workload_parity():
+    batch = make_batch("diff", 12, seed=0)
+    res = gpu_run(batch, grad=True)
+    ref = oracle_run(batch, grad=True)
+    check_forward(batch, res, O.solve(batch.Q, batch.q, batch.A, batch.b, batch.G, batch.h,
+                                      tol=1e-12, nthreads=8))
+    check_grads(res, ref)
+
+
+@pytest.mark.parametrize("n,m,p", [(37, 53, 3), (1, 3, 0), (5, 0, 2), (7, 12, 0), (64, 128, 6),
+                                   (3, 1, 1)])
+def test_ragged_and_edge_sizes(n, m, p):
+    batch = make_batch("small", 9, seed=5, n=n, m=m, p=p)
+    res = gpu_run(batch, grad=True)
+    ref = oracle_run(batch, grad=True)
+    check_forward(batch, res, O.solve(batch.Q, batch.q, batch.A, batch.b, batch.G, batch.h,
+                                      tol=1e-12, nthreads=8))
+    check_grads(res, ref)
+
+
+def test_unconstrained_closed_form():
+    batch = make_batch("small", 5, seed=2, m=0, p=0)
+    res = gpu_run(batch, grad=True)
+    Q, q, g = (a.astype(np.float64) for a in (batch.Q, batch.q, batch.g))
+    x = -np.linalg.solve(Q, q[..., None])[..., 0]
+    assert rel_err_inf(res["x"], x).max() <= TOL_X
+    dx = -np.linalg.solve(Q, g[..., None])[..., 0]
+    assert rel_err_2(res["dq"], dx).max() <= TOL_G
+
+
+def test_empty_batch():
+    batch = make_batch("small", 0)
+    from paper_2605_17913_gb300.solver import QPSolver
+
+    slv = QPSolver(0, batch.n, batch.p, batch.m)
+    T = _dev(batch)
+    out = slv.solve(T["Q"], T["q"], T["A"], T["b"], T["G"], T["h"])
+    assert out["x"].shape == (0, batch.n)
+
+
+def test_bad_input_flagged_per_instance():
+    batch = make_batch("small", 6, seed=3)
+    batch.G[2, 1, 3] = np.nan
+    batch.q[4, 0] = np.inf
+    res = gpu_run(batch)
+    assert res["status"][2] == 4 and res["status"][4] == 4
+    good = [0, 1, 3, 5]
+    assert np.all(res["status"][good] == 0)
+    assert np.all(np.isnan(res["x"][2]))
+
+
+def test_standard_formulation_same_optimum():
+    batch = make_batch("small", 32, seed=4)
+    res = gpu_run(batch, formulation="standard")
+    ref = oracle_run(batch)
+    check_forward(batch, res, ref)
+
+
+def test_batch_independence_bitwise():
+    """Per-instance arithmetic does not depend on the batch it runs in."""
+    big = make_batch("small", 16, seed=6)
+    one = make_batch("small", 1, seed=6, start=7)
+    rb, r1 = gpu_run(big, grad=True), gpu_run(one, grad=True)
+    for k in ("x", "y", "z", "s", "dQ", "dG"):
+        np.testing.assert_array_equal(rb[k][7], r1[k][0])
+
+
+def test_warm_start_from_solution():
+    from paper_2605_17913_gb300.solver import QPSolver
+
+    batch = make_batch("small", 8, seed=8)
+    T = _dev(batch)
+    slv = QPSolver(batch.batch, batch.n, batch.p, batch.m)
+    out = slv.solve(T["Q"], T["q"], T["A"], T["b"], T["G"], T["h"])
+    cold = out["iters"].cpu().numpy().copy()
+    out2 = slv.solve(T["Q"], T["q"], T["A"], T["b"], T["G"], T["h"], out=out, warm_start=1)
+    warm = out2["iters"].cpu().numpy()
+    assert np.all(out2["status"].cpu().numpy() == 0)
+    assert warm.max() <= 2 < cold.min()
+
+
+def test_autograd_function_matches_direct_backward():
+    from paper_2605_17913_gb300.solver import qp_layer
+
+    batch = make_batch("small", 8, seed=9)
+    T = _dev(batch)
+    leaves = {k: T[k].clone().requires_grad_(True) for k in ("Q", "q", "A", "b", "G", "h")}
+    x, status = qp_layer(*(leaves[k] for k in ("Q", "q", "A", "b", "G", "h")))
+    (x * T["g"]).sum().backward()
+    res = gpu_run(batch, grad=True)
+    for k, gk in zip(("Q", "q", "A", "b", "G", "h"), GRAD_KEYS):
+        np.testing.assert_allclose(leaves[k].grad.cpu().numpy(), res[gk], rtol=0, atol=1e-6)
+    assert torch.all(status == 0)
+
+
+# ---------------------------------------------------------------- full size
+def test_degenerate_full_size_sampled():
+    """The benchmark's workload: 4096 degenerate QPs (n=50, m=100, p=10),
+    solve + relax + backward in one launch each; every instance against the
+    known optimum and the FP64 KKT measure, a sample against the oracle."""
+    batch = make_batch("degenerate", 4096, seed=0)
+    res = gpu_run(batch, grad=True)
+    assert np.all(res["status"] == 0), np.unique(res["status"], return_counts=True)
+    rep = kkt_report(batch.Q, batch.q, batch.A, batch.b, batch.G, batch.h, res["x"], res["y"],
+                     res["z"], res["s"])
+    assert rep["scaled"].max() <= TOL_KKT
+    assert rel_err_inf(res["x"], batch.x0).max() <= TOL_X
+    idx = [0, 1, 777, 2048, 4095]
+    sub = make_batch("degenerate", 1, seed=0, start=idx[0])
+    for i in idx:
+        sub = make_batch("degenerate", 1, seed=0, start=i)
+        ref = oracle_run(sub, grad=True)
+        for k in GRAD_KEYS:
+            assert rel_err_2(res[k][i:i + 1], ref[k]).max() <= TOL_G, (i, k)
