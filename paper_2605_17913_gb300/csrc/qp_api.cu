@@ -18,6 +18,7 @@ struct qp_handle {
   size_t fwd_smem;
   int bwd_threads;
   size_t bwd_smem;
+  int amax;
   long long cache_stride;  // floats per instance in the gradient cache
 };
 
@@ -67,7 +68,7 @@ const char* qp_status_string(int code) {
 
 size_t qp_smem_bytes(int32_t n, int32_t n_eq, int32_t n_ineq) {
   if (n < 1 || n_eq < 0 || n_eq > n || n_ineq < 0) return 0;
-  return forward_smem_bytes(n, n_ineq, n_eq, nullptr);
+  return forward_config(n, n_ineq, n_eq, nullptr, nullptr);
 }
 
 int qp_handle_create(const qp_dims* dims, qp_handle** out) {
@@ -77,9 +78,9 @@ int qp_handle_create(const qp_dims* dims, qp_handle** out) {
   if (!h) return QP_ENOMEM;
   h->dims = *dims;
   const int n = dims->n, m = dims->n_ineq, p = dims->n_eq;
-  h->fwd_smem = forward_smem_bytes(n, m, p, &h->fwd_threads);
-  h->bwd_smem = backward_smem_bytes(n, m, p, &h->bwd_threads);
-  h->cache_stride = cache_layout(n, m, p).stride;
+  h->fwd_smem = forward_config(n, m, p, &h->fwd_threads, &h->amax);
+  h->bwd_smem = backward_smem_bytes(n, m, p, h->amax, &h->bwd_threads);
+  h->cache_stride = cache_layout(n, m, p, h->amax).stride;
   if (h->fwd_smem == 0 || h->bwd_smem == 0) {
     free(h);
     return QP_ENOTSUP;
@@ -109,8 +110,10 @@ int qp_handle_destroy(qp_handle* h) {
 
 size_t qp_grad_cache_bytes(const qp_dims* dims) {
   if (!dims_ok(dims)) return 0;
-  return (size_t)dims->batch * (size_t)cache_layout(dims->n, dims->n_ineq, dims->n_eq).stride *
-         sizeof(float);
+  int amax = 0;
+  if (forward_config(dims->n, dims->n_ineq, dims->n_eq, nullptr, &amax) == 0) return 0;
+  return (size_t)dims->batch *
+         (size_t)cache_layout(dims->n, dims->n_ineq, dims->n_eq, amax).stride * sizeof(float);
 }
 
 int qp_solve_batch(qp_handle* h, const qp_settings* st, const float* Q, const float* q,
@@ -135,7 +138,7 @@ int qp_solve_batch(qp_handle* h, const qp_settings* st, const float* Q, const fl
     return QP_EINVAL;
   FwdParams P;
   memset(&P, 0, sizeof(P));
-  P.batch = B; P.n = n; P.m = m; P.p = p;
+  P.batch = B; P.n = n; P.m = m; P.p = p; P.amax = h->amax;
   P.Q = Q; P.q = q; P.A = A; P.b = b; P.G = G; P.h = hv;
   P.x = x; P.y = y; P.z = z; P.s = s;
   P.status = status; P.iters = iters; P.kkt = kkt_res;
@@ -176,7 +179,7 @@ int qp_backward_batch(qp_handle* h, const float* grad_cache, const float* G, con
   for (const void* ptr : ptrs)
     if (ptr && !aligned4(ptr)) return QP_EINVAL;
   BwdParams P;
-  P.batch = B; P.n = n; P.m = m; P.p = p;
+  P.batch = B; P.n = n; P.m = m; P.p = p; P.amax = h->amax;
   P.G = G; P.g = dl_dx; P.cache = grad_cache; P.cache_stride = h->cache_stride;
   P.dQ = dQ; P.dq = dq; P.dA = p > 0 ? dA : nullptr; P.db = p > 0 ? db : nullptr;
   P.dG = m > 0 ? dG : nullptr; P.dh = m > 0 ? dh : nullptr;

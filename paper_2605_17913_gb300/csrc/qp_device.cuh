@@ -17,6 +17,7 @@ namespace qpgpu {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kRedK = 16;  // maximum quantities reduced by one block_reduce call
+constexpr int kMaxWarps = 16;  // blocks have at most 512 threads
 
 __host__ __device__ inline int round4(int v) { return (v + 3) & ~3; }
 __host__ __device__ inline int ld_vec(int n) {
@@ -25,47 +26,6 @@ __host__ __device__ inline int ld_vec(int n) {
   return l;
 }
 __host__ __device__ inline int ld_odd(int n) { return n | 1; }
-
-// Shared-memory layout of one instance, in floats (all offsets multiples of 4).
-struct Layout {
-  int n, m, p;
-  int ldg, ldk, ldx, lds;
-  int nv, mv, pv;
-  int oQ, oG, oA, oK, oX, oS, oCol, oRed;
-  int o_q, o_x, o_rt, o_dinv, o_sdinv, o_tn;
-  int o_b, o_y, o_re, o_r3a, o_r3b, o_dya, o_dyb;
-  int o_h, o_z, o_s, o_ri, o_rz, o_rs, o_W, o_ibs, o_ea, o_eb, o_ta, o_tb;
-  int total;
-};
-
-__host__ __device__ inline Layout make_layout(int n, int m, int p, int nthreads) {
-  Layout L;
-  L.n = n; L.m = m; L.p = p;
-  L.ldg = ld_vec(n);
-  L.ldk = ld_odd(n);
-  L.ldx = round4(n);
-  L.lds = ld_odd(p > 0 ? p : 1);
-  L.nv = round4(n); L.mv = round4(m > 0 ? m : 1); L.pv = round4(p > 0 ? p : 1);
-  int o = 0;
-  auto take = [&](int cnt) { int r = o; o += round4(cnt); return r; };
-  L.oQ = take(n * L.ldg);
-  L.oG = take(m * L.ldg);
-  L.oA = take(p * L.ldg);
-  L.oK = take(n * L.ldk);
-  L.oX = take((p + 2) * L.ldx);
-  L.oS = take(p * L.lds);
-  L.oCol = take(2 * nthreads);
-  L.oRed = take(2 * 32 * kRedK);
-  L.o_q = take(L.nv); L.o_x = take(L.nv); L.o_rt = take(L.nv); L.o_dinv = take(L.nv);
-  L.o_tn = take(L.nv); L.o_sdinv = take(L.pv);
-  L.o_b = take(L.pv); L.o_y = take(L.pv); L.o_re = take(L.pv); L.o_r3a = take(L.pv);
-  L.o_r3b = take(L.pv); L.o_dya = take(L.pv); L.o_dyb = take(L.pv);
-  L.o_h = take(L.mv); L.o_z = take(L.mv); L.o_s = take(L.mv); L.o_ri = take(L.mv);
-  L.o_rz = take(L.mv); L.o_rs = take(L.mv); L.o_W = take(L.mv); L.o_ibs = take(L.mv);
-  L.o_ea = take(L.mv); L.o_eb = take(L.mv); L.o_ta = take(L.mv); L.o_tb = take(L.mv);
-  L.total = o;
-  return L;
-}
 
 // ---------------------------------------------------------------------------
 // Retraction (eq. 11) in the cancellation-free form of App. C, evaluated for
@@ -98,7 +58,7 @@ __device__ __forceinline__ void block_reduce(float (&v)[K], float* red, int& par
   for (int k = 0; k < K; ++k)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v[k] = op(v[k], __shfl_xor_sync(kFull, v[k], o));
-  float* buf = red + parity * (32 * kRedK);
+  float* buf = red + parity * (kMaxWarps * kRedK);
   parity ^= 1;
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   if (l == 0) {
@@ -206,13 +166,15 @@ __device__ void col_dot(const float* M, int ld, int rows, int cols, const float*
 }
 
 // ---------------------------------------------------------------------------
-// K = Q + G' diag(W) G, lower triangle, 4x4 register tiles (eq. 14 with dv
-// eliminated).  Tiles are split over the contraction when there are fewer
-// tiles than threads; partial sums are added in a fixed order.
+// Lower triangle of K = Q + G' diag(W) G with 4x4 register tiles.  Q is read
+// from K's strict upper triangle (Q[i][j] = K[j][i] for j < i, never written
+// here) and its diagonal from qd; rows with W = 0 add nothing.  Tiles are
+// split over the contraction when there are fewer tiles than threads; the
+// partial sums are added in a fixed order (deterministic).
 // ---------------------------------------------------------------------------
 template <int NT>
-__device__ void syrk_gwg(const float* Q, int ldg, const float* G, const float* W, int m, int n,
-                         float* K, int ldk) {
+__device__ void syrk_gwg(float* K, int ldk, const float* qd, const float* G, int ldg,
+                         const float* W, int m, int n) {
   const int nt = (n + 3) >> 2;
   const int T = nt * (nt + 1) / 2;
   int ns = NT / T;
@@ -224,7 +186,6 @@ __device__ void syrk_gwg(const float* Q, int ldg, const float* G, const float* W
     const bool active = item < T * ns;
     const int t = active ? item % T : 0;
     const int sp = active ? item / T : 0;
-    // tile index -> (I, J), J <= I
     int I = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
     while ((I + 1) * (I + 2) / 2 <= t) ++I;
     while (I * (I + 1) / 2 > t) --I;
@@ -238,9 +199,9 @@ __device__ void syrk_gwg(const float* Q, int ldg, const float* G, const float* W
       const int r0 = sp * chunk, r1 = min(m, r0 + chunk);
 #pragma unroll 2
       for (int r = r0; r < r1; ++r) {
+        const float w = W[r];
         const float4 a = *reinterpret_cast<const float4*>(G + r * ldg + 4 * I);
         const float4 c = *reinterpret_cast<const float4*>(G + r * ldg + 4 * J);
-        const float w = W[r];
         const float aw[4] = {a.x * w, a.y * w, a.z * w, a.w * w};
         const float cv[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
@@ -258,7 +219,8 @@ __device__ void syrk_gwg(const float* Q, int ldg, const float* G, const float* W
             const int i = 4 * I + ii, j = 4 * J + jj;
             if (i < n && j <= i) {
               float* dst = K + i * ldk + j;
-              *dst = (phase == 0 ? Q[i * ldg + j] : *dst) + acc[ii][jj];
+              const float base = phase != 0 ? *dst : (j == i ? qd[i] : K[j * ldk + i]);
+              *dst = base + acc[ii][jj];
             }
           }
       }
@@ -295,6 +257,60 @@ __device__ bool cholesky(float* K, int ldk, int n, float* dinv) {
   for (int r = w; r < n; r += nw) {
     for (int c = l; c < r; c += 32) K[r * ldk + c] *= dinv[c];
     if (l == 0) K[r * ldk + r] = 1.0f / dinv[r];
+  }
+  __syncthreads();
+  return ok;
+}
+
+
+// ---------------------------------------------------------------------------
+// Bordered Cholesky.  Eliminates the n leading pivots of the symmetric matrix
+//     [ K   F' ]
+//     [ F   C0 ]
+// K: n x n lower triangle (stride ldk), F: nf rows of length n in Y (stride
+// ldy, odd), C: nf x nf lower triangle (stride ldc) holding C0 on entry.
+// On exit K's lower triangle is L (K = L L'), Y = F L^-T and C = C0 + Y Y'
+// (the negated Schur complement of the bordered system), dinv[j] = 1/L[j][j].
+// The rows of F and the C block ride along in the same parallel trailing
+// updates as K, so no triangular solve is needed to form Y or Y Y'.
+// Only K's lower triangle and diagonal are written.  Returns false if a
+// pivot is not positive and finite.  Ends with a barrier.
+// ---------------------------------------------------------------------------
+template <int NT>
+__device__ bool cholesky_bordered(float* K, int ldk, int n, float* Y, int ldy, int nf, float* C,
+                                  int ldc, float* dinv) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  constexpr int nw = NT / 32;
+  bool ok = true;
+  for (int j = 0; j < n; ++j) {
+    const float d = K[j * ldk + j];
+    if (!(d > 0.0f) || !(d < INFINITY)) ok = false;
+    const float inv = 1.0f / d;
+    const int nK = n - j - 1;
+    for (int rr = w; rr < nK + nf; rr += nw) {
+      if (rr < nK) {
+        const int r = j + 1 + rr;
+        const float lrj = K[r * ldk + j] * inv;
+        for (int c = j + 1 + l; c <= r; c += 32) K[r * ldk + c] = fmaf(-lrj, K[c * ldk + j], K[r * ldk + c]);
+      } else {
+        const int k = rr - nK;
+        const float lkj = Y[k * ldy + j] * inv;
+        for (int c = j + 1 + l; c < n; c += 32) Y[k * ldy + c] = fmaf(-lkj, K[c * ldk + j], Y[k * ldy + c]);
+        for (int c = l; c <= k; c += 32) C[k * ldc + c] = fmaf(lkj, Y[c * ldy + j], C[k * ldc + c]);
+      }
+    }
+    __syncthreads();
+  }
+  for (int j = threadIdx.x; j < n; j += NT) dinv[j] = 1.0f / sqrtf(K[j * ldk + j]);
+  __syncthreads();
+  for (int r = w; r < n + nf; r += nw) {
+    if (r < n) {
+      for (int c = l; c < r; c += 32) K[r * ldk + c] *= dinv[c];
+      if (l == 0) K[r * ldk + r] = 1.0f / dinv[r];
+    } else {
+      const int k = r - n;
+      for (int c = l; c < n; c += 32) Y[k * ldy + c] *= dinv[c];
+    }
   }
   __syncthreads();
   return ok;

@@ -1,6 +1,5 @@
-// qp_forward.cu -- host-side dispatch of the forward kernel by block size.
-#include "qp_device.cuh"
-#include "qp_internal.h"
+// qp_forward.cu -- host-side sizing and dispatch of the forward kernel.
+#include "qp_forward.cuh"
 
 namespace qpgpu {
 
@@ -9,13 +8,27 @@ cudaError_t launch_forward_nt(const FwdParams& P, size_t smem, int grid, cudaStr
 template <int NT>
 int forward_blocks_per_sm_nt(size_t smem);
 
-size_t forward_smem_bytes(int n, int m, int p, int* nthreads) {
+// Threads per CTA by n; amax = rows kept as multipliers, at most min(m, n)
+// (at a non-degenerate solution at most n - p rows are active), lowered to
+// fit shared memory but never below min(m, n - p); amax + p <= 128 (warp
+// solves hold at most 128 rows).
+size_t forward_config(int n, int m, int p, int* nthreads, int* amax_out) {
   const int nt = n <= 24 ? 128 : (n <= 72 ? 256 : 512);
-  const Layout L = make_layout(n, m, p, nt);
-  const size_t bytes = (size_t)L.total * sizeof(float);
   if (nthreads) *nthreads = nt;
-  if (n > 128 || p > 128 || bytes > 227 * 1024) return 0;
-  return bytes;
+  if (amax_out) *amax_out = 0;
+  if (n < 1 || n > 128 || p > 128 || p > n || m < 0) return 0;
+  int amax = m < n ? m : n;
+  if (amax + p > 128) amax = 128 - p;
+  const int floor_a = m < n - p ? m : n - p;
+  for (; amax >= floor_a && amax >= 0; --amax) {
+    const fwd::FLayout L = fwd::make_fwd_layout(n, m, p, amax, nt);
+    const size_t bytes = (size_t)L.total * sizeof(float);
+    if (bytes <= 227 * 1024) {
+      if (amax_out) *amax_out = amax;
+      return bytes;
+    }
+  }
+  return 0;
 }
 
 cudaError_t launch_forward(const FwdParams& P, int nthreads, size_t smem, int grid,

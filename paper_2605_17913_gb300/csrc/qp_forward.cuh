@@ -1,33 +1,42 @@
 // qp_forward.cuh -- batched implicit-complementarity IPM (Alg. 1, Alg. 2) for
 // QPs whose data fit in one SM's shared memory.  One CTA solves one QP.
 //
-// Per Newton iteration (Alg. 1):
-//   v = z - s, kappa = s'z / m_ineq                       (manifold coordinates)
-//   r_t = Qx + q + G'z + A'y, r_e = Ax - b, r_i = Gx + s - h,
-//   r_z = z - b_k(v), r_s = s - b_k(-v)                  (eq. 4, eq. 10)
-//   stop if the residual measure < tol
-//   W = B_k(v) / B_k(-v) = b_k(v) / b_k(-v)              (eq. 12 with b'(v) = b(v)/rho)
-//   K = Q + G' W G;  K = L L';  U = L^-1 A';  S = U'U = L_S L_S'
-//   eq. 14 with dv eliminated:  K dx + A'dy = -r_t + G't,  A dx = -r_e,
-//     t = r_z - W (r_i - r_s) + r_kappa / b_k(-v)
-//   The solution is affine in r_kappa = kappa - kappa_target, so one pass over
-//   the factor solves for the two right-hand sides t_A = r_z - W(r_i - r_s) and
-//   t_B = 1/b_k(-v); any kappa_target then costs only vector work:
-//     dx = dx_A + r_kappa dx_B (same for dy and e = G dx),
-//     ds = -e - r_i,   dz = -r_z + W (e + r_i - r_s) - r_kappa / b_k(-v),
-//     dv = dz - ds + r_z - r_s,  dkappa = -r_kappa       (eq. 13 rows 3-6)
-//   predictor kappa_target = 0 -> alpha_aff (eq. 7), mu_aff, sigma = (mu_aff/kappa)^3;
-//   corrector kappa_target = max(sigma kappa, kappa_min);
-//   alpha from eq. 7;  x += a dx, y += a dy, v += a dv, kappa += a dkappa;
-//   z = b_k(v), s = b_k(-v)                               (retraction, eq. 11, App. C)
+// Newton system.  eq. 14 (symmetric, every block bounded):
+//   [ Q - G'G   G'     A' ] [dx]     [ rho1 ]   rho1 = r_t - G'(r_i + r_z - r_s)
+//   [ G        -B_-    0  ] [dv] = - [ rho2 ]   rho2 = r_i - r_s - c r_kappa
+//   [ A         0      0  ] [dy]     [ r_e  ]   B_+ = B_k(v), B_- = B_k(-v), c = 1/(b_k(v)+b_k(-v))
+// Eliminating every dv would give K = Q + G'WG with W = B_+/B_- = z/s, whose
+// entries grow like 1/kappa on active rows; FP32 Cholesky of it fails once
+// kappa is near the tolerance.  Instead the rows are split by W:
+//   inactive I = {W <= tau}: dv_I = (G_I dx + rho2_I) / B_-   (B_- >= 1/2 there),
+//   active   A = {W >  tau}: keep lambda = dv_A - G_A dx, scaled by 1/B_+ (>= 1/2),
+// which leaves the bounded saddle-point system (tau = 1 unless more than amax
+// rows are active)
+//   [ K_I   F'] [dx]   [ rhs1 ]     K_I = Q + G_I' W_I G_I  (W_I <= tau)
+//   [ F    -D ] [mu] = [ rhs2 ]     F = [G_A; A],  D = diag(1/W_A, 0)  (1/W_A < 1/tau)
+// with rhs1 = -rho1 - G_I' (rho2_I / B_-),  rhs2 = (-rho2_A / B_+, -r_e),  mu = (lambda, dy).
+// K_I = L L' (Cholesky); Y = F L^-T and C = D + Y Y' come out of the same
+// bordered elimination; C = L_C L_C' (Cholesky, with a 1e-6 relative diagonal
+// shift that only matters when F is rank-deficient, i.e. degenerate problems).
+// Solve:  u = L^-1 rhs1,  C mu = Y u - rhs2,  dx = L^-T (u - Y' mu).
+// Recovery (eq. 13 rows 4-5): dv_I as above, dv_A = lambda + G_A dx,
+//   dz = -r_z + B_+ dv - c r_kappa,  ds = -r_s - B_- dv - c r_kappa,  dkappa = -r_kappa.
+// In exact arithmetic this is eq. 14's solution; no W-sized number is formed.
 //
-// Alg. 2 (relax) repeats the step with kappa_target = kappa_relax from the
-// solution, then the Newton matrix is factored once more at the relaxed point
-// and cached with W and the relaxed (x, y, z) for the backward pass (Alg. 3).
+// The right-hand sides are affine in r_kappa = kappa - kappa_target, so one
+// pass over the factors solves the two columns (r_kappa = 0, d/dr_kappa):
+// the predictor (kappa_target = 0 -> alpha_aff, mu_aff, Mehrotra sigma) and
+// the corrector (kappa_target = max(sigma kappa, kappa_min)) then cost only
+// vector work.  Step: alpha from eq. 7, x += a dx, y += a dy, v += a dv,
+// kappa += a dkappa, z = b_k(v), s = b_k(-v) (retraction, eq. 11, App. C).
 //
-// The explicit-complementarity ablation (eq. 6 / eq. 8, Mehrotra predictor-
-// corrector, fraction-to-boundary 0.99) uses the same factorisation with
-// W = z ./ s and a second solve for the corrector.
+// Alg. 2 (relax) repeats the step with kappa_target = kappa_relax, then the
+// system is factored once more at the relaxed point and the factors, W, the
+// active-row map and the relaxed (x, y, z) go to the gradient cache (Alg. 3).
+//
+// The explicit-complementarity ablation (eq. 6 / eq. 8) uses the same
+// two-level factorisation with W = z ./ s, a Mehrotra predictor-corrector
+// (second solve for the corrector) and fraction-to-boundary 0.99.
 #pragma once
 #include "qp_device.cuh"
 #include "qp_internal.h"
@@ -37,33 +46,81 @@ namespace qpgpu {
 namespace fwd {
 
 constexpr int ST_SOLVED = 0, ST_MAX_ITER = 1, ST_STALLED = 2, ST_NUMERICAL = 3, ST_BAD_INPUT = 4;
+constexpr float kCReg = 1e-6f;  // relative diagonal shift of C
+
+struct FLayout {
+  int n, m, p, amax, fmax;
+  int ldk, ldg, ldx, ldc, nv, mv, pv, fv;
+  int oK, oqd, oG, oA, oY, oC, oR, oCol, oRed;
+  int o_q, o_x, o_rt, o_dinv, o_tn;
+  int o_b, o_y, o_re;
+  int o_cdinv, o_D, o_ua, o_ub, o_act;
+  int o_h, o_z, o_s, o_ri, o_rz, o_rs, o_bz, o_bs, o_ea, o_eb, o_ta, o_tb, o_pos;
+  int total;
+};
+
+__host__ __device__ inline FLayout make_fwd_layout(int n, int m, int p, int amax, int nthreads) {
+  FLayout L;
+  L.n = n; L.m = m; L.p = p; L.amax = amax; L.fmax = amax + p;
+  L.ldk = ld_odd(n);
+  L.ldg = ld_vec(n);
+  L.ldx = round4(n);
+  L.ldc = ld_odd(L.fmax > 0 ? L.fmax : 1);
+  L.nv = round4(n); L.mv = round4(m > 0 ? m : 1); L.pv = round4(p > 0 ? p : 1);
+  L.fv = round4(L.fmax > 0 ? L.fmax : 1);
+  int o = 0;
+  auto take = [&](int cnt) -> int { int r = o; o += round4(cnt); return r; };
+  L.oK = take(n * L.ldk);
+  L.oqd = take(L.nv);
+  L.oG = take(m * L.ldg);
+  L.oA = take(p * L.ldg);
+  L.oY = take(L.fmax * L.ldk);
+  L.oC = take(L.fmax * L.ldc);
+  L.oR = take(2 * L.ldx);
+  L.oCol = take(2 * nthreads);
+  L.oRed = take(2 * kMaxWarps * kRedK);
+  L.o_q = take(L.nv); L.o_x = take(L.nv); L.o_rt = take(L.nv); L.o_dinv = take(L.nv);
+  L.o_tn = take(L.nv);
+  L.o_b = take(L.pv); L.o_y = take(L.pv); L.o_re = take(L.pv);
+  L.o_cdinv = take(L.fv); L.o_D = take(L.fv); L.o_ua = take(L.fv); L.o_ub = take(L.fv);
+  L.o_act = take(L.fv);
+  L.o_h = take(L.mv); L.o_z = take(L.mv); L.o_s = take(L.mv); L.o_ri = take(L.mv);
+  L.o_rz = take(L.mv); L.o_rs = take(L.mv); L.o_bz = take(L.mv); L.o_bs = take(L.mv);
+  L.o_ea = take(L.mv); L.o_eb = take(L.mv); L.o_ta = take(L.mv); L.o_tb = take(L.mv);
+  L.o_pos = take(L.mv);
+  L.total = o;
+  return L;
+}
 
 template <int NT>
 struct Solver {
-  Layout L;
-  float *Q, *G, *A, *K, *X, *S, *col, *red;
-  float *q, *x, *rt, *dinv, *tn, *sdinv;
-  float *b, *y, *re, *r3a, *r3b, *dya, *dyb;
-  float *h, *z, *s, *ri, *rz, *rs, *W, *ibs, *ea, *eb, *ta, *tb;
+  FLayout L;
+  float *K, *qd, *G, *A, *Y, *C, *R, *col, *red;
+  float *q, *x, *rt, *dinv, *tn, *b, *y, *re, *cdinv, *D, *ua, *ub;
+  float *h, *z, *s, *ri, *rz, *rs, *bz, *bs, *ea, *eb, *ta, *tb;
+  int *act, *pos;
   int parity;
-  float qn, bn, hn;  // |q|_inf, |b|_inf, |h|_inf
+  int a, nf;         // active rows, rows of F = a + p
+  float qn, bn, hn;  // |q|, |b|, |h| (infinity norms)
 
-  __device__ void bind(float* sm, int n, int m, int p) {
-    L = make_layout(n, m, p, NT);
-    Q = sm + L.oQ; G = sm + L.oG; A = sm + L.oA; K = sm + L.oK; X = sm + L.oX; S = sm + L.oS;
-    col = sm + L.oCol; red = sm + L.oRed;
+  __device__ void bind(float* sm, int n, int m, int p, int amax) {
+    L = make_fwd_layout(n, m, p, amax, NT);
+    K = sm + L.oK; qd = sm + L.oqd; G = sm + L.oG; A = sm + L.oA; Y = sm + L.oY; C = sm + L.oC;
+    R = sm + L.oR; col = sm + L.oCol; red = sm + L.oRed;
     q = sm + L.o_q; x = sm + L.o_x; rt = sm + L.o_rt; dinv = sm + L.o_dinv; tn = sm + L.o_tn;
-    sdinv = sm + L.o_sdinv;
-    b = sm + L.o_b; y = sm + L.o_y; re = sm + L.o_re; r3a = sm + L.o_r3a; r3b = sm + L.o_r3b;
-    dya = sm + L.o_dya; dyb = sm + L.o_dyb;
+    b = sm + L.o_b; y = sm + L.o_y; re = sm + L.o_re;
+    cdinv = sm + L.o_cdinv; D = sm + L.o_D; ua = sm + L.o_ua; ub = sm + L.o_ub;
+    act = reinterpret_cast<int*>(sm + L.o_act);
     h = sm + L.o_h; z = sm + L.o_z; s = sm + L.o_s; ri = sm + L.o_ri; rz = sm + L.o_rz;
-    rs = sm + L.o_rs; W = sm + L.o_W; ibs = sm + L.o_ibs; ea = sm + L.o_ea; eb = sm + L.o_eb;
+    rs = sm + L.o_rs; bz = sm + L.o_bz; bs = sm + L.o_bs; ea = sm + L.o_ea; eb = sm + L.o_eb;
     ta = sm + L.o_ta; tb = sm + L.o_tb;
+    pos = reinterpret_cast<int*>(sm + L.o_pos);
     parity = 0;
+    a = 0;
+    nf = p;
   }
 
-  // ---- load one instance into shared memory (pads stay zero) ----
-  // Returns false if any datum is not finite.
+  // ---- load one instance; Q's strict upper triangle goes to K's upper part ----
   __device__ bool load(const FwdParams& P, int bi, float* sm) {
     const int n = L.n, m = L.m, p = L.p, t = threadIdx.x;
     for (int i = t; i < L.total; i += NT) sm[i] = 0.0f;
@@ -74,9 +131,10 @@ struct Solver {
     float chk = 0.f;  // 1 if some datum is NaN or infinite
     for (int e = t; e < n * n; e += NT) {
       const int r = e / n, c = e - r * n;
+      if (c < r) continue;  // the solver reads the upper triangle of the symmetric Q
       const float v = gQ[e];
       chk = isfinite(v) ? chk : 1.0f;
-      Q[r * L.ldg + c] = v;
+      if (c == r) qd[r] = v; else K[r * L.ldk + c] = v;
     }
     for (int e = t; e < m * n; e += NT) {
       const int r = e / n, c = e - r * n;
@@ -109,85 +167,148 @@ struct Solver {
     return v[0] == 0.0f;
   }
 
-  // ---- factorisation of the reduced Newton matrix for the current W ----
-  __device__ bool factor() {
-    const int n = L.n, p = L.p, w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    syrk_gwg<NT>(Q, L.ldg, G, W, L.m, n, K, L.ldk);
-    bool ok = cholesky<NT>(K, L.ldk, n, dinv);
-    if (p > 0) {
-      for (int k = w; k < p; k += NT / 32)
-        for (int i = l; i < n; i += 32) X[k * L.ldx + i] = A[k * L.ldg + i];
-      __syncthreads();
-      solve_rows<NT, false>(K, L.ldk, dinv, n, X, L.ldx, 0, p);  // U' rows = L^-1 a_k
-      const int np = p * (p + 1) / 2;
-      for (int e = threadIdx.x; e < np; e += NT) {
-        int a = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-        while ((a + 1) * (a + 2) / 2 <= e) ++a;
-        while (a * (a + 1) / 2 > e) --a;
-        const int c = e - a * (a + 1) / 2;
-        S[a * L.lds + c] = row_dot(X, L.ldx, a, X + c * L.ldx, L.nv);
+  // (Q x)_i from K's strict upper triangle and the diagonal qd.
+  __device__ __forceinline__ float q_row_dot(int i) const {
+    float acc = qd[i] * x[i];
+    for (int j = 0; j < i; ++j) acc = fmaf(K[j * L.ldk + i], x[j], acc);
+    for (int j = i + 1; j < L.n; ++j) acc = fmaf(K[i * L.ldk + j], x[j], acc);
+    return acc;
+  }
+
+  // ---- split rows by W = bz/bs; build F = [G_A; A], D and the SYRK weights (in ea) ----
+  __device__ void partition() {
+    const int m = L.m, p = L.p, n = L.n, t = threadIdx.x, w = t >> 5, lane = t & 31;
+    float tau = 1.0f;
+    for (int round = 0; round < 40; ++round) {
+      float cnt[1] = {0.f};
+      for (int r = t; r < m; r += NT) cnt[0] += (bz[r] > tau * bs[r]) ? 1.f : 0.f;
+      block_reduce<NT, 1>(cnt, red, parity, OpSum());
+      if ((int)cnt[0] <= L.amax) break;
+      tau *= 10.0f;
+    }
+    // ordered compaction of the active rows: one warp scans all rows
+    if (w == 0) {
+      int base = 0;
+      for (int r0 = 0; r0 < m; r0 += 32) {
+        const int r = r0 + lane;
+        const bool on = r < m && bz[r] > tau * bs[r];
+        const unsigned mask = __ballot_sync(kFull, on);
+        const int k = base + __popc(mask & ((1u << lane) - 1u));
+        const bool keep = on && k < L.amax;  // always true after the tau loop; keeps act[] in bounds
+        if (r < m) pos[r] = keep ? k : -1;
+        if (keep) act[k] = r;
+        base += __popc(mask);
       }
+      if (lane == 0) reinterpret_cast<int*>(col)[0] = min(base, L.amax);  // count (col is free here)
+    }
+    __syncthreads();
+    a = reinterpret_cast<int*>(col)[0];
+    __syncthreads();
+    nf = a + p;
+    // F rows, D, C = diag(D), SYRK weights
+    for (int k = w; k < nf; k += NT / 32) {
+      const float* src = k < a ? G + act[k] * L.ldg : A + (k - a) * L.ldg;
+      for (int c = lane; c < n; c += 32) Y[k * L.ldk + c] = src[c];
+      for (int c = lane; c <= k; c += 32) C[k * L.ldc + c] = 0.f;
+    }
+    for (int k = t; k < nf; k += NT) {
+      const float d = k < a ? bs[act[k]] / bz[act[k]] : 0.f;
+      D[k] = d;
+    }
+    for (int r = t; r < m; r += NT) ea[r] = pos[r] < 0 ? bz[r] / bs[r] : 0.f;
+    __syncthreads();
+    for (int k = t; k < nf; k += NT) C[k * L.ldc + k] = D[k];
+    __syncthreads();
+  }
+
+  // ---- factor K_I and the bordered block ----
+  __device__ bool factor() {
+    syrk_gwg<NT>(K, L.ldk, qd, G, L.ldg, ea, L.m, L.n);
+    bool ok = cholesky_bordered<NT>(K, L.ldk, L.n, Y, L.ldk, nf, C, L.ldc, dinv);
+    if (nf > 0) {
+      float dm[1] = {1.0f};
+      for (int k = threadIdx.x; k < nf; k += NT) dm[0] = fmaxf(dm[0], C[k * L.ldc + k]);
+      block_reduce<NT, 1>(dm, red, parity, OpMax());
+      const float shift = kCReg * dm[0];
+      for (int k = threadIdx.x; k < nf; k += NT) C[k * L.ldc + k] += shift;
       __syncthreads();
-      ok = cholesky<NT>(S, L.lds, p, sdinv) && ok;
+      ok = cholesky<NT>(C, L.ldc, nf, cdinv) && ok;
     }
     return ok;
   }
 
-  // Small p x p solves L_S L_S' y = r for one right-hand side held by a warp.
   template <int SP>
-  __device__ void small_solve(float* v) {
+  __device__ void c_solve(float* v) {
     const int lane = threadIdx.x & 31;
     float r[1][SP];
 #pragma unroll
     for (int s2 = 0; s2 < SP; ++s2) {
       const int i = lane + 32 * s2;
-      r[0][s2] = i < L.p ? v[i] : 0.f;
+      r[0][s2] = i < nf ? v[i] : 0.f;
     }
-    warp_lower_solve<SP, 1>(S, L.lds, sdinv, L.p, r);
-    warp_upper_solve<SP, 1>(S, L.lds, sdinv, L.p, r);
+    warp_lower_solve<SP, 1>(C, L.ldc, cdinv, nf, r);
+    warp_upper_solve<SP, 1>(C, L.ldc, cdinv, nf, r);
 #pragma unroll
     for (int s2 = 0; s2 < SP; ++s2) {
       const int i = lane + 32 * s2;
-      if (i < L.p) v[i] = r[0][s2];
+      if (i < nf) v[i] = r[0][s2];
     }
   }
 
-  // ---- solve K dx + A'dy = r1_k, A dx = r3_k for nrhs (1 or 2) systems ----
-  // r1_k in X row p+k, r3 in r3a/r3b; dx_k returned in X row p+k, dy in dya/dyb.
-  __device__ void solve(int nrhs) {
-    const int n = L.n, p = L.p, t = threadIdx.x, w = t >> 5;
-    solve_rows<NT, false>(K, L.ldk, dinv, n, X, L.ldx, p, nrhs);
-    if (p > 0) {
-      for (int e = t; e < p * nrhs; e += NT) {
-        const int k = e / p, a = e - k * p;
-        float* dy = k == 0 ? dya : dyb;
-        const float* r3 = k == 0 ? r3a : r3b;
-        dy[a] = row_dot(X, L.ldx, a, X + (p + k) * L.ldx, L.nv) - r3[a];
+  // ---- solve [K_I F'; F -D] (dx, mu) = (rhs1, rhs2) for columns slot0..slot0+nrhs-1 ----
+  // rhs1 in R rows, rhs2 in ua (column 0) / ub (column 1); dx returned in R, mu in ua/ub.
+  __device__ void solve(int slot0, int nrhs) {
+    const int n = L.n, t = threadIdx.x, w = t >> 5;
+    solve_rows<NT, false>(K, L.ldk, dinv, n, R, L.ldx, slot0, nrhs);
+    if (nf > 0) {
+      for (int e = t; e < nf * nrhs; e += NT) {
+        const int k = e % nf, col_ = slot0 + e / nf;
+        float* u = col_ == 0 ? ua : ub;
+        const float* yk = Y + k * L.ldk;
+        const float* rr = R + col_ * L.ldx;
+        float acc = 0.f;
+        for (int i = 0; i < n; ++i) acc = fmaf(yk[i], rr[i], acc);
+        u[k] = acc - u[k];
       }
       __syncthreads();
       if (w < nrhs) {
-        float* dy = w == 0 ? dya : dyb;
-        if (p <= 32) small_solve<1>(dy);
-        else if (p <= 64) small_solve<2>(dy);
-        else if (p <= 96) small_solve<3>(dy);
-        else small_solve<4>(dy);
+        float* u = (slot0 + w) == 0 ? ua : ub;
+        if (nf <= 32) c_solve<1>(u);
+        else if (nf <= 64) c_solve<2>(u);
+        else if (nf <= 96) c_solve<3>(u);
+        else c_solve<4>(u);
       }
       __syncthreads();
       for (int e = t; e < n * nrhs; e += NT) {
-        const int k = e / n, i = e - k * n;
-        const float* dy = k == 0 ? dya : dyb;
-        float acc = X[(p + k) * L.ldx + i];
-        for (int a = 0; a < p; ++a) acc = fmaf(-X[a * L.ldx + i], dy[a], acc);
-        X[(p + k) * L.ldx + i] = acc;
+        const int i = e % n, col_ = slot0 + e / n;
+        const float* u = col_ == 0 ? ua : ub;
+        float acc = R[col_ * L.ldx + i];
+        for (int k = 0; k < nf; ++k) acc = fmaf(-Y[k * L.ldk + i], u[k], acc);
+        R[col_ * L.ldx + i] = acc;
       }
       __syncthreads();
     }
-    solve_rows<NT, true>(K, L.ldk, dinv, n, X, L.ldx, p, nrhs);
+    solve_rows<NT, true>(K, L.ldk, dinv, n, R, L.ldx, slot0, nrhs);
   }
 
-  // ---- residuals (eq. 4) and the measure; for the implicit method also the
-  // retraction residuals (eq. 10), W, 1/b_k(-v) and t_A.  kappa is s'z/m.
-  // mode: 0 solve (complementarity term max z.*s), 1 relax (|kappa-kr|/kr).
+  // e_k = G dx_k for the solved columns
+  __device__ void g_times_dx(int slot0, int nrhs) {
+    for (int r = threadIdx.x; r < L.m; r += NT) {
+      if (nrhs == 2) {
+        float u, v;
+        row_dot2(G, L.ldg, r, R, R + L.ldx, L.nv, u, v);
+        ea[r] = u;
+        eb[r] = v;
+      } else {
+        (slot0 == 0 ? ea : eb)[r] = row_dot(G, L.ldg, r, R + slot0 * L.ldx, L.nv);
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- residuals (eq. 4, eq. 10) and the measure ----
+  // implicit: bz = b_k(v), bs = b_k(-v) with kappa = s'z/m; standard: bz = z, bs = s.
+  // mode 0: complementarity term max z.*s; mode 1 (relax): |kappa - kr| / kr.
   __device__ float residuals(const FwdParams& P, bool implicit, int mode, float& kappa) {
     const int n = L.n, m = L.m, p = L.p, t = threadIdx.x;
     float ks[1] = {0.f};
@@ -199,21 +320,19 @@ struct Solver {
       float* oo[1] = {tn};
       col_dot<NT, 1>(G, L.ldg, m, n, vv, oo, col);
     }
-    // maxima: 0 |rt| 1 |Qx| 2 |A'y| 3 |G'z| 4 |re| 5 |Ax| 6 |ri| 7 |Gx| 8 |s| 9 zs 10 |rz,rs| 11 |z|
-    float mx[12];
+    // 0 |rt| 1 |Qx| 2 |A'y| 3 |G'z| 4 |re| 5 |Ax| 6 |ri| 7 |Gx| 8 |s| 9 zs 10 |rz,rs| 11 |z| 12 nonfinite
+    float mx[13];
 #pragma unroll
-    for (int k = 0; k < 12; ++k) mx[k] = 0.f;
-    float nanflag = 0.f;  // fmaxf drops NaN, so count non-finite values separately
-    const int tot = n + m + p;
-    for (int u = t; u < tot; u += NT) {
+    for (int k = 0; k < 13; ++k) mx[k] = 0.f;
+    for (int u = t; u < n + m + p; u += NT) {
       if (u < n) {
         const int i = u;
-        const float qx = row_dot(Q, L.ldg, i, x, L.nv);
+        const float qx = q_row_dot(i);
         float aty = 0.f;
         for (int k = 0; k < p; ++k) aty = fmaf(A[k * L.ldg + i], y[k], aty);
         const float r = qx + q[i] + tn[i] + aty;
         rt[i] = r;
-        nanflag += isfinite(r) ? 0.f : 1.f;
+        mx[12] += isfinite(r) ? 0.f : 1.f;
         mx[0] = fmaxf(mx[0], fabsf(r)); mx[1] = fmaxf(mx[1], fabsf(qx));
         mx[2] = fmaxf(mx[2], fabsf(aty)); mx[3] = fmaxf(mx[3], fabsf(tn[i]));
       } else if (u < n + m) {
@@ -221,85 +340,92 @@ struct Solver {
         const float gx = row_dot(G, L.ldg, r, x, L.nv);
         const float rii = gx + s[r] - h[r];
         ri[r] = rii;
-        nanflag += (isfinite(rii) && isfinite(z[r]) && isfinite(s[r])) ? 0.f : 1.f;
+        mx[12] += (isfinite(rii) && isfinite(z[r]) && isfinite(s[r])) ? 0.f : 1.f;
         mx[6] = fmaxf(mx[6], fabsf(rii)); mx[7] = fmaxf(mx[7], fabsf(gx));
         mx[8] = fmaxf(mx[8], fabsf(s[r])); mx[9] = fmaxf(mx[9], z[r] * s[r]);
         mx[11] = fmaxf(mx[11], fabsf(z[r]));
         if (implicit) {
-          float bz, bs;
-          retract_pair(z[r] - s[r], kappa, bz, bs);
-          const float rzz = z[r] - bz, rss = s[r] - bs;
-          rz[r] = rzz; rs[r] = rss;
-          const float Wr = bz / bs;
-          W[r] = Wr;
-          ibs[r] = 1.0f / bs;
-          ta[r] = rzz - Wr * (rii - rss);
+          float pz, ps;
+          retract_pair(z[r] - s[r], kappa, pz, ps);
+          const float rzz = z[r] - pz, rss = s[r] - ps;
+          rz[r] = rzz; rs[r] = rss; bz[r] = pz; bs[r] = ps;
           mx[10] = fmaxf(mx[10], fmaxf(fabsf(rzz), fabsf(rss)));
         } else {
-          const float Wr = z[r] / s[r];
-          W[r] = Wr;
-          ibs[r] = 1.0f / s[r];
+          bz[r] = z[r]; bs[r] = s[r];
         }
       } else {
         const int k = u - n - m;
         const float ax = row_dot(A, L.ldg, k, x, L.nv);
         const float r = ax - b[k];
         re[k] = r;
+        mx[12] += isfinite(r) ? 0.f : 1.f;
         mx[4] = fmaxf(mx[4], fabsf(r)); mx[5] = fmaxf(mx[5], fabsf(ax));
       }
     }
-    float v[13];
-#pragma unroll
-    for (int k = 0; k < 12; ++k) v[k] = mx[k];
-    v[12] = nanflag;
-    block_reduce<NT, 13>(v, red, parity, OpMax());
-    if (v[12] > 0.f) return NAN;
-    float comp = v[9];
+    block_reduce<NT, 13>(mx, red, parity, OpMax());
+    if (mx[12] > 0.f) return NAN;
+    float comp = mx[9];
     if (mode == 1) comp = fabsf(kappa - P.kappa_relax) / P.kappa_relax;
-    if (P.norm_abs) {
-      return fmaxf(fmaxf(fmaxf(v[0], v[4]), fmaxf(v[6], comp)), v[10]);
-    }
-    const float dt = fmaxf(fmaxf(1.0f, qn), fmaxf(fmaxf(v[1], v[2]), v[3]));
-    const float de = fmaxf(fmaxf(1.0f, bn), v[5]);
-    const float di = fmaxf(fmaxf(1.0f, hn), fmaxf(v[7], v[8]));
-    const float dz = fmaxf(1.0f, fmaxf(v[11], v[8]));
-    return fmaxf(fmaxf(fmaxf(v[0] / dt, v[4] / de), fmaxf(v[6] / di, comp)), v[10] / dz);
+    if (P.norm_abs) return fmaxf(fmaxf(fmaxf(mx[0], mx[4]), fmaxf(mx[6], comp)), mx[10]);
+    const float dt = fmaxf(fmaxf(1.0f, qn), fmaxf(fmaxf(mx[1], mx[2]), mx[3]));
+    const float de = fmaxf(fmaxf(1.0f, bn), mx[5]);
+    const float di = fmaxf(fmaxf(1.0f, hn), fmaxf(mx[7], mx[8]));
+    const float dz = fmaxf(1.0f, fmaxf(mx[11], mx[8]));
+    return fmaxf(fmaxf(fmaxf(mx[0] / dt, mx[4] / de), fmaxf(mx[6] / di, comp)), mx[10] / dz);
   }
 
-  // Right-hand sides of the two implicit systems: r1_A = -r_t + G't_A, r1_B = G'(1/b(-v)).
+  // ---- implicit right-hand sides, two columns (r_kappa = 0 and d/dr_kappa) ----
   __device__ void implicit_rhs() {
-    const int p = L.p;
-    const float* vv[2] = {ta, ibs};
-    float* oo[2] = {X + p * L.ldx, X + (p + 1) * L.ldx};
-    col_dot<NT, 2>(G, L.ldg, L.m, L.n, vv, oo, col, rt, -1.0f);
-    for (int k = threadIdx.x; k < p; k += NT) { r3a[k] = -re[k]; r3b[k] = 0.f; }
-  }
-
-  // e_A = G dx_A, e_B = G dx_B
-  __device__ void g_times_dx(int nrhs) {
-    const int p = L.p;
-    for (int r = threadIdx.x; r < L.m; r += NT) {
-      if (nrhs == 2) {
-        float a, c;
-        row_dot2(G, L.ldg, r, X + p * L.ldx, X + (p + 1) * L.ldx, L.nv, a, c);
-        ea[r] = a; eb[r] = c;
+    const int m = L.m, t = threadIdx.x;
+    for (int r = t; r < m; r += NT) {
+      const float rho = bz[r] + bs[r];
+      const bool inact = pos[r] < 0;
+      const float dri = ri[r] - rs[r];
+      ta[r] = ri[r] + rz[r] - rs[r] - (inact ? dri * rho / bs[r] : 0.f);
+      tb[r] = inact ? 1.0f / bs[r] : 0.f;
+    }
+    for (int k = t; k < nf; k += NT) {
+      if (k < a) {
+        const int r = act[k];
+        const float rho = bz[r] + bs[r];
+        ua[k] = -(ri[r] - rs[r]) * rho / bz[r];
+        ub[k] = 1.0f / bz[r];
       } else {
-        ea[r] = row_dot(G, L.ldg, r, X + p * L.ldx, L.nv);
+        ua[k] = -re[k - a];
+        ub[k] = 0.f;
       }
     }
     __syncthreads();
+    const float* vv[2] = {ta, tb};
+    float* oo[2] = {R, R + L.ldx};
+    col_dot<NT, 2>(G, L.ldg, L.m, L.n, vv, oo, col, rt, -1.0f);
   }
 
-  // Step length (eq. 7) of the implicit direction for a given r_kappa; stores dv in tb.
+  // ds, dz, dv of the implicit direction for r_kappa = rk on row r
+  __device__ __forceinline__ void implicit_dir(int r, float rk, float& dsr, float& dzr,
+                                               float& dvr) const {
+    const float rho = bz[r] + bs[r];
+    const float c = 1.0f / rho;
+    const float e = fmaf(rk, eb[r], ea[r]);
+    const int k = pos[r];
+    if (k < 0) {
+      const float rho2 = ri[r] - rs[r] - c * rk;
+      dvr = (e + rho2) * rho / bs[r];
+    } else {
+      dvr = fmaf(rk, ub[k], ua[k]) + e;
+    }
+    dzr = -rz[r] + (bz[r] * c) * dvr - c * rk;
+    dsr = -rs[r] - (bs[r] * c) * dvr - c * rk;
+  }
+
   __device__ float implicit_alpha(float rk, bool store) {
     float amin[1] = {1.0f};
     for (int r = threadIdx.x; r < L.m; r += NT) {
-      const float e = fmaf(rk, eb[r], ea[r]);
-      const float dsr = -e - ri[r];
-      const float dzr = -rz[r] + W[r] * (e + ri[r] - rs[r]) - rk * ibs[r];
+      float dsr, dzr, dvr;
+      implicit_dir(r, rk, dsr, dzr, dvr);
       if (dsr < 0.f) amin[0] = fminf(amin[0], -s[r] / dsr);
       if (dzr < 0.f) amin[0] = fminf(amin[0], -z[r] / dzr);
-      if (store) tb[r] = dzr - dsr + rz[r] - rs[r];
+      if (store) tb[r] = dvr;
     }
     block_reduce<NT, 1>(amin, red, parity, OpMin());
     return amin[0];
@@ -308,50 +434,157 @@ struct Solver {
   __device__ float implicit_mu_aff(float rk, float alpha) {
     float acc[1] = {0.f};
     for (int r = threadIdx.x; r < L.m; r += NT) {
-      const float e = fmaf(rk, eb[r], ea[r]);
-      const float dsr = -e - ri[r];
-      const float dzr = -rz[r] + W[r] * (e + ri[r] - rs[r]) - rk * ibs[r];
+      float dsr, dzr, dvr;
+      implicit_dir(r, rk, dsr, dzr, dvr);
       acc[0] = fmaf(fmaf(alpha, dsr, s[r]), fmaf(alpha, dzr, z[r]), acc[0]);
     }
     block_reduce<NT, 1>(acc, red, parity, OpSum());
     return acc[0] / (float)L.m;
   }
 
-  // x += a (dx_A + rk dx_B), y likewise, v += a dv, kappa' = kappa - a rk, retract.
   __device__ void implicit_update(float alpha, float rk, float kappa) {
     const int p = L.p, t = threadIdx.x;
     const float knew = kappa - alpha * rk;
-    for (int i = t; i < L.n; i += NT)
-      x[i] = fmaf(alpha, fmaf(rk, X[(p + 1) * L.ldx + i], X[p * L.ldx + i]), x[i]);
-    for (int k = t; k < p; k += NT) y[k] = fmaf(alpha, fmaf(rk, dyb[k], dya[k]), y[k]);
+    for (int i = t; i < L.n; i += NT) x[i] = fmaf(alpha, fmaf(rk, R[L.ldx + i], R[i]), x[i]);
+    for (int k = t; k < p; k += NT) y[k] = fmaf(alpha, fmaf(rk, ub[a + k], ua[a + k]), y[k]);
     for (int r = t; r < L.m; r += NT) {
       const float vn = fmaf(alpha, tb[r], z[r] - s[r]);
-      float bz, bs;
-      retract_pair(vn, knew, bz, bs);
-      z[r] = bz;
-      s[r] = bs;
+      float pz, ps;
+      retract_pair(vn, knew, pz, ps);
+      z[r] = pz;
+      s[r] = ps;
     }
     __syncthreads();
   }
 
-  // CVXOPT-style start: (Q + G'G) x + A'y = -q + G'h, Ax = b; z = Gx - h, s = -z, shifted.
-  __device__ bool initialize() {
-    const int p = L.p, m = L.m, t = threadIdx.x;
-    for (int r = t; r < m; r += NT) W[r] = 1.0f;
+  // One implicit Newton step (Alg. 1 with predictor-corrector, or Alg. 2 when
+  // kt_fixed >= 0).  Returns false on a factorisation failure.
+  __device__ bool implicit_step(const FwdParams& P, float kappa, float kt_fixed) {
+    partition();
+    implicit_rhs();
+    if (!factor()) return false;
+    solve(0, 2);
+    g_times_dx(0, 2);
+    float kt;
+    if (kt_fixed >= 0.f) {
+      kt = kt_fixed;
+    } else {
+      float sigma;
+      if (P.sigma_mode == 1) {
+        sigma = P.sigma;
+      } else {
+        const float aa = implicit_alpha(kappa, false);
+        const float mua = implicit_mu_aff(kappa, aa);
+        const float ratio = mua / kappa;
+        sigma = ratio * ratio * ratio;
+        if (!(sigma >= 0.f)) sigma = 0.f;
+        if (sigma > 1.f) sigma = 1.f;
+      }
+      kt = fmaxf(sigma * kappa, P.kappa_min);
+    }
+    const float rk = kappa - kt;
+    const float alpha = P.step_frac * implicit_alpha(rk, true);
+    implicit_update(alpha, rk, kappa);
+    return true;
+  }
+
+  // ---- explicit complementarity (ablation) ----
+  // rhs for r_c (per row, r_c / s and r_c / z): t_I = -W r_i + r_c/s (inactive rows),
+  // rhs2_A = -(r_i - r_c/z), rhs2_eq = -r_e.  base = false drops the r_t, r_i, r_e terms.
+  __device__ bool standard_step(const FwdParams& P, float mu) {
+    const int m = L.m, p = L.p, t = threadIdx.x;
+    partition();
+    // predictor (slot 0): r_c = z.*s
+    for (int r = t; r < m; r += NT) ta[r] = pos[r] < 0 ? -(z[r] / s[r]) * ri[r] + z[r] : 0.f;
+    for (int k = t; k < nf; k += NT) ua[k] = k < a ? -(ri[act[k]] - s[act[k]]) : -re[k - a];
     __syncthreads();
     {
+      const float* vv[1] = {ta};
+      float* oo[1] = {R};
+      col_dot<NT, 1>(G, L.ldg, m, L.n, vv, oo, col, rt, -1.0f);
+    }
+    if (!factor()) return false;
+    solve(0, 1);
+    g_times_dx(0, 1);
+    float amin[1] = {1.0f};
+    for (int r = t; r < m; r += NT) {
+      const float e = ea[r];
+      const float dzr = pos[r] < 0 ? (z[r] / s[r]) * (e + ri[r]) - z[r] : ua[pos[r]];
+      const float dsr = -ri[r] - e;
+      rz[r] = dsr;  // keep ds_aff
+      rs[r] = dzr;  // keep dz_aff
+      if (dsr < 0.f) amin[0] = fminf(amin[0], -s[r] / dsr);
+      if (dzr < 0.f) amin[0] = fminf(amin[0], -z[r] / dzr);
+    }
+    block_reduce<NT, 1>(amin, red, parity, OpMin());
+    const float aa = amin[0];
+    float acc[1] = {0.f};
+    for (int r = t; r < m; r += NT) acc[0] = fmaf(fmaf(aa, rz[r], s[r]), fmaf(aa, rs[r], z[r]), acc[0]);
+    block_reduce<NT, 1>(acc, red, parity, OpSum());
+    const float ratio = (acc[0] / (float)m) / mu;
+    float sigma = ratio * ratio * ratio;
+    if (!(sigma >= 0.f)) sigma = 0.f;
+    if (sigma > 1.f) sigma = 1.f;
+    if (P.sigma_mode == 1) sigma = P.sigma;
+    const float smu = sigma * mu;
+    // corrector increment (slot 1): r_c' = ds_a .* dz_a - sigma mu, zero base residuals
+    for (int r = t; r < m; r += NT) {
+      const float rc = rz[r] * rs[r] - smu;
+      ta[r] = rc;  // keep r_c'
+      tb[r] = pos[r] < 0 ? rc / s[r] : 0.f;
+    }
+    for (int k = t; k < nf; k += NT) ub[k] = k < a ? ta[act[k]] / z[act[k]] : 0.f;
+    __syncthreads();
+    {
+      const float* vv[1] = {tb};
+      float* oo[1] = {R + L.ldx};
+      col_dot<NT, 1>(G, L.ldg, m, L.n, vv, oo, col);
+    }
+    solve(1, 1);
+    g_times_dx(1, 1);
+    float amin2[1] = {1.0f};
+    for (int r = t; r < m; r += NT) {
+      const float e = eb[r];
+      const float dzc = pos[r] < 0 ? (z[r] / s[r]) * e - ta[r] / s[r] : ub[pos[r]];
+      const float dsr = rz[r] - e;
+      const float dzr = rs[r] + dzc;
+      rz[r] = dsr;
+      rs[r] = dzr;
+      if (dsr < 0.f) amin2[0] = fminf(amin2[0], -s[r] / dsr);
+      if (dzr < 0.f) amin2[0] = fminf(amin2[0], -z[r] / dzr);
+    }
+    block_reduce<NT, 1>(amin2, red, parity, OpMin());
+    const float alpha = fminf(1.0f, 0.99f * amin2[0]);
+    for (int i = t; i < L.n; i += NT) x[i] = fmaf(alpha, R[i] + R[L.ldx + i], x[i]);
+    for (int k = t; k < p; k += NT) y[k] = fmaf(alpha, ua[a + k] + ub[a + k], y[k]);
+    for (int r = t; r < m; r += NT) {
+      z[r] = fmaf(alpha, rs[r], z[r]);
+      s[r] = fmaf(alpha, rz[r], s[r]);
+    }
+    __syncthreads();
+    return true;
+  }
+
+  // CVXOPT-style start: (Q + G'G) x + A'y = -q + G'h, A x = b; z = G x - h, s = -z, shifted.
+  // With m = 0 this is the exact solution of the equality-constrained QP.
+  __device__ bool initialize() {
+    const int m = L.m, p = L.p, t = threadIdx.x;
+    for (int r = t; r < m; r += NT) { bz[r] = 1.0f; bs[r] = 1.0f; }
+    __syncthreads();
+    partition();  // W = 1 everywhere: no active rows, F = A
+    for (int k = t; k < p; k += NT) ua[k] = b[k];
+    {
       const float* vv[1] = {h};
-      float* oo[1] = {X + p * L.ldx};
+      float* oo[1] = {R};
       col_dot<NT, 1>(G, L.ldg, m, L.n, vv, oo, col, q, -1.0f);
     }
-    for (int k = t; k < p; k += NT) r3a[k] = b[k];
+    const bool ok = factor();
+    solve(0, 1);
+    for (int i = t; i < L.n; i += NT) x[i] = R[i];
+    for (int k = t; k < p; k += NT) y[k] = ua[k];
     __syncthreads();
-    bool ok = factor();
-    solve(1);
-    for (int i = t; i < L.n; i += NT) x[i] = X[p * L.ldx + i];
-    for (int k = t; k < p; k += NT) y[k] = dya[k];
-    __syncthreads();
-    float mx[4] = {-INFINITY, -INFINITY, 0.f, 0.f};
+    if (m == 0) return ok;
+    float mx[3] = {-INFINITY, -INFINITY, 0.f};
     for (int r = t; r < m; r += NT) {
       const float zr = row_dot(G, L.ldg, r, x, L.nv) - h[r];
       z[r] = zr;
@@ -360,7 +593,7 @@ struct Solver {
       mx[1] = fmaxf(mx[1], -zr);  // -min(z)
       mx[2] = fmaxf(mx[2], fabsf(zr));
     }
-    block_reduce<NT, 4>(mx, red, parity, OpMax());
+    block_reduce<NT, 3>(mx, red, parity, OpMax());
     const float thr = -1e-8f * fmaxf(1.0f, mx[2]);
     const bool shs = mx[0] >= thr, shz = mx[1] >= thr;
     for (int r = t; r < m; r += NT) {
@@ -371,96 +604,52 @@ struct Solver {
     return ok;
   }
 
-  // Equality-only problem: one solve of [Q A'; A 0] is exact.
-  __device__ bool solve_eq_only() {
-    const int p = L.p, t = threadIdx.x;
-    for (int i = t; i < L.n; i += NT) X[p * L.ldx + i] = -q[i];
-    for (int k = t; k < p; k += NT) r3a[k] = b[k];
+  // ---- gradient cache: factors, W, active map and the point (Alg. 3 input) ----
+  __device__ void write_cache(const FwdParams& P, int bi) {
+    const int n = L.n, m = L.m, p = L.p, t = threadIdx.x;
+    const CacheLayout cl = cache_layout(n, m, p, L.amax);
+    float* c = P.cache + (size_t)bi * (size_t)P.cache_stride;
+    if (t == 0) {
+      reinterpret_cast<int*>(c + cl.oHdr)[0] = a;
+      reinterpret_cast<int*>(c + cl.oHdr)[1] = nf;
+    }
+    const int nl = n * (n + 1) / 2;
+    for (int e = t; e < nl; e += NT) {
+      int i = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+      while ((i + 1) * (i + 2) / 2 <= e) ++i;
+      while (i * (i + 1) / 2 > e) --i;
+      c[cl.oL + e] = K[i * L.ldk + (e - i * (i + 1) / 2)];
+    }
+    for (int e = t; e < nf * n; e += NT) {
+      const int k = e / n, i = e - k * n;
+      c[cl.oY + e] = Y[k * L.ldk + i];
+    }
+    const int fl = nf * (nf + 1) / 2;
+    for (int e = t; e < fl; e += NT) {
+      int i = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+      while ((i + 1) * (i + 2) / 2 <= e) ++i;
+      while (i * (i + 1) / 2 > e) --i;
+      c[cl.oLC + e] = C[i * L.ldc + (e - i * (i + 1) / 2)];
+    }
+    for (int r = t; r < m; r += NT) {
+      c[cl.oW + r] = ea[r];  // W of inactive rows (0 on active rows)
+      reinterpret_cast<int*>(c + cl.oPos)[r] = pos[r];
+      c[cl.oz + r] = z[r];
+    }
+    for (int i = t; i < n; i += NT) c[cl.ox + i] = x[i];
+    for (int k = t; k < p; k += NT) c[cl.oy + k] = y[k];
     __syncthreads();
-    bool ok = factor();
-    solve(1);
-    for (int i = t; i < L.n; i += NT) x[i] = X[p * L.ldx + i];
-    for (int k = t; k < p; k += NT) y[k] = dya[k];
-    __syncthreads();
-    return ok;
   }
 
-  // ---- explicit complementarity (ablation): Mehrotra predictor-corrector ----
-  // rhs t = -W r_i + r_c ./ s with r_c = z.*s (predictor) or the corrector term.
-  __device__ float standard_step(float mu, float sigma_const) {
-    const int p = L.p, m = L.m, t = threadIdx.x;
-    // predictor system A: t_A = -W r_i + z
-    for (int r = t; r < m; r += NT) ta[r] = -W[r] * ri[r] + z[r];
-    __syncthreads();
-    {
-      const float* vv[1] = {ta};
-      float* oo[1] = {X + p * L.ldx};
-      col_dot<NT, 1>(G, L.ldg, m, L.n, vv, oo, col, rt, -1.0f);
-    }
-    for (int k = t; k < p; k += NT) r3a[k] = -re[k];
-    __syncthreads();
-    bool ok = factor();
-    solve(1);
-    g_times_dx(1);
-    // predictor ds, dz; alpha_aff
-    float amin[1] = {1.0f};
+  __device__ void write_solution(const FwdParams& P, int bi, bool good) {
+    const int n = L.n, m = L.m, p = L.p, t = threadIdx.x;
+    const float nanv = NAN;
+    for (int i = t; i < n; i += NT) P.x[(size_t)bi * n + i] = good ? x[i] : nanv;
+    for (int k = t; k < p; k += NT) P.y[(size_t)bi * p + k] = good ? y[k] : nanv;
     for (int r = t; r < m; r += NT) {
-      const float dzr = W[r] * (ea[r] + ri[r]) - z[r];
-      const float dsr = -ea[r] - ri[r];
-      eb[r] = dzr;  // keep dz_aff
-      tb[r] = dsr;  // keep ds_aff
-      if (dsr < 0.f) amin[0] = fminf(amin[0], -s[r] / dsr);
-      if (dzr < 0.f) amin[0] = fminf(amin[0], -z[r] / dzr);
+      P.z[(size_t)bi * m + r] = good ? z[r] : nanv;
+      P.s[(size_t)bi * m + r] = good ? s[r] : nanv;
     }
-    block_reduce<NT, 1>(amin, red, parity, OpMin());
-    const float aa = amin[0];
-    float acc[1] = {0.f};
-    for (int r = t; r < m; r += NT) acc[0] = fmaf(fmaf(aa, tb[r], s[r]), fmaf(aa, eb[r], z[r]), acc[0]);
-    block_reduce<NT, 1>(acc, red, parity, OpSum());
-    const float mua = acc[0] / (float)m;
-    const float ratio = mua / mu;
-    float sigma = ratio * ratio * ratio;  // Mehrotra
-    if (!(sigma >= 0.f)) sigma = 0.f;
-    if (sigma > 1.f) sigma = 1.f;
-    if (sigma_const >= 0.f) sigma = sigma_const;
-    const float smu = sigma * mu;
-    // keep predictor dx, dy
-    for (int i = t; i < L.n; i += NT) tn[i] = X[p * L.ldx + i];
-    for (int k = t; k < p; k += NT) dyb[k] = dya[k];
-    // corrector system C: r_c = ds_a.*dz_a - sigma mu  ->  t_C = r_c ./ s, r1 = G't_C
-    for (int r = t; r < m; r += NT) ta[r] = (tb[r] * eb[r] - smu) * ibs[r];
-    __syncthreads();
-    {
-      const float* vv[1] = {ta};
-      float* oo[1] = {X + p * L.ldx};
-      col_dot<NT, 1>(G, L.ldg, m, L.n, vv, oo, col);
-    }
-    for (int k = t; k < p; k += NT) r3a[k] = 0.f;
-    __syncthreads();
-    solve(1);
-    g_times_dx(1);
-    // total direction = predictor + corrector
-    float amin2[1] = {1.0f};
-    for (int r = t; r < m; r += NT) {
-      const float e = ea[r];
-      // ds = ds_a - e_C ; dz = dz_a + W e_C - t_C
-      const float dsr = tb[r] - e;
-      const float dzr = eb[r] + W[r] * e - ta[r];
-      eb[r] = dzr;
-      tb[r] = dsr;
-      if (dsr < 0.f) amin2[0] = fminf(amin2[0], -s[r] / dsr);
-      if (dzr < 0.f) amin2[0] = fminf(amin2[0], -z[r] / dzr);
-    }
-    block_reduce<NT, 1>(amin2, red, parity, OpMin());
-    const float alpha = fminf(1.0f, 0.99f * amin2[0]);
-    for (int i = t; i < L.n; i += NT) x[i] = fmaf(alpha, tn[i] + X[p * L.ldx + i], x[i]);
-    for (int k = t; k < p; k += NT) y[k] = fmaf(alpha, dyb[k] + dya[k], y[k]);
-    for (int r = t; r < m; r += NT) {
-      z[r] = fmaf(alpha, eb[r], z[r]);
-      s[r] = fmaf(alpha, tb[r], s[r]);
-    }
-    __syncthreads();
-    return ok ? alpha : NAN;
   }
 
   // ---- whole instance ----
@@ -468,19 +657,13 @@ struct Solver {
     const int n = L.n, m = L.m, p = L.p, t = threadIdx.x;
     const bool implicit = P.formulation == 0;
     int status = ST_SOLVED, iters = 0;
-    float meas = 0.f;
+    float meas = NAN;
     const bool good = load(P, bi, sm);
     if (!good) {
       status = ST_BAD_INPUT;
-      meas = NAN;
-    } else if (m == 0) {
-      if (!solve_eq_only()) status = ST_NUMERICAL;
-      iters = 1;
-      float kap;
-      meas = residuals(P, implicit, 0, kap);
     } else {
       bool warm = false;
-      if (P.warm_start) {
+      if (P.warm_start && m > 0) {
         float mn[1] = {INFINITY};
         for (int i = t; i < n; i += NT) x[i] = P.x[(size_t)bi * n + i];
         for (int k = t; k < p; k += NT) y[k] = P.y[(size_t)bi * p + k];
@@ -493,139 +676,59 @@ struct Solver {
         warm = mn[0] > 0.f;
       }
       if (!warm && !initialize()) status = ST_NUMERICAL;
-      // ---- Alg. 1 ----
-      float best = INFINITY;
-      int since_best = 0;
-      for (int it = 0; status == ST_SOLVED; ++it) {
-        float kappa;
-        meas = residuals(P, implicit, 0, kappa);
-        if (!(meas == meas)) { status = ST_NUMERICAL; break; }
-        if (meas < P.tol) break;
-        if (it >= P.max_iter) { status = ST_MAX_ITER; break; }
-        if (meas < 0.9f * best) { best = meas; since_best = 0; }
-        else if (++since_best >= 10) { status = ST_STALLED; break; }
-        if (implicit) {
-          implicit_rhs();
-          if (!factor()) { status = ST_NUMERICAL; break; }
-          solve(2);
-          g_times_dx(2);
-          float sigma;
-          if (P.sigma_mode == 1) {
-            sigma = P.sigma;
-          } else {
-            const float aa = implicit_alpha(kappa, false);
-            const float mua = implicit_mu_aff(kappa, aa);
-            const float ratio = mua / kappa;
-            sigma = ratio * ratio * ratio;
-            if (!(sigma >= 0.f)) sigma = 0.f;
-            if (sigma > 1.f) sigma = 1.f;
-          }
-          const float kt = fmaxf(sigma * kappa, P.kappa_min);
-          const float rk = kappa - kt;
-          const float alpha = P.step_frac * implicit_alpha(rk, true);
-          implicit_update(alpha, rk, kappa);
-        } else {
-          const float a = standard_step(kappa, P.sigma_mode == 1 ? P.sigma : -1.0f);
-          if (!(a == a)) { status = ST_NUMERICAL; break; }
+      if (m == 0) {
+        iters = 1;
+        float kap;
+        meas = residuals(P, implicit, 0, kap);
+      } else {
+        // ---- Alg. 1 ----
+        float best = INFINITY;
+        int since_best = 0;
+        for (int it = 0; status == ST_SOLVED; ++it) {
+          float kappa;
+          meas = residuals(P, implicit, 0, kappa);
+          if (!(meas == meas)) { status = ST_NUMERICAL; break; }
+          if (meas < P.tol) break;
+          if (it >= P.max_iter) { status = ST_MAX_ITER; break; }
+          if (meas < 0.9f * best) { best = meas; since_best = 0; }
+          else if (++since_best >= 10) { status = ST_STALLED; break; }
+          const bool ok = implicit ? implicit_step(P, kappa, -1.0f) : standard_step(P, kappa);
+          if (!ok) { status = ST_NUMERICAL; break; }
+          iters = it + 1;
         }
-        iters = it + 1;
       }
-      // ---- Alg. 2 (relax) and the cached factor at the relaxed point ----
-      if (P.cache && P.kappa_relax > 0.f && (status == ST_SOLVED || status == ST_MAX_ITER ||
-                                             status == ST_STALLED)) {
-        // write the solution of Alg. 1 now; the relaxed point only goes to the cache
-        for (int i = t; i < n; i += NT) P.x[(size_t)bi * n + i] = x[i];
-        for (int k = t; k < p; k += NT) P.y[(size_t)bi * p + k] = y[k];
-        for (int r = t; r < m; r += NT) { P.z[(size_t)bi * m + r] = z[r]; P.s[(size_t)bi * m + r] = s[r]; }
+    }
+    write_solution(P, bi, good);
+    // ---- Alg. 2 (relax) and the factor at the relaxed point ----
+    if (P.cache && status != ST_BAD_INPUT) {
+      if (m > 0 && P.kappa_relax > 0.f && status != ST_NUMERICAL) {
         int rstatus = ST_MAX_ITER;
-        const int rmax = P.relax_max_iter;
         for (int it = 0;; ++it) {
           float kappa;
           const float rm = residuals(P, true, 1, kappa);
           if (!(rm == rm)) { rstatus = ST_NUMERICAL; break; }
           if (rm < P.relax_tol) { rstatus = ST_SOLVED; break; }
-          if (it >= rmax) break;
-          implicit_rhs();
-          if (!factor()) { rstatus = ST_NUMERICAL; break; }
-          solve(2);
-          g_times_dx(2);
-          const float rk = kappa - P.kappa_relax;
-          const float alpha = P.step_frac * implicit_alpha(rk, true);
-          implicit_update(alpha, rk, kappa);
+          if (it >= P.relax_max_iter) break;
+          if (!implicit_step(P, kappa, P.kappa_relax)) { rstatus = ST_NUMERICAL; break; }
           ++iters;
         }
         if (status == ST_SOLVED) status = rstatus;
-        // factor at the relaxed point: W = b_k(v)/b_k(-v) with kappa = kappa_relax
-        for (int r = t; r < m; r += NT) {
-          float bz, bs;
-          retract_pair(z[r] - s[r], P.kappa_relax, bz, bs);
-          W[r] = bz / bs;
-        }
+        for (int r = t; r < m; r += NT) retract_pair(z[r] - s[r], P.kappa_relax, bz[r], bs[r]);
         __syncthreads();
-        if (!factor() && status == ST_SOLVED) status = ST_NUMERICAL;
-        write_cache(P, bi);
-        if (t == 0) {
-          if (P.status) P.status[bi] = status;
-          if (P.iters) P.iters[bi] = iters;
-          if (P.kkt) P.kkt[bi] = meas;
-        }
+      } else if (m > 0) {
+        // gradients at the solution itself: W = z ./ s
+        for (int r = t; r < m; r += NT) { bz[r] = z[r]; bs[r] = s[r]; }
         __syncthreads();
-        return;
       }
-    }
-    if (P.cache && status != ST_BAD_INPUT) {
-      // gradients at the solution itself (kappa_relax = 0) or the equality-only case
-      if (m > 0) {
-        for (int r = t; r < m; r += NT) W[r] = z[r] / s[r];
-        __syncthreads();
-        factor();
-      }
+      if (m > 0) partition();
+      if (!factor() && status == ST_SOLVED) status = ST_NUMERICAL;
       write_cache(P, bi);
-    }
-    // outputs
-    const float nanv = NAN;
-    for (int i = t; i < n; i += NT) P.x[(size_t)bi * n + i] = good ? x[i] : nanv;
-    for (int k = t; k < p; k += NT) P.y[(size_t)bi * p + k] = good ? y[k] : nanv;
-    for (int r = t; r < m; r += NT) {
-      P.z[(size_t)bi * m + r] = good ? z[r] : nanv;
-      P.s[(size_t)bi * m + r] = good ? s[r] : nanv;
     }
     if (t == 0) {
       if (P.status) P.status[bi] = status;
       if (P.iters) P.iters[bi] = iters;
       if (P.kkt) P.kkt[bi] = meas;
     }
-    __syncthreads();
-  }
-
-  __device__ void write_cache(const FwdParams& P, int bi) {
-    const int n = L.n, m = L.m, p = L.p, t = threadIdx.x;
-    const CacheLayout cl = cache_layout(n, m, p);
-    float* c = P.cache + (size_t)bi * (size_t)P.cache_stride;
-    const int nl = n * (n + 1) / 2;
-    for (int e = t; e < nl; e += NT) {
-      int i = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-      while ((i + 1) * (i + 2) / 2 <= e) ++i;
-      while (i * (i + 1) / 2 > e) --i;
-      const int j = e - i * (i + 1) / 2;
-      c[cl.oL + e] = K[i * L.ldk + j];
-    }
-    for (int e = t; e < p * n; e += NT) {
-      const int k = e / n, i = e - k * n;
-      c[cl.oU + e] = X[k * L.ldx + i];
-    }
-    const int pl = p * (p + 1) / 2;
-    for (int e = t; e < pl; e += NT) {
-      int i = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-      while ((i + 1) * (i + 2) / 2 <= e) ++i;
-      while (i * (i + 1) / 2 > e) --i;
-      const int j = e - i * (i + 1) / 2;
-      c[cl.oLs + e] = S[i * L.lds + j];
-    }
-    for (int r = t; r < m; r += NT) { c[cl.oW + r] = W[r]; c[cl.oz + r] = z[r]; }
-    for (int i = t; i < n; i += NT) c[cl.ox + i] = x[i];
-    for (int k = t; k < p; k += NT) c[cl.oy + k] = y[k];
-    __syncthreads();
   }
 };
 
@@ -633,7 +736,7 @@ template <int NT>
 __global__ void __launch_bounds__(NT) qp_forward_kernel(const FwdParams P) {
   extern __shared__ __align__(16) float sm[];
   Solver<NT> slv;
-  slv.bind(sm, P.n, P.m, P.p);
+  slv.bind(sm, P.n, P.m, P.p, P.amax);
   slv.run(P, blockIdx.x, sm);
 }
 

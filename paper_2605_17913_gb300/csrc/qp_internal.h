@@ -14,6 +14,7 @@ struct FwdParams {
   float *x, *y, *z, *s;
   int32_t *status, *iters;
   float* kkt;
+  int amax;  // rows kept as multipliers at most (shared-memory budget)
   // settings
   float tol, sigma, kappa_min, kappa_relax, relax_tol, step_frac;
   int max_iter, relax_max_iter, sigma_mode, formulation, norm_abs, warm_start, refine_steps;
@@ -23,7 +24,7 @@ struct FwdParams {
 };
 
 struct BwdParams {
-  int batch, n, m, p;
+  int batch, n, m, p, amax;
   const float* G;
   const float* g;
   const float* cache;
@@ -31,19 +32,26 @@ struct BwdParams {
   float *dQ, *dq, *dA, *db, *dG, *dh;
 };
 
-// Per-instance layout of the factor cache, in floats (offsets multiples of 4).
+// Per-instance layout of the gradient cache, in floats (offsets multiples of
+// 4): header (active rows a, rows nf = a + p of F, as int32), L of
+// K_I = Q + G_I'W_I G_I (packed lower), Y = F L^-T (nf rows of n), L_C of
+// C = D + Y Y' (packed lower), W of the inactive rows, the row -> position map
+// (int32, -1 for inactive rows) and the point (x, y, z).
 struct CacheLayout {
-  int oL, oU, oLs, oW, ox, oy, oz, stride;
+  int oHdr, oL, oY, oLC, oW, oPos, ox, oy, oz, stride;
 };
 
-__host__ __device__ inline CacheLayout cache_layout(int n, int m, int p) {
+__host__ __device__ inline CacheLayout cache_layout(int n, int m, int p, int amax) {
   auto r4 = [](long long v) -> int { return (int)((v + 3) & ~3LL); };
+  const long long f = (long long)amax + p;
   CacheLayout c;
   int o = 0;
+  c.oHdr = o; o += 4;
   c.oL = o; o += r4((long long)n * (n + 1) / 2);
-  c.oU = o; o += r4((long long)p * n);
-  c.oLs = o; o += r4((long long)p * (p + 1) / 2);
+  c.oY = o; o += r4(f * n);
+  c.oLC = o; o += r4(f * (f + 1) / 2);
   c.oW = o; o += r4(m);
+  c.oPos = o; o += r4(m);
   c.ox = o; o += r4(n);
   c.oy = o; o += r4(p);
   c.oz = o; o += r4(m);
@@ -51,14 +59,14 @@ __host__ __device__ inline CacheLayout cache_layout(int n, int m, int p) {
   return c;
 }
 
-// Shared-memory bytes of the forward kernel for a size (0 if unsupported),
-// and the thread count it launches with.
-size_t forward_smem_bytes(int n, int m, int p, int* nthreads);
+// Launch configuration of the forward kernel for a size: shared-memory bytes
+// (0 if unsupported), threads per CTA and the active-row cap amax.
+size_t forward_config(int n, int m, int p, int* nthreads, int* amax);
 cudaError_t launch_forward(const FwdParams& P, int nthreads, size_t smem, int grid,
                            cudaStream_t stream);
 int forward_blocks_per_sm(int nthreads, size_t smem);
 
-size_t backward_smem_bytes(int n, int m, int p, int* nthreads);
+size_t backward_smem_bytes(int n, int m, int p, int amax, int* nthreads);
 cudaError_t launch_backward(const BwdParams& P, int nthreads, size_t smem, cudaStream_t stream);
 
 }  // namespace qpgpu
