@@ -44,7 +44,9 @@ def parse():
     ap.add_argument("--workload", default="degenerate")
     ap.add_argument("--batch", type=int, default=None)
     ap.add_argument("--kappa-relax", type=float, default=1e-4)
-    ap.add_argument("--tol", type=float, default=1e-5)
+    # the FP32 stopping test runs at half the 1e-5 bar so that the FP64
+    # evaluation of every returned point stays within it
+    ap.add_argument("--tol", type=float, default=5e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
@@ -233,7 +235,7 @@ def run_ours(args, rank, world, local_rank):
                   grad_cache=cache, out=out)
         if ev is not None:
             ev[1].record(stream)
-        slv.backward(cache, T["G"], T["g"], out=gout)
+        slv.backward(cache, T["Q"], T["A"], T["G"], T["g"], out=gout)
         if ev is not None:
             ev[2].record(stream)
 

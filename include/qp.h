@@ -89,21 +89,22 @@ typedef struct {
   float kappa_min;      /* floor on kappa_target (0: 1e-2 * tol)                    */
   float kappa_relax;    /* central-path parameter of the gradients (Alg. 2); 0:
                            gradients at the solution itself                         */
-  float relax_tol;      /* Alg. 2 stop tolerance (0: tol)                           */
+  float relax_tol;      /* Alg. 2 stop tolerance (0: tol / 10)                      */
   int32_t relax_max_iter; /* Alg. 2 iteration cap (0: max_iter)                     */
   int32_t formulation;  /* QP_IMPLICIT or QP_STANDARD                               */
   int32_t residual_norm; /* QP_NORM_*                                               */
   int32_t gwg_precision; /* QP_GWG_* (only QP_GWG_FP32 for n that fits on chip)      */
-  int32_t refine_steps;  /* iterative-refinement sweeps of each Newton solve        */
+  int32_t refine_steps;  /* iterative-refinement sweeps of the adjoint solve of
+                            Alg. 3 against the bounded system (default 3)           */
   int32_t warm_start;    /* 1: start from the x, y, z, s passed in (z, s > 0)       */
 } qp_settings;
 
 typedef struct qp_handle qp_handle;
 
 /* Fill `s` with the defaults: tol 1e-5, max_iter 100, Mehrotra sigma,
- * sigma 0.1, kappa_min 0 (-> 1e-2 tol), kappa_relax 1e-4, relax_tol 0,
- * relax_max_iter 0, implicit, scaled norm, FP32 G'WG, no refinement, cold
- * start.  (Defaults follow the paper's ablation settings where it states
+ * sigma 0.1, kappa_min 0 (-> 1e-2 tol), kappa_relax 1e-4, relax_tol 0
+ * (-> tol / 10), relax_max_iter 0, implicit, scaled norm, FP32 G'WG, 3
+ * refinement sweeps, cold start.  (Defaults follow the paper's ablation settings where it states
  * them: max_iter 100, kappa_relax 1e-4.) */
 void qp_settings_default(qp_settings* s);
 
@@ -142,13 +143,15 @@ int qp_solve_batch(qp_handle* h, const qp_settings* settings, const float* Q, co
 
 /* Vector-Jacobian product (Alg. 3) of the solve that filled grad_cache:
  * given dl_dx[B][n], writes the gradients of <dl_dx, x(kappa_relax)> with
- * respect to Q (symmetrised, (dx x' + x dx')/2), q, A, b, G and h.  G must be
- * the data passed to that solve.  Any gradient pointer may be NULL to skip
- * that block.  The result is undefined if grad_cache was not filled by a
- * qp_solve_batch of the same size enqueued before this call. */
-int qp_backward_batch(qp_handle* h, const float* grad_cache, const float* G, const float* dl_dx,
-                      float* dQ, float* dq, float* dA, float* db, float* dG, float* dh,
-                      void* stream);
+ * respect to Q (symmetrised, (dx x' + x dx')/2), q, A, b, G and h.  Q, A and
+ * G must be the data passed to that solve: the adjoint solve is refined
+ * against the Newton system built from them.  Any gradient pointer may be
+ * NULL to skip that block.  A cache not written by a solve of this size
+ * gives NaN gradients (never an out-of-bounds access); the result is
+ * undefined if the cache belongs to a different batch of the same size. */
+int qp_backward_batch(qp_handle* h, const float* grad_cache, const float* Q, const float* A,
+                      const float* G, const float* dl_dx, float* dQ, float* dq, float* dA,
+                      float* db, float* dG, float* dh, void* stream);
 
 /* Human-readable name of a return or status code. */
 const char* qp_status_string(int code);

@@ -76,7 +76,7 @@ def lib():
         L.oqp_kkt_measure.argtypes = [ctypes.POINTER(_Problem), vp, vp, vp, vp, i]
         L.oqp_batch.restype = i
         L.oqp_batch.argtypes = ([i, i, i, i, i] + [vp] * 7 + [ctypes.POINTER(_Settings), d]
-                                + [vp] * 8 + [vp] * 6 + [i])
+                                + [vp] * 8 + [vp] * 4 + [vp] * 6 + [i])
         _lib = L
     return _lib
 
@@ -134,9 +134,10 @@ def solve(Q, q, A, b, G, h, *, tol: float = 1e-12, max_iter: int = 100, sigma_mo
           kappa_relax: Optional[float] = None, g=None, nthreads: int = 1) -> dict:
     """Run the oracle on one problem (2-D Q) or a batch (3-D Q) of one size.
 
-    Returns a dict with x, y, z, s (relaxed when ``kappa_relax`` is given),
+    Returns a dict with the solution x, y, z, s of Alg. 1, the relaxed point
+    xr, yr, zr, sr of Alg. 2 (equal to the solution without ``kappa_relax``),
     status, iters, relax_iters, res and, when ``g`` is given, the gradients
-    dQ, dq, dA, db, dG, dh of <g, x> (at the relaxed point when relaxing).
+    dQ, dq, dA, db, dG, dh of <g, x> at the relaxed point.
     """
     single, Q, q, A, b, G, h = _as_batch(Q, q, A, b, G, h)
     B, n, p, m = Q.shape[0], Q.shape[1], A.shape[1], G.shape[1]
@@ -154,7 +155,8 @@ def solve(Q, q, A, b, G, h, *, tol: float = 1e-12, max_iter: int = 100, sigma_mo
     elif formulation != "implicit":
         raise ValueError(formulation)
     out = {k: np.zeros((B,) + shp) for k, shp in
-           dict(x=(n,), y=(p,), z=(m,), s=(m,), res=()).items()}
+           dict(x=(n,), y=(p,), z=(m,), s=(m,), res=(), xr=(n,), yr=(p,), zr=(m,),
+                sr=(m,)).items()}
     out["status"] = np.zeros(B, dtype=np.int32)
     out["iters"] = np.zeros(B, dtype=np.int32)
     out["relax_iters"] = np.zeros(B, dtype=np.int32)
@@ -166,7 +168,7 @@ def solve(Q, q, A, b, G, h, *, tol: float = 1e-12, max_iter: int = 100, sigma_mo
     lib().oqp_batch(B, n, p, m, mode, *[_ptr(a) for a in (Q, q, A, b, G, h, g)],
                     ctypes.byref(S), float(kappa_relax or 0.0),
                     *[_ptr(out[k]) for k in ("x", "y", "z", "s", "res", "status", "iters",
-                                             "relax_iters")],
+                                             "relax_iters", "xr", "yr", "zr", "sr")],
                     *[_ptr(a) for a in grads], int(nthreads))
     if single:
         out = {k: v[0] for k, v in out.items()}

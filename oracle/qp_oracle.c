@@ -695,6 +695,7 @@ int oqp_solve_standard(const oqp_problem* P, const oqp_settings* S, double* x, d
  *   mode bit 0: solve (implicit; or standard when bit 3 is set)
  *   mode bit 1: relax to kappa_relax after the solve
  *   mode bit 2: gradients at the relaxed point (needs g)
+ * x, y, z, s receive the solution; xr, yr, zr, sr (optional) the relaxed point.
  * ------------------------------------------------------------------------- */
 typedef struct {
   int B, n, p, m, mode;
@@ -702,6 +703,7 @@ typedef struct {
   oqp_settings S;
   double kappa_relax;
   double *x, *y, *z, *s, *res;
+  double *xr, *yr, *zr, *sr; /* relaxed point (optional) */
   double *dQ, *dq, *dA, *db, *dG, *dh;
   int *status, *iters, *relax_iters;
   int next;
@@ -726,9 +728,18 @@ static void* batch_worker(void* arg) {
       st = oqp_solve_standard(&P, &J->S, x, y, z, s, &it, &res);
     else
       st = oqp_solve(&P, &J->S, x, y, z, s, &it, &res);
+    /* the relaxed point lives in xr..sr (a copy of the solution when not relaxing) */
+    double* xr = J->xr ? J->xr + (size_t)i * n : x;
+    double* yr = J->yr ? J->yr + (size_t)i * p : y;
+    double* zr = J->zr ? J->zr + (size_t)i * m : z;
+    double* sr = J->sr ? J->sr + (size_t)i * m : s;
+    if (xr != x) memcpy(xr, x, sizeof(double) * (size_t)n);
+    if (yr != y) memcpy(yr, y, sizeof(double) * (size_t)p);
+    if (zr != z) memcpy(zr, z, sizeof(double) * (size_t)m);
+    if (sr != s) memcpy(sr, s, sizeof(double) * (size_t)m);
     if ((J->mode & 2) && st == OQP_SOLVED && m > 0) {
       double rres;
-      int rst = oqp_relax(&P, &J->S, J->kappa_relax, x, y, z, s, &rit, &rres);
+      int rst = oqp_relax(&P, &J->S, J->kappa_relax, xr, yr, zr, sr, &rit, &rres);
       if (rst != OQP_SOLVED) st = rst;
     }
     if ((J->mode & 4) && J->g) {
@@ -737,7 +748,7 @@ static void* batch_worker(void* arg) {
         for (int k = 0; k < m; ++k) kr += z[k] * s[k];
         kr /= (double)m;
       }
-      oqp_gradients(&P, kr, x, y, z, s, J->g + (size_t)i * n, J->dQ + (size_t)i * n * n,
+      oqp_gradients(&P, kr, xr, yr, zr, sr, J->g + (size_t)i * n, J->dQ + (size_t)i * n * n,
                     J->dq + (size_t)i * n, J->dA + (size_t)i * p * n, J->db + (size_t)i * p,
                     J->dG + (size_t)i * m * n, J->dh + (size_t)i * m);
     }
@@ -753,10 +764,10 @@ int oqp_batch(int B, int n, int p, int m, int mode, const double* Q, const doubl
               const double* A, const double* b, const double* G, const double* h,
               const double* g, const oqp_settings* S, double kappa_relax, double* x, double* y,
               double* z, double* s, double* res, int* status, int* iters, int* relax_iters,
-              double* dQ, double* dq, double* dA, double* db, double* dG, double* dh,
-              int nthreads) {
+              double* xr, double* yr, double* zr, double* sr, double* dQ, double* dq,
+              double* dA, double* db, double* dG, double* dh, int nthreads) {
   oqp_batch_job J = {B, n, p, m, mode, Q, q, A, b, G, h, g, *S, kappa_relax, x, y, z, s, res,
-                     dQ, dq, dA, db, dG, dh, status, iters, relax_iters, 0};
+                     xr, yr, zr, sr, dQ, dq, dA, db, dG, dh, status, iters, relax_iters, 0};
   if (nthreads < 1) nthreads = 1;
   if (nthreads > 256) nthreads = 256;
   if (nthreads == 1) {

@@ -80,7 +80,7 @@ def lib() -> ctypes.CDLL:
     L.qp_solve_batch.restype = ctypes.c_int
     L.qp_solve_batch.argtypes = [vp, ctypes.POINTER(Settings)] + [vp] * 14 + [vp]
     L.qp_backward_batch.restype = ctypes.c_int
-    L.qp_backward_batch.argtypes = [vp] * 11
+    L.qp_backward_batch.argtypes = [vp] * 13
     _lib = L
     return L
 

@@ -44,7 +44,7 @@ void qp_settings_default(qp_settings* s) {
   s->formulation = QP_IMPLICIT;
   s->residual_norm = QP_NORM_SCALED;
   s->gwg_precision = QP_GWG_FP32;
-  s->refine_steps = 0;
+  s->refine_steps = 3;
   s->warm_start = 0;
 }
 
@@ -146,7 +146,7 @@ int qp_solve_batch(qp_handle* h, const qp_settings* st, const float* Q, const fl
   P.sigma = st->sigma;
   P.kappa_min = st->kappa_min > 0.0f ? st->kappa_min : 1e-2f * st->tol;
   P.kappa_relax = st->kappa_relax;
-  P.relax_tol = st->relax_tol > 0.0f ? st->relax_tol : st->tol;
+  P.relax_tol = st->relax_tol > 0.0f ? st->relax_tol : 0.1f * st->tol;
   P.step_frac = 1.0f;
   P.max_iter = st->max_iter;
   P.relax_max_iter = st->relax_max_iter > 0 ? st->relax_max_iter : st->max_iter;
@@ -167,20 +167,20 @@ int qp_solve_batch(qp_handle* h, const qp_settings* st, const float* Q, const fl
   return QP_OK;
 }
 
-int qp_backward_batch(qp_handle* h, const float* grad_cache, const float* G, const float* dl_dx,
-                      float* dQ, float* dq, float* dA, float* db, float* dG, float* dh,
-                      void* stream) {
+int qp_backward_batch(qp_handle* h, const float* grad_cache, const float* Q, const float* A,
+                      const float* G, const float* dl_dx, float* dQ, float* dq, float* dA,
+                      float* db, float* dG, float* dh, void* stream) {
   if (!h) return QP_EINVAL;
   const int B = h->dims.batch, n = h->dims.n, m = h->dims.n_ineq, p = h->dims.n_eq;
   if (B == 0) return QP_OK;
-  if (!grad_cache || !dl_dx || (m > 0 && !G)) return QP_EINVAL;
+  if (!grad_cache || !dl_dx || !Q || (m > 0 && !G) || (p > 0 && !A)) return QP_EINVAL;
   if (reinterpret_cast<uintptr_t>(grad_cache) & 15) return QP_EINVAL;
-  const void* ptrs[] = {G, dl_dx, dQ, dq, dA, db, dG, dh};
+  const void* ptrs[] = {Q, A, G, dl_dx, dQ, dq, dA, db, dG, dh};
   for (const void* ptr : ptrs)
     if (ptr && !aligned4(ptr)) return QP_EINVAL;
   BwdParams P;
   P.batch = B; P.n = n; P.m = m; P.p = p; P.amax = h->amax;
-  P.G = G; P.g = dl_dx; P.cache = grad_cache; P.cache_stride = h->cache_stride;
+  P.Q = Q; P.A = A; P.G = G; P.g = dl_dx; P.cache = grad_cache; P.cache_stride = h->cache_stride;
   P.dQ = dQ; P.dq = dq; P.dA = p > 0 ? dA : nullptr; P.db = p > 0 ? db : nullptr;
   P.dG = m > 0 ? dG : nullptr; P.dh = m > 0 ? dh : nullptr;
   cudaError_t e = launch_backward(P, h->bwd_threads, h->bwd_smem, (cudaStream_t)stream);

@@ -3,19 +3,23 @@
 // At the relaxed point the forward kernel cached the two-level factors of the
 // Newton matrix (eq. 14 with the inactive dv eliminated):
 //   K_I = Q + G_I' W_I G_I = L L',   Y = F L^-T with F = [G_A; A],
-//   C = D + Y Y' = L_C L_C',         D = diag(1/W_A, 0),
-// with W, the row -> position map and the relaxed (x, y, z).  eq. 14 is
-// symmetric, so the adjoint solve of the implicit function theorem (App. A)
-// is the same solve with right-hand side (-g, 0, 0), g = dl/dx:
-//   u = L^-1 (-g),  C mu = Y u,  dx = L^-T (u - Y' mu),  mu = (lambda, dy),
+//   C = D + Y Y' (+ a 1e-7 relative shift) = L_C L_C',  D = diag(1/W_A, 0),
+// with W / (1/W), the row -> position map and the relaxed (x, y, z).  eq. 14
+// is symmetric, so the adjoint solve of the implicit function theorem
+// (App. A) is the same solve with right-hand side (-g, 0, 0), g = dl/dx:
+//   [ K_I  F' ] [dx]   [ -g ]
+//   [ F   -D  ] [mu] = [  0 ],     mu = (lambda, dy)
+//   u = L^-1 r1,  C mu = Y u - r2,  dx = L^-T (u - Y' mu),
+// refined `refine` times against the unshifted bounded system (residuals
+// from Q, G, A, W, D in FP32; every coefficient is bounded, so they are
+// accurate), then
 //   dz_A = lambda (= W_A G_A dx),  dz_I = W_I (G_I dx)
-// (dz = B_k(v) dv is eq. 13's fourth row with zero residuals).  Then, as
-// printed in Alg. 3,
+// (dz = B_k(v) dv is eq. 13's fourth row with zero residuals), and as printed
+// in Alg. 3
 //   dQ = (dx x' + x dx')/2, dq = dx, dA = dy x' + y dx', db = -dy,
 //   dG = dz x' + z dx',     dh = -dz.
-// One CTA per instance.  The solves are short; the kernel's time is the
-// streaming read of G and the cache and the write of the gradient blocks, so
-// all outputs go out as coalesced 16-byte streaming stores where aligned.
+// One CTA per instance: Q, A, G and the factors are staged in shared memory
+// once; the gradient blocks go out as coalesced 16-byte streaming stores.
 #include "qp_device.cuh"
 #include "qp_internal.h"
 
@@ -24,16 +28,18 @@ namespace qpgpu {
 namespace {
 
 struct BLayout {
-  int ldk, ldc, ldx, nv, mv, pv, fv;
-  int oK, oY, oC, oR, o_dinv, o_cdinv, o_mu, o_x, o_y, o_z, o_W, o_pos, o_dz, total;
+  int ldk, ldc, ldx, ldg, nv, mv, pv, fv;
+  int oK, oY, oC, oQ, oG, oA, oR, oCol, o_dinv, o_cdinv, o_mu, o_dmu, o_g, o_x, o_y, o_z, o_W,
+      o_pos, o_act, o_e, o_tv, o_dz, total;
 };
 
-__host__ __device__ inline BLayout make_blayout(int n, int m, int p, int amax) {
+__host__ __device__ inline BLayout make_blayout(int n, int m, int p, int amax, int nthreads) {
   BLayout B;
   const int f = amax + p;
   B.ldk = ld_odd(n);
   B.ldc = ld_odd(f > 0 ? f : 1);
   B.ldx = round4(n);
+  B.ldg = ld_vec(n);
   B.nv = round4(n); B.mv = round4(m > 0 ? m : 1); B.pv = round4(p > 0 ? p : 1);
   B.fv = round4(f > 0 ? f : 1);
   int o = 0;
@@ -41,10 +47,15 @@ __host__ __device__ inline BLayout make_blayout(int n, int m, int p, int amax) {
   B.oK = take(n * B.ldk);
   B.oY = take(f * B.ldk);
   B.oC = take(f * B.ldc);
-  B.oR = take(B.ldx);
-  B.o_dinv = take(B.nv); B.o_cdinv = take(B.fv); B.o_mu = take(B.fv);
-  B.o_x = take(B.nv); B.o_y = take(B.pv); B.o_z = take(B.mv); B.o_W = take(B.mv);
-  B.o_pos = take(B.mv); B.o_dz = take(B.mv);
+  B.oQ = take(n * B.ldg);
+  B.oG = take(m * B.ldg);
+  B.oA = take(p * B.ldg);
+  B.oR = take(2 * B.ldx);
+  B.oCol = take(2 * nthreads);
+  B.o_dinv = take(B.nv); B.o_cdinv = take(B.fv); B.o_mu = take(B.fv); B.o_dmu = take(B.fv);
+  B.o_g = take(B.nv); B.o_x = take(B.nv); B.o_y = take(B.pv); B.o_z = take(B.mv);
+  B.o_W = take(B.mv); B.o_pos = take(B.mv); B.o_act = take(B.fv); B.o_e = take(B.mv);
+  B.o_tv = take(B.mv); B.o_dz = take(B.mv);
   B.total = o;
   return B;
 }
@@ -101,57 +112,116 @@ __device__ void small_chol_solve(const float* C, int ldc, const float* cdinv, in
   }
 }
 
+// Solve [K_I F'; F -D] (d, t) = (r1, r2) with the cached factors: r1 in R
+// (row 0), r2 in t; the solution overwrites both.
+template <int NT>
+__device__ void two_level_solve(const float* K, int ldk, const float* dinv, const float* Y,
+                                const float* C, int ldc, const float* cdinv, int n, int nf,
+                                float* R, int ldx, float* t) {
+  const int tid = threadIdx.x;
+  solve_rows<NT, false>(K, ldk, dinv, n, R, ldx, 0, 1);
+  if (nf > 0) {
+    for (int k = tid; k < nf; k += NT) {
+      float acc = 0.f;
+      for (int i = 0; i < n; ++i) acc = fmaf(Y[k * ldk + i], R[i], acc);
+      t[k] = acc - t[k];
+    }
+    __syncthreads();
+    if (tid < 32) {
+      if (nf <= 32) small_chol_solve<1>(C, ldc, cdinv, nf, t);
+      else if (nf <= 64) small_chol_solve<2>(C, ldc, cdinv, nf, t);
+      else if (nf <= 96) small_chol_solve<3>(C, ldc, cdinv, nf, t);
+      else small_chol_solve<4>(C, ldc, cdinv, nf, t);
+    }
+    __syncthreads();
+    for (int i = tid; i < n; i += NT) {
+      float acc = R[i];
+      for (int k = 0; k < nf; ++k) acc = fmaf(-Y[k * ldk + i], t[k], acc);
+      R[i] = acc;
+    }
+    __syncthreads();
+  }
+  solve_rows<NT, true>(K, ldk, dinv, n, R, ldx, 0, 1);
+}
+
 template <int NT>
 __global__ void __launch_bounds__(NT) qp_backward_kernel(const BwdParams P) {
   extern __shared__ __align__(16) float sm[];
-  const int n = P.n, m = P.m, p = P.p, t = threadIdx.x, w = t >> 5, lane = t & 31;
+  const int n = P.n, m = P.m, p = P.p, t = threadIdx.x;
   const int bi = blockIdx.x;
-  const BLayout B = make_blayout(n, m, p, P.amax);
+  const BLayout B = make_blayout(n, m, p, P.amax, NT);
   const CacheLayout cl = cache_layout(n, m, p, P.amax);
   const float* c = P.cache + (size_t)bi * (size_t)P.cache_stride;
   float* K = sm + B.oK;
   float* Y = sm + B.oY;
   float* C = sm + B.oC;
+  float* Qs = sm + B.oQ;
+  float* Gs = sm + B.oG;
+  float* As = sm + B.oA;
   float* R = sm + B.oR;
+  float* col = sm + B.oCol;
   float* dinv = sm + B.o_dinv;
   float* cdinv = sm + B.o_cdinv;
   float* mu = sm + B.o_mu;
+  float* dmu = sm + B.o_dmu;
+  float* gv = sm + B.o_g;
   float* xs = sm + B.o_x;
   float* ys = sm + B.o_y;
   float* zs = sm + B.o_z;
   float* Ws = sm + B.o_W;
   int* pos = reinterpret_cast<int*>(sm + B.o_pos);
+  int* act = reinterpret_cast<int*>(sm + B.o_act);
+  float* e = sm + B.o_e;
+  float* tv = sm + B.o_tv;
   float* dz = sm + B.o_dz;
   const int a = reinterpret_cast<const int*>(c + cl.oHdr)[0];
   const int nf = reinterpret_cast<const int*>(c + cl.oHdr)[1];
+  int refine = reinterpret_cast<const int*>(c + cl.oHdr)[2];
+  refine = refine < 0 ? 0 : (refine > 16 ? 16 : refine);
   // a cache that was not written by a forward solve of this size cannot index
   // out of bounds: its gradients come out NaN instead
   const bool valid = a >= 0 && a <= P.amax && nf == a + p;
-  // ---- load the cached factors and point ----
+  // ---- stage the data, the cached factors and the point ----
   for (int i = t; i < B.total; i += NT) sm[i] = 0.0f;
   __syncthreads();
+  const float* gQ = P.Q + (size_t)bi * n * n;
+  const float* gG = P.G + (size_t)bi * m * n;
+  const float* gA = P.A + (size_t)bi * p * n;
+  for (int e2 = t; e2 < n * n; e2 += NT) {
+    const int r = e2 / n;
+    Qs[r * B.ldg + (e2 - r * n)] = __ldg(gQ + e2);
+  }
+  for (int e2 = t; e2 < m * n; e2 += NT) {
+    const int r = e2 / n;
+    Gs[r * B.ldg + (e2 - r * n)] = __ldg(gG + e2);
+  }
+  for (int e2 = t; e2 < p * n; e2 += NT) {
+    const int r = e2 / n;
+    As[r * B.ldg + (e2 - r * n)] = __ldg(gA + e2);
+  }
   const int nl = n * (n + 1) / 2;
-  for (int e = t; e < nl; e += NT) {
-    const int i = tri_row(e), j = e - i * (i + 1) / 2;
-    const float v = __ldg(c + cl.oL + e);
+  for (int e2 = t; e2 < nl; e2 += NT) {
+    const int i = tri_row(e2), j = e2 - i * (i + 1) / 2;
+    const float v = __ldg(c + cl.oL + e2);
     K[i * B.ldk + j] = v;
     if (i == j) dinv[i] = 1.0f / v;
   }
   const int nfl = valid ? nf : 0;
-  for (int e = t; e < nfl * n; e += NT) {
-    const int k = e / n, i = e - k * n;
-    Y[k * B.ldk + i] = __ldg(c + cl.oY + e);
+  for (int e2 = t; e2 < nfl * n; e2 += NT) {
+    const int k = e2 / n, i = e2 - k * n;
+    Y[k * B.ldk + i] = __ldg(c + cl.oY + e2);
   }
   const int fl = nfl * (nfl + 1) / 2;
-  for (int e = t; e < fl; e += NT) {
-    const int i = tri_row(e), j = e - i * (i + 1) / 2;
-    const float v = __ldg(c + cl.oLC + e);
+  for (int e2 = t; e2 < fl; e2 += NT) {
+    const int i = tri_row(e2), j = e2 - i * (i + 1) / 2;
+    const float v = __ldg(c + cl.oLC + e2);
     C[i * B.ldc + j] = v;
     if (i == j) cdinv[i] = 1.0f / v;
   }
   for (int i = t; i < n; i += NT) {
     xs[i] = __ldg(c + cl.ox + i);
-    R[i] = -__ldg(P.g + (size_t)bi * n + i);
+    gv[i] = __ldg(P.g + (size_t)bi * n + i);
+    R[i] = -gv[i];
   }
   for (int k = t; k < p; k += NT) ys[k] = __ldg(c + cl.oy + k);
   int bad = valid ? 0 : 1;
@@ -161,56 +231,60 @@ __global__ void __launch_bounds__(NT) qp_backward_kernel(const BwdParams P) {
     int k = __ldg(reinterpret_cast<const int*>(c + cl.oPos) + r);
     if (k >= a || k < -1) { k = -1; bad = 1; }
     pos[r] = k;
+    if (k >= 0) act[k] = r;
   }
   if (__syncthreads_or(bad)) {
     const float nanv = NAN;
-    if (P.dQ) for (int e = t; e < n * n; e += NT) P.dQ[(size_t)bi * n * n + e] = nanv;
-    if (P.dq) for (int e = t; e < n; e += NT) P.dq[(size_t)bi * n + e] = nanv;
-    if (P.dA) for (int e = t; e < p * n; e += NT) P.dA[(size_t)bi * p * n + e] = nanv;
-    if (P.db) for (int e = t; e < p; e += NT) P.db[(size_t)bi * p + e] = nanv;
-    if (P.dG) for (int e = t; e < m * n; e += NT) P.dG[(size_t)bi * m * n + e] = nanv;
-    if (P.dh) for (int e = t; e < m; e += NT) P.dh[(size_t)bi * m + e] = nanv;
+    if (P.dQ) for (int i = t; i < n * n; i += NT) P.dQ[(size_t)bi * n * n + i] = nanv;
+    if (P.dq) for (int i = t; i < n; i += NT) P.dq[(size_t)bi * n + i] = nanv;
+    if (P.dA) for (int i = t; i < p * n; i += NT) P.dA[(size_t)bi * p * n + i] = nanv;
+    if (P.db) for (int i = t; i < p; i += NT) P.db[(size_t)bi * p + i] = nanv;
+    if (P.dG) for (int i = t; i < m * n; i += NT) P.dG[(size_t)bi * m * n + i] = nanv;
+    if (P.dh) for (int i = t; i < m; i += NT) P.dh[(size_t)bi * m + i] = nanv;
     return;
   }
-  // ---- adjoint solve ----
-  solve_rows<NT, false>(K, B.ldk, dinv, n, R, B.ldx, 0, 1);
-  if (nf > 0) {
-    for (int k = t; k < nf; k += NT) {
-      float acc = 0.f;
-      for (int i = 0; i < n; ++i) acc = fmaf(Y[k * B.ldk + i], R[i], acc);
-      mu[k] = acc;
+  // ---- adjoint solve, then refinement against the bounded system ----
+  two_level_solve<NT>(K, B.ldk, dinv, Y, C, B.ldc, cdinv, n, nf, R, B.ldx, mu);
+  float* dx = R + B.ldx;  // accumulated solution; R row 0 is the work row
+  for (int i = t; i < n; i += NT) dx[i] = R[i];
+  __syncthreads();
+  for (int it = 0; it < refine; ++it) {
+    // e = G dx;  tv = W_I e_I on inactive rows, lambda on active rows
+    for (int r = t; r < m; r += NT) {
+      const float er = row_dot(Gs, B.ldg, r, dx, B.nv);
+      e[r] = er;
+      tv[r] = pos[r] < 0 ? Ws[r] * er : mu[pos[r]];
     }
     __syncthreads();
-    if (w == 0) {
-      if (nf <= 32) small_chol_solve<1>(C, B.ldc, cdinv, nf, mu);
-      else if (nf <= 64) small_chol_solve<2>(C, B.ldc, cdinv, nf, mu);
-      else if (nf <= 96) small_chol_solve<3>(C, B.ldc, cdinv, nf, mu);
-      else small_chol_solve<4>(C, B.ldc, cdinv, nf, mu);
+    {
+      const float* vv[1] = {tv};
+      float* oo[1] = {R};
+      col_dot<NT, 1>(Gs, B.ldg, m, n, vv, oo, col);  // R = G' tv
     }
-    __syncthreads();
     for (int i = t; i < n; i += NT) {
-      float acc = R[i];
-      for (int k = 0; k < nf; ++k) acc = fmaf(-Y[k * B.ldk + i], mu[k], acc);
-      R[i] = acc;
+      float acc = row_dot(Qs, B.ldg, i, dx, B.nv) + R[i];
+      for (int k = 0; k < p; ++k) acc = fmaf(As[k * B.ldg + i], mu[a + k], acc);
+      R[i] = -gv[i] - acc;  // r1 = -g - (K_I dx + F' mu)
     }
+    for (int k = t; k < nf; k += NT) {
+      if (k < a) {
+        const int r = act[k];
+        dmu[k] = -(e[r] - Ws[r] * mu[k]);  // r2 = -(F dx - D mu), D = 1/W on active rows
+      } else {
+        dmu[k] = -row_dot(As, B.ldg, k - a, dx, B.nv);
+      }
+    }
+    __syncthreads();
+    two_level_solve<NT>(K, B.ldk, dinv, Y, C, B.ldc, cdinv, n, nf, R, B.ldx, dmu);
+    for (int i = t; i < n; i += NT) dx[i] += R[i];
+    for (int k = t; k < nf; k += NT) mu[k] += dmu[k];
     __syncthreads();
   }
-  solve_rows<NT, true>(K, B.ldk, dinv, n, R, B.ldx, 0, 1);
-  const float* dx = R;
   const float* dy = mu + a;
   // ---- dz: active rows from the multipliers, inactive rows W (G dx) ----
-  const float* gG = P.G + (size_t)bi * m * n;
-  for (int r = w; r < m; r += NT / 32) {
+  for (int r = t; r < m; r += NT) {
     const int k = pos[r];
-    if (k >= 0) {
-      if (lane == 0) dz[r] = mu[k];
-      continue;
-    }
-    float acc = 0.f;
-    for (int j = lane; j < n; j += 32) acc = fmaf(__ldg(gG + (size_t)r * n + j), dx[j], acc);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-    if (lane == 0) dz[r] = Ws[r] * acc;
+    dz[r] = k >= 0 ? mu[k] : Ws[r] * row_dot(Gs, B.ldg, r, dx, B.nv);
   }
   __syncthreads();
   // ---- gradient blocks (Alg. 3) ----
@@ -239,7 +313,7 @@ __global__ void __launch_bounds__(NT) qp_backward_kernel(const BwdParams P) {
 size_t backward_smem_bytes(int n, int m, int p, int amax, int* nthreads) {
   if (nthreads) *nthreads = 256;
   if (n > 128 || amax + p > 128) return 0;
-  BLayout B = make_blayout(n, m, p, amax);
+  BLayout B = make_blayout(n, m, p, amax, 256);
   size_t bytes = (size_t)B.total * sizeof(float);
   return bytes > 227 * 1024 ? 0 : bytes;
 }

@@ -16,8 +16,10 @@
 //   [ F    -D ] [mu] = [ rhs2 ]     F = [G_A; A],  D = diag(1/W_A, 0)  (1/W_A < 1/tau)
 // with rhs1 = -rho1 - G_I' (rho2_I / B_-),  rhs2 = (-rho2_A / B_+, -r_e),  mu = (lambda, dy).
 // K_I = L L' (Cholesky); Y = F L^-T and C = D + Y Y' come out of the same
-// bordered elimination; C = L_C L_C' (Cholesky, with a 1e-6 relative diagonal
-// shift that only matters when F is rank-deficient, i.e. degenerate problems).
+// bordered elimination; C = L_C L_C' (Cholesky, with a 1e-7 relative diagonal
+// shift that keeps FP32 Cholesky defined when F is rank-deficient, i.e. on
+// degenerate problems; Newton corrects the step, and the backward pass
+// refines its solve against the unshifted system).
 // Solve:  u = L^-1 rhs1,  C mu = Y u - rhs2,  dx = L^-T (u - Y' mu).
 // Recovery (eq. 13 rows 4-5): dv_I as above, dv_A = lambda + G_A dx,
 //   dz = -r_z + B_+ dv - c r_kappa,  ds = -r_s - B_- dv - c r_kappa,  dkappa = -r_kappa.
@@ -46,7 +48,7 @@ namespace qpgpu {
 namespace fwd {
 
 constexpr int ST_SOLVED = 0, ST_MAX_ITER = 1, ST_STALLED = 2, ST_NUMERICAL = 3, ST_BAD_INPUT = 4;
-constexpr float kCReg = 1e-6f;  // relative diagonal shift of C
+constexpr float kCReg = 1e-7f;  // relative diagonal shift of C
 
 struct FLayout {
   int n, m, p, amax, fmax;
@@ -612,6 +614,7 @@ struct Solver {
     if (t == 0) {
       reinterpret_cast<int*>(c + cl.oHdr)[0] = a;
       reinterpret_cast<int*>(c + cl.oHdr)[1] = nf;
+      reinterpret_cast<int*>(c + cl.oHdr)[2] = P.refine_steps;
     }
     const int nl = n * (n + 1) / 2;
     for (int e = t; e < nl; e += NT) {
@@ -632,7 +635,7 @@ struct Solver {
       c[cl.oLC + e] = C[i * L.ldc + (e - i * (i + 1) / 2)];
     }
     for (int r = t; r < m; r += NT) {
-      c[cl.oW + r] = ea[r];  // W of inactive rows (0 on active rows)
+      c[cl.oW + r] = pos[r] < 0 ? ea[r] : D[pos[r]];  // W (inactive rows) or 1/W (active rows)
       reinterpret_cast<int*>(c + cl.oPos)[r] = pos[r];
       c[cl.oz + r] = z[r];
     }
@@ -677,9 +680,22 @@ struct Solver {
       }
       if (!warm && !initialize()) status = ST_NUMERICAL;
       if (m == 0) {
-        iters = 1;
-        float kap;
-        meas = residuals(P, implicit, 0, kap);
+        // equality-only QP: the start is the exact solve; Newton steps on the
+        // linear KKT system refine it with the same factorisation
+        for (int it = 0; status == ST_SOLVED; ++it) {
+          float kap;
+          meas = residuals(P, implicit, 0, kap);
+          if (!(meas == meas)) { status = ST_NUMERICAL; break; }
+          if (meas < P.tol || it >= P.max_iter) break;
+          for (int i = t; i < n; i += NT) R[i] = -rt[i];
+          for (int k = t; k < p; k += NT) ua[k] = -re[k];
+          __syncthreads();
+          solve(0, 1);
+          for (int i = t; i < n; i += NT) x[i] += R[i];
+          for (int k = t; k < p; k += NT) y[k] += ua[k];
+          __syncthreads();
+          iters = it + 1;
+        }
       } else {
         // ---- Alg. 1 ----
         float best = INFINITY;

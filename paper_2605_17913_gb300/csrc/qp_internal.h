@@ -25,7 +25,7 @@ struct FwdParams {
 
 struct BwdParams {
   int batch, n, m, p, amax;
-  const float* G;
+  const float *Q, *A, *G;
   const float* g;
   const float* cache;
   long long cache_stride;
@@ -33,9 +33,11 @@ struct BwdParams {
 };
 
 // Per-instance layout of the gradient cache, in floats (offsets multiples of
-// 4): header (active rows a, rows nf = a + p of F, as int32), L of
+// 4): header (active rows a, rows nf = a + p of F, refinement sweeps of the
+// adjoint solve, as int32), L of
 // K_I = Q + G_I'W_I G_I (packed lower), Y = F L^-T (nf rows of n), L_C of
-// C = D + Y Y' (packed lower), W of the inactive rows, the row -> position map
+// C = D + Y Y' (packed lower), W of the inactive rows and 1/W of the active
+// rows, the row -> position map
 // (int32, -1 for inactive rows) and the point (x, y, z).
 struct CacheLayout {
   int oHdr, oL, oY, oLC, oW, oPos, ox, oy, oz, stride;

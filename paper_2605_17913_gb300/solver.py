@@ -89,10 +89,13 @@ class QPSolver:
         check(rc, "qp_solve_batch")
         return out
 
-    def backward(self, grad_cache: torch.Tensor, G, dl_dx, out: Optional[Dict] = None,
+    def backward(self, grad_cache: torch.Tensor, Q, A, G, dl_dx, out: Optional[Dict] = None,
                  stream: Optional[torch.cuda.Stream] = None) -> Dict[str, torch.Tensor]:
-        """Alg. 3: gradients of <dl_dx, x(kappa_relax)> w.r.t. Q, q, A, b, G, h."""
+        """Alg. 3: gradients of <dl_dx, x(kappa_relax)> w.r.t. Q, q, A, b, G, h.
+        Q, A, G are the data of the solve that filled ``grad_cache``."""
         B, n, p, m = self.batch, self.n, self.n_eq, self.n_ineq
+        Q = self._check("Q", Q, (B, n, n))
+        A = self._check("A", A, (B, p, n))
         G = self._check("G", G, (B, m, n))
         dl_dx = self._check("dl_dx", dl_dx, (B, n))
         dev = self.device
@@ -101,7 +104,8 @@ class QPSolver:
                        dA=torch.empty(B, p, n, device=dev), db=torch.empty(B, p, device=dev),
                        dG=torch.empty(B, m, n, device=dev), dh=torch.empty(B, m, device=dev))
         rc = _lib.lib().qp_backward_batch(
-            self._h, ptr(grad_cache), ptr(G), ptr(dl_dx), ptr(out["dQ"]), ptr(out["dq"]),
+            self._h, ptr(grad_cache), ptr(Q), ptr(A), ptr(G), ptr(dl_dx), ptr(out["dQ"]),
+            ptr(out["dq"]),
             ptr(out["dA"]), ptr(out["db"]), ptr(out["dG"]), ptr(out["dh"]),
             _stream_handle(stream))
         check(rc, "qp_backward_batch")
@@ -134,14 +138,15 @@ class QPFunction(torch.autograd.Function):
                            G.contiguous(), h.contiguous(), grad_cache=cache, **settings)
         ctx.solver = solver
         ctx.cache = cache
-        ctx.save_for_backward(G)
+        ctx.save_for_backward(Q, A, G)
         ctx.mark_non_differentiable(out["status"])
         return out["x"], out["status"]
 
     @staticmethod
     def backward(ctx, gx, _gstatus):
-        (G,) = ctx.saved_tensors
-        g = ctx.solver.backward(ctx.cache, G.contiguous(), gx.contiguous())
+        Q, A, G = ctx.saved_tensors
+        g = ctx.solver.backward(ctx.cache, Q.contiguous(), A.contiguous(), G.contiguous(),
+                                gx.contiguous())
         p, m = ctx.solver.n_eq, ctx.solver.n_ineq
         return (g["dQ"], g["dq"], g["dA"] if p else g["dA"], g["db"], g["dG"] if m else g["dG"],
                 g["dh"], None)

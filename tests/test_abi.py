@@ -63,7 +63,7 @@ def test_host_validation_without_gpu(L):
         assert L.qp_grad_cache_bytes(ctypes.byref(dims)) == 0
     assert L.qp_handle_create(None, ctypes.byref(h)) == _lib.QP_EINVAL
     assert L.qp_solve_batch(None, None, *([None] * 15)) == _lib.QP_EINVAL
-    assert L.qp_backward_batch(*([None] * 11)) == _lib.QP_EINVAL
+    assert L.qp_backward_batch(*([None] * 13)) == _lib.QP_EINVAL
     assert L.qp_handle_destroy(None) == _lib.QP_EINVAL
 
 

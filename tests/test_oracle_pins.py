@@ -192,7 +192,7 @@ def test_batch_matches_single_and_threads():
                  g=st["g"], nthreads=3)
     for i, d in enumerate(ds):
         r1 = _solve(d, kappa_relax=1e-4, g=d["g"])
-        for k in ("x", "y", "z", "s", "dQ", "dG", "dh"):
+        for k in ("x", "y", "z", "s", "xr", "zr", "dQ", "dG", "dh"):
             np.testing.assert_array_equal(rb[k][i], r1[k])
 
 
@@ -203,7 +203,7 @@ def test_relaxed_point_is_central_path_point():
         d = make_instance("small", 3)
         r = _solve(d, tol=1e-13, kappa_relax=kr)
         assert r["status"] == O.SOLVED
-        x, y, z, s = r["x"], r["y"], r["z"], r["s"]
+        x, y, z, s = r["xr"], r["yr"], r["zr"], r["sr"]
         Q, q, A, b, G, h = (d[k] for k in ("Q", "q", "A", "b", "G", "h"))
         np.testing.assert_allclose(z * s, kr, rtol=1e-10)
         assert np.abs(Q @ x + q + G.T @ z + A.T @ y).max() < 1e-10
@@ -214,7 +214,7 @@ def test_relaxed_point_is_central_path_point():
 def test_relaxed_point_tends_to_optimum():
     d = make_instance("small", 5)
     x_star = _solve(d, tol=1e-13)["x"]
-    errs = [np.abs(_solve(d, tol=1e-13, kappa_relax=kr)["x"] - x_star).max()
+    errs = [np.abs(_solve(d, tol=1e-13, kappa_relax=kr)["xr"] - x_star).max()
             for kr in (1e-2, 1e-4, 1e-6, 1e-8)]
     assert errs[0] > errs[1] > errs[2] > errs[3]
     assert errs[3] < 1e-6
@@ -240,7 +240,7 @@ def _relaxed_x(d, kr, **over):
     e.update(over)
     r = O.solve(e["Q"], e["q"], e["A"], e["b"], e["G"], e["h"], tol=1e-13, kappa_relax=kr)
     assert r["status"] == O.SOLVED
-    return r["x"]
+    return r["xr"]
 
 
 @pytest.mark.parametrize("index", [0, 1])
@@ -275,7 +275,7 @@ def test_gradient_matches_hard_projection_jacobian():
         d = make_instance("projection", 0, n=20, m=25, m_act=10, d=1.0)
         r = O.solve(d["Q"], d["q"], d["A"], d["b"], d["G"], d["h"], tol=1e-13,
                     kappa_relax=kr, g=d["g"])
-        np.testing.assert_allclose(r["x"], d["x0"], atol=50 * kr + 1e-9)
+        np.testing.assert_allclose(r["xr"], d["x0"], atol=50 * kr + 1e-9)
         GA = d["G"][: d["n_active"]]
         J = np.eye(20) - GA.T @ np.linalg.solve(GA @ GA.T, GA)
         g_hard = J @ d["g"]
