@@ -30,10 +30,12 @@ namespace {
 struct BLayout {
   int ldk, ldc, ldx, ldg, nv, mv, pv, fv;
   int oK, oY, oC, oQ, oG, oA, oR, oCol, o_dinv, o_cdinv, o_mu, o_dmu, o_g, o_x, o_y, o_z, o_W,
-      o_pos, o_act, o_e, o_tv, o_dz, total;
+      o_pos, o_act, o_e, o_tv, o_dz, o_qdx, o_adx, total;
 };
 
-__host__ __device__ inline BLayout make_blayout(int n, int m, int p, int amax, int nthreads) {
+// kStage: Q, G, A copied to shared memory (when they fit), else read from global.
+__host__ __device__ inline BLayout make_blayout(int n, int m, int p, int amax, int nthreads,
+                                                bool stage) {
   BLayout B;
   const int f = amax + p;
   B.ldk = ld_odd(n);
@@ -47,15 +49,15 @@ __host__ __device__ inline BLayout make_blayout(int n, int m, int p, int amax, i
   B.oK = take(n * B.ldk);
   B.oY = take(f * B.ldk);
   B.oC = take(f * B.ldc);
-  B.oQ = take(n * B.ldg);
-  B.oG = take(m * B.ldg);
-  B.oA = take(p * B.ldg);
+  B.oQ = take(stage ? n * B.ldg : 0);
+  B.oG = take(stage ? m * B.ldg : 0);
+  B.oA = take(stage ? p * B.ldg : 0);
   B.oR = take(2 * B.ldx);
   B.oCol = take(2 * nthreads);
   B.o_dinv = take(B.nv); B.o_cdinv = take(B.fv); B.o_mu = take(B.fv); B.o_dmu = take(B.fv);
   B.o_g = take(B.nv); B.o_x = take(B.nv); B.o_y = take(B.pv); B.o_z = take(B.mv);
   B.o_W = take(B.mv); B.o_pos = take(B.mv); B.o_act = take(B.fv); B.o_e = take(B.mv);
-  B.o_tv = take(B.mv); B.o_dz = take(B.mv);
+  B.o_tv = take(B.mv); B.o_dz = take(B.mv); B.o_qdx = take(B.nv); B.o_adx = take(B.pv);
   B.total = o;
   return B;
 }
@@ -112,6 +114,23 @@ __device__ void small_chol_solve(const float* C, int ldc, const float* cdinv, in
   }
 }
 
+// out[r] = M[r][:] . v for r < rows: one warp per row, lanes over columns
+// (coalesced from global memory, conflict-free from shared memory).  Ends
+// with a barrier.
+template <int NT>
+__device__ void warp_rows_dot(const float* M, int ld, int rows, int cols, const float* v,
+                              float* out) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int r = w; r < rows; r += NT / 32) {
+    float acc = 0.f;
+    for (int j = lane; j < cols; j += 32) acc = fmaf(M[(size_t)r * ld + j], v[j], acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+    if (lane == 0) out[r] = acc;
+  }
+  __syncthreads();
+}
+
 // Solve [K_I F'; F -D] (d, t) = (r1, r2) with the cached factors: r1 in R
 // (row 0), r2 in t; the solution overwrites both.
 template <int NT>
@@ -144,12 +163,12 @@ __device__ void two_level_solve(const float* K, int ldk, const float* dinv, cons
   solve_rows<NT, true>(K, ldk, dinv, n, R, ldx, 0, 1);
 }
 
-template <int NT>
+template <int NT, bool kStage>
 __global__ void __launch_bounds__(NT) qp_backward_kernel(const BwdParams P) {
   extern __shared__ __align__(16) float sm[];
   const int n = P.n, m = P.m, p = P.p, t = threadIdx.x;
   const int bi = blockIdx.x;
-  const BLayout B = make_blayout(n, m, p, P.amax, NT);
+  const BLayout B = make_blayout(n, m, p, P.amax, NT, kStage);
   const CacheLayout cl = cache_layout(n, m, p, P.amax);
   const float* c = P.cache + (size_t)bi * (size_t)P.cache_stride;
   float* K = sm + B.oK;
@@ -174,6 +193,8 @@ __global__ void __launch_bounds__(NT) qp_backward_kernel(const BwdParams P) {
   float* e = sm + B.o_e;
   float* tv = sm + B.o_tv;
   float* dz = sm + B.o_dz;
+  float* qdx = sm + B.o_qdx;  // Q dx (n)
+  float* adx = sm + B.o_adx;  // A dx (p)
   const int a = reinterpret_cast<const int*>(c + cl.oHdr)[0];
   const int nf = reinterpret_cast<const int*>(c + cl.oHdr)[1];
   int refine = reinterpret_cast<const int*>(c + cl.oHdr)[2];
@@ -187,18 +208,25 @@ __global__ void __launch_bounds__(NT) qp_backward_kernel(const BwdParams P) {
   const float* gQ = P.Q + (size_t)bi * n * n;
   const float* gG = P.G + (size_t)bi * m * n;
   const float* gA = P.A + (size_t)bi * p * n;
-  for (int e2 = t; e2 < n * n; e2 += NT) {
-    const int r = e2 / n;
-    Qs[r * B.ldg + (e2 - r * n)] = __ldg(gQ + e2);
+  if (kStage) {
+    for (int e2 = t; e2 < n * n; e2 += NT) {
+      const int r = e2 / n;
+      Qs[r * B.ldg + (e2 - r * n)] = __ldg(gQ + e2);
+    }
+    for (int e2 = t; e2 < m * n; e2 += NT) {
+      const int r = e2 / n;
+      Gs[r * B.ldg + (e2 - r * n)] = __ldg(gG + e2);
+    }
+    for (int e2 = t; e2 < p * n; e2 += NT) {
+      const int r = e2 / n;
+      As[r * B.ldg + (e2 - r * n)] = __ldg(gA + e2);
+    }
   }
-  for (int e2 = t; e2 < m * n; e2 += NT) {
-    const int r = e2 / n;
-    Gs[r * B.ldg + (e2 - r * n)] = __ldg(gG + e2);
-  }
-  for (int e2 = t; e2 < p * n; e2 += NT) {
-    const int r = e2 / n;
-    As[r * B.ldg + (e2 - r * n)] = __ldg(gA + e2);
-  }
+  // generic pointers: shared-memory copies, or the caller's global arrays
+  const float* Qm = kStage ? Qs : gQ;
+  const float* Gm = kStage ? Gs : gG;
+  const float* Am = kStage ? As : gA;
+  const int ldm = kStage ? B.ldg : n;
   const int nl = n * (n + 1) / 2;
   for (int e2 = t; e2 < nl; e2 += NT) {
     const int i = tri_row(e2), j = e2 - i * (i + 1) / 2;
@@ -250,20 +278,19 @@ __global__ void __launch_bounds__(NT) qp_backward_kernel(const BwdParams P) {
   __syncthreads();
   for (int it = 0; it < refine; ++it) {
     // e = G dx;  tv = W_I e_I on inactive rows, lambda on active rows
-    for (int r = t; r < m; r += NT) {
-      const float er = row_dot(Gs, B.ldg, r, dx, B.nv);
-      e[r] = er;
-      tv[r] = pos[r] < 0 ? Ws[r] * er : mu[pos[r]];
-    }
+    warp_rows_dot<NT>(Gm, ldm, m, n, dx, e);
+    for (int r = t; r < m; r += NT) tv[r] = pos[r] < 0 ? Ws[r] * e[r] : mu[pos[r]];
     __syncthreads();
     {
       const float* vv[1] = {tv};
       float* oo[1] = {R};
-      col_dot<NT, 1>(Gs, B.ldg, m, n, vv, oo, col);  // R = G' tv
+      col_dot<NT, 1>(Gm, ldm, m, n, vv, oo, col);  // R = G' tv
     }
+    warp_rows_dot<NT>(Qm, ldm, n, n, dx, qdx);
+    warp_rows_dot<NT>(Am, ldm, p, n, dx, adx);
     for (int i = t; i < n; i += NT) {
-      float acc = row_dot(Qs, B.ldg, i, dx, B.nv) + R[i];
-      for (int k = 0; k < p; ++k) acc = fmaf(As[k * B.ldg + i], mu[a + k], acc);
+      float acc = qdx[i] + R[i];
+      for (int k = 0; k < p; ++k) acc = fmaf(Am[(size_t)k * ldm + i], mu[a + k], acc);
       R[i] = -gv[i] - acc;  // r1 = -g - (K_I dx + F' mu)
     }
     for (int k = t; k < nf; k += NT) {
@@ -271,7 +298,7 @@ __global__ void __launch_bounds__(NT) qp_backward_kernel(const BwdParams P) {
         const int r = act[k];
         dmu[k] = -(e[r] - Ws[r] * mu[k]);  // r2 = -(F dx - D mu), D = 1/W on active rows
       } else {
-        dmu[k] = -row_dot(As, B.ldg, k - a, dx, B.nv);
+        dmu[k] = -adx[k - a];
       }
     }
     __syncthreads();
@@ -282,9 +309,10 @@ __global__ void __launch_bounds__(NT) qp_backward_kernel(const BwdParams P) {
   }
   const float* dy = mu + a;
   // ---- dz: active rows from the multipliers, inactive rows W (G dx) ----
+  warp_rows_dot<NT>(Gm, ldm, m, n, dx, e);
   for (int r = t; r < m; r += NT) {
     const int k = pos[r];
-    dz[r] = k >= 0 ? mu[k] : Ws[r] * row_dot(Gs, B.ldg, r, dx, B.nv);
+    dz[r] = k >= 0 ? mu[k] : Ws[r] * e[r];
   }
   __syncthreads();
   // ---- gradient blocks (Alg. 3) ----
@@ -313,21 +341,31 @@ __global__ void __launch_bounds__(NT) qp_backward_kernel(const BwdParams P) {
 size_t backward_smem_bytes(int n, int m, int p, int amax, int* nthreads) {
   if (nthreads) *nthreads = 256;
   if (n > 128 || amax + p > 128) return 0;
-  BLayout B = make_blayout(n, m, p, amax, 256);
-  size_t bytes = (size_t)B.total * sizeof(float);
-  return bytes > 227 * 1024 ? 0 : bytes;
+  const size_t staged = (size_t)make_blayout(n, m, p, amax, 256, true).total * sizeof(float);
+  if (staged <= 227 * 1024) return staged;
+  const size_t direct = (size_t)make_blayout(n, m, p, amax, 256, false).total * sizeof(float);
+  return direct <= 227 * 1024 ? direct : 0;
 }
 
 cudaError_t launch_backward(const BwdParams& P, int nthreads, size_t smem, cudaStream_t st) {
   if (nthreads != 256) return cudaErrorInvalidValue;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(qp_backward_kernel<256>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  const bool stage =
+      (size_t)make_blayout(P.n, P.m, P.p, P.amax, 256, true).total * sizeof(float) == smem;
+  static bool configured[2] = {false, false};
+  if (!configured[stage]) {
+    cudaError_t e = stage ? cudaFuncSetAttribute(qp_backward_kernel<256, true>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 227 * 1024)
+                          : cudaFuncSetAttribute(qp_backward_kernel<256, false>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 227 * 1024);
     if (e != cudaSuccess) return e;
-    configured = true;
+    configured[stage] = true;
   }
-  qp_backward_kernel<256><<<P.batch, 256, smem, st>>>(P);
+  if (stage)
+    qp_backward_kernel<256, true><<<P.batch, 256, smem, st>>>(P);
+  else
+    qp_backward_kernel<256, false><<<P.batch, 256, smem, st>>>(P);
   return cudaGetLastError();
 }
 

@@ -223,20 +223,32 @@ struct Solver {
     __syncthreads();
   }
 
-  // ---- factor K_I and the bordered block ----
-  __device__ bool factor() {
+  // ---- factor K_I and the bordered block (F, D and C = D must have just been
+  // set by partition(): the elimination overwrites them) ----
+  __device__ bool factor_once(float creg) {
     syrk_gwg<NT>(K, L.ldk, qd, G, L.ldg, ea, L.m, L.n);
     bool ok = cholesky_bordered<NT>(K, L.ldk, L.n, Y, L.ldk, nf, C, L.ldc, dinv);
     if (nf > 0) {
       float dm[1] = {1.0f};
       for (int k = threadIdx.x; k < nf; k += NT) dm[0] = fmaxf(dm[0], C[k * L.ldc + k]);
       block_reduce<NT, 1>(dm, red, parity, OpMax());
-      const float shift = kCReg * dm[0];
+      const float shift = creg * dm[0];
       for (int k = threadIdx.x; k < nf; k += NT) C[k * L.ldc + k] += shift;
       __syncthreads();
       ok = cholesky<NT>(C, L.ldc, nf, cdinv) && ok;
     }
     return ok;
+  }
+
+  // partition + factor; if FP32 Cholesky of C meets a non-positive pivot
+  // (rank-deficient F), redo it with a 100x and then 10^4x larger shift.
+  __device__ bool factor() {
+    float creg = kCReg;
+    for (int attempt = 0; attempt < 3; ++attempt, creg *= 100.0f) {
+      if (attempt > 0) partition();
+      if (factor_once(creg)) return true;
+    }
+    return false;
   }
 
   template <int SP>
@@ -736,7 +748,7 @@ struct Solver {
         for (int r = t; r < m; r += NT) { bz[r] = z[r]; bs[r] = s[r]; }
         __syncthreads();
       }
-      if (m > 0) partition();
+      partition();
       if (!factor() && status == ST_SOLVED) status = ST_NUMERICAL;
       write_cache(P, bi);
     }

@@ -221,7 +221,7 @@ def test_autograd_function_matches_direct_backward():
     batch = make_batch("small", 8, seed=9)
     T = _dev(batch)
     leaves = {k: T[k].clone().requires_grad_(True) for k in ("Q", "q", "A", "b", "G", "h")}
-    x, status = qp_layer(*(leaves[k] for k in ("Q", "q", "A", "b", "G", "h")))
+    x, status = qp_layer(*(leaves[k] for k in ("Q", "q", "A", "b", "G", "h")), tol=SOLVER_TOL)
     (x * T["g"]).sum().backward()
     res = gpu_run(batch, grad=True)
     for k, gk in zip(("Q", "q", "A", "b", "G", "h"), GRAD_KEYS):
