@@ -316,6 +316,179 @@ __device__ bool cholesky_bordered(float* K, int ldk, int n, float* Y, int ldy, i
   return ok;
 }
 
+
+// ---------------------------------------------------------------------------
+// Blocked (panel width 8) right-looking Cholesky of a bordered system.
+//
+// Phase 1 eliminates the n leading pivots of  [ K  F' ; F  C0 ]  as in
+// cholesky_bordered, but a panel of 8 columns at a time:
+//   (1) one warp factors the 8x8 diagonal block of K;
+//   (2) every row below it -- K rows and F rows alike -- is solved against
+//       the block (one thread per row, 8-term forward substitution) and its
+//       8 panel values are copied to Pb (stride kPbLd, conflict-free float4);
+//   (3) the trailing part of the combined lower triangle is updated by one
+//       register-tiled (4x4) product of the panel with itself: K rows
+//       subtract, F rows subtract, and the C block accumulates Y Y'.
+// Phase 2 factors C the same way (then only C rows exist).
+// Outputs: K lower = L, Y = F L^-T, C lower = L_C (C = D + Y Y' + shift is
+// applied by the caller between the phases), dinv / cdinv = 1 / diag.
+// Pb needs (n + nf + 4) * kPbLd floats.  Ends with a barrier.
+// ---------------------------------------------------------------------------
+constexpr int kPbLd = 12;  // 8 panel values + 4 pad: 8 consecutive rows hit distinct banks
+
+template <int NT>
+__device__ bool block_diag_factor(float* M, int ld, int j0, int jb, float* dinv) {
+  // one warp: unblocked Cholesky of the jb x jb block at (j0, j0)
+  bool ok = true;
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    for (int jj = 0; jj < jb; ++jj) {
+      const float d = M[(j0 + jj) * ld + j0 + jj];
+      if (!(d > 0.0f) || !(d < INFINITY)) ok = false;
+      const float sd = sqrtf(d);
+      const float inv = 1.0f / sd;
+      __syncwarp();
+      if (lane > jj && lane < jb) M[(j0 + lane) * ld + j0 + jj] *= inv;
+      if (lane == jj) {
+        M[(j0 + jj) * ld + j0 + jj] = sd;
+        dinv[j0 + jj] = inv;
+      }
+      __syncwarp();
+      if (lane > jj && lane < jb) {
+        const float lr = M[(j0 + lane) * ld + j0 + jj];
+        for (int c = jj + 1; c <= lane; ++c)
+          M[(j0 + lane) * ld + j0 + c] = fmaf(-lr, M[(j0 + c) * ld + j0 + jj], M[(j0 + lane) * ld + j0 + c]);
+      }
+      __syncwarp();
+    }
+  }
+  return __syncthreads_and(ok ? 1 : 0) != 0;
+}
+
+// Solve the panel rows against the factored diagonal block and copy them to Pb.
+// Row rr < nA is row (rowA0 + rr) of A (stride lda), else row rr - nA of B (stride ldb);
+// columns j0 .. j0+jb-1.
+template <int NT>
+__device__ void panel_trsm(const float* Ldiag, int ldl, int j0, int jb, const float* dinv,
+                           float* A, int lda, int rowA0, int nA, float* B, int ldb, int nB,
+                           float* Pb) {
+  for (int rr = threadIdx.x; rr < nA + nB; rr += NT) {
+    float* row = rr < nA ? A + (rowA0 + rr) * lda + j0 : B + (rr - nA) * ldb + j0;
+    float v[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) v[t] = t < jb ? row[t] : 0.0f;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      if (t < jb) {
+        float acc = v[t];
+#pragma unroll
+        for (int u = 0; u < t; ++u) acc = fmaf(-v[u], Ldiag[(j0 + t) * ldl + j0 + u], acc);
+        v[t] = acc * dinv[j0 + t];
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      if (t < jb) row[t] = v[t];
+      Pb[rr * kPbLd + t] = v[t];
+    }
+  }
+  // zero the pad rows of the last tile row
+  const int N = nA + nB;
+  for (int e = threadIdx.x; e < 4 * kPbLd; e += NT) Pb[N * kPbLd + e] = 0.0f;
+  __syncthreads();
+}
+
+// Trailing update with the panel in Pb over the combined row set
+// [A rows rowA0 .. rowA0+nA-1 ; B rows 0 .. nB-1] (lower triangle):
+//   (A, A): A[rowA0+r][colA0+c] -= P_r . P_c     (colA0 = rowA0 for the square part)
+//   (B, A): B[k][colA0+c]        -= P_k . P_c
+//   (B, B): C[k][l]              += P_k . P_l     (when C != nullptr)
+template <int NT>
+__device__ void panel_syrk(const float* Pb, float* A, int lda, int rowA0, int nA, float* B,
+                           int ldb, int nB, float* C, int ldc, float csign) {
+  const int N = nA + nB;
+  const int nt = (N + 3) >> 2;
+  const int T = nt * (nt + 1) / 2;
+  for (int t = threadIdx.x; t < T; t += NT) {
+    int I = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while ((I + 1) * (I + 2) / 2 <= t) ++I;
+    while (I * (I + 1) / 2 > t) --I;
+    const int J = t - I * (I + 1) / 2;
+    float acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+#pragma unroll
+    for (int h2 = 0; h2 < 2; ++h2) {
+      float4 ra[4], cb[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) ra[a] = *reinterpret_cast<const float4*>(Pb + (4 * I + a) * kPbLd + 4 * h2);
+#pragma unroll
+      for (int b = 0; b < 4; ++b) cb[b] = *reinterpret_cast<const float4*>(Pb + (4 * J + b) * kPbLd + 4 * h2);
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          acc[a][b] = fmaf(ra[a].x, cb[b].x, acc[a][b]);
+          acc[a][b] = fmaf(ra[a].y, cb[b].y, acc[a][b]);
+          acc[a][b] = fmaf(ra[a].z, cb[b].z, acc[a][b]);
+          acc[a][b] = fmaf(ra[a].w, cb[b].w, acc[a][b]);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int r = 4 * I + a;
+      if (r >= N) continue;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int c = 4 * J + b;
+        if (c > r) continue;
+        if (r < nA) {
+          A[(rowA0 + r) * lda + rowA0 + c] -= acc[a][b];
+        } else if (c < nA) {
+          B[(r - nA) * ldb + rowA0 + c] -= acc[a][b];
+        } else if (C != nullptr) {
+          C[(r - nA) * ldc + (c - nA)] += csign * acc[a][b];
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Phase 1: K (n x n, ldk odd) bordered by Y (nf rows, stride ldy) with C
+// accumulating Y Y'.  Phase 2 is blocked_cholesky on C alone.
+template <int NT>
+__device__ bool blocked_cholesky_bordered(float* K, int ldk, int n, float* Y, int ldy, int nf,
+                                          float* C, int ldc, float* dinv, float* Pb) {
+  bool ok = true;
+  for (int j0 = 0; j0 < n; j0 += 8) {
+    const int jb = min(8, n - j0);
+    ok = block_diag_factor<NT>(K, ldk, j0, jb, dinv) && ok;
+    const int nK = n - j0 - jb;
+    panel_trsm<NT>(K, ldk, j0, jb, dinv, K, ldk, j0 + jb, nK, Y, ldy, nf, Pb);
+    if (nK + nf > 0) panel_syrk<NT>(Pb, K, ldk, j0 + jb, nK, Y, ldy, nf, C, ldc, 1.0f);
+  }
+  return ok;
+}
+
+// In-place blocked Cholesky of the lower triangle of M (n x n, stride ld).
+template <int NT>
+__device__ bool blocked_cholesky(float* M, int ld, int n, float* dinv, float* Pb) {
+  bool ok = true;
+  for (int j0 = 0; j0 < n; j0 += 8) {
+    const int jb = min(8, n - j0);
+    ok = block_diag_factor<NT>(M, ld, j0, jb, dinv) && ok;
+    const int nR = n - j0 - jb;
+    if (nR > 0) {
+      panel_trsm<NT>(M, ld, j0, jb, dinv, M, ld, j0 + jb, nR, nullptr, 0, 0, Pb);
+      panel_syrk<NT>(Pb, M, ld, j0 + jb, nR, nullptr, 0, 0, nullptr, 0, 0.0f);
+    }
+  }
+  return ok;
+}
+
 // ---------------------------------------------------------------------------
 // Warp-level triangular solves for R right-hand sides held in registers
 // (lane owns rows lane + 32 s, s < S).  L stride ldk (odd => conflict-free).

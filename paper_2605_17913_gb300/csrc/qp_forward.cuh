@@ -16,10 +16,10 @@
 //   [ F    -D ] [mu] = [ rhs2 ]     F = [G_A; A],  D = diag(1/W_A, 0)  (1/W_A < 1/tau)
 // with rhs1 = -rho1 - G_I' (rho2_I / B_-),  rhs2 = (-rho2_A / B_+, -r_e),  mu = (lambda, dy).
 // K_I = L L' (Cholesky); Y = F L^-T and C = D + Y Y' come out of the same
-// bordered elimination; C = L_C L_C' (Cholesky, with a 1e-7 relative diagonal
-// shift that keeps FP32 Cholesky defined when F is rank-deficient, i.e. on
-// degenerate problems; Newton corrects the step, and the backward pass
-// refines its solve against the unshifted system).
+// blocked bordered elimination; C = L_C L_C' (Cholesky, with a 1e-7 relative
+// diagonal shift that keeps FP32 Cholesky defined when F is rank-deficient,
+// i.e. on degenerate problems; Newton corrects the step, and the backward
+// pass refines its solve against the unshifted system).
 // Solve:  u = L^-1 rhs1,  C mu = Y u - rhs2,  dx = L^-T (u - Y' mu).
 // Recovery (eq. 13 rows 4-5): dv_I as above, dv_A = lambda + G_A dx,
 //   dz = -r_z + B_+ dv - c r_kappa,  ds = -r_s - B_- dv - c r_kappa,  dkappa = -r_kappa.
@@ -39,6 +39,9 @@
 // The explicit-complementarity ablation (eq. 6 / eq. 8) uses the same
 // two-level factorisation with W = z ./ s, a Mehrotra predictor-corrector
 // (second solve for the corrector) and fraction-to-boundary 0.99.
+//
+// Register budget: the layout lives in shared memory and each method forms
+// only the addresses it uses, so that no pointer stays live across phases.
 #pragma once
 #include "qp_device.cuh"
 #include "qp_internal.h"
@@ -53,7 +56,7 @@ constexpr float kCReg = 1e-7f;  // relative diagonal shift of C
 struct FLayout {
   int n, m, p, amax, fmax;
   int ldk, ldg, ldx, ldc, nv, mv, pv, fv;
-  int oK, oqd, oG, oA, oY, oC, oR, oCol, oRed;
+  int o_K, o_qd, o_G, o_A, o_Y, o_C, o_R, o_col, o_red, o_Pb;
   int o_q, o_x, o_rt, o_dinv, o_tn;
   int o_b, o_y, o_re;
   int o_cdinv, o_D, o_ua, o_ub, o_act;
@@ -72,15 +75,16 @@ __host__ __device__ inline FLayout make_fwd_layout(int n, int m, int p, int amax
   L.fv = round4(L.fmax > 0 ? L.fmax : 1);
   int o = 0;
   auto take = [&](int cnt) -> int { int r = o; o += round4(cnt); return r; };
-  L.oK = take(n * L.ldk);
-  L.oqd = take(L.nv);
-  L.oG = take(m * L.ldg);
-  L.oA = take(p * L.ldg);
-  L.oY = take(L.fmax * L.ldk);
-  L.oC = take(L.fmax * L.ldc);
-  L.oR = take(2 * L.ldx);
-  L.oCol = take(2 * nthreads);
-  L.oRed = take(2 * kMaxWarps * kRedK);
+  L.o_K = take(n * L.ldk);
+  L.o_qd = take(L.nv);
+  L.o_G = take(m * L.ldg);
+  L.o_A = take(p * L.ldg);
+  L.o_Y = take(L.fmax * L.ldk);
+  L.o_C = take(L.fmax * L.ldc);
+  L.o_R = take(2 * L.ldx);
+  L.o_col = take(2 * nthreads);
+  L.o_red = take(2 * kMaxWarps * kRedK);
+  L.o_Pb = take((n + L.fmax + 4) * kPbLd);
   L.o_q = take(L.nv); L.o_x = take(L.nv); L.o_rt = take(L.nv); L.o_dinv = take(L.nv);
   L.o_tn = take(L.nv);
   L.o_b = take(L.pv); L.o_y = take(L.pv); L.o_re = take(L.pv);
@@ -94,43 +98,47 @@ __host__ __device__ inline FLayout make_fwd_layout(int n, int m, int p, int amax
   return L;
 }
 
+// Per-CTA scalars kept in shared memory.
+struct SharedState {
+  FLayout L;
+  int a, nf;         // active rows, rows of F = a + p (set by partition())
+  float qn, bn, hn;  // |q|, |b|, |h| (infinity norms)
+};
+
+// address of array `name` in the per-instance shared-memory layout
+#define QP_ARR(name) float* const name = sm + st->L.o_##name
+#define QP_IARR(name) int* const name = reinterpret_cast<int*>(sm + st->L.o_##name)
+
 template <int NT>
 struct Solver {
-  FLayout L;
-  float *K, *qd, *G, *A, *Y, *C, *R, *col, *red;
-  float *q, *x, *rt, *dinv, *tn, *b, *y, *re, *cdinv, *D, *ua, *ub;
-  float *h, *z, *s, *ri, *rz, *rs, *bz, *bs, *ea, *eb, *ta, *tb;
-  int *act, *pos;
+  float* sm;
+  SharedState* st;
   int parity;
-  int a, nf;         // active rows, rows of F = a + p
-  float qn, bn, hn;  // |q|, |b|, |h| (infinity norms)
 
-  __device__ void bind(float* sm, int n, int m, int p, int amax) {
-    L = make_fwd_layout(n, m, p, amax, NT);
-    K = sm + L.oK; qd = sm + L.oqd; G = sm + L.oG; A = sm + L.oA; Y = sm + L.oY; C = sm + L.oC;
-    R = sm + L.oR; col = sm + L.oCol; red = sm + L.oRed;
-    q = sm + L.o_q; x = sm + L.o_x; rt = sm + L.o_rt; dinv = sm + L.o_dinv; tn = sm + L.o_tn;
-    b = sm + L.o_b; y = sm + L.o_y; re = sm + L.o_re;
-    cdinv = sm + L.o_cdinv; D = sm + L.o_D; ua = sm + L.o_ua; ub = sm + L.o_ub;
-    act = reinterpret_cast<int*>(sm + L.o_act);
-    h = sm + L.o_h; z = sm + L.o_z; s = sm + L.o_s; ri = sm + L.o_ri; rz = sm + L.o_rz;
-    rs = sm + L.o_rs; bz = sm + L.o_bz; bs = sm + L.o_bs; ea = sm + L.o_ea; eb = sm + L.o_eb;
-    ta = sm + L.o_ta; tb = sm + L.o_tb;
-    pos = reinterpret_cast<int*>(sm + L.o_pos);
+  __device__ void bind(float* sm_, SharedState* st_, int n, int m, int p, int amax) {
+    sm = sm_;
+    st = st_;
+    if (threadIdx.x == 0) {
+      st->L = make_fwd_layout(n, m, p, amax, NT);
+      st->a = 0;
+      st->nf = p;
+    }
+    __syncthreads();
     parity = 0;
-    a = 0;
-    nf = p;
   }
 
   // ---- load one instance; Q's strict upper triangle goes to K's upper part ----
-  __device__ bool load(const FwdParams& P, int bi, float* sm) {
+  // Returns false if some datum is not finite.
+  __device__ bool load(const FwdParams& P, int bi) {
+    const FLayout& L = st->L;
     const int n = L.n, m = L.m, p = L.p, t = threadIdx.x;
+    QP_ARR(K); QP_ARR(qd); QP_ARR(G); QP_ARR(A); QP_ARR(q); QP_ARR(b); QP_ARR(h); QP_ARR(red);
     for (int i = t; i < L.total; i += NT) sm[i] = 0.0f;
     __syncthreads();
     const float* gQ = P.Q + (size_t)bi * n * n;
     const float* gG = P.G + (size_t)bi * m * n;
     const float* gA = P.A + (size_t)bi * p * n;
-    float chk = 0.f;  // 1 if some datum is NaN or infinite
+    float chk = 0.f;
     for (int e = t; e < n * n; e += NT) {
       const int r = e / n, c = e - r * n;
       if (c < r) continue;  // the solver reads the upper triangle of the symmetric Q
@@ -165,21 +173,18 @@ struct Solver {
     }
     float v[4] = {chk, lq, lb, lh};
     block_reduce<NT, 4>(v, red, parity, OpMax());
-    qn = v[1]; bn = v[2]; hn = v[3];
+    if (t == 0) { st->qn = v[1]; st->bn = v[2]; st->hn = v[3]; }
+    __syncthreads();
     return v[0] == 0.0f;
   }
 
-  // (Q x)_i from K's strict upper triangle and the diagonal qd.
-  __device__ __forceinline__ float q_row_dot(int i) const {
-    float acc = qd[i] * x[i];
-    for (int j = 0; j < i; ++j) acc = fmaf(K[j * L.ldk + i], x[j], acc);
-    for (int j = i + 1; j < L.n; ++j) acc = fmaf(K[i * L.ldk + j], x[j], acc);
-    return acc;
-  }
-
-  // ---- split rows by W = bz/bs; build F = [G_A; A], D and the SYRK weights (in ea) ----
+  // ---- split rows by W = bz/bs; build F = [G_A; A], D, C = diag(D) and the
+  // SYRK weights (W on inactive rows, 0 on active rows, in ea) ----
   __device__ void partition() {
+    const FLayout& L = st->L;
     const int m = L.m, p = L.p, n = L.n, t = threadIdx.x, w = t >> 5, lane = t & 31;
+    QP_ARR(bz); QP_ARR(bs); QP_ARR(red); QP_ARR(G); QP_ARR(A); QP_ARR(Y);
+    QP_ARR(C); QP_ARR(D); QP_ARR(ea); QP_IARR(act); QP_IARR(pos);
     float tau = 1.0f;
     for (int round = 0; round < 40; ++round) {
       float cnt[1] = {0.f};
@@ -201,33 +206,34 @@ struct Solver {
         if (keep) act[k] = r;
         base += __popc(mask);
       }
-      if (lane == 0) reinterpret_cast<int*>(col)[0] = min(base, L.amax);  // count (col is free here)
+      if (lane == 0) {
+        st->a = min(base, L.amax);
+        st->nf = st->a + p;
+      }
     }
     __syncthreads();
-    a = reinterpret_cast<int*>(col)[0];
-    __syncthreads();
-    nf = a + p;
-    // F rows, D, C = diag(D), SYRK weights
+    const int a = st->a, nf = st->nf;
     for (int k = w; k < nf; k += NT / 32) {
       const float* src = k < a ? G + act[k] * L.ldg : A + (k - a) * L.ldg;
       for (int c = lane; c < n; c += 32) Y[k * L.ldk + c] = src[c];
       for (int c = lane; c <= k; c += 32) C[k * L.ldc + c] = 0.f;
     }
-    for (int k = t; k < nf; k += NT) {
-      const float d = k < a ? bs[act[k]] / bz[act[k]] : 0.f;
-      D[k] = d;
-    }
+    for (int k = t; k < nf; k += NT) D[k] = k < a ? bs[act[k]] / bz[act[k]] : 0.f;
     for (int r = t; r < m; r += NT) ea[r] = pos[r] < 0 ? bz[r] / bs[r] : 0.f;
     __syncthreads();
     for (int k = t; k < nf; k += NT) C[k * L.ldc + k] = D[k];
     __syncthreads();
   }
 
-  // ---- factor K_I and the bordered block (F, D and C = D must have just been
-  // set by partition(): the elimination overwrites them) ----
+  // ---- factor K_I and the bordered block.  F, D and C = D must have just
+  // been set by partition(): the elimination overwrites them. ----
   __device__ bool factor_once(float creg) {
+    const FLayout& L = st->L;
+    QP_ARR(K); QP_ARR(qd); QP_ARR(G); QP_ARR(ea); QP_ARR(Y); QP_ARR(C); QP_ARR(dinv);
+    QP_ARR(cdinv); QP_ARR(Pb); QP_ARR(red);
+    const int nf = st->nf;
     syrk_gwg<NT>(K, L.ldk, qd, G, L.ldg, ea, L.m, L.n);
-    bool ok = cholesky_bordered<NT>(K, L.ldk, L.n, Y, L.ldk, nf, C, L.ldc, dinv);
+    bool ok = blocked_cholesky_bordered<NT>(K, L.ldk, L.n, Y, L.ldk, nf, C, L.ldc, dinv, Pb);
     if (nf > 0) {
       float dm[1] = {1.0f};
       for (int k = threadIdx.x; k < nf; k += NT) dm[0] = fmaxf(dm[0], C[k * L.ldc + k]);
@@ -235,13 +241,13 @@ struct Solver {
       const float shift = creg * dm[0];
       for (int k = threadIdx.x; k < nf; k += NT) C[k * L.ldc + k] += shift;
       __syncthreads();
-      ok = cholesky<NT>(C, L.ldc, nf, cdinv) && ok;
+      ok = blocked_cholesky<NT>(C, L.ldc, nf, cdinv, Pb) && ok;
     }
     return ok;
   }
 
-  // partition + factor; if FP32 Cholesky of C meets a non-positive pivot
-  // (rank-deficient F), redo it with a 100x and then 10^4x larger shift.
+  // factor; if FP32 Cholesky of C meets a non-positive pivot (rank-deficient
+  // F), redo the partition and factorisation with a 100x, then 10^4x larger shift.
   __device__ bool factor() {
     float creg = kCReg;
     for (int attempt = 0; attempt < 3; ++attempt, creg *= 100.0f) {
@@ -252,7 +258,9 @@ struct Solver {
   }
 
   template <int SP>
-  __device__ void c_solve(float* v) {
+  __device__ void c_solve(float* v, int nf) {
+    const FLayout& L = st->L;
+    QP_ARR(C); QP_ARR(cdinv);
     const int lane = threadIdx.x & 31;
     float r[1][SP];
 #pragma unroll
@@ -270,16 +278,18 @@ struct Solver {
   }
 
   // ---- solve [K_I F'; F -D] (dx, mu) = (rhs1, rhs2) for columns slot0..slot0+nrhs-1 ----
-  // rhs1 in R rows, rhs2 in ua (column 0) / ub (column 1); dx returned in R, mu in ua/ub.
+  // rhs1 in R rows, rhs2 in ua (column 0) / ub (column 1); dx returned in R, mu in ua / ub.
   __device__ void solve(int slot0, int nrhs) {
-    const int n = L.n, t = threadIdx.x, w = t >> 5;
+    const FLayout& L = st->L;
+    QP_ARR(K); QP_ARR(dinv); QP_ARR(R); QP_ARR(Y); QP_ARR(ua); QP_ARR(ub);
+    const int n = L.n, t = threadIdx.x, w = t >> 5, nf = st->nf;
     solve_rows<NT, false>(K, L.ldk, dinv, n, R, L.ldx, slot0, nrhs);
     if (nf > 0) {
       for (int e = t; e < nf * nrhs; e += NT) {
-        const int k = e % nf, col_ = slot0 + e / nf;
-        float* u = col_ == 0 ? ua : ub;
+        const int k = e % nf, cc = slot0 + e / nf;
+        float* u = cc == 0 ? ua : ub;
         const float* yk = Y + k * L.ldk;
-        const float* rr = R + col_ * L.ldx;
+        const float* rr = R + cc * L.ldx;
         float acc = 0.f;
         for (int i = 0; i < n; ++i) acc = fmaf(yk[i], rr[i], acc);
         u[k] = acc - u[k];
@@ -287,26 +297,28 @@ struct Solver {
       __syncthreads();
       if (w < nrhs) {
         float* u = (slot0 + w) == 0 ? ua : ub;
-        if (nf <= 32) c_solve<1>(u);
-        else if (nf <= 64) c_solve<2>(u);
-        else if (nf <= 96) c_solve<3>(u);
-        else c_solve<4>(u);
+        if (nf <= 32) c_solve<1>(u, nf);
+        else if (nf <= 64) c_solve<2>(u, nf);
+        else if (nf <= 96) c_solve<3>(u, nf);
+        else c_solve<4>(u, nf);
       }
       __syncthreads();
       for (int e = t; e < n * nrhs; e += NT) {
-        const int i = e % n, col_ = slot0 + e / n;
-        const float* u = col_ == 0 ? ua : ub;
-        float acc = R[col_ * L.ldx + i];
+        const int i = e % n, cc = slot0 + e / n;
+        const float* u = cc == 0 ? ua : ub;
+        float acc = R[cc * L.ldx + i];
         for (int k = 0; k < nf; ++k) acc = fmaf(-Y[k * L.ldk + i], u[k], acc);
-        R[col_ * L.ldx + i] = acc;
+        R[cc * L.ldx + i] = acc;
       }
       __syncthreads();
     }
     solve_rows<NT, true>(K, L.ldk, dinv, n, R, L.ldx, slot0, nrhs);
   }
 
-  // e_k = G dx_k for the solved columns
+  // e = G dx for the solved columns (ea for column 0, eb for column 1)
   __device__ void g_times_dx(int slot0, int nrhs) {
+    const FLayout& L = st->L;
+    QP_ARR(G); QP_ARR(R); QP_ARR(ea); QP_ARR(eb);
     for (int r = threadIdx.x; r < L.m; r += NT) {
       if (nrhs == 2) {
         float u, v;
@@ -324,7 +336,11 @@ struct Solver {
   // implicit: bz = b_k(v), bs = b_k(-v) with kappa = s'z/m; standard: bz = z, bs = s.
   // mode 0: complementarity term max z.*s; mode 1 (relax): |kappa - kr| / kr.
   __device__ float residuals(const FwdParams& P, bool implicit, int mode, float& kappa) {
+    const FLayout& L = st->L;
     const int n = L.n, m = L.m, p = L.p, t = threadIdx.x;
+    QP_ARR(K); QP_ARR(qd); QP_ARR(G); QP_ARR(A); QP_ARR(q); QP_ARR(b); QP_ARR(h); QP_ARR(x);
+    QP_ARR(y); QP_ARR(z); QP_ARR(s); QP_ARR(rt); QP_ARR(re); QP_ARR(ri); QP_ARR(rz); QP_ARR(rs);
+    QP_ARR(bz); QP_ARR(bs); QP_ARR(tn); QP_ARR(red); QP_ARR(col);
     float ks[1] = {0.f};
     for (int r = t; r < m; r += NT) ks[0] = fmaf(z[r], s[r], ks[0]);
     block_reduce<NT, 1>(ks, red, parity, OpSum());
@@ -341,7 +357,10 @@ struct Solver {
     for (int u = t; u < n + m + p; u += NT) {
       if (u < n) {
         const int i = u;
-        const float qx = q_row_dot(i);
+        // (Q x)_i from K's strict upper triangle and the diagonal qd
+        float qx = qd[i] * x[i];
+        for (int j = 0; j < i; ++j) qx = fmaf(K[j * L.ldk + i], x[j], qx);
+        for (int j = i + 1; j < n; ++j) qx = fmaf(K[i * L.ldk + j], x[j], qx);
         float aty = 0.f;
         for (int k = 0; k < p; ++k) aty = fmaf(A[k * L.ldg + i], y[k], aty);
         const float r = qx + q[i] + tn[i] + aty;
@@ -381,16 +400,20 @@ struct Solver {
     float comp = mx[9];
     if (mode == 1) comp = fabsf(kappa - P.kappa_relax) / P.kappa_relax;
     if (P.norm_abs) return fmaxf(fmaxf(fmaxf(mx[0], mx[4]), fmaxf(mx[6], comp)), mx[10]);
-    const float dt = fmaxf(fmaxf(1.0f, qn), fmaxf(fmaxf(mx[1], mx[2]), mx[3]));
-    const float de = fmaxf(fmaxf(1.0f, bn), mx[5]);
-    const float di = fmaxf(fmaxf(1.0f, hn), fmaxf(mx[7], mx[8]));
+    const float dt = fmaxf(fmaxf(1.0f, st->qn), fmaxf(fmaxf(mx[1], mx[2]), mx[3]));
+    const float de = fmaxf(fmaxf(1.0f, st->bn), mx[5]);
+    const float di = fmaxf(fmaxf(1.0f, st->hn), fmaxf(mx[7], mx[8]));
     const float dz = fmaxf(1.0f, fmaxf(mx[11], mx[8]));
     return fmaxf(fmaxf(fmaxf(mx[0] / dt, mx[4] / de), fmaxf(mx[6] / di, comp)), mx[10] / dz);
   }
 
   // ---- implicit right-hand sides, two columns (r_kappa = 0 and d/dr_kappa) ----
   __device__ void implicit_rhs() {
-    const int m = L.m, t = threadIdx.x;
+    const FLayout& L = st->L;
+    QP_ARR(bz); QP_ARR(bs); QP_ARR(ri); QP_ARR(rz); QP_ARR(rs); QP_ARR(re); QP_ARR(ta);
+    QP_ARR(tb); QP_ARR(ua); QP_ARR(ub); QP_ARR(R); QP_ARR(G); QP_ARR(rt); QP_ARR(col);
+    QP_IARR(pos); QP_IARR(act);
+    const int m = L.m, t = threadIdx.x, a = st->a, nf = st->nf;
     for (int r = t; r < m; r += NT) {
       const float rho = bz[r] + bs[r];
       const bool inact = pos[r] < 0;
@@ -412,12 +435,14 @@ struct Solver {
     __syncthreads();
     const float* vv[2] = {ta, tb};
     float* oo[2] = {R, R + L.ldx};
-    col_dot<NT, 2>(G, L.ldg, L.m, L.n, vv, oo, col, rt, -1.0f);
+    col_dot<NT, 2>(G, L.ldg, m, L.n, vv, oo, col, rt, -1.0f);
   }
 
   // ds, dz, dv of the implicit direction for r_kappa = rk on row r
   __device__ __forceinline__ void implicit_dir(int r, float rk, float& dsr, float& dzr,
                                                float& dvr) const {
+    QP_ARR(bz); QP_ARR(bs); QP_ARR(ea); QP_ARR(eb); QP_ARR(ri); QP_ARR(rz); QP_ARR(rs);
+    QP_ARR(ua); QP_ARR(ub); QP_IARR(pos);
     const float rho = bz[r] + bs[r];
     const float c = 1.0f / rho;
     const float e = fmaf(rk, eb[r], ea[r]);
@@ -433,8 +458,9 @@ struct Solver {
   }
 
   __device__ float implicit_alpha(float rk, bool store) {
+    QP_ARR(s); QP_ARR(z); QP_ARR(tb); QP_ARR(red);
     float amin[1] = {1.0f};
-    for (int r = threadIdx.x; r < L.m; r += NT) {
+    for (int r = threadIdx.x; r < st->L.m; r += NT) {
       float dsr, dzr, dvr;
       implicit_dir(r, rk, dsr, dzr, dvr);
       if (dsr < 0.f) amin[0] = fminf(amin[0], -s[r] / dsr);
@@ -446,18 +472,21 @@ struct Solver {
   }
 
   __device__ float implicit_mu_aff(float rk, float alpha) {
+    QP_ARR(s); QP_ARR(z); QP_ARR(red);
     float acc[1] = {0.f};
-    for (int r = threadIdx.x; r < L.m; r += NT) {
+    for (int r = threadIdx.x; r < st->L.m; r += NT) {
       float dsr, dzr, dvr;
       implicit_dir(r, rk, dsr, dzr, dvr);
       acc[0] = fmaf(fmaf(alpha, dsr, s[r]), fmaf(alpha, dzr, z[r]), acc[0]);
     }
     block_reduce<NT, 1>(acc, red, parity, OpSum());
-    return acc[0] / (float)L.m;
+    return acc[0] / (float)st->L.m;
   }
 
   __device__ void implicit_update(float alpha, float rk, float kappa) {
-    const int p = L.p, t = threadIdx.x;
+    const FLayout& L = st->L;
+    QP_ARR(x); QP_ARR(y); QP_ARR(z); QP_ARR(s); QP_ARR(R); QP_ARR(ua); QP_ARR(ub); QP_ARR(tb);
+    const int p = L.p, t = threadIdx.x, a = st->a;
     const float knew = kappa - alpha * rk;
     for (int i = t; i < L.n; i += NT) x[i] = fmaf(alpha, fmaf(rk, R[L.ldx + i], R[i]), x[i]);
     for (int k = t; k < p; k += NT) y[k] = fmaf(alpha, fmaf(rk, ub[a + k], ua[a + k]), y[k]);
@@ -502,12 +531,17 @@ struct Solver {
     return true;
   }
 
-  // ---- explicit complementarity (ablation) ----
-  // rhs for r_c (per row, r_c / s and r_c / z): t_I = -W r_i + r_c/s (inactive rows),
-  // rhs2_A = -(r_i - r_c/z), rhs2_eq = -r_e.  base = false drops the r_t, r_i, r_e terms.
+  // ---- explicit complementarity (ablation): Mehrotra predictor-corrector on
+  // eq. 8 in the same two-level form.  For r_c (z.*s, then the corrector term)
+  // rhs1 = -r_t + G_I'(-W r_i + r_c/s), rhs2 = (-(r_i - r_c/z)_A, -r_e). ----
   __device__ bool standard_step(const FwdParams& P, float mu) {
+    const FLayout& L = st->L;
     const int m = L.m, p = L.p, t = threadIdx.x;
     partition();
+    QP_ARR(z); QP_ARR(s); QP_ARR(ri); QP_ARR(re); QP_ARR(rz); QP_ARR(rs); QP_ARR(ta); QP_ARR(tb);
+    QP_ARR(ua); QP_ARR(ub); QP_ARR(ea); QP_ARR(eb); QP_ARR(R); QP_ARR(G); QP_ARR(rt);
+    QP_ARR(col); QP_ARR(red); QP_ARR(x); QP_ARR(y); QP_IARR(pos); QP_IARR(act);
+    const int a = st->a, nf = st->nf;
     // predictor (slot 0): r_c = z.*s
     for (int r = t; r < m; r += NT) ta[r] = pos[r] < 0 ? -(z[r] / s[r]) * ri[r] + z[r] : 0.f;
     for (int k = t; k < nf; k += NT) ua[k] = k < a ? -(ri[act[k]] - s[act[k]]) : -re[k - a];
@@ -582,7 +616,10 @@ struct Solver {
   // CVXOPT-style start: (Q + G'G) x + A'y = -q + G'h, A x = b; z = G x - h, s = -z, shifted.
   // With m = 0 this is the exact solution of the equality-constrained QP.
   __device__ bool initialize() {
+    const FLayout& L = st->L;
     const int m = L.m, p = L.p, t = threadIdx.x;
+    QP_ARR(bz); QP_ARR(bs); QP_ARR(ua); QP_ARR(b); QP_ARR(h); QP_ARR(R); QP_ARR(G); QP_ARR(col);
+    QP_ARR(q); QP_ARR(x); QP_ARR(y); QP_ARR(z); QP_ARR(s); QP_ARR(red);
     for (int r = t; r < m; r += NT) { bz[r] = 1.0f; bs[r] = 1.0f; }
     __syncthreads();
     partition();  // W = 1 everywhere: no active rows, F = A
@@ -620,7 +657,10 @@ struct Solver {
 
   // ---- gradient cache: factors, W, active map and the point (Alg. 3 input) ----
   __device__ void write_cache(const FwdParams& P, int bi) {
-    const int n = L.n, m = L.m, p = L.p, t = threadIdx.x;
+    const FLayout& L = st->L;
+    QP_ARR(K); QP_ARR(Y); QP_ARR(C); QP_ARR(ea); QP_ARR(D); QP_ARR(x); QP_ARR(y); QP_ARR(z);
+    QP_IARR(pos);
+    const int n = L.n, m = L.m, p = L.p, t = threadIdx.x, a = st->a, nf = st->nf;
     const CacheLayout cl = cache_layout(n, m, p, L.amax);
     float* c = P.cache + (size_t)bi * (size_t)P.cache_stride;
     if (t == 0) {
@@ -657,6 +697,8 @@ struct Solver {
   }
 
   __device__ void write_solution(const FwdParams& P, int bi, bool good) {
+    const FLayout& L = st->L;
+    QP_ARR(x); QP_ARR(y); QP_ARR(z); QP_ARR(s);
     const int n = L.n, m = L.m, p = L.p, t = threadIdx.x;
     const float nanv = NAN;
     for (int i = t; i < n; i += NT) P.x[(size_t)bi * n + i] = good ? x[i] : nanv;
@@ -668,17 +710,18 @@ struct Solver {
   }
 
   // ---- whole instance ----
-  __device__ void run(const FwdParams& P, int bi, float* sm) {
-    const int n = L.n, m = L.m, p = L.p, t = threadIdx.x;
+  __device__ void run(const FwdParams& P, int bi) {
+    const int n = st->L.n, m = st->L.m, p = st->L.p, t = threadIdx.x;
     const bool implicit = P.formulation == 0;
     int status = ST_SOLVED, iters = 0;
     float meas = NAN;
-    const bool good = load(P, bi, sm);
+    const bool good = load(P, bi);
     if (!good) {
       status = ST_BAD_INPUT;
     } else {
       bool warm = false;
       if (P.warm_start && m > 0) {
+        QP_ARR(x); QP_ARR(y); QP_ARR(z); QP_ARR(s); QP_ARR(red);
         float mn[1] = {INFINITY};
         for (int i = t; i < n; i += NT) x[i] = P.x[(size_t)bi * n + i];
         for (int k = t; k < p; k += NT) y[k] = P.y[(size_t)bi * p + k];
@@ -699,6 +742,7 @@ struct Solver {
           meas = residuals(P, implicit, 0, kap);
           if (!(meas == meas)) { status = ST_NUMERICAL; break; }
           if (meas < P.tol || it >= P.max_iter) break;
+          QP_ARR(R); QP_ARR(rt); QP_ARR(ua); QP_ARR(re); QP_ARR(x); QP_ARR(y);
           for (int i = t; i < n; i += NT) R[i] = -rt[i];
           for (int k = t; k < p; k += NT) ua[k] = -re[k];
           __syncthreads();
@@ -729,6 +773,7 @@ struct Solver {
     write_solution(P, bi, good);
     // ---- Alg. 2 (relax) and the factor at the relaxed point ----
     if (P.cache && status != ST_BAD_INPUT) {
+      QP_ARR(z); QP_ARR(s); QP_ARR(bz); QP_ARR(bs);
       if (m > 0 && P.kappa_relax > 0.f && status != ST_NUMERICAL) {
         int rstatus = ST_MAX_ITER;
         for (int it = 0;; ++it) {
@@ -760,12 +805,21 @@ struct Solver {
   }
 };
 
+#undef QP_ARR
+#undef QP_IARR
+
+// minimum resident CTAs per SM the register budget is sized for
+template <int NT> struct MinBlocks { static constexpr int value = 1; };
+template <> struct MinBlocks<128> { static constexpr int value = 4; };
+template <> struct MinBlocks<256> { static constexpr int value = 3; };
+
 template <int NT>
-__global__ void __launch_bounds__(NT) qp_forward_kernel(const FwdParams P) {
+__global__ void __launch_bounds__(NT, MinBlocks<NT>::value) qp_forward_kernel(const FwdParams P) {
   extern __shared__ __align__(16) float sm[];
+  __shared__ SharedState st;
   Solver<NT> slv;
-  slv.bind(sm, P.n, P.m, P.p, P.amax);
-  slv.run(P, blockIdx.x, sm);
+  slv.bind(sm, &st, P.n, P.m, P.p, P.amax);
+  slv.run(P, blockIdx.x);
 }
 
 }  // namespace fwd
