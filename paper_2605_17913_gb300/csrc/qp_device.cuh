@@ -264,60 +264,6 @@ __device__ bool cholesky(float* K, int ldk, int n, float* dinv) {
 
 
 // ---------------------------------------------------------------------------
-// Bordered Cholesky.  Eliminates the n leading pivots of the symmetric matrix
-//     [ K   F' ]
-//     [ F   C0 ]
-// K: n x n lower triangle (stride ldk), F: nf rows of length n in Y (stride
-// ldy, odd), C: nf x nf lower triangle (stride ldc) holding C0 on entry.
-// On exit K's lower triangle is L (K = L L'), Y = F L^-T and C = C0 + Y Y'
-// (the negated Schur complement of the bordered system), dinv[j] = 1/L[j][j].
-// The rows of F and the C block ride along in the same parallel trailing
-// updates as K, so no triangular solve is needed to form Y or Y Y'.
-// Only K's lower triangle and diagonal are written.  Returns false if a
-// pivot is not positive and finite.  Ends with a barrier.
-// ---------------------------------------------------------------------------
-template <int NT>
-__device__ bool cholesky_bordered(float* K, int ldk, int n, float* Y, int ldy, int nf, float* C,
-                                  int ldc, float* dinv) {
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  constexpr int nw = NT / 32;
-  bool ok = true;
-  for (int j = 0; j < n; ++j) {
-    const float d = K[j * ldk + j];
-    if (!(d > 0.0f) || !(d < INFINITY)) ok = false;
-    const float inv = 1.0f / d;
-    const int nK = n - j - 1;
-    for (int rr = w; rr < nK + nf; rr += nw) {
-      if (rr < nK) {
-        const int r = j + 1 + rr;
-        const float lrj = K[r * ldk + j] * inv;
-        for (int c = j + 1 + l; c <= r; c += 32) K[r * ldk + c] = fmaf(-lrj, K[c * ldk + j], K[r * ldk + c]);
-      } else {
-        const int k = rr - nK;
-        const float lkj = Y[k * ldy + j] * inv;
-        for (int c = j + 1 + l; c < n; c += 32) Y[k * ldy + c] = fmaf(-lkj, K[c * ldk + j], Y[k * ldy + c]);
-        for (int c = l; c <= k; c += 32) C[k * ldc + c] = fmaf(lkj, Y[c * ldy + j], C[k * ldc + c]);
-      }
-    }
-    __syncthreads();
-  }
-  for (int j = threadIdx.x; j < n; j += NT) dinv[j] = 1.0f / sqrtf(K[j * ldk + j]);
-  __syncthreads();
-  for (int r = w; r < n + nf; r += nw) {
-    if (r < n) {
-      for (int c = l; c < r; c += 32) K[r * ldk + c] *= dinv[c];
-      if (l == 0) K[r * ldk + r] = 1.0f / dinv[r];
-    } else {
-      const int k = r - n;
-      for (int c = l; c < n; c += 32) Y[k * ldy + c] *= dinv[c];
-    }
-  }
-  __syncthreads();
-  return ok;
-}
-
-
-// ---------------------------------------------------------------------------
 // Blocked (panel width 8) right-looking Cholesky of a bordered system.
 //
 // Phase 1 eliminates the n leading pivots of  [ K  F' ; F  C0 ]  as in
@@ -332,9 +278,10 @@ __device__ bool cholesky_bordered(float* K, int ldk, int n, float* Y, int ldy, i
 // Phase 2 factors C the same way (then only C rows exist).
 // Outputs: K lower = L, Y = F L^-T, C lower = L_C (C = D + Y Y' + shift is
 // applied by the caller between the phases), dinv / cdinv = 1 / diag.
-// Pb needs (n + nf + 4) * kPbLd floats.  Ends with a barrier.
+// Pb needs (n + nf + 4) * ldpb floats.  Ends with a barrier.
 // ---------------------------------------------------------------------------
-constexpr int kPbLd = 12;  // 8 panel values + 4 pad: 8 consecutive rows hit distinct banks
+// Panel rows are stored with stride ldpb = 12 floats (8 values + 4 pad: 8
+// consecutive rows then hit distinct banks) or 8 when shared memory is tight.
 
 template <int NT>
 __device__ bool block_diag_factor(float* M, int ld, int j0, int jb, float* dinv) {
@@ -371,7 +318,7 @@ __device__ bool block_diag_factor(float* M, int ld, int j0, int jb, float* dinv)
 template <int NT>
 __device__ void panel_trsm(const float* Ldiag, int ldl, int j0, int jb, const float* dinv,
                            float* A, int lda, int rowA0, int nA, float* B, int ldb, int nB,
-                           float* Pb) {
+                           float* Pb, int ldpb) {
   for (int rr = threadIdx.x; rr < nA + nB; rr += NT) {
     float* row = rr < nA ? A + (rowA0 + rr) * lda + j0 : B + (rr - nA) * ldb + j0;
     float v[8];
@@ -389,12 +336,12 @@ __device__ void panel_trsm(const float* Ldiag, int ldl, int j0, int jb, const fl
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
       if (t < jb) row[t] = v[t];
-      Pb[rr * kPbLd + t] = v[t];
+      Pb[rr * ldpb + t] = v[t];
     }
   }
   // zero the pad rows of the last tile row
   const int N = nA + nB;
-  for (int e = threadIdx.x; e < 4 * kPbLd; e += NT) Pb[N * kPbLd + e] = 0.0f;
+  for (int e = threadIdx.x; e < 4 * ldpb; e += NT) Pb[N * ldpb + e] = 0.0f;
   __syncthreads();
 }
 
@@ -404,8 +351,8 @@ __device__ void panel_trsm(const float* Ldiag, int ldl, int j0, int jb, const fl
 //   (B, A): B[k][colA0+c]        -= P_k . P_c
 //   (B, B): C[k][l]              += P_k . P_l     (when C != nullptr)
 template <int NT>
-__device__ void panel_syrk(const float* Pb, float* A, int lda, int rowA0, int nA, float* B,
-                           int ldb, int nB, float* C, int ldc, float csign) {
+__device__ void panel_syrk(const float* Pb, int ldpb, float* A, int lda, int rowA0, int nA,
+                           float* B, int ldb, int nB, float* C, int ldc, float csign) {
   const int N = nA + nB;
   const int nt = (N + 3) >> 2;
   const int T = nt * (nt + 1) / 2;
@@ -423,9 +370,9 @@ __device__ void panel_syrk(const float* Pb, float* A, int lda, int rowA0, int nA
     for (int h2 = 0; h2 < 2; ++h2) {
       float4 ra[4], cb[4];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) ra[a] = *reinterpret_cast<const float4*>(Pb + (4 * I + a) * kPbLd + 4 * h2);
+      for (int a = 0; a < 4; ++a) ra[a] = *reinterpret_cast<const float4*>(Pb + (4 * I + a) * ldpb + 4 * h2);
 #pragma unroll
-      for (int b = 0; b < 4; ++b) cb[b] = *reinterpret_cast<const float4*>(Pb + (4 * J + b) * kPbLd + 4 * h2);
+      for (int b = 0; b < 4; ++b) cb[b] = *reinterpret_cast<const float4*>(Pb + (4 * J + b) * ldpb + 4 * h2);
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -461,29 +408,29 @@ __device__ void panel_syrk(const float* Pb, float* A, int lda, int rowA0, int nA
 // accumulating Y Y'.  Phase 2 is blocked_cholesky on C alone.
 template <int NT>
 __device__ bool blocked_cholesky_bordered(float* K, int ldk, int n, float* Y, int ldy, int nf,
-                                          float* C, int ldc, float* dinv, float* Pb) {
+                                          float* C, int ldc, float* dinv, float* Pb, int ldpb) {
   bool ok = true;
   for (int j0 = 0; j0 < n; j0 += 8) {
     const int jb = min(8, n - j0);
     ok = block_diag_factor<NT>(K, ldk, j0, jb, dinv) && ok;
     const int nK = n - j0 - jb;
-    panel_trsm<NT>(K, ldk, j0, jb, dinv, K, ldk, j0 + jb, nK, Y, ldy, nf, Pb);
-    if (nK + nf > 0) panel_syrk<NT>(Pb, K, ldk, j0 + jb, nK, Y, ldy, nf, C, ldc, 1.0f);
+    panel_trsm<NT>(K, ldk, j0, jb, dinv, K, ldk, j0 + jb, nK, Y, ldy, nf, Pb, ldpb);
+    if (nK + nf > 0) panel_syrk<NT>(Pb, ldpb, K, ldk, j0 + jb, nK, Y, ldy, nf, C, ldc, 1.0f);
   }
   return ok;
 }
 
 // In-place blocked Cholesky of the lower triangle of M (n x n, stride ld).
 template <int NT>
-__device__ bool blocked_cholesky(float* M, int ld, int n, float* dinv, float* Pb) {
+__device__ bool blocked_cholesky(float* M, int ld, int n, float* dinv, float* Pb, int ldpb) {
   bool ok = true;
   for (int j0 = 0; j0 < n; j0 += 8) {
     const int jb = min(8, n - j0);
     ok = block_diag_factor<NT>(M, ld, j0, jb, dinv) && ok;
     const int nR = n - j0 - jb;
     if (nR > 0) {
-      panel_trsm<NT>(M, ld, j0, jb, dinv, M, ld, j0 + jb, nR, nullptr, 0, 0, Pb);
-      panel_syrk<NT>(Pb, M, ld, j0 + jb, nR, nullptr, 0, 0, nullptr, 0, 0.0f);
+      panel_trsm<NT>(M, ld, j0, jb, dinv, M, ld, j0 + jb, nR, nullptr, 0, 0, Pb, ldpb);
+      panel_syrk<NT>(Pb, ldpb, M, ld, j0 + jb, nR, nullptr, 0, 0, nullptr, 0, 0.0f);
     }
   }
   return ok;

@@ -52,10 +52,11 @@ namespace fwd {
 
 constexpr int ST_SOLVED = 0, ST_MAX_ITER = 1, ST_STALLED = 2, ST_NUMERICAL = 3, ST_BAD_INPUT = 4;
 constexpr float kCReg = 1e-7f;  // relative diagonal shift of C
+constexpr int kStaticSmem = 1024;  // upper bound of the kernel's static shared memory
 
 struct FLayout {
   int n, m, p, amax, fmax;
-  int ldk, ldg, ldx, ldc, nv, mv, pv, fv;
+  int ldk, ldg, ldx, ldc, ldpb, nv, mv, pv, fv;
   int o_K, o_qd, o_G, o_A, o_Y, o_C, o_R, o_col, o_red, o_Pb;
   int o_q, o_x, o_rt, o_dinv, o_tn;
   int o_b, o_y, o_re;
@@ -64,9 +65,13 @@ struct FLayout {
   int total;
 };
 
-__host__ __device__ inline FLayout make_fwd_layout(int n, int m, int p, int amax, int nthreads) {
+// The panel buffer Pb of the blocked factorisation is only live inside
+// factor_once(), so it shares one region with col, ta, tb, eb and tn, which
+// are dead there.
+__host__ __device__ inline FLayout make_fwd_layout(int n, int m, int p, int amax, int nthreads,
+                                                   int ldpb) {
   FLayout L;
-  L.n = n; L.m = m; L.p = p; L.amax = amax; L.fmax = amax + p;
+  L.n = n; L.m = m; L.p = p; L.amax = amax; L.fmax = amax + p; L.ldpb = ldpb;
   L.ldk = ld_odd(n);
   L.ldg = ld_vec(n);
   L.ldx = round4(n);
@@ -82,23 +87,31 @@ __host__ __device__ inline FLayout make_fwd_layout(int n, int m, int p, int amax
   L.o_Y = take(L.fmax * L.ldk);
   L.o_C = take(L.fmax * L.ldc);
   L.o_R = take(2 * L.ldx);
-  L.o_col = take(2 * nthreads);
-  L.o_red = take(2 * kMaxWarps * kRedK);
-  L.o_Pb = take((n + L.fmax + 4) * kPbLd);
+  L.o_red = take(2 * (nthreads / 32) * kRedK);
+  {
+    // union: Pb | (col, ta, tb, eb, tn)
+    const int base = o;
+    const int pb = round4((n + L.fmax + 4) * ldpb);
+    L.o_Pb = base;
+    L.o_col = take(2 * nthreads);
+    L.o_ta = take(L.mv); L.o_tb = take(L.mv); L.o_eb = take(L.mv);
+    L.o_tn = take(L.nv);
+    if (o < base + pb) o = base + pb;
+  }
   L.o_q = take(L.nv); L.o_x = take(L.nv); L.o_rt = take(L.nv); L.o_dinv = take(L.nv);
-  L.o_tn = take(L.nv);
   L.o_b = take(L.pv); L.o_y = take(L.pv); L.o_re = take(L.pv);
   L.o_cdinv = take(L.fv); L.o_D = take(L.fv); L.o_ua = take(L.fv); L.o_ub = take(L.fv);
   L.o_act = take(L.fv);
   L.o_h = take(L.mv); L.o_z = take(L.mv); L.o_s = take(L.mv); L.o_ri = take(L.mv);
   L.o_rz = take(L.mv); L.o_rs = take(L.mv); L.o_bz = take(L.mv); L.o_bs = take(L.mv);
-  L.o_ea = take(L.mv); L.o_eb = take(L.mv); L.o_ta = take(L.mv); L.o_tb = take(L.mv);
+  L.o_ea = take(L.mv);
   L.o_pos = take(L.mv);
   L.total = o;
   return L;
 }
 
-// Per-CTA scalars kept in shared memory.
+// Per-CTA scalars kept in shared memory (static; the dynamic allocation must
+// leave kStaticSmem bytes of the 227 KB per-CTA limit for it).
 struct SharedState {
   FLayout L;
   int a, nf;         // active rows, rows of F = a + p (set by partition())
@@ -115,11 +128,11 @@ struct Solver {
   SharedState* st;
   int parity;
 
-  __device__ void bind(float* sm_, SharedState* st_, int n, int m, int p, int amax) {
+  __device__ void bind(float* sm_, SharedState* st_, int n, int m, int p, int amax, int ldpb) {
     sm = sm_;
     st = st_;
     if (threadIdx.x == 0) {
-      st->L = make_fwd_layout(n, m, p, amax, NT);
+      st->L = make_fwd_layout(n, m, p, amax, NT, ldpb);
       st->a = 0;
       st->nf = p;
     }
@@ -233,7 +246,8 @@ struct Solver {
     QP_ARR(cdinv); QP_ARR(Pb); QP_ARR(red);
     const int nf = st->nf;
     syrk_gwg<NT>(K, L.ldk, qd, G, L.ldg, ea, L.m, L.n);
-    bool ok = blocked_cholesky_bordered<NT>(K, L.ldk, L.n, Y, L.ldk, nf, C, L.ldc, dinv, Pb);
+    bool ok = blocked_cholesky_bordered<NT>(K, L.ldk, L.n, Y, L.ldk, nf, C, L.ldc, dinv, Pb,
+                                            L.ldpb);
     if (nf > 0) {
       float dm[1] = {1.0f};
       for (int k = threadIdx.x; k < nf; k += NT) dm[0] = fmaxf(dm[0], C[k * L.ldc + k]);
@@ -241,7 +255,7 @@ struct Solver {
       const float shift = creg * dm[0];
       for (int k = threadIdx.x; k < nf; k += NT) C[k * L.ldc + k] += shift;
       __syncthreads();
-      ok = blocked_cholesky<NT>(C, L.ldc, nf, cdinv, Pb) && ok;
+      ok = blocked_cholesky<NT>(C, L.ldc, nf, cdinv, Pb, L.ldpb) && ok;
     }
     return ok;
   }
@@ -818,7 +832,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) qp_forward_kernel(co
   extern __shared__ __align__(16) float sm[];
   __shared__ SharedState st;
   Solver<NT> slv;
-  slv.bind(sm, &st, P.n, P.m, P.p, P.amax);
+  slv.bind(sm, &st, P.n, P.m, P.p, P.amax, P.ldpb);
   slv.run(P, blockIdx.x);
 }
 
@@ -827,12 +841,12 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) qp_forward_kernel(co
 // Instantiated once per block size in qp_forward_<NT>.cu.
 template <int NT>
 cudaError_t launch_forward_nt(const FwdParams& P, size_t smem, int grid, cudaStream_t st) {
-  static bool configured = false;  // the attribute is per function and per process
-  if (!configured) {
+  static size_t configured = 0;  // the attribute is per function and per process
+  if (smem > configured) {
     cudaError_t e = cudaFuncSetAttribute(fwd::qp_forward_kernel<NT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    configured = true;
+    configured = smem;
   }
   fwd::qp_forward_kernel<NT><<<grid, NT, smem, st>>>(P);
   return cudaGetLastError();
@@ -841,8 +855,9 @@ cudaError_t launch_forward_nt(const FwdParams& P, size_t smem, int grid, cudaStr
 template <int NT>
 int forward_blocks_per_sm_nt(size_t smem) {
   int nb = 0;
-  cudaFuncSetAttribute(fwd::qp_forward_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       227 * 1024);
+  if (cudaFuncSetAttribute(fwd::qp_forward_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess)
+    return 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fwd::qp_forward_kernel<NT>, NT, smem) !=
       cudaSuccess)
     return 0;
