@@ -794,7 +794,13 @@ struct Solver {
           float kappa;
           const float rm = residuals(P, true, 1, kappa);
           if (!(rm == rm)) { rstatus = ST_NUMERICAL; break; }
-          if (rm < P.relax_tol) { rstatus = ST_SOLVED; break; }
+          if (rm < P.relax_tol) {
+            // one more (quadratically convergent) Newton step polishes the
+            // relaxed point the gradients are taken at
+            rstatus = ST_SOLVED;
+            if (implicit_step(P, kappa, P.kappa_relax)) ++iters;
+            break;
+          }
           if (it >= P.relax_max_iter) break;
           if (!implicit_step(P, kappa, P.kappa_relax)) { rstatus = ST_NUMERICAL; break; }
           ++iters;
