@@ -52,7 +52,7 @@ namespace fwd {
 
 constexpr int ST_SOLVED = 0, ST_MAX_ITER = 1, ST_STALLED = 2, ST_NUMERICAL = 3, ST_BAD_INPUT = 4;
 constexpr float kCReg = 1e-7f;  // relative diagonal shift of C
-constexpr int kStaticSmem = 1024;  // upper bound of the kernel's static shared memory
+constexpr int kStaticSmem = 1024;  // upper bound of the kernel's static shared memory (state + params)
 
 struct FLayout {
   int n, m, p, amax, fmax;
@@ -114,9 +114,29 @@ __host__ __device__ inline FLayout make_fwd_layout(int n, int m, int p, int amax
 // leave kStaticSmem bytes of the 227 KB per-CTA limit for it).
 struct SharedState {
   FLayout L;
+  long long t_mark;  // phase timers only
   int a, nf;         // active rows, rows of F = a + p (set by partition())
   float qn, bn, hn;  // |q|, |b|, |h| (infinity norms)
 };
+
+// Phase timers (tracing facility, compiled only with -DQP_PHASE_TIMERS): thread
+// 0 of each CTA adds the cycles between consecutive marks, taken at barrier
+// boundaries, to g_qp_phase_cycles[phase]; qp_debug_phase_cycles() reads them.
+enum Phase { PH_LOAD, PH_RESID, PH_PART, PH_RHS, PH_SYRK, PH_BORDER, PH_CCHOL, PH_SOLVE, PH_GDX,
+             PH_STEP, PH_CACHE, PH_COUNT };
+#ifdef QP_PHASE_TIMERS
+__device__ unsigned long long g_qp_phase_cycles[PH_COUNT];
+#define QP_MARK(ph)                                                                    \
+  do {                                                                                 \
+    if (threadIdx.x == 0) {                                                            \
+      const long long now_ = clock64();                                                \
+      atomicAdd(&g_qp_phase_cycles[ph], (unsigned long long)(now_ - st->t_mark));     \
+      st->t_mark = now_;                                                               \
+    }                                                                                  \
+  } while (0)
+#else
+#define QP_MARK(ph) do {} while (0)
+#endif
 
 // address of array `name` in the per-instance shared-memory layout
 #define QP_ARR(name) float* const name = sm + st->L.o_##name
@@ -135,6 +155,7 @@ struct Solver {
       st->L = make_fwd_layout(n, m, p, amax, NT, ldpb);
       st->a = 0;
       st->nf = p;
+      st->t_mark = clock64();
     }
     __syncthreads();
     parity = 0;
@@ -142,7 +163,7 @@ struct Solver {
 
   // ---- load one instance; Q's strict upper triangle goes to K's upper part ----
   // Returns false if some datum is not finite.
-  __device__ bool load(const FwdParams& P, int bi) {
+  __device__ __noinline__ bool load(const FwdParams& P, int bi) {
     const FLayout& L = st->L;
     const int n = L.n, m = L.m, p = L.p, t = threadIdx.x;
     QP_ARR(K); QP_ARR(qd); QP_ARR(G); QP_ARR(A); QP_ARR(q); QP_ARR(b); QP_ARR(h); QP_ARR(red);
@@ -188,12 +209,13 @@ struct Solver {
     block_reduce<NT, 4>(v, red, parity, OpMax());
     if (t == 0) { st->qn = v[1]; st->bn = v[2]; st->hn = v[3]; }
     __syncthreads();
+    QP_MARK(PH_LOAD);
     return v[0] == 0.0f;
   }
 
   // ---- split rows by W = bz/bs; build F = [G_A; A], D, C = diag(D) and the
   // SYRK weights (W on inactive rows, 0 on active rows, in ea) ----
-  __device__ void partition() {
+  __device__ __noinline__ void partition() {
     const FLayout& L = st->L;
     const int m = L.m, p = L.p, n = L.n, t = threadIdx.x, w = t >> 5, lane = t & 31;
     QP_ARR(bz); QP_ARR(bs); QP_ARR(red); QP_ARR(G); QP_ARR(A); QP_ARR(Y);
@@ -236,18 +258,21 @@ struct Solver {
     __syncthreads();
     for (int k = t; k < nf; k += NT) C[k * L.ldc + k] = D[k];
     __syncthreads();
+    QP_MARK(PH_PART);
   }
 
   // ---- factor K_I and the bordered block.  F, D and C = D must have just
   // been set by partition(): the elimination overwrites them. ----
-  __device__ bool factor_once(float creg) {
+  __device__ __noinline__ bool factor_once(float creg) {
     const FLayout& L = st->L;
     QP_ARR(K); QP_ARR(qd); QP_ARR(G); QP_ARR(ea); QP_ARR(Y); QP_ARR(C); QP_ARR(dinv);
     QP_ARR(cdinv); QP_ARR(Pb); QP_ARR(red);
     const int nf = st->nf;
     syrk_gwg<NT>(K, L.ldk, qd, G, L.ldg, ea, L.m, L.n);
+    QP_MARK(PH_SYRK);
     bool ok = blocked_cholesky_bordered<NT>(K, L.ldk, L.n, Y, L.ldk, nf, C, L.ldc, dinv, Pb,
                                             L.ldpb);
+    QP_MARK(PH_BORDER);
     if (nf > 0) {
       float dm[1] = {1.0f};
       for (int k = threadIdx.x; k < nf; k += NT) dm[0] = fmaxf(dm[0], C[k * L.ldc + k]);
@@ -256,13 +281,14 @@ struct Solver {
       for (int k = threadIdx.x; k < nf; k += NT) C[k * L.ldc + k] += shift;
       __syncthreads();
       ok = blocked_cholesky<NT>(C, L.ldc, nf, cdinv, Pb, L.ldpb) && ok;
+      QP_MARK(PH_CCHOL);
     }
     return ok;
   }
 
   // factor; if FP32 Cholesky of C meets a non-positive pivot (rank-deficient
   // F), redo the partition and factorisation with a 100x, then 10^4x larger shift.
-  __device__ bool factor() {
+  __device__ __noinline__ bool factor() {
     float creg = kCReg;
     for (int attempt = 0; attempt < 3; ++attempt, creg *= 100.0f) {
       if (attempt > 0) partition();
@@ -293,7 +319,7 @@ struct Solver {
 
   // ---- solve [K_I F'; F -D] (dx, mu) = (rhs1, rhs2) for columns slot0..slot0+nrhs-1 ----
   // rhs1 in R rows, rhs2 in ua (column 0) / ub (column 1); dx returned in R, mu in ua / ub.
-  __device__ void solve(int slot0, int nrhs) {
+  __device__ __noinline__ void solve(int slot0, int nrhs) {
     const FLayout& L = st->L;
     QP_ARR(K); QP_ARR(dinv); QP_ARR(R); QP_ARR(Y); QP_ARR(ua); QP_ARR(ub);
     const int n = L.n, t = threadIdx.x, w = t >> 5, nf = st->nf;
@@ -327,10 +353,11 @@ struct Solver {
       __syncthreads();
     }
     solve_rows<NT, true>(K, L.ldk, dinv, n, R, L.ldx, slot0, nrhs);
+    QP_MARK(PH_SOLVE);
   }
 
   // e = G dx for the solved columns (ea for column 0, eb for column 1)
-  __device__ void g_times_dx(int slot0, int nrhs) {
+  __device__ __noinline__ void g_times_dx(int slot0, int nrhs) {
     const FLayout& L = st->L;
     QP_ARR(G); QP_ARR(R); QP_ARR(ea); QP_ARR(eb);
     for (int r = threadIdx.x; r < L.m; r += NT) {
@@ -344,12 +371,13 @@ struct Solver {
       }
     }
     __syncthreads();
+    QP_MARK(PH_GDX);
   }
 
   // ---- residuals (eq. 4, eq. 10) and the measure ----
   // implicit: bz = b_k(v), bs = b_k(-v) with kappa = s'z/m; standard: bz = z, bs = s.
   // mode 0: complementarity term max z.*s; mode 1 (relax): |kappa - kr| / kr.
-  __device__ float residuals(const FwdParams& P, bool implicit, int mode, float& kappa) {
+  __device__ __noinline__ float residuals(const FwdParams& P, bool implicit, int mode, float& kappa) {
     const FLayout& L = st->L;
     const int n = L.n, m = L.m, p = L.p, t = threadIdx.x;
     QP_ARR(K); QP_ARR(qd); QP_ARR(G); QP_ARR(A); QP_ARR(q); QP_ARR(b); QP_ARR(h); QP_ARR(x);
@@ -410,6 +438,7 @@ struct Solver {
       }
     }
     block_reduce<NT, 13>(mx, red, parity, OpMax());
+    QP_MARK(PH_RESID);
     if (mx[12] > 0.f) return NAN;
     float comp = mx[9];
     if (mode == 1) comp = fabsf(kappa - P.kappa_relax) / P.kappa_relax;
@@ -422,7 +451,7 @@ struct Solver {
   }
 
   // ---- implicit right-hand sides, two columns (r_kappa = 0 and d/dr_kappa) ----
-  __device__ void implicit_rhs() {
+  __device__ __noinline__ void implicit_rhs() {
     const FLayout& L = st->L;
     QP_ARR(bz); QP_ARR(bs); QP_ARR(ri); QP_ARR(rz); QP_ARR(rs); QP_ARR(re); QP_ARR(ta);
     QP_ARR(tb); QP_ARR(ua); QP_ARR(ub); QP_ARR(R); QP_ARR(G); QP_ARR(rt); QP_ARR(col);
@@ -450,6 +479,7 @@ struct Solver {
     const float* vv[2] = {ta, tb};
     float* oo[2] = {R, R + L.ldx};
     col_dot<NT, 2>(G, L.ldg, m, L.n, vv, oo, col, rt, -1.0f);
+    QP_MARK(PH_RHS);
   }
 
   // ds, dz, dv of the implicit direction for r_kappa = rk on row r
@@ -471,7 +501,7 @@ struct Solver {
     dsr = -rs[r] - (bs[r] * c) * dvr - c * rk;
   }
 
-  __device__ float implicit_alpha(float rk, bool store) {
+  __device__ __noinline__ float implicit_alpha(float rk, bool store) {
     QP_ARR(s); QP_ARR(z); QP_ARR(tb); QP_ARR(red);
     float amin[1] = {1.0f};
     for (int r = threadIdx.x; r < st->L.m; r += NT) {
@@ -485,7 +515,7 @@ struct Solver {
     return amin[0];
   }
 
-  __device__ float implicit_mu_aff(float rk, float alpha) {
+  __device__ __noinline__ float implicit_mu_aff(float rk, float alpha) {
     QP_ARR(s); QP_ARR(z); QP_ARR(red);
     float acc[1] = {0.f};
     for (int r = threadIdx.x; r < st->L.m; r += NT) {
@@ -497,7 +527,7 @@ struct Solver {
     return acc[0] / (float)st->L.m;
   }
 
-  __device__ void implicit_update(float alpha, float rk, float kappa) {
+  __device__ __noinline__ void implicit_update(float alpha, float rk, float kappa) {
     const FLayout& L = st->L;
     QP_ARR(x); QP_ARR(y); QP_ARR(z); QP_ARR(s); QP_ARR(R); QP_ARR(ua); QP_ARR(ub); QP_ARR(tb);
     const int p = L.p, t = threadIdx.x, a = st->a;
@@ -516,7 +546,7 @@ struct Solver {
 
   // One implicit Newton step (Alg. 1 with predictor-corrector, or Alg. 2 when
   // kt_fixed >= 0).  Returns false on a factorisation failure.
-  __device__ bool implicit_step(const FwdParams& P, float kappa, float kt_fixed) {
+  __device__ __noinline__ bool implicit_step(const FwdParams& P, float kappa, float kt_fixed) {
     partition();
     implicit_rhs();
     if (!factor()) return false;
@@ -542,13 +572,14 @@ struct Solver {
     const float rk = kappa - kt;
     const float alpha = P.step_frac * implicit_alpha(rk, true);
     implicit_update(alpha, rk, kappa);
+    QP_MARK(PH_STEP);
     return true;
   }
 
   // ---- explicit complementarity (ablation): Mehrotra predictor-corrector on
   // eq. 8 in the same two-level form.  For r_c (z.*s, then the corrector term)
   // rhs1 = -r_t + G_I'(-W r_i + r_c/s), rhs2 = (-(r_i - r_c/z)_A, -r_e). ----
-  __device__ bool standard_step(const FwdParams& P, float mu) {
+  __device__ __noinline__ bool standard_step(const FwdParams& P, float mu) {
     const FLayout& L = st->L;
     const int m = L.m, p = L.p, t = threadIdx.x;
     partition();
@@ -629,7 +660,7 @@ struct Solver {
 
   // CVXOPT-style start: (Q + G'G) x + A'y = -q + G'h, A x = b; z = G x - h, s = -z, shifted.
   // With m = 0 this is the exact solution of the equality-constrained QP.
-  __device__ bool initialize() {
+  __device__ __noinline__ bool initialize() {
     const FLayout& L = st->L;
     const int m = L.m, p = L.p, t = threadIdx.x;
     QP_ARR(bz); QP_ARR(bs); QP_ARR(ua); QP_ARR(b); QP_ARR(h); QP_ARR(R); QP_ARR(G); QP_ARR(col);
@@ -670,7 +701,7 @@ struct Solver {
   }
 
   // ---- gradient cache: factors, W, active map and the point (Alg. 3 input) ----
-  __device__ void write_cache(const FwdParams& P, int bi) {
+  __device__ __noinline__ void write_cache(const FwdParams& P, int bi) {
     const FLayout& L = st->L;
     QP_ARR(K); QP_ARR(Y); QP_ARR(C); QP_ARR(ea); QP_ARR(D); QP_ARR(x); QP_ARR(y); QP_ARR(z);
     QP_IARR(pos);
@@ -710,7 +741,7 @@ struct Solver {
     __syncthreads();
   }
 
-  __device__ void write_solution(const FwdParams& P, int bi, bool good) {
+  __device__ __noinline__ void write_solution(const FwdParams& P, int bi, bool good) {
     const FLayout& L = st->L;
     QP_ARR(x); QP_ARR(y); QP_ARR(z); QP_ARR(s);
     const int n = L.n, m = L.m, p = L.p, t = threadIdx.x;
@@ -724,7 +755,7 @@ struct Solver {
   }
 
   // ---- whole instance ----
-  __device__ void run(const FwdParams& P, int bi) {
+  __device__ __noinline__ void run(const FwdParams& P, int bi) {
     const int n = st->L.n, m = st->L.m, p = st->L.p, t = threadIdx.x;
     const bool implicit = P.formulation == 0;
     int status = ST_SOLVED, iters = 0;
@@ -816,6 +847,7 @@ struct Solver {
       partition();
       if (!factor() && status == ST_SOLVED) status = ST_NUMERICAL;
       write_cache(P, bi);
+      QP_MARK(PH_CACHE);
     }
     if (t == 0) {
       if (P.status) P.status[bi] = status;
@@ -837,12 +869,29 @@ template <int NT>
 __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) qp_forward_kernel(const FwdParams P) {
   extern __shared__ __align__(16) float sm[];
   __shared__ SharedState st;
+  // the phases take the parameters by reference: keep them in shared memory
+  // rather than letting each thread copy the whole block to local memory
+  __shared__ FwdParams sP;
+  if (threadIdx.x == 0) sP = P;
   Solver<NT> slv;
-  slv.bind(sm, &st, P.n, P.m, P.p, P.amax, P.ldpb);
-  slv.run(P, blockIdx.x);
+  slv.bind(sm, &st, P.n, P.m, P.p, P.amax, P.ldpb);  // ends with a barrier
+  slv.run(sP, blockIdx.x);
 }
 
 }  // namespace fwd
+
+#ifdef QP_PHASE_TIMERS
+// Copy (and optionally clear) the phase cycle counters of this translation unit.
+inline cudaError_t read_phase_cycles(unsigned long long* host, int clear) {
+  cudaError_t e = cudaMemcpyFromSymbol(host, fwd::g_qp_phase_cycles,
+                                       sizeof(unsigned long long) * fwd::PH_COUNT);
+  if (e == cudaSuccess && clear) {
+    unsigned long long zero[fwd::PH_COUNT] = {};
+    e = cudaMemcpyToSymbol(fwd::g_qp_phase_cycles, zero, sizeof(zero));
+  }
+  return e;
+}
+#endif
 
 // Instantiated once per block size in qp_forward_<NT>.cu.
 template <int NT>
