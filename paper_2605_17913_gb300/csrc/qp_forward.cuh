@@ -125,7 +125,7 @@ struct SharedState {
 enum Phase { PH_LOAD, PH_RESID, PH_PART, PH_RHS, PH_SYRK, PH_BORDER, PH_CCHOL, PH_SOLVE, PH_GDX,
              PH_STEP, PH_CACHE, PH_COUNT };
 #ifdef QP_PHASE_TIMERS
-__device__ unsigned long long g_qp_phase_cycles[PH_COUNT];
+static __device__ unsigned long long g_qp_phase_cycles[PH_COUNT];  // one per translation unit
 #define QP_MARK(ph)                                                                    \
   do {                                                                                 \
     if (threadIdx.x == 0) {                                                            \
@@ -882,7 +882,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) qp_forward_kernel(co
 
 #ifdef QP_PHASE_TIMERS
 // Copy (and optionally clear) the phase cycle counters of this translation unit.
-inline cudaError_t read_phase_cycles(unsigned long long* host, int clear) {
+static inline cudaError_t read_phase_cycles(unsigned long long* host, int clear) {
   cudaError_t e = cudaMemcpyFromSymbol(host, fwd::g_qp_phase_cycles,
                                        sizeof(unsigned long long) * fwd::PH_COUNT);
   if (e == cudaSuccess && clear) {
