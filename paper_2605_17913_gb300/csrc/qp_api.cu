@@ -29,7 +29,17 @@ static bool dims_ok(const qp_dims* d) {
   return d && d->batch >= 0 && d->n >= 1 && d->n_eq >= 0 && d->n_eq <= d->n && d->n_ineq >= 0;
 }
 
+#ifdef QP_PHASE_TIMERS
+static unsigned long long* g_phase_counters = nullptr;
+#endif
+
 extern "C" {
+
+#ifdef QP_PHASE_TIMERS
+// Tracing build only: device array of phase-cycle counters the forward
+// kernel adds to (NULL turns the timers off).
+void qp_debug_set_phase_counters(unsigned long long* dev) { g_phase_counters = dev; }
+#endif
 
 void qp_settings_default(qp_settings* s) {
   if (!s) return;
@@ -158,6 +168,9 @@ int qp_solve_batch(qp_handle* h, const qp_settings* st, const float* Q, const fl
   P.refine_steps = st->refine_steps;
   P.cache = grad_cache;
   P.cache_stride = h->cache_stride;
+#ifdef QP_PHASE_TIMERS
+  P.timers = g_phase_counters;
+#endif
   // one CTA per instance: the block scheduler hands a new instance to an SM
   // as soon as one finishes, which balances uneven iteration counts
   cudaError_t e = launch_forward(P, h->fwd_threads, h->fwd_smem, B, (cudaStream_t)stream);

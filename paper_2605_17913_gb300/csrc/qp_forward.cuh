@@ -114,23 +114,23 @@ __host__ __device__ inline FLayout make_fwd_layout(int n, int m, int p, int amax
 // leave kStaticSmem bytes of the 227 KB per-CTA limit for it).
 struct SharedState {
   FLayout L;
-  long long t_mark;  // phase timers only
+  long long t_mark;                // phase timers only
+  unsigned long long* timers;      // phase timers only
   int a, nf;         // active rows, rows of F = a + p (set by partition())
   float qn, bn, hn;  // |q|, |b|, |h| (infinity norms)
 };
 
 // Phase timers (tracing facility, compiled only with -DQP_PHASE_TIMERS): thread
 // 0 of each CTA adds the cycles between consecutive marks, taken at barrier
-// boundaries, to g_qp_phase_cycles[phase]; qp_debug_phase_cycles() reads them.
+// boundaries, to the caller's counter array (qp_debug_set_phase_counters()).
 enum Phase { PH_LOAD, PH_RESID, PH_PART, PH_RHS, PH_SYRK, PH_BORDER, PH_CCHOL, PH_SOLVE, PH_GDX,
              PH_STEP, PH_CACHE, PH_COUNT };
 #ifdef QP_PHASE_TIMERS
-static __device__ unsigned long long g_qp_phase_cycles[PH_COUNT];  // one per translation unit
 #define QP_MARK(ph)                                                                    \
   do {                                                                                 \
-    if (threadIdx.x == 0) {                                                            \
+    if (threadIdx.x == 0 && st->timers) {                                              \
       const long long now_ = clock64();                                                \
-      atomicAdd(&g_qp_phase_cycles[ph], (unsigned long long)(now_ - st->t_mark));     \
+      atomicAdd(&st->timers[ph], (unsigned long long)(now_ - st->t_mark));             \
       st->t_mark = now_;                                                               \
     }                                                                                  \
   } while (0)
@@ -156,6 +156,7 @@ struct Solver {
       st->a = 0;
       st->nf = p;
       st->t_mark = clock64();
+      st->timers = nullptr;
     }
     __syncthreads();
     parity = 0;
@@ -875,23 +876,14 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) qp_forward_kernel(co
   if (threadIdx.x == 0) sP = P;
   Solver<NT> slv;
   slv.bind(sm, &st, P.n, P.m, P.p, P.amax, P.ldpb);  // ends with a barrier
+#ifdef QP_PHASE_TIMERS
+  if (threadIdx.x == 0) st.timers = P.timers;
+  __syncthreads();
+#endif
   slv.run(sP, blockIdx.x);
 }
 
 }  // namespace fwd
-
-#ifdef QP_PHASE_TIMERS
-// Copy (and optionally clear) the phase cycle counters of this translation unit.
-static inline cudaError_t read_phase_cycles(unsigned long long* host, int clear) {
-  cudaError_t e = cudaMemcpyFromSymbol(host, fwd::g_qp_phase_cycles,
-                                       sizeof(unsigned long long) * fwd::PH_COUNT);
-  if (e == cudaSuccess && clear) {
-    unsigned long long zero[fwd::PH_COUNT] = {};
-    e = cudaMemcpyToSymbol(fwd::g_qp_phase_cycles, zero, sizeof(zero));
-  }
-  return e;
-}
-#endif
 
 // Instantiated once per block size in qp_forward_<NT>.cu.
 template <int NT>

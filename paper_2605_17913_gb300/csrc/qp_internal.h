@@ -22,6 +22,9 @@ struct FwdParams {
   // gradient cache (nullptr: no relax, no cache)
   float* cache;
   long long cache_stride;
+#ifdef QP_PHASE_TIMERS
+  unsigned long long* timers;  // device counters of the phase timers (tracing build)
+#endif
 };
 
 struct BwdParams {
