@@ -19,7 +19,6 @@ struct qp_handle {
   int bwd_threads;
   size_t bwd_smem;
   int amax;
-  int ldpb;
   long long cache_stride;  // floats per instance in the gradient cache
 };
 
@@ -89,7 +88,7 @@ int qp_handle_create(const qp_dims* dims, qp_handle** out) {
   if (!h) return QP_ENOMEM;
   h->dims = *dims;
   const int n = dims->n, m = dims->n_ineq, p = dims->n_eq;
-  h->fwd_smem = forward_config(n, m, p, &h->fwd_threads, &h->amax, &h->ldpb);
+  h->fwd_smem = forward_config(n, m, p, &h->fwd_threads, &h->amax);
   h->bwd_smem = backward_smem_bytes(n, m, p, h->amax, &h->bwd_threads);
   h->cache_stride = cache_layout(n, m, p, h->amax).stride;
   if (h->fwd_smem == 0 || h->bwd_smem == 0) {
@@ -149,7 +148,7 @@ int qp_solve_batch(qp_handle* h, const qp_settings* st, const float* Q, const fl
     return QP_EINVAL;
   FwdParams P;
   memset(&P, 0, sizeof(P));
-  P.batch = B; P.n = n; P.m = m; P.p = p; P.amax = h->amax; P.ldpb = h->ldpb;
+  P.batch = B; P.n = n; P.m = m; P.p = p; P.amax = h->amax;
   P.Q = Q; P.q = q; P.A = A; P.b = b; P.G = G; P.h = hv;
   P.x = x; P.y = y; P.z = z; P.s = s;
   P.status = status; P.iters = iters; P.kkt = kkt_res;

@@ -266,98 +266,120 @@ __device__ bool cholesky(float* K, int ldk, int n, float* dinv) {
 // ---------------------------------------------------------------------------
 // Blocked (panel width 8) right-looking Cholesky of a bordered system.
 //
-// Phase 1 eliminates the n leading pivots of  [ K  F' ; F  C0 ]  as in
-// cholesky_bordered, but a panel of 8 columns at a time:
-//   (1) one warp factors the 8x8 diagonal block of K;
-//   (2) every row below it -- K rows and F rows alike -- is solved against
-//       the block (one thread per row, 8-term forward substitution) and its
-//       8 panel values are copied to Pb (stride kPbLd, conflict-free float4);
-//   (3) the trailing part of the combined lower triangle is updated by one
-//       register-tiled (4x4) product of the panel with itself: K rows
-//       subtract, F rows subtract, and the C block accumulates Y Y'.
-// Phase 2 factors C the same way (then only C rows exist).
-// Outputs: K lower = L, Y = F L^-T, C lower = L_C (C = D + Y Y' + shift is
-// applied by the caller between the phases), dinv / cdinv = 1 / diag.
-// Pb needs (n + nf + 4) * ldpb floats.  Ends with a barrier.
+// Eliminates the n leading pivots of  [ K  F' ; F  C0 ]  a panel of 8 columns
+// at a time:
+//   (1) every thread that owns a row below the diagonal block -- K rows and
+//       border (F) rows alike -- factors the 8x8 diagonal block itself, in
+//       registers (rsqrtf pivots), and solves its row against it; threads
+//       0..7 write the block's factor back (no serial one-warp phase);
+//   (2) the panel rows, copied to Pb, update the trailing part of the
+//       combined lower triangle with one register-tiled (4x4) product: K rows
+//       subtract, F rows subtract, and the C block (if any) accumulates Y Y'.
+// Outputs: K lower = L, Y = F L^-T, C (+)= Y Y', dinv = 1 / diag(L).
+// Border rows may include right-hand sides: their rows become L^-1 r (as
+// rows), and their C entries Y L^-1 r -- forward substitution for free.
+// Pb holds panel rows in groups of 4 (8 values each) padded to 36 floats, so
+// a warp's float4 loads of 4-row groups hit distinct banks; it needs
+// pb_floats(n + nB) floats.  Two barriers per panel.
 // ---------------------------------------------------------------------------
-// Panel rows are stored with stride ldpb = 12 floats (8 values + 4 pad: 8
-// consecutive rows then hit distinct banks) or 8 when shared memory is tight.
+__host__ __device__ inline int pb_floats(int rows) { return ((rows + 3) / 4 + 1) * 36; }
+__device__ __forceinline__ int pb_off(int r) { return (r >> 2) * 36 + (r & 3) * 8; }
 
 template <int NT>
-__device__ bool block_diag_factor(float* M, int ld, int j0, int jb, float* dinv) {
-  // one warp: unblocked Cholesky of the jb x jb block at (j0, j0)
+__device__ bool panel_factor_trsm(float* M, int ld, int j0, int jb, float* dinv, float* A,
+                                  int lda, int rowA0, int nA, float* B, int ldb, int nB,
+                                  float* Pb) {
+  const int N = nA + nB;
   bool ok = true;
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    for (int jj = 0; jj < jb; ++jj) {
-      const float d = M[(j0 + jj) * ld + j0 + jj];
+  const int tid = threadIdx.x;
+  float lmine[8];  // this thread's row of the block factor (threads 0..jb-1)
+  float imine = 0.f;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) lmine[j] = 0.f;
+  for (int rr = tid; rr < (N > 8 ? N : 8); rr += NT) {
+    // the diagonal block, padded to 8x8 with the identity
+    float l[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j <= i; ++j)
+        l[i][j] = (i < jb && j < jb) ? M[(j0 + i) * ld + j0 + j] : (i == j ? 1.0f : 0.0f);
+    float inv[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float d = l[j][j];
       if (!(d > 0.0f) || !(d < INFINITY)) ok = false;
-      const float sd = sqrtf(d);
-      const float inv = 1.0f / sd;
-      __syncwarp();
-      if (lane > jj && lane < jb) M[(j0 + lane) * ld + j0 + jj] *= inv;
-      if (lane == jj) {
-        M[(j0 + jj) * ld + j0 + jj] = sd;
-        dinv[j0 + jj] = inv;
-      }
-      __syncwarp();
-      if (lane > jj && lane < jb) {
-        const float lr = M[(j0 + lane) * ld + j0 + jj];
-        for (int c = jj + 1; c <= lane; ++c)
-          M[(j0 + lane) * ld + j0 + c] = fmaf(-lr, M[(j0 + c) * ld + j0 + jj], M[(j0 + lane) * ld + j0 + c]);
-      }
-      __syncwarp();
+      inv[j] = rsqrtf(d);
+      l[j][j] = d * inv[j];
+#pragma unroll
+      for (int i = j + 1; i < 8; ++i) l[i][j] *= inv[j];
+#pragma unroll
+      for (int i = j + 1; i < 8; ++i)
+#pragma unroll
+        for (int k = j + 1; k <= i; ++k) l[i][k] = fmaf(-l[i][j], l[k][j], l[i][k]);
     }
-  }
-  return __syncthreads_and(ok ? 1 : 0) != 0;
-}
-
-// Solve the panel rows against the factored diagonal block and copy them to Pb.
-// Row rr < nA is row (rowA0 + rr) of A (stride lda), else row rr - nA of B (stride ldb);
-// columns j0 .. j0+jb-1.
-template <int NT>
-__device__ void panel_trsm(const float* Ldiag, int ldl, int j0, int jb, const float* dinv,
-                           float* A, int lda, int rowA0, int nA, float* B, int ldb, int nB,
-                           float* Pb, int ldpb) {
-  for (int rr = threadIdx.x; rr < nA + nB; rr += NT) {
-    float* row = rr < nA ? A + (rowA0 + rr) * lda + j0 : B + (rr - nA) * ldb + j0;
-    float v[8];
+    if (rr < N) {
+      float* row = rr < nA ? A + (rowA0 + rr) * lda + j0 : B + (rr - nA) * ldb + j0;
+      float v[8];
 #pragma unroll
-    for (int t = 0; t < 8; ++t) v[t] = t < jb ? row[t] : 0.0f;
+      for (int t = 0; t < 8; ++t) v[t] = t < jb ? row[t] : 0.0f;
 #pragma unroll
-    for (int t = 0; t < 8; ++t) {
-      if (t < jb) {
+      for (int t = 0; t < 8; ++t) {
         float acc = v[t];
 #pragma unroll
-        for (int u = 0; u < t; ++u) acc = fmaf(-v[u], Ldiag[(j0 + t) * ldl + j0 + u], acc);
-        v[t] = acc * dinv[j0 + t];
+        for (int u = 0; u < t; ++u) acc = fmaf(-v[u], l[t][u], acc);
+        v[t] = acc * inv[t];
       }
-    }
+      float* pr = Pb + pb_off(rr);
+      reinterpret_cast<float4*>(pr)[0] = make_float4(v[0], v[1], v[2], v[3]);
+      reinterpret_cast<float4*>(pr)[1] = make_float4(v[4], v[5], v[6], v[7]);
 #pragma unroll
-    for (int t = 0; t < 8; ++t) {
-      if (t < jb) row[t] = v[t];
-      Pb[rr * ldpb + t] = v[t];
+      for (int t = 0; t < 8; ++t)
+        if (t < jb) row[t] = v[t];
+    }
+    if (rr == tid) {
+      // keep row `tid` of the block factor (selected without dynamic indexing)
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (i == tid) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) lmine[j] = l[i][j];
+          imine = inv[i];
+        }
     }
   }
-  // zero the pad rows of the last tile row
-  const int N = nA + nB;
-  for (int e = threadIdx.x; e < 4 * ldpb; e += NT) Pb[N * ldpb + e] = 0.0f;
-  __syncthreads();
+  // zero the pad rows of the last 4-row group
+  if (tid < 8 * 4) {
+    const int r = N + (tid >> 3);
+    if ((r >> 2) == (N >> 2) && (N & 3)) Pb[pb_off(r) + (tid & 7)] = 0.0f;
+  }
+  const bool all_ok = __syncthreads_and(ok ? 1 : 0) != 0;
+  // every thread has read the block: threads 0..jb-1 now store its factor
+  // (nothing reads it before the next barrier)
+  if (tid < jb) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (j <= tid) M[(j0 + tid) * ld + j0 + j] = lmine[j];
+    dinv[j0 + tid] = imine;
+  }
+  return all_ok;
 }
 
 // Trailing update with the panel in Pb over the combined row set
 // [A rows rowA0 .. rowA0+nA-1 ; B rows 0 .. nB-1] (lower triangle):
-//   (A, A): A[rowA0+r][colA0+c] -= P_r . P_c     (colA0 = rowA0 for the square part)
-//   (B, A): B[k][colA0+c]        -= P_k . P_c
+//   (A, A): A[rowA0+r][rowA0+c] -= P_r . P_c
+//   (B, A): B[k][rowA0+c]        -= P_k . P_c
 //   (B, B): C[k][l]              += P_k . P_l     (when C != nullptr)
 template <int NT>
-__device__ void panel_syrk(const float* Pb, int ldpb, float* A, int lda, int rowA0, int nA,
-                           float* B, int ldb, int nB, float* C, int ldc, float csign) {
+__device__ void panel_syrk(const float* Pb, float* A, int lda, int rowA0, int nA, float* B,
+                           int ldb, int nB, float* C, int ldc) {
   const int N = nA + nB;
   const int nt = (N + 3) >> 2;
   const int T = nt * (nt + 1) / 2;
   for (int t = threadIdx.x; t < T; t += NT) {
-    int I = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    // tile index -> (I, J), J <= I (square root estimate, then exact correction)
+    const float x8 = 8.0f * (float)t + 1.0f;
+    int I = (int)((x8 * rsqrtf(x8) - 1.0f) * 0.5f);
     while ((I + 1) * (I + 2) / 2 <= t) ++I;
     while (I * (I + 1) / 2 > t) --I;
     const int J = t - I * (I + 1) / 2;
@@ -370,9 +392,11 @@ __device__ void panel_syrk(const float* Pb, int ldpb, float* A, int lda, int row
     for (int h2 = 0; h2 < 2; ++h2) {
       float4 ra[4], cb[4];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) ra[a] = *reinterpret_cast<const float4*>(Pb + (4 * I + a) * ldpb + 4 * h2);
+      for (int a = 0; a < 4; ++a)
+        ra[a] = reinterpret_cast<const float4*>(Pb + I * 36 + a * 8)[h2];
 #pragma unroll
-      for (int b = 0; b < 4; ++b) cb[b] = *reinterpret_cast<const float4*>(Pb + (4 * J + b) * ldpb + 4 * h2);
+      for (int b = 0; b < 4; ++b)
+        cb[b] = reinterpret_cast<const float4*>(Pb + J * 36 + b * 8)[h2];
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -396,7 +420,7 @@ __device__ void panel_syrk(const float* Pb, int ldpb, float* A, int lda, int row
         } else if (c < nA) {
           B[(r - nA) * ldb + rowA0 + c] -= acc[a][b];
         } else if (C != nullptr) {
-          C[(r - nA) * ldc + (c - nA)] += csign * acc[a][b];
+          C[(r - nA) * ldc + (c - nA)] += acc[a][b];
         }
       }
     }
@@ -404,35 +428,21 @@ __device__ void panel_syrk(const float* Pb, int ldpb, float* A, int lda, int row
   __syncthreads();
 }
 
-// Phase 1: K (n x n, ldk odd) bordered by Y (nf rows, stride ldy) with C
-// accumulating Y Y'.  Phase 2 is blocked_cholesky on C alone.
+// Eliminate the n pivots of K (n x n lower, stride ldk) bordered by nB rows
+// in Y (stride ldy); C (nB x nB lower, stride ldc, may be null) accumulates
+// Y Y'.  With C == nullptr this is a plain blocked Cholesky of K (nB = 0) or
+// a Cholesky plus triangular solve of the border rows.
 template <int NT>
-__device__ bool blocked_cholesky_bordered(float* K, int ldk, int n, float* Y, int ldy, int nf,
-                                          float* C, int ldc, float* dinv, float* Pb, int ldpb) {
+__device__ bool blocked_cholesky_bordered(float* K, int ldk, int n, float* Y, int ldy, int nB,
+                                          float* C, int ldc, float* dinv, float* Pb) {
   bool ok = true;
   for (int j0 = 0; j0 < n; j0 += 8) {
     const int jb = min(8, n - j0);
-    ok = block_diag_factor<NT>(K, ldk, j0, jb, dinv) && ok;
     const int nK = n - j0 - jb;
-    panel_trsm<NT>(K, ldk, j0, jb, dinv, K, ldk, j0 + jb, nK, Y, ldy, nf, Pb, ldpb);
-    if (nK + nf > 0) panel_syrk<NT>(Pb, ldpb, K, ldk, j0 + jb, nK, Y, ldy, nf, C, ldc, 1.0f);
+    ok = panel_factor_trsm<NT>(K, ldk, j0, jb, dinv, K, ldk, j0 + jb, nK, Y, ldy, nB, Pb) && ok;
+    if (nK + nB > 0) panel_syrk<NT>(Pb, K, ldk, j0 + jb, nK, Y, ldy, nB, C, ldc);
   }
-  return ok;
-}
-
-// In-place blocked Cholesky of the lower triangle of M (n x n, stride ld).
-template <int NT>
-__device__ bool blocked_cholesky(float* M, int ld, int n, float* dinv, float* Pb, int ldpb) {
-  bool ok = true;
-  for (int j0 = 0; j0 < n; j0 += 8) {
-    const int jb = min(8, n - j0);
-    ok = block_diag_factor<NT>(M, ld, j0, jb, dinv) && ok;
-    const int nR = n - j0 - jb;
-    if (nR > 0) {
-      panel_trsm<NT>(M, ld, j0, jb, dinv, M, ld, j0 + jb, nR, nullptr, 0, 0, Pb, ldpb);
-      panel_syrk<NT>(Pb, ldpb, M, ld, j0 + jb, nR, nullptr, 0, 0, nullptr, 0, 0.0f);
-    }
-  }
+  __syncthreads();  // the last diagonal block is written after the panel's barrier
   return ok;
 }
 

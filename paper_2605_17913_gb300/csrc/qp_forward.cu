@@ -10,28 +10,25 @@ int forward_blocks_per_sm_nt(size_t smem);
 
 // Threads per CTA by n; amax = rows kept as multipliers, at most min(m, n)
 // (at a non-degenerate solution at most n - p rows are active), lowered to
-// fit shared memory but never below min(m, n - p); amax + p <= 128 (warp
-// solves hold at most 128 rows).  The panel stride drops from 12 to 8 floats
-// before amax is lowered.
-size_t forward_config(int n, int m, int p, int* nthreads, int* amax_out, int* ldpb_out) {
+// fit shared memory but not more than 4 below min(m, n - p); amax + p <= 126
+// (warp solves hold at most 128 rows, two of them folded right-hand sides).
+// Rows beyond amax with W > 1 go to K_I with the smallest W first (tau grows).
+size_t forward_config(int n, int m, int p, int* nthreads, int* amax_out) {
   const int nt = n <= 24 ? 128 : (n <= 72 ? 256 : 512);
   if (nthreads) *nthreads = nt;
   if (amax_out) *amax_out = 0;
-  if (ldpb_out) *ldpb_out = 12;
   if (n < 1 || n > 128 || p > 128 || p > n || m < 0) return 0;
   int amax0 = m < n ? m : n;
-  if (amax0 + p > 128) amax0 = 128 - p;
-  const int floor_a = m < n - p ? m : n - p;
+  if (amax0 + p > 126) amax0 = 126 - p;
+  int floor_a = (m < n - p ? m : n - p) - 4;
+  if (floor_a < 0) floor_a = 0;
   const size_t budget = 227 * 1024 - fwd::kStaticSmem;
   for (int amax = amax0; amax >= floor_a && amax >= 0; --amax) {
-    for (int ldpb = 12; ldpb >= 8; ldpb -= 4) {
-      const fwd::FLayout L = fwd::make_fwd_layout(n, m, p, amax, nt, ldpb);
-      const size_t bytes = (size_t)L.total * sizeof(float);
-      if (bytes <= budget) {
-        if (amax_out) *amax_out = amax;
-        if (ldpb_out) *ldpb_out = ldpb;
-        return bytes;
-      }
+    const fwd::FLayout L = fwd::make_fwd_layout(n, m, p, amax, nt);
+    const size_t bytes = (size_t)L.total * sizeof(float);
+    if (bytes <= budget) {
+      if (amax_out) *amax_out = amax;
+      return bytes;
     }
   }
   return 0;

@@ -56,26 +56,27 @@ constexpr int kStaticSmem = 1024;  // upper bound of the kernel's static shared 
 
 struct FLayout {
   int n, m, p, amax, fmax;
-  int ldk, ldg, ldx, ldc, ldpb, nv, mv, pv, fv;
+  int ldk, ldg, ldx, ldc, nv, mv, pv, fv;
   int o_K, o_qd, o_G, o_A, o_Y, o_C, o_R, o_col, o_red, o_Pb;
   int o_q, o_x, o_rt, o_dinv, o_tn;
   int o_b, o_y, o_re;
   int o_cdinv, o_D, o_ua, o_ub, o_act;
-  int o_h, o_z, o_s, o_ri, o_rz, o_rs, o_bz, o_bs, o_ea, o_eb, o_ta, o_tb, o_pos;
+  int o_h, o_z, o_s, o_ri, o_bz, o_bs, o_ea, o_eb, o_ta, o_tb, o_pos;
   int total;
 };
 
 // The panel buffer Pb of the blocked factorisation is only live inside
 // factor_once(), so it shares one region with col, ta, tb, eb and tn, which
 // are dead there.
-__host__ __device__ inline FLayout make_fwd_layout(int n, int m, int p, int amax, int nthreads,
-                                                   int ldpb) {
+// Y and C carry two extra rows: the right-hand sides folded into the
+// factorisation of an implicit step.
+__host__ __device__ inline FLayout make_fwd_layout(int n, int m, int p, int amax, int nthreads) {
   FLayout L;
-  L.n = n; L.m = m; L.p = p; L.amax = amax; L.fmax = amax + p; L.ldpb = ldpb;
+  L.n = n; L.m = m; L.p = p; L.amax = amax; L.fmax = amax + p;
   L.ldk = ld_odd(n);
   L.ldg = ld_vec(n);
   L.ldx = round4(n);
-  L.ldc = ld_odd(L.fmax > 0 ? L.fmax : 1);
+  L.ldc = ld_odd(L.fmax + 2);
   L.nv = round4(n); L.mv = round4(m > 0 ? m : 1); L.pv = round4(p > 0 ? p : 1);
   L.fv = round4(L.fmax > 0 ? L.fmax : 1);
   int o = 0;
@@ -84,14 +85,14 @@ __host__ __device__ inline FLayout make_fwd_layout(int n, int m, int p, int amax
   L.o_qd = take(L.nv);
   L.o_G = take(m * L.ldg);
   L.o_A = take(p * L.ldg);
-  L.o_Y = take(L.fmax * L.ldk);
-  L.o_C = take(L.fmax * L.ldc);
+  L.o_Y = take((L.fmax + 2) * L.ldk);
+  L.o_C = take((L.fmax + 2) * L.ldc);
   L.o_R = take(2 * L.ldx);
   L.o_red = take(2 * (nthreads / 32) * kRedK);
   {
     // union: Pb | (col, ta, tb, eb, tn)
     const int base = o;
-    const int pb = round4((n + L.fmax + 4) * ldpb);
+    const int pb = round4(pb_floats(n + L.fmax + 2));
     L.o_Pb = base;
     L.o_col = take(2 * nthreads);
     L.o_ta = take(L.mv); L.o_tb = take(L.mv); L.o_eb = take(L.mv);
@@ -103,7 +104,7 @@ __host__ __device__ inline FLayout make_fwd_layout(int n, int m, int p, int amax
   L.o_cdinv = take(L.fv); L.o_D = take(L.fv); L.o_ua = take(L.fv); L.o_ub = take(L.fv);
   L.o_act = take(L.fv);
   L.o_h = take(L.mv); L.o_z = take(L.mv); L.o_s = take(L.mv); L.o_ri = take(L.mv);
-  L.o_rz = take(L.mv); L.o_rs = take(L.mv); L.o_bz = take(L.mv); L.o_bs = take(L.mv);
+  L.o_bz = take(L.mv); L.o_bs = take(L.mv);
   L.o_ea = take(L.mv);
   L.o_pos = take(L.mv);
   L.total = o;
@@ -148,11 +149,11 @@ struct Solver {
   SharedState* st;
   int parity;
 
-  __device__ void bind(float* sm_, SharedState* st_, int n, int m, int p, int amax, int ldpb) {
+  __device__ void bind(float* sm_, SharedState* st_, int n, int m, int p, int amax) {
     sm = sm_;
     st = st_;
     if (threadIdx.x == 0) {
-      st->L = make_fwd_layout(n, m, p, amax, NT, ldpb);
+      st->L = make_fwd_layout(n, m, p, amax, NT);
       st->a = 0;
       st->nf = p;
       st->t_mark = clock64();
@@ -262,17 +263,36 @@ struct Solver {
     QP_MARK(PH_PART);
   }
 
+  // ---- fold the two right-hand sides of an implicit step into the border:
+  // Y rows nf, nf+1 <- r1 (columns A, B) and C rows nf, nf+1 <- -rhs2, so that
+  // the factorisation leaves u = L^-1 r1 in Y and w = L_C^-1 (Y u - rhs2) in C.
+  __device__ void fold_rhs() {
+    const FLayout& L = st->L;
+    QP_ARR(R); QP_ARR(Y); QP_ARR(C); QP_ARR(ua); QP_ARR(ub);
+    const int n = L.n, nf = st->nf, t = threadIdx.x;
+    for (int e = t; e < 2 * n; e += NT) {
+      const int c = e / n, i = e - c * n;
+      Y[(nf + c) * L.ldk + i] = R[c * L.ldx + i];
+    }
+    for (int e = t; e < 2 * (nf + 2); e += NT) {
+      const int c = e / (nf + 2), k = e - c * (nf + 2);
+      C[(nf + c) * L.ldc + k] = k < nf ? -(c == 0 ? ua : ub)[k] : 0.f;
+    }
+    __syncthreads();
+  }
+
   // ---- factor K_I and the bordered block.  F, D and C = D must have just
-  // been set by partition(): the elimination overwrites them. ----
-  __device__ __noinline__ bool factor_once(float creg) {
+  // been set by partition() (and the right-hand sides by fold_rhs() when
+  // nfold = 2): the elimination overwrites them. ----
+  __device__ __noinline__ bool factor_once(float creg, int nfold) {
     const FLayout& L = st->L;
     QP_ARR(K); QP_ARR(qd); QP_ARR(G); QP_ARR(ea); QP_ARR(Y); QP_ARR(C); QP_ARR(dinv);
     QP_ARR(cdinv); QP_ARR(Pb); QP_ARR(red);
     const int nf = st->nf;
     syrk_gwg<NT>(K, L.ldk, qd, G, L.ldg, ea, L.m, L.n);
     QP_MARK(PH_SYRK);
-    bool ok = blocked_cholesky_bordered<NT>(K, L.ldk, L.n, Y, L.ldk, nf, C, L.ldc, dinv, Pb,
-                                            L.ldpb);
+    bool ok = blocked_cholesky_bordered<NT>(K, L.ldk, L.n, Y, L.ldk, nf + nfold, C, L.ldc, dinv,
+                                            Pb);
     QP_MARK(PH_BORDER);
     if (nf > 0) {
       float dm[1] = {1.0f};
@@ -281,7 +301,8 @@ struct Solver {
       const float shift = creg * dm[0];
       for (int k = threadIdx.x; k < nf; k += NT) C[k * L.ldc + k] += shift;
       __syncthreads();
-      ok = blocked_cholesky<NT>(C, L.ldc, nf, cdinv, Pb, L.ldpb) && ok;
+      ok = blocked_cholesky_bordered<NT>(C, L.ldc, nf, C + nf * L.ldc, L.ldc, nfold, nullptr, 0,
+                                         cdinv, Pb) && ok;
       QP_MARK(PH_CCHOL);
     }
     return ok;
@@ -289,17 +310,52 @@ struct Solver {
 
   // factor; if FP32 Cholesky of C meets a non-positive pivot (rank-deficient
   // F), redo the partition and factorisation with a 100x, then 10^4x larger shift.
-  __device__ __noinline__ bool factor() {
+  __device__ bool factor(int nfold = 0) {
     float creg = kCReg;
     for (int attempt = 0; attempt < 3; ++attempt, creg *= 100.0f) {
-      if (attempt > 0) partition();
-      if (factor_once(creg)) return true;
+      if (attempt > 0) {
+        partition();
+        if (nfold) fold_rhs();
+      }
+      if (factor_once(creg, nfold)) return true;
     }
     return false;
   }
 
+  // ---- finish a folded solve: mu = L_C^-T w, dx = L^-T (u - Y' mu) for both
+  // columns; dx returned in R rows 0, 1 and mu in ua / ub ----
+  __device__ void solve_folded() {
+    const FLayout& L = st->L;
+    QP_ARR(K); QP_ARR(dinv); QP_ARR(R); QP_ARR(Y); QP_ARR(C); QP_ARR(cdinv); QP_ARR(ua);
+    QP_ARR(ub);
+    const int n = L.n, t = threadIdx.x, w = t >> 5, nf = st->nf;
+    if (nf > 0) {
+      if (w < 2) {
+        float* u = w == 0 ? ua : ub;
+        const float* wrow = C + (nf + w) * L.ldc;
+        for (int k = t & 31; k < nf; k += 32) u[k] = wrow[k];
+        __syncwarp();
+        if (nf <= 32) c_solve<1>(u, nf, true);
+        else if (nf <= 64) c_solve<2>(u, nf, true);
+        else if (nf <= 96) c_solve<3>(u, nf, true);
+        else c_solve<4>(u, nf, true);
+      }
+      __syncthreads();
+    }
+    for (int e = t; e < 2 * n; e += NT) {
+      const int c = e / n, i = e - c * n;
+      const float* u = c == 0 ? ua : ub;
+      float acc = Y[(nf + c) * L.ldk + i];
+      for (int k = 0; k < nf; ++k) acc = fmaf(-Y[k * L.ldk + i], u[k], acc);
+      R[c * L.ldx + i] = acc;
+    }
+    __syncthreads();
+    solve_rows<NT, true>(K, L.ldk, dinv, n, R, L.ldx, 0, 2);
+    QP_MARK(PH_SOLVE);
+  }
+
   template <int SP>
-  __device__ void c_solve(float* v, int nf) {
+  __device__ void c_solve(float* v, int nf, bool upper_only = false) {
     const FLayout& L = st->L;
     QP_ARR(C); QP_ARR(cdinv);
     const int lane = threadIdx.x & 31;
@@ -309,7 +365,7 @@ struct Solver {
       const int i = lane + 32 * s2;
       r[0][s2] = i < nf ? v[i] : 0.f;
     }
-    warp_lower_solve<SP, 1>(C, L.ldc, cdinv, nf, r);
+    if (!upper_only) warp_lower_solve<SP, 1>(C, L.ldc, cdinv, nf, r);
     warp_upper_solve<SP, 1>(C, L.ldc, cdinv, nf, r);
 #pragma unroll
     for (int s2 = 0; s2 < SP; ++s2) {
@@ -382,7 +438,7 @@ struct Solver {
     const FLayout& L = st->L;
     const int n = L.n, m = L.m, p = L.p, t = threadIdx.x;
     QP_ARR(K); QP_ARR(qd); QP_ARR(G); QP_ARR(A); QP_ARR(q); QP_ARR(b); QP_ARR(h); QP_ARR(x);
-    QP_ARR(y); QP_ARR(z); QP_ARR(s); QP_ARR(rt); QP_ARR(re); QP_ARR(ri); QP_ARR(rz); QP_ARR(rs);
+    QP_ARR(y); QP_ARR(z); QP_ARR(s); QP_ARR(rt); QP_ARR(re); QP_ARR(ri);
     QP_ARR(bz); QP_ARR(bs); QP_ARR(tn); QP_ARR(red); QP_ARR(col);
     float ks[1] = {0.f};
     for (int r = t; r < m; r += NT) ks[0] = fmaf(z[r], s[r], ks[0]);
@@ -424,7 +480,7 @@ struct Solver {
           float pz, ps;
           retract_pair(z[r] - s[r], kappa, pz, ps);
           const float rzz = z[r] - pz, rss = s[r] - ps;
-          rz[r] = rzz; rs[r] = rss; bz[r] = pz; bs[r] = ps;
+          bz[r] = pz; bs[r] = ps;  // r_z = z - bz and r_s = s - bs are formed where used
           mx[10] = fmaxf(mx[10], fmaxf(fabsf(rzz), fabsf(rss)));
         } else {
           bz[r] = z[r]; bs[r] = s[r];
@@ -454,22 +510,23 @@ struct Solver {
   // ---- implicit right-hand sides, two columns (r_kappa = 0 and d/dr_kappa) ----
   __device__ __noinline__ void implicit_rhs() {
     const FLayout& L = st->L;
-    QP_ARR(bz); QP_ARR(bs); QP_ARR(ri); QP_ARR(rz); QP_ARR(rs); QP_ARR(re); QP_ARR(ta);
+    QP_ARR(bz); QP_ARR(bs); QP_ARR(z); QP_ARR(s); QP_ARR(ri); QP_ARR(re); QP_ARR(ta);
     QP_ARR(tb); QP_ARR(ua); QP_ARR(ub); QP_ARR(R); QP_ARR(G); QP_ARR(rt); QP_ARR(col);
     QP_IARR(pos); QP_IARR(act);
     const int m = L.m, t = threadIdx.x, a = st->a, nf = st->nf;
     for (int r = t; r < m; r += NT) {
       const float rho = bz[r] + bs[r];
       const bool inact = pos[r] < 0;
-      const float dri = ri[r] - rs[r];
-      ta[r] = ri[r] + rz[r] - rs[r] - (inact ? dri * rho / bs[r] : 0.f);
+      const float rzr = z[r] - bz[r], rsr = s[r] - bs[r];
+      const float dri = ri[r] - rsr;
+      ta[r] = ri[r] + rzr - rsr - (inact ? dri * rho / bs[r] : 0.f);
       tb[r] = inact ? 1.0f / bs[r] : 0.f;
     }
     for (int k = t; k < nf; k += NT) {
       if (k < a) {
         const int r = act[k];
         const float rho = bz[r] + bs[r];
-        ua[k] = -(ri[r] - rs[r]) * rho / bz[r];
+        ua[k] = -(ri[r] - (s[r] - bs[r])) * rho / bz[r];
         ub[k] = 1.0f / bz[r];
       } else {
         ua[k] = -re[k - a];
@@ -486,20 +543,21 @@ struct Solver {
   // ds, dz, dv of the implicit direction for r_kappa = rk on row r
   __device__ __forceinline__ void implicit_dir(int r, float rk, float& dsr, float& dzr,
                                                float& dvr) const {
-    QP_ARR(bz); QP_ARR(bs); QP_ARR(ea); QP_ARR(eb); QP_ARR(ri); QP_ARR(rz); QP_ARR(rs);
+    QP_ARR(bz); QP_ARR(bs); QP_ARR(ea); QP_ARR(eb); QP_ARR(ri); QP_ARR(z); QP_ARR(s);
     QP_ARR(ua); QP_ARR(ub); QP_IARR(pos);
+    const float rzr = z[r] - bz[r], rsr = s[r] - bs[r];
     const float rho = bz[r] + bs[r];
     const float c = 1.0f / rho;
     const float e = fmaf(rk, eb[r], ea[r]);
     const int k = pos[r];
     if (k < 0) {
-      const float rho2 = ri[r] - rs[r] - c * rk;
+      const float rho2 = ri[r] - rsr - c * rk;
       dvr = (e + rho2) * rho / bs[r];
     } else {
       dvr = fmaf(rk, ub[k], ua[k]) + e;
     }
-    dzr = -rz[r] + (bz[r] * c) * dvr - c * rk;
-    dsr = -rs[r] - (bs[r] * c) * dvr - c * rk;
+    dzr = -rzr + (bz[r] * c) * dvr - c * rk;
+    dsr = -rsr - (bs[r] * c) * dvr - c * rk;
   }
 
   __device__ __noinline__ float implicit_alpha(float rk, bool store) {
@@ -550,8 +608,9 @@ struct Solver {
   __device__ __noinline__ bool implicit_step(const FwdParams& P, float kappa, float kt_fixed) {
     partition();
     implicit_rhs();
-    if (!factor()) return false;
-    solve(0, 2);
+    fold_rhs();
+    if (!factor(2)) return false;
+    solve_folded();
     g_times_dx(0, 2);
     float kt;
     if (kt_fixed >= 0.f) {
@@ -584,7 +643,7 @@ struct Solver {
     const FLayout& L = st->L;
     const int m = L.m, p = L.p, t = threadIdx.x;
     partition();
-    QP_ARR(z); QP_ARR(s); QP_ARR(ri); QP_ARR(re); QP_ARR(rz); QP_ARR(rs); QP_ARR(ta); QP_ARR(tb);
+    QP_ARR(z); QP_ARR(s); QP_ARR(ri); QP_ARR(re); QP_ARR(ta); QP_ARR(tb);
     QP_ARR(ua); QP_ARR(ub); QP_ARR(ea); QP_ARR(eb); QP_ARR(R); QP_ARR(G); QP_ARR(rt);
     QP_ARR(col); QP_ARR(red); QP_ARR(x); QP_ARR(y); QP_IARR(pos); QP_IARR(act);
     const int a = st->a, nf = st->nf;
@@ -598,6 +657,9 @@ struct Solver {
       col_dot<NT, 1>(G, L.ldg, m, L.n, vv, oo, col, rt, -1.0f);
     }
     if (!factor()) return false;
+    // W lives in the factors now: bz / bs serve as ds / dz scratch below
+    float* const rz = sm + st->L.o_bz;
+    float* const rs = sm + st->L.o_bs;
     solve(0, 1);
     g_times_dx(0, 1);
     float amin[1] = {1.0f};
@@ -875,7 +937,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) qp_forward_kernel(co
   __shared__ FwdParams sP;
   if (threadIdx.x == 0) sP = P;
   Solver<NT> slv;
-  slv.bind(sm, &st, P.n, P.m, P.p, P.amax, P.ldpb);  // ends with a barrier
+  slv.bind(sm, &st, P.n, P.m, P.p, P.amax);  // ends with a barrier
 #ifdef QP_PHASE_TIMERS
   if (threadIdx.x == 0) st.timers = P.timers;
   __syncthreads();

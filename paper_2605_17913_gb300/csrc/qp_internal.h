@@ -15,7 +15,6 @@ struct FwdParams {
   int32_t *status, *iters;
   float* kkt;
   int amax;  // rows kept as multipliers at most (shared-memory budget)
-  int ldpb;  // panel-buffer row stride of the blocked factorisation (12 or 8)
   // settings
   float tol, sigma, kappa_min, kappa_relax, relax_tol, step_frac;
   int max_iter, relax_max_iter, sigma_mode, formulation, norm_abs, warm_start, refine_steps;
@@ -67,7 +66,7 @@ __host__ __device__ inline CacheLayout cache_layout(int n, int m, int p, int ama
 
 // Launch configuration of the forward kernel for a size: shared-memory bytes
 // (0 if unsupported), threads per CTA and the active-row cap amax.
-size_t forward_config(int n, int m, int p, int* nthreads, int* amax, int* ldpb = nullptr);
+size_t forward_config(int n, int m, int p, int* nthreads, int* amax);
 cudaError_t launch_forward(const FwdParams& P, int nthreads, size_t smem, int grid,
                            cudaStream_t stream);
 int forward_blocks_per_sm(int nthreads, size_t smem);
