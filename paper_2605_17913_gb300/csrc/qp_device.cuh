@@ -166,27 +166,29 @@ __device__ void col_dot(const float* M, int ld, int rows, int cols, const float*
 }
 
 // ---------------------------------------------------------------------------
-// Lower triangle of K = Q + G' diag(W) G with 4x4 register tiles.  Q is read
-// from K's strict upper triangle (Q[i][j] = K[j][i] for j < i, never written
-// here) and its diagonal from qd; rows with W = 0 add nothing.  Tiles are
-// split over the contraction when there are fewer tiles than threads; the
-// partial sums are added in a fixed order (deterministic).
+// Lower triangle of K = Q + G' diag(W) G with 4x4 register tiles, summing
+// only over the rows listed in rows[0 .. nrows) (rows with W = 0 add
+// nothing and are left out).  Q is read from K's strict upper triangle
+// (Q[i][j] = K[j][i] for j < i, never written here) and its diagonal from
+// qd.  Tiles are split over the contraction when there are fewer tiles than
+// threads; the partial sums are added in a fixed order (deterministic).
 // ---------------------------------------------------------------------------
 template <int NT>
 __device__ void syrk_gwg(float* K, int ldk, const float* qd, const float* G, int ldg,
-                         const float* W, int m, int n) {
+                         const float* W, const int* rows, int nrows, int n) {
   const int nt = (n + 3) >> 2;
   const int T = nt * (nt + 1) / 2;
   int ns = NT / T;
   if (ns < 1) ns = 1;
   if (ns > 4) ns = 4;
-  const int chunk = (m + ns - 1) / ns;
+  const int chunk = (nrows + ns - 1) / ns;
   for (int item0 = 0; item0 < T * ns; item0 += NT) {
     const int item = item0 + (int)threadIdx.x;
     const bool active = item < T * ns;
     const int t = active ? item % T : 0;
     const int sp = active ? item / T : 0;
-    int I = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    const float x8 = 8.0f * (float)t + 1.0f;
+    int I = (int)((x8 * rsqrtf(x8) - 1.0f) * 0.5f);
     while ((I + 1) * (I + 2) / 2 <= t) ++I;
     while (I * (I + 1) / 2 > t) --I;
     const int J = t - I * (I + 1) / 2;
@@ -196,18 +198,19 @@ __device__ void syrk_gwg(float* K, int ldk, const float* qd, const float* G, int
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc[a][c] = 0.f;
     if (active) {
-      const int r0 = sp * chunk, r1 = min(m, r0 + chunk);
+      const int i0 = sp * chunk, i1 = min(nrows, i0 + chunk);
 #pragma unroll 2
-      for (int r = r0; r < r1; ++r) {
+      for (int ii = i0; ii < i1; ++ii) {
+        const int r = rows[ii];
         const float w = W[r];
         const float4 a = *reinterpret_cast<const float4*>(G + r * ldg + 4 * I);
         const float4 c = *reinterpret_cast<const float4*>(G + r * ldg + 4 * J);
         const float aw[4] = {a.x * w, a.y * w, a.z * w, a.w * w};
         const float cv[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
-        for (int ii = 0; ii < 4; ++ii)
+        for (int q = 0; q < 4; ++q)
 #pragma unroll
-          for (int jj = 0; jj < 4; ++jj) acc[ii][jj] = fmaf(aw[ii], cv[jj], acc[ii][jj]);
+          for (int jj = 0; jj < 4; ++jj) acc[q][jj] = fmaf(aw[q], cv[jj], acc[q][jj]);
       }
     }
     for (int phase = 0; phase < ns; ++phase) {
@@ -280,7 +283,8 @@ __device__ bool cholesky(float* K, int ldk, int n, float* dinv) {
 // rows), and their C entries Y L^-1 r -- forward substitution for free.
 // Pb holds panel rows in groups of 4 (8 values each) padded to 36 floats, so
 // a warp's float4 loads of 4-row groups hit distinct banks; it needs
-// pb_floats(n + nB) floats.  Two barriers per panel.
+// pb_floats(n + nB + 4) floats (B rows start at a multiple of 4).  Two
+// barriers per panel.
 // ---------------------------------------------------------------------------
 __host__ __device__ inline int pb_floats(int rows) { return ((rows + 3) / 4 + 1) * 36; }
 __device__ __forceinline__ int pb_off(int r) { return (r >> 2) * 36 + (r & 3) * 8; }
@@ -289,6 +293,9 @@ template <int NT>
 __device__ bool panel_factor_trsm(float* M, int ld, int j0, int jb, float* dinv, float* A,
                                   int lda, int rowA0, int nA, float* B, int ldb, int nB,
                                   float* Pb) {
+  // Pb index of a row: A rows at 0 .. nA-1, B rows from the next multiple of
+  // 4, so that every 4-row tile of the trailing update lies in one block.
+  const int nA4 = (nA + 3) & ~3;
   const int N = nA + nB;
   bool ok = true;
   const int tid = threadIdx.x;
@@ -319,7 +326,8 @@ __device__ bool panel_factor_trsm(float* M, int ld, int j0, int jb, float* dinv,
         for (int k = j + 1; k <= i; ++k) l[i][k] = fmaf(-l[i][j], l[k][j], l[i][k]);
     }
     if (rr < N) {
-      float* row = rr < nA ? A + (rowA0 + rr) * lda + j0 : B + (rr - nA) * ldb + j0;
+      const bool inA = rr < nA;
+      float* row = inA ? A + (rowA0 + rr) * lda + j0 : B + (rr - nA) * ldb + j0;
       float v[8];
 #pragma unroll
       for (int t = 0; t < 8; ++t) v[t] = t < jb ? row[t] : 0.0f;
@@ -330,7 +338,7 @@ __device__ bool panel_factor_trsm(float* M, int ld, int j0, int jb, float* dinv,
         for (int u = 0; u < t; ++u) acc = fmaf(-v[u], l[t][u], acc);
         v[t] = acc * inv[t];
       }
-      float* pr = Pb + pb_off(rr);
+      float* pr = Pb + pb_off(inA ? rr : nA4 + (rr - nA));
       reinterpret_cast<float4*>(pr)[0] = make_float4(v[0], v[1], v[2], v[3]);
       reinterpret_cast<float4*>(pr)[1] = make_float4(v[4], v[5], v[6], v[7]);
 #pragma unroll
@@ -348,10 +356,12 @@ __device__ bool panel_factor_trsm(float* M, int ld, int j0, int jb, float* dinv,
         }
     }
   }
-  // zero the pad rows of the last 4-row group
-  if (tid < 8 * 4) {
-    const int r = N + (tid >> 3);
-    if ((r >> 2) == (N >> 2) && (N & 3)) Pb[pb_off(r) + (tid & 7)] = 0.0f;
+  // zero the pad rows: nA .. nA4-1 and after the last B row up to the group end
+  if (tid < 64) {
+    const int k = tid >> 3, c = tid & 7;
+    const int r = k < 4 ? nA + k : nA4 + nB + (k - 4);
+    const bool pad = k < 4 ? r < nA4 : (r & 3) != 0 && (r >> 2) == ((nA4 + nB) >> 2);
+    if (pad) Pb[pb_off(r) + c] = 0.0f;
   }
   const bool all_ok = __syncthreads_and(ok ? 1 : 0) != 0;
   // every thread has read the block: threads 0..jb-1 now store its factor
@@ -370,11 +380,14 @@ __device__ bool panel_factor_trsm(float* M, int ld, int j0, int jb, float* dinv,
 //   (A, A): A[rowA0+r][rowA0+c] -= P_r . P_c
 //   (B, A): B[k][rowA0+c]        -= P_k . P_c
 //   (B, B): C[k][l]              += P_k . P_l     (when C != nullptr)
+// B rows start at a multiple of 4 in Pb, so each 4x4 tile is in one block:
+// one base pointer and stride per tile, predicated only at the edges.
 template <int NT>
 __device__ void panel_syrk(const float* Pb, float* A, int lda, int rowA0, int nA, float* B,
                            int ldb, int nB, float* C, int ldc) {
-  const int N = nA + nB;
-  const int nt = (N + 3) >> 2;
+  const int nA4 = (nA + 3) & ~3;
+  const int ntA = nA4 >> 2;
+  const int nt = ntA + ((nB + 3) >> 2);
   const int T = nt * (nt + 1) / 2;
   for (int t = threadIdx.x; t < T; t += NT) {
     // tile index -> (I, J), J <= I (square root estimate, then exact correction)
@@ -383,6 +396,29 @@ __device__ void panel_syrk(const float* Pb, float* A, int lda, int rowA0, int nA
     while ((I + 1) * (I + 2) / 2 <= t) ++I;
     while (I * (I + 1) / 2 > t) --I;
     const int J = t - I * (I + 1) / 2;
+    const bool rowA = I < ntA, colA = J < ntA;
+    if (!rowA && !colA && C == nullptr) continue;
+    float* dst;
+    int ld, rmax, cmax;
+    float sgn = -1.0f;
+    if (rowA) {  // then colA too
+      dst = A + (rowA0 + 4 * I) * lda + rowA0 + 4 * J;
+      ld = lda;
+      rmax = nA - 4 * I;
+      cmax = nA - 4 * J;
+    } else if (colA) {
+      dst = B + (4 * I - nA4) * ldb + rowA0 + 4 * J;
+      ld = ldb;
+      rmax = nB - (4 * I - nA4);
+      cmax = nA - 4 * J;
+    } else {
+      dst = C + (4 * I - nA4) * ldc + (4 * J - nA4);
+      ld = ldc;
+      rmax = nB - (4 * I - nA4);
+      cmax = nB - (4 * J - nA4);
+      sgn = 1.0f;
+    }
+    const bool diag = I == J;
     float acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -408,22 +444,11 @@ __device__ void panel_syrk(const float* Pb, float* A, int lda, int rowA0, int nA
         }
     }
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const int r = 4 * I + a;
-      if (r >= N) continue;
+    for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int c = 4 * J + b;
-        if (c > r) continue;
-        if (r < nA) {
-          A[(rowA0 + r) * lda + rowA0 + c] -= acc[a][b];
-        } else if (c < nA) {
-          B[(r - nA) * ldb + rowA0 + c] -= acc[a][b];
-        } else if (C != nullptr) {
-          C[(r - nA) * ldc + (c - nA)] += acc[a][b];
-        }
-      }
-    }
+      for (int b = 0; b < 4; ++b)
+        if (a < rmax && b < cmax && (!diag || b <= a))
+          dst[a * ld + b] = fmaf(sgn, acc[a][b], dst[a * ld + b]);
   }
   __syncthreads();
 }

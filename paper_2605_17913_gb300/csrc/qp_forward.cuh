@@ -61,7 +61,7 @@ struct FLayout {
   int o_q, o_x, o_rt, o_dinv, o_tn;
   int o_b, o_y, o_re;
   int o_cdinv, o_D, o_ua, o_ub, o_act;
-  int o_h, o_z, o_s, o_ri, o_bz, o_bs, o_ea, o_eb, o_ta, o_tb, o_pos;
+  int o_h, o_z, o_s, o_ri, o_bz, o_bs, o_ea, o_eb, o_ta, o_tb, o_pos, o_ina;
   int total;
 };
 
@@ -92,7 +92,7 @@ __host__ __device__ inline FLayout make_fwd_layout(int n, int m, int p, int amax
   {
     // union: Pb | (col, ta, tb, eb, tn)
     const int base = o;
-    const int pb = round4(pb_floats(n + L.fmax + 2));
+    const int pb = round4(pb_floats(n + L.fmax + 2 + 4));
     L.o_Pb = base;
     L.o_col = take(2 * nthreads);
     L.o_ta = take(L.mv); L.o_tb = take(L.mv); L.o_eb = take(L.mv);
@@ -107,6 +107,7 @@ __host__ __device__ inline FLayout make_fwd_layout(int n, int m, int p, int amax
   L.o_bz = take(L.mv); L.o_bs = take(L.mv);
   L.o_ea = take(L.mv);
   L.o_pos = take(L.mv);
+  L.o_ina = take(L.mv);
   L.total = o;
   return L;
 }
@@ -118,6 +119,7 @@ struct SharedState {
   long long t_mark;                // phase timers only
   unsigned long long* timers;      // phase timers only
   int a, nf;         // active rows, rows of F = a + p (set by partition())
+  int ni;            // inactive rows (listed in ina)
   float qn, bn, hn;  // |q|, |b|, |h| (infinity norms)
 };
 
@@ -221,7 +223,7 @@ struct Solver {
     const FLayout& L = st->L;
     const int m = L.m, p = L.p, n = L.n, t = threadIdx.x, w = t >> 5, lane = t & 31;
     QP_ARR(bz); QP_ARR(bs); QP_ARR(red); QP_ARR(G); QP_ARR(A); QP_ARR(Y);
-    QP_ARR(C); QP_ARR(D); QP_ARR(ea); QP_IARR(act); QP_IARR(pos);
+    QP_ARR(C); QP_ARR(D); QP_ARR(ea); QP_IARR(act); QP_IARR(pos); QP_IARR(ina);
     float tau = 1.0f;
     for (int round = 0; round < 40; ++round) {
       float cnt[1] = {0.f};
@@ -232,20 +234,25 @@ struct Solver {
     }
     // ordered compaction of the active rows: one warp scans all rows
     if (w == 0) {
-      int base = 0;
+      int base = 0, ibase = 0;
       for (int r0 = 0; r0 < m; r0 += 32) {
         const int r = r0 + lane;
         const bool on = r < m && bz[r] > tau * bs[r];
         const unsigned mask = __ballot_sync(kFull, on);
         const int k = base + __popc(mask & ((1u << lane) - 1u));
         const bool keep = on && k < L.amax;  // always true after the tau loop; keeps act[] in bounds
+        const bool off = r < m && !keep;
+        const unsigned imask = __ballot_sync(kFull, off);
         if (r < m) pos[r] = keep ? k : -1;
         if (keep) act[k] = r;
+        if (off) ina[ibase + __popc(imask & ((1u << lane) - 1u))] = r;
         base += __popc(mask);
+        ibase += __popc(imask);
       }
       if (lane == 0) {
         st->a = min(base, L.amax);
         st->nf = st->a + p;
+        st->ni = ibase;
       }
     }
     __syncthreads();
@@ -287,9 +294,9 @@ struct Solver {
   __device__ __noinline__ bool factor_once(float creg, int nfold) {
     const FLayout& L = st->L;
     QP_ARR(K); QP_ARR(qd); QP_ARR(G); QP_ARR(ea); QP_ARR(Y); QP_ARR(C); QP_ARR(dinv);
-    QP_ARR(cdinv); QP_ARR(Pb); QP_ARR(red);
+    QP_ARR(cdinv); QP_ARR(Pb); QP_ARR(red); QP_IARR(ina);
     const int nf = st->nf;
-    syrk_gwg<NT>(K, L.ldk, qd, G, L.ldg, ea, L.m, L.n);
+    syrk_gwg<NT>(K, L.ldk, qd, G, L.ldg, ea, ina, st->ni, L.n);
     QP_MARK(PH_SYRK);
     bool ok = blocked_cholesky_bordered<NT>(K, L.ldk, L.n, Y, L.ldk, nf + nfold, C, L.ldc, dinv,
                                             Pb);
