@@ -457,15 +457,25 @@ __device__ void panel_syrk(const float* Pb, float* A, int lda, int rowA0, int nA
 // in Y (stride ldy); C (nB x nB lower, stride ldc, may be null) accumulates
 // Y Y'.  With C == nullptr this is a plain blocked Cholesky of K (nB = 0) or
 // a Cholesky plus triangular solve of the border rows.
+// sub (tracing builds only, may be null): cycles of the factor+TRSM stage and
+// of the trailing updates are added to sub[0] and sub[1] by thread 0.
 template <int NT>
 __device__ bool blocked_cholesky_bordered(float* K, int ldk, int n, float* Y, int ldy, int nB,
-                                          float* C, int ldc, float* dinv, float* Pb) {
+                                          float* C, int ldc, float* dinv, float* Pb,
+                                          unsigned long long* sub = nullptr) {
   bool ok = true;
   for (int j0 = 0; j0 < n; j0 += 8) {
     const int jb = min(8, n - j0);
     const int nK = n - j0 - jb;
+    const long long c0 = sub ? clock64() : 0;
     ok = panel_factor_trsm<NT>(K, ldk, j0, jb, dinv, K, ldk, j0 + jb, nK, Y, ldy, nB, Pb) && ok;
+    const long long c1 = sub ? clock64() : 0;
     if (nK + nB > 0) panel_syrk<NT>(Pb, K, ldk, j0 + jb, nK, Y, ldy, nB, C, ldc);
+    if (sub && threadIdx.x == 0) {
+      const long long c2 = clock64();
+      atomicAdd(&sub[0], (unsigned long long)(c1 - c0));
+      atomicAdd(&sub[1], (unsigned long long)(c2 - c1));
+    }
   }
   __syncthreads();  // the last diagonal block is written after the panel's barrier
   return ok;

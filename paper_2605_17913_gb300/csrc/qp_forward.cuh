@@ -298,8 +298,13 @@ struct Solver {
     const int nf = st->nf;
     syrk_gwg<NT>(K, L.ldk, qd, G, L.ldg, ea, ina, st->ni, L.n);
     QP_MARK(PH_SYRK);
+#ifdef QP_PHASE_TIMERS
+    unsigned long long* const sub = st->timers ? st->timers + PH_COUNT : nullptr;
+#else
+    unsigned long long* const sub = nullptr;
+#endif
     bool ok = blocked_cholesky_bordered<NT>(K, L.ldk, L.n, Y, L.ldk, nf + nfold, C, L.ldc, dinv,
-                                            Pb);
+                                            Pb, sub);
     QP_MARK(PH_BORDER);
     if (nf > 0) {
       float dm[1] = {1.0f};
@@ -309,7 +314,7 @@ struct Solver {
       for (int k = threadIdx.x; k < nf; k += NT) C[k * L.ldc + k] += shift;
       __syncthreads();
       ok = blocked_cholesky_bordered<NT>(C, L.ldc, nf, C + nf * L.ldc, L.ldc, nfold, nullptr, 0,
-                                         cdinv, Pb) && ok;
+                                         cdinv, Pb, sub ? sub + 2 : nullptr) && ok;
       QP_MARK(PH_CCHOL);
     }
     return ok;
