@@ -253,11 +253,12 @@ __global__ void __launch_bounds__(NT) qp_backward_kernel(const BwdParams P) {
   }
   for (int k = t; k < p; k += NT) ys[k] = __ldg(c + cl.oy + k);
   int bad = valid ? 0 : 1;
+  const int acap = valid ? a : 0;  // an unchecked header must not bound the row map
   for (int r = t; r < m; r += NT) {
     zs[r] = __ldg(c + cl.oz + r);
     Ws[r] = __ldg(c + cl.oW + r);
     int k = __ldg(reinterpret_cast<const int*>(c + cl.oPos) + r);
-    if (k >= a || k < -1) { k = -1; bad = 1; }
+    if (k >= acap || k < -1) { k = -1; bad = 1; }
     pos[r] = k;
     if (k >= 0) act[k] = r;
   }

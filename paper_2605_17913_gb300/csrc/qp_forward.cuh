@@ -923,6 +923,14 @@ struct Solver {
       if (!factor() && status == ST_SOLVED) status = ST_NUMERICAL;
       write_cache(P, bi);
       QP_MARK(PH_CACHE);
+    } else if (P.cache && t == 0) {
+      // non-finite data: mark the slot unwritten (active count -1) so the
+      // backward pass gives NaN gradients instead of reading stale contents
+      int* hdr = reinterpret_cast<int*>(P.cache + (size_t)bi * (size_t)P.cache_stride +
+                                        cache_layout(n, m, p, st->L.amax).oHdr);
+      hdr[0] = -1;
+      hdr[1] = -1;
+      hdr[2] = 0;
     }
     if (t == 0) {
       if (P.status) P.status[bi] = status;

@@ -184,6 +184,34 @@ def test_bad_input_flagged_per_instance():
     assert np.all(np.isnan(res["x"][2]))
 
 
+def test_unwritten_cache_slots_give_nan_gradients():
+    """A cache slot the solve did not fill -- an instance with non-finite data,
+    or memory that never held a solve -- gives NaN gradients whatever it
+    contains (random bits here), and the other instances are unaffected."""
+    from paper_2605_17913_gb300.solver import QPSolver
+
+    batch = make_batch("degenerate", 8, seed=11)
+    batch.q[3, 0] = np.nan
+    T = _dev(batch)
+    slv = QPSolver(batch.batch, batch.n, batch.p, batch.m)
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    junk = torch.rand(slv.new_grad_cache().shape, device="cuda", generator=gen)
+    cache = junk.clone()
+    out = slv.solve(T["Q"], T["q"], T["A"], T["b"], T["G"], T["h"], grad_cache=cache,
+                    tol=SOLVER_TOL)
+    g = {k: v.cpu().numpy() for k, v in slv.backward(cache, T["Q"], T["A"], T["G"],
+                                                      T["g"]).items()}
+    ref = gpu_run(batch, grad=True)
+    st = out["status"].cpu().numpy()
+    assert st[3] == 4 and np.all(np.delete(st, 3) == 0)
+    for k in GRAD_KEYS:
+        assert np.all(np.isnan(g[k][3])), k
+        np.testing.assert_array_equal(np.delete(g[k], 3, axis=0), np.delete(ref[k], 3, axis=0))
+    never = slv.backward(junk, T["Q"], T["A"], T["G"], T["g"])
+    for k in GRAD_KEYS:
+        assert torch.all(torch.isnan(never[k])), k
+
+
 def test_standard_formulation_same_optimum():
     batch = make_batch("small", 32, seed=4)
     res = gpu_run(batch, formulation="standard")
