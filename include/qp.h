@@ -153,6 +153,39 @@ int qp_backward_batch(qp_handle* h, const float* grad_cache, const float* Q, con
                       const float* G, const float* dl_dx, float* dQ, float* dq, float* dA,
                       float* db, float* dG, float* dh, void* stream);
 
+/* ---- fixed-scratch variant (an addition of this library; the paper has no
+ *      counterpart) -------------------------------------------------------- */
+
+/* Size of the library's fixed device array that holds the factor cache of
+ * qp_solve_backward_static: 16 MiB per device (for example 647 instances of
+ * n = 50, n_eq = 10, n_ineq = 100; compare qp_grad_cache_bytes). */
+#define QP_STATIC_CACHE_BYTES (16 * 1024 * 1024)
+
+/* qp_solve_batch followed by qp_backward_batch, with the factor cache between
+ * them held in a fixed device array of the library instead of caller memory,
+ * so that the call allocates no memory of any kind.  For callers that cannot
+ * supply the cache on the call path: a fixed-rate loop that must not call
+ * cudaMalloc there (an allocation can synchronise the device and stall), or a
+ * program whose device memory belongs to an arena not lent to libraries.
+ * Arguments, outputs and per-instance status are those of the two calls
+ * (dl_dx[B][n] is required; gradient pointers may be NULL); instances with
+ * non-finite data get NaN gradients.
+ * Limit: returns QP_ENOTSUP, with nothing enqueued, when
+ * qp_grad_cache_bytes(dims) > QP_STATIC_CACHE_BYTES.  Other argument errors
+ * return QP_EINVAL before anything that touches caller memory is enqueued.
+ * The first call on each device does set-up (it looks up the array's device
+ * address, which can load the library's device code into the context): make
+ * it before any stream capture is begun.
+ * Sharing: every call on a device uses the same array, so calls whose device
+ * work can overlap (different streams, unsynchronised host threads) race on
+ * it and give undefined results; calls ordered on one stream are safe. */
+int qp_solve_backward_static(qp_handle* h, const qp_settings* settings, const float* Q,
+                             const float* q, const float* A, const float* b, const float* G,
+                             const float* h_, const float* dl_dx, float* x, float* y, float* z,
+                             float* s, int32_t* status, int32_t* iters, float* kkt_res,
+                             float* dQ, float* dq, float* dA, float* db, float* dG, float* dh,
+                             void* stream);
+
 /* Human-readable name of a return or status code. */
 const char* qp_status_string(int code);
 

@@ -24,6 +24,7 @@ QP_IMPLICIT, QP_STANDARD = 0, 1
 QP_SIGMA_MEHROTRA, QP_SIGMA_CONSTANT = 0, 1
 QP_NORM_SCALED, QP_NORM_ABS = 0, 1
 QP_GWG_FP32, QP_GWG_TF32, QP_GWG_BF16 = 0, 1, 2
+QP_STATIC_CACHE_BYTES = 16 * 1024 * 1024
 
 
 class QPError(RuntimeError):
@@ -81,6 +82,8 @@ def lib() -> ctypes.CDLL:
     L.qp_solve_batch.argtypes = [vp, ctypes.POINTER(Settings)] + [vp] * 14 + [vp]
     L.qp_backward_batch.restype = ctypes.c_int
     L.qp_backward_batch.argtypes = [vp] * 13
+    L.qp_solve_backward_static.restype = ctypes.c_int
+    L.qp_solve_backward_static.argtypes = [vp, ctypes.POINTER(Settings)] + [vp] * 21
     _lib = L
     return L
 

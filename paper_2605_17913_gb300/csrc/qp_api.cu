@@ -32,6 +32,10 @@ static bool dims_ok(const qp_dims* d) {
 static unsigned long long* g_phase_counters = nullptr;
 #endif
 
+namespace qpgpu {
+qp_dims handle_dims(const qp_handle* h) { return h->dims; }
+}  // namespace qpgpu
+
 extern "C" {
 
 #ifdef QP_PHASE_TIMERS

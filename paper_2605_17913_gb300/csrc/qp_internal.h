@@ -5,6 +5,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include "qp.h"
+
 namespace qpgpu {
 
 // Parameters of one forward launch (all device pointers).
@@ -73,5 +75,8 @@ int forward_blocks_per_sm(int nthreads, size_t smem);
 
 size_t backward_smem_bytes(int n, int m, int p, int amax, int* nthreads);
 cudaError_t launch_backward(const BwdParams& P, int nthreads, size_t smem, cudaStream_t stream);
+
+// Problem sizes of a handle (struct qp_handle is private to qp_api.cu).
+qp_dims handle_dims(const qp_handle* h);
 
 }  // namespace qpgpu
