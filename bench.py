@@ -141,7 +141,7 @@ def cpu_oracle_rate(workload, n_target_s, seed=0, kappa_relax=1e-4):
     O.solve(probe.Q, probe.q, probe.A, probe.b, probe.G, probe.h, tol=1e-12,
             kappa_relax=kappa_relax, g=probe.g, nthreads=cores)
     dt = time.perf_counter() - t0
-    count = int(min(4096, max(2 * cores, probe.batch * n_target_s / max(dt, 1e-6))))
+    count = int(min(16384, max(2 * cores, probe.batch * n_target_s / max(dt, 1e-6))))
     smp = make_batch(workload, count, seed=seed, start=0)
     t0 = time.perf_counter()
     O.solve(smp.Q, smp.q, smp.A, smp.b, smp.G, smp.h, tol=1e-12, kappa_relax=kappa_relax,
