@@ -30,9 +30,10 @@ METRIC = "QP solves+grads/sec on 1 GB300 at KKT res≤1e-5 (FP32); serve p50/p99
 UNIT = "QP solves+grads/s"
 L2_BYTES = 129 * 1024 * 1024
 
-# DRAM bytes per launch of the forward kernel from the ncu capture summarised in
-# profiles/forward_degenerate_n50.md (None until captured for the current kernel).
-FORWARD_TRAFFIC_BYTES = None
+# DRAM bytes per launch of the forward kernel on the default workload (4096
+# instances), scaled by instance count from the ncu capture of 1024 instances
+# summarised in profiles/forward_degenerate_n50.md; None once the kernel changes.
+FORWARD_TRAFFIC_BYTES = 342.0e6
 
 
 def parse():
