@@ -291,7 +291,10 @@ def run_ours(args, rank, world, local_rank):
     fwd_avg = sum(fwd_ms) / len(fwd_ms)
     achieved = flops / (fwd_avg / 1e3) / 1e12
     peak = fp32_alu_peak_tflops()
-    traffic = FORWARD_TRAFFIC_BYTES
+    # the captured figure is per 4096-instance degenerate launch; other
+    # workloads have no capture
+    traffic = (FORWARD_TRAFFIC_BYTES * B / 4096
+               if FORWARD_TRAFFIC_BYTES is not None and args.workload == "degenerate" else None)
     bwd_avg = sum(bwd_ms) / len(bwd_ms)
     bwd_gbs = backward_bytes(n, m, p, B) / (bwd_avg / 1e3) / 1e9
     # ---- end to end through the public API with pinned host buffers ----
