@@ -131,47 +131,57 @@ enum Phase { PH_LOAD, PH_RESID, PH_PART, PH_RHS, PH_SYRK, PH_BORDER, PH_CCHOL, P
 #ifdef QP_PHASE_TIMERS
 #define QP_MARK(ph)                                                                    \
   do {                                                                                 \
-    if (threadIdx.x == 0 && st->timers) {                                              \
+    if (threadIdx.x == 0 && fwd_state.timers) {                                              \
       const long long now_ = clock64();                                                \
-      atomicAdd(&st->timers[ph], (unsigned long long)(now_ - st->t_mark));             \
-      st->t_mark = now_;                                                               \
+      atomicAdd(&fwd_state.timers[ph], (unsigned long long)(now_ - fwd_state.t_mark));             \
+      fwd_state.t_mark = now_;                                                               \
     }                                                                                  \
   } while (0)
 #else
 #define QP_MARK(ph) do {} while (0)
 #endif
 
+// Per-CTA state at namespace scope.  The phases are noinline functions; they
+// reach the layout, the scalars and the dynamic shared memory through fixed
+// shared addresses, so nothing of the solver's state lives in local memory
+// (which would miss in the small L1 left beside the shared-memory carve-out).
+extern __shared__ __align__(16) float fwd_dyn[];   // the per-instance layout
+static __shared__ SharedState fwd_state;
+static __shared__ unsigned char fwd_parity[512];   // block_reduce buffer parity, per thread
+
 // address of array `name` in the per-instance shared-memory layout
-#define QP_ARR(name) float* const name = sm + st->L.o_##name
-#define QP_IARR(name) int* const name = reinterpret_cast<int*>(sm + st->L.o_##name)
+#define QP_ARR(name) float* const name = fwd_dyn + fwd_state.L.o_##name
+#define QP_IARR(name) int* const name = reinterpret_cast<int*>(fwd_dyn + fwd_state.L.o_##name)
 
 template <int NT>
 struct Solver {
-  float* sm;
-  SharedState* st;
-  int parity;
-
-  __device__ void bind(float* sm_, SharedState* st_, int n, int m, int p, int amax) {
-    sm = sm_;
-    st = st_;
+  static __device__ void init(int n, int m, int p, int amax) {
     if (threadIdx.x == 0) {
-      st->L = make_fwd_layout(n, m, p, amax, NT);
-      st->a = 0;
-      st->nf = p;
-      st->t_mark = clock64();
-      st->timers = nullptr;
+      fwd_state.L = make_fwd_layout(n, m, p, amax, NT);
+      fwd_state.a = 0;
+      fwd_state.nf = p;
+      fwd_state.t_mark = clock64();
+      fwd_state.timers = nullptr;
     }
+    fwd_parity[threadIdx.x] = 0;
     __syncthreads();
-    parity = 0;
+  }
+
+  // block reduction with this thread's buffer parity kept in shared memory
+  template <int K, class Op>
+  static __device__ __forceinline__ void reduce(float (&v)[K], float* red, Op op) {
+    int parity = fwd_parity[threadIdx.x];
+    block_reduce<NT, K>(v, red, parity, op);
+    fwd_parity[threadIdx.x] = (unsigned char)parity;
   }
 
   // ---- load one instance; Q's strict upper triangle goes to K's upper part ----
   // Returns false if some datum is not finite.
-  __device__ __noinline__ bool load(const FwdParams& P, int bi) {
-    const FLayout& L = st->L;
+  static __device__ __noinline__ bool load(const FwdParams& P, int bi) {
+    const FLayout& L = fwd_state.L;
     const int n = L.n, m = L.m, p = L.p, t = threadIdx.x;
     QP_ARR(K); QP_ARR(qd); QP_ARR(G); QP_ARR(A); QP_ARR(q); QP_ARR(b); QP_ARR(h); QP_ARR(red);
-    for (int i = t; i < L.total; i += NT) sm[i] = 0.0f;
+    for (int i = t; i < L.total; i += NT) fwd_dyn[i] = 0.0f;
     __syncthreads();
     const float* gQ = P.Q + (size_t)bi * n * n;
     const float* gG = P.G + (size_t)bi * m * n;
@@ -210,8 +220,8 @@ struct Solver {
       h[i] = v; lh = fmaxf(lh, fabsf(v)); chk = isfinite(v) ? chk : 1.0f;
     }
     float v[4] = {chk, lq, lb, lh};
-    block_reduce<NT, 4>(v, red, parity, OpMax());
-    if (t == 0) { st->qn = v[1]; st->bn = v[2]; st->hn = v[3]; }
+    reduce<4>(v, red, OpMax());
+    if (t == 0) { fwd_state.qn = v[1]; fwd_state.bn = v[2]; fwd_state.hn = v[3]; }
     __syncthreads();
     QP_MARK(PH_LOAD);
     return v[0] == 0.0f;
@@ -219,8 +229,8 @@ struct Solver {
 
   // ---- split rows by W = bz/bs; build F = [G_A; A], D, C = diag(D) and the
   // SYRK weights (W on inactive rows, 0 on active rows, in ea) ----
-  __device__ __noinline__ void partition() {
-    const FLayout& L = st->L;
+  static __device__ __noinline__ void partition() {
+    const FLayout& L = fwd_state.L;
     const int m = L.m, p = L.p, n = L.n, t = threadIdx.x, w = t >> 5, lane = t & 31;
     QP_ARR(bz); QP_ARR(bs); QP_ARR(red); QP_ARR(G); QP_ARR(A); QP_ARR(Y);
     QP_ARR(C); QP_ARR(D); QP_ARR(ea); QP_IARR(act); QP_IARR(pos); QP_IARR(ina);
@@ -228,7 +238,7 @@ struct Solver {
     for (int round = 0; round < 40; ++round) {
       float cnt[1] = {0.f};
       for (int r = t; r < m; r += NT) cnt[0] += (bz[r] > tau * bs[r]) ? 1.f : 0.f;
-      block_reduce<NT, 1>(cnt, red, parity, OpSum());
+      reduce<1>(cnt, red, OpSum());
       if ((int)cnt[0] <= L.amax) break;
       tau *= 10.0f;
     }
@@ -250,13 +260,13 @@ struct Solver {
         ibase += __popc(imask);
       }
       if (lane == 0) {
-        st->a = min(base, L.amax);
-        st->nf = st->a + p;
-        st->ni = ibase;
+        fwd_state.a = min(base, L.amax);
+        fwd_state.nf = fwd_state.a + p;
+        fwd_state.ni = ibase;
       }
     }
     __syncthreads();
-    const int a = st->a, nf = st->nf;
+    const int a = fwd_state.a, nf = fwd_state.nf;
     for (int k = w; k < nf; k += NT / 32) {
       const float* src = k < a ? G + act[k] * L.ldg : A + (k - a) * L.ldg;
       for (int c = lane; c < n; c += 32) Y[k * L.ldk + c] = src[c];
@@ -273,10 +283,10 @@ struct Solver {
   // ---- fold the two right-hand sides of an implicit step into the border:
   // Y rows nf, nf+1 <- r1 (columns A, B) and C rows nf, nf+1 <- -rhs2, so that
   // the factorisation leaves u = L^-1 r1 in Y and w = L_C^-1 (Y u - rhs2) in C.
-  __device__ void fold_rhs() {
-    const FLayout& L = st->L;
+  static __device__ void fold_rhs() {
+    const FLayout& L = fwd_state.L;
     QP_ARR(R); QP_ARR(Y); QP_ARR(C); QP_ARR(ua); QP_ARR(ub);
-    const int n = L.n, nf = st->nf, t = threadIdx.x;
+    const int n = L.n, nf = fwd_state.nf, t = threadIdx.x;
     for (int e = t; e < 2 * n; e += NT) {
       const int c = e / n, i = e - c * n;
       Y[(nf + c) * L.ldk + i] = R[c * L.ldx + i];
@@ -291,15 +301,15 @@ struct Solver {
   // ---- factor K_I and the bordered block.  F, D and C = D must have just
   // been set by partition() (and the right-hand sides by fold_rhs() when
   // nfold = 2): the elimination overwrites them. ----
-  __device__ __noinline__ bool factor_once(float creg, int nfold) {
-    const FLayout& L = st->L;
+  static __device__ __noinline__ bool factor_once(float creg, int nfold) {
+    const FLayout& L = fwd_state.L;
     QP_ARR(K); QP_ARR(qd); QP_ARR(G); QP_ARR(ea); QP_ARR(Y); QP_ARR(C); QP_ARR(dinv);
     QP_ARR(cdinv); QP_ARR(Pb); QP_ARR(red); QP_IARR(ina);
-    const int nf = st->nf;
-    syrk_gwg<NT>(K, L.ldk, qd, G, L.ldg, ea, ina, st->ni, L.n);
+    const int nf = fwd_state.nf;
+    syrk_gwg<NT>(K, L.ldk, qd, G, L.ldg, ea, ina, fwd_state.ni, L.n);
     QP_MARK(PH_SYRK);
 #ifdef QP_PHASE_TIMERS
-    unsigned long long* const sub = st->timers ? st->timers + PH_COUNT : nullptr;
+    unsigned long long* const sub = fwd_state.timers ? fwd_state.timers + PH_COUNT : nullptr;
 #else
     unsigned long long* const sub = nullptr;
 #endif
@@ -309,7 +319,7 @@ struct Solver {
     if (nf > 0) {
       float dm[1] = {1.0f};
       for (int k = threadIdx.x; k < nf; k += NT) dm[0] = fmaxf(dm[0], C[k * L.ldc + k]);
-      block_reduce<NT, 1>(dm, red, parity, OpMax());
+      reduce<1>(dm, red, OpMax());
       const float shift = creg * dm[0];
       for (int k = threadIdx.x; k < nf; k += NT) C[k * L.ldc + k] += shift;
       __syncthreads();
@@ -322,7 +332,7 @@ struct Solver {
 
   // factor; if FP32 Cholesky of C meets a non-positive pivot (rank-deficient
   // F), redo the partition and factorisation with a 100x, then 10^4x larger shift.
-  __device__ bool factor(int nfold = 0) {
+  static __device__ bool factor(int nfold = 0) {
     float creg = kCReg;
     for (int attempt = 0; attempt < 3; ++attempt, creg *= 100.0f) {
       if (attempt > 0) {
@@ -336,11 +346,11 @@ struct Solver {
 
   // ---- finish a folded solve: mu = L_C^-T w, dx = L^-T (u - Y' mu) for both
   // columns; dx returned in R rows 0, 1 and mu in ua / ub ----
-  __device__ void solve_folded() {
-    const FLayout& L = st->L;
+  static __device__ void solve_folded() {
+    const FLayout& L = fwd_state.L;
     QP_ARR(K); QP_ARR(dinv); QP_ARR(R); QP_ARR(Y); QP_ARR(C); QP_ARR(cdinv); QP_ARR(ua);
     QP_ARR(ub);
-    const int n = L.n, t = threadIdx.x, w = t >> 5, nf = st->nf;
+    const int n = L.n, t = threadIdx.x, w = t >> 5, nf = fwd_state.nf;
     if (nf > 0) {
       if (w < 2) {
         float* u = w == 0 ? ua : ub;
@@ -367,8 +377,8 @@ struct Solver {
   }
 
   template <int SP>
-  __device__ void c_solve(float* v, int nf, bool upper_only = false) {
-    const FLayout& L = st->L;
+  static __device__ void c_solve(float* v, int nf, bool upper_only = false) {
+    const FLayout& L = fwd_state.L;
     QP_ARR(C); QP_ARR(cdinv);
     const int lane = threadIdx.x & 31;
     float r[1][SP];
@@ -388,10 +398,10 @@ struct Solver {
 
   // ---- solve [K_I F'; F -D] (dx, mu) = (rhs1, rhs2) for columns slot0..slot0+nrhs-1 ----
   // rhs1 in R rows, rhs2 in ua (column 0) / ub (column 1); dx returned in R, mu in ua / ub.
-  __device__ __noinline__ void solve(int slot0, int nrhs) {
-    const FLayout& L = st->L;
+  static __device__ __noinline__ void solve(int slot0, int nrhs) {
+    const FLayout& L = fwd_state.L;
     QP_ARR(K); QP_ARR(dinv); QP_ARR(R); QP_ARR(Y); QP_ARR(ua); QP_ARR(ub);
-    const int n = L.n, t = threadIdx.x, w = t >> 5, nf = st->nf;
+    const int n = L.n, t = threadIdx.x, w = t >> 5, nf = fwd_state.nf;
     solve_rows<NT, false>(K, L.ldk, dinv, n, R, L.ldx, slot0, nrhs);
     if (nf > 0) {
       for (int e = t; e < nf * nrhs; e += NT) {
@@ -426,8 +436,8 @@ struct Solver {
   }
 
   // e = G dx for the solved columns (ea for column 0, eb for column 1)
-  __device__ __noinline__ void g_times_dx(int slot0, int nrhs) {
-    const FLayout& L = st->L;
+  static __device__ __noinline__ void g_times_dx(int slot0, int nrhs) {
+    const FLayout& L = fwd_state.L;
     QP_ARR(G); QP_ARR(R); QP_ARR(ea); QP_ARR(eb);
     for (int r = threadIdx.x; r < L.m; r += NT) {
       if (nrhs == 2) {
@@ -446,16 +456,16 @@ struct Solver {
   // ---- residuals (eq. 4, eq. 10) and the measure ----
   // implicit: bz = b_k(v), bs = b_k(-v) with kappa = s'z/m; standard: bz = z, bs = s.
   // mode 0: complementarity term max z.*s; mode 1 (relax): |kappa - kr| / kr.
-  __device__ __noinline__ float residuals(const FwdParams& P, bool implicit, int mode, float& kappa) {
-    const FLayout& L = st->L;
+  static __device__ __noinline__ float2 residuals(const FwdParams& P, bool implicit, int mode) {
+    const FLayout& L = fwd_state.L;
     const int n = L.n, m = L.m, p = L.p, t = threadIdx.x;
     QP_ARR(K); QP_ARR(qd); QP_ARR(G); QP_ARR(A); QP_ARR(q); QP_ARR(b); QP_ARR(h); QP_ARR(x);
     QP_ARR(y); QP_ARR(z); QP_ARR(s); QP_ARR(rt); QP_ARR(re); QP_ARR(ri);
     QP_ARR(bz); QP_ARR(bs); QP_ARR(tn); QP_ARR(red); QP_ARR(col);
     float ks[1] = {0.f};
     for (int r = t; r < m; r += NT) ks[0] = fmaf(z[r], s[r], ks[0]);
-    block_reduce<NT, 1>(ks, red, parity, OpSum());
-    kappa = m > 0 ? ks[0] / (float)m : 0.f;
+    reduce<1>(ks, red, OpSum());
+    const float kappa = m > 0 ? ks[0] / (float)m : 0.f;
     {
       const float* vv[1] = {z};
       float* oo[1] = {tn};
@@ -506,26 +516,28 @@ struct Solver {
         mx[4] = fmaxf(mx[4], fabsf(r)); mx[5] = fmaxf(mx[5], fabsf(ax));
       }
     }
-    block_reduce<NT, 13>(mx, red, parity, OpMax());
+    reduce<13>(mx, red, OpMax());
     QP_MARK(PH_RESID);
-    if (mx[12] > 0.f) return NAN;
+    if (mx[12] > 0.f) return make_float2(NAN, kappa);
     float comp = mx[9];
     if (mode == 1) comp = fabsf(kappa - P.kappa_relax) / P.kappa_relax;
-    if (P.norm_abs) return fmaxf(fmaxf(fmaxf(mx[0], mx[4]), fmaxf(mx[6], comp)), mx[10]);
-    const float dt = fmaxf(fmaxf(1.0f, st->qn), fmaxf(fmaxf(mx[1], mx[2]), mx[3]));
-    const float de = fmaxf(fmaxf(1.0f, st->bn), mx[5]);
-    const float di = fmaxf(fmaxf(1.0f, st->hn), fmaxf(mx[7], mx[8]));
+    if (P.norm_abs)
+      return make_float2(fmaxf(fmaxf(fmaxf(mx[0], mx[4]), fmaxf(mx[6], comp)), mx[10]), kappa);
+    const float dt = fmaxf(fmaxf(1.0f, fwd_state.qn), fmaxf(fmaxf(mx[1], mx[2]), mx[3]));
+    const float de = fmaxf(fmaxf(1.0f, fwd_state.bn), mx[5]);
+    const float di = fmaxf(fmaxf(1.0f, fwd_state.hn), fmaxf(mx[7], mx[8]));
     const float dz = fmaxf(1.0f, fmaxf(mx[11], mx[8]));
-    return fmaxf(fmaxf(fmaxf(mx[0] / dt, mx[4] / de), fmaxf(mx[6] / di, comp)), mx[10] / dz);
+    return make_float2(
+        fmaxf(fmaxf(fmaxf(mx[0] / dt, mx[4] / de), fmaxf(mx[6] / di, comp)), mx[10] / dz), kappa);
   }
 
   // ---- implicit right-hand sides, two columns (r_kappa = 0 and d/dr_kappa) ----
-  __device__ __noinline__ void implicit_rhs() {
-    const FLayout& L = st->L;
+  static __device__ __noinline__ void implicit_rhs() {
+    const FLayout& L = fwd_state.L;
     QP_ARR(bz); QP_ARR(bs); QP_ARR(z); QP_ARR(s); QP_ARR(ri); QP_ARR(re); QP_ARR(ta);
     QP_ARR(tb); QP_ARR(ua); QP_ARR(ub); QP_ARR(R); QP_ARR(G); QP_ARR(rt); QP_ARR(col);
     QP_IARR(pos); QP_IARR(act);
-    const int m = L.m, t = threadIdx.x, a = st->a, nf = st->nf;
+    const int m = L.m, t = threadIdx.x, a = fwd_state.a, nf = fwd_state.nf;
     for (int r = t; r < m; r += NT) {
       const float rho = bz[r] + bs[r];
       const bool inact = pos[r] < 0;
@@ -553,8 +565,8 @@ struct Solver {
   }
 
   // ds, dz, dv of the implicit direction for r_kappa = rk on row r
-  __device__ __forceinline__ void implicit_dir(int r, float rk, float& dsr, float& dzr,
-                                               float& dvr) const {
+  static __device__ __forceinline__ void implicit_dir(int r, float rk, float& dsr, float& dzr,
+                                                      float& dvr) {
     QP_ARR(bz); QP_ARR(bs); QP_ARR(ea); QP_ARR(eb); QP_ARR(ri); QP_ARR(z); QP_ARR(s);
     QP_ARR(ua); QP_ARR(ub); QP_IARR(pos);
     const float rzr = z[r] - bz[r], rsr = s[r] - bs[r];
@@ -572,36 +584,36 @@ struct Solver {
     dsr = -rsr - (bs[r] * c) * dvr - c * rk;
   }
 
-  __device__ __noinline__ float implicit_alpha(float rk, bool store) {
+  static __device__ __noinline__ float implicit_alpha(float rk, bool store) {
     QP_ARR(s); QP_ARR(z); QP_ARR(tb); QP_ARR(red);
     float amin[1] = {1.0f};
-    for (int r = threadIdx.x; r < st->L.m; r += NT) {
+    for (int r = threadIdx.x; r < fwd_state.L.m; r += NT) {
       float dsr, dzr, dvr;
       implicit_dir(r, rk, dsr, dzr, dvr);
       if (dsr < 0.f) amin[0] = fminf(amin[0], -s[r] / dsr);
       if (dzr < 0.f) amin[0] = fminf(amin[0], -z[r] / dzr);
       if (store) tb[r] = dvr;
     }
-    block_reduce<NT, 1>(amin, red, parity, OpMin());
+    reduce<1>(amin, red, OpMin());
     return amin[0];
   }
 
-  __device__ __noinline__ float implicit_mu_aff(float rk, float alpha) {
+  static __device__ __noinline__ float implicit_mu_aff(float rk, float alpha) {
     QP_ARR(s); QP_ARR(z); QP_ARR(red);
     float acc[1] = {0.f};
-    for (int r = threadIdx.x; r < st->L.m; r += NT) {
+    for (int r = threadIdx.x; r < fwd_state.L.m; r += NT) {
       float dsr, dzr, dvr;
       implicit_dir(r, rk, dsr, dzr, dvr);
       acc[0] = fmaf(fmaf(alpha, dsr, s[r]), fmaf(alpha, dzr, z[r]), acc[0]);
     }
-    block_reduce<NT, 1>(acc, red, parity, OpSum());
-    return acc[0] / (float)st->L.m;
+    reduce<1>(acc, red, OpSum());
+    return acc[0] / (float)fwd_state.L.m;
   }
 
-  __device__ __noinline__ void implicit_update(float alpha, float rk, float kappa) {
-    const FLayout& L = st->L;
+  static __device__ __noinline__ void implicit_update(float alpha, float rk, float kappa) {
+    const FLayout& L = fwd_state.L;
     QP_ARR(x); QP_ARR(y); QP_ARR(z); QP_ARR(s); QP_ARR(R); QP_ARR(ua); QP_ARR(ub); QP_ARR(tb);
-    const int p = L.p, t = threadIdx.x, a = st->a;
+    const int p = L.p, t = threadIdx.x, a = fwd_state.a;
     const float knew = kappa - alpha * rk;
     for (int i = t; i < L.n; i += NT) x[i] = fmaf(alpha, fmaf(rk, R[L.ldx + i], R[i]), x[i]);
     for (int k = t; k < p; k += NT) y[k] = fmaf(alpha, fmaf(rk, ub[a + k], ua[a + k]), y[k]);
@@ -617,7 +629,7 @@ struct Solver {
 
   // One implicit Newton step (Alg. 1 with predictor-corrector, or Alg. 2 when
   // kt_fixed >= 0).  Returns false on a factorisation failure.
-  __device__ __noinline__ bool implicit_step(const FwdParams& P, float kappa, float kt_fixed) {
+  static __device__ __noinline__ bool implicit_step(const FwdParams& P, float kappa, float kt_fixed) {
     partition();
     implicit_rhs();
     fold_rhs();
@@ -651,14 +663,14 @@ struct Solver {
   // ---- explicit complementarity (ablation): Mehrotra predictor-corrector on
   // eq. 8 in the same two-level form.  For r_c (z.*s, then the corrector term)
   // rhs1 = -r_t + G_I'(-W r_i + r_c/s), rhs2 = (-(r_i - r_c/z)_A, -r_e). ----
-  __device__ __noinline__ bool standard_step(const FwdParams& P, float mu) {
-    const FLayout& L = st->L;
+  static __device__ __noinline__ bool standard_step(const FwdParams& P, float mu) {
+    const FLayout& L = fwd_state.L;
     const int m = L.m, p = L.p, t = threadIdx.x;
     partition();
     QP_ARR(z); QP_ARR(s); QP_ARR(ri); QP_ARR(re); QP_ARR(ta); QP_ARR(tb);
     QP_ARR(ua); QP_ARR(ub); QP_ARR(ea); QP_ARR(eb); QP_ARR(R); QP_ARR(G); QP_ARR(rt);
     QP_ARR(col); QP_ARR(red); QP_ARR(x); QP_ARR(y); QP_IARR(pos); QP_IARR(act);
-    const int a = st->a, nf = st->nf;
+    const int a = fwd_state.a, nf = fwd_state.nf;
     // predictor (slot 0): r_c = z.*s
     for (int r = t; r < m; r += NT) ta[r] = pos[r] < 0 ? -(z[r] / s[r]) * ri[r] + z[r] : 0.f;
     for (int k = t; k < nf; k += NT) ua[k] = k < a ? -(ri[act[k]] - s[act[k]]) : -re[k - a];
@@ -670,8 +682,8 @@ struct Solver {
     }
     if (!factor()) return false;
     // W lives in the factors now: bz / bs serve as ds / dz scratch below
-    float* const rz = sm + st->L.o_bz;
-    float* const rs = sm + st->L.o_bs;
+    float* const rz = fwd_dyn + fwd_state.L.o_bz;
+    float* const rs = fwd_dyn + fwd_state.L.o_bs;
     solve(0, 1);
     g_times_dx(0, 1);
     float amin[1] = {1.0f};
@@ -684,11 +696,11 @@ struct Solver {
       if (dsr < 0.f) amin[0] = fminf(amin[0], -s[r] / dsr);
       if (dzr < 0.f) amin[0] = fminf(amin[0], -z[r] / dzr);
     }
-    block_reduce<NT, 1>(amin, red, parity, OpMin());
+    reduce<1>(amin, red, OpMin());
     const float aa = amin[0];
     float acc[1] = {0.f};
     for (int r = t; r < m; r += NT) acc[0] = fmaf(fmaf(aa, rz[r], s[r]), fmaf(aa, rs[r], z[r]), acc[0]);
-    block_reduce<NT, 1>(acc, red, parity, OpSum());
+    reduce<1>(acc, red, OpSum());
     const float ratio = (acc[0] / (float)m) / mu;
     float sigma = ratio * ratio * ratio;
     if (!(sigma >= 0.f)) sigma = 0.f;
@@ -721,7 +733,7 @@ struct Solver {
       if (dsr < 0.f) amin2[0] = fminf(amin2[0], -s[r] / dsr);
       if (dzr < 0.f) amin2[0] = fminf(amin2[0], -z[r] / dzr);
     }
-    block_reduce<NT, 1>(amin2, red, parity, OpMin());
+    reduce<1>(amin2, red, OpMin());
     const float alpha = fminf(1.0f, 0.99f * amin2[0]);
     for (int i = t; i < L.n; i += NT) x[i] = fmaf(alpha, R[i] + R[L.ldx + i], x[i]);
     for (int k = t; k < p; k += NT) y[k] = fmaf(alpha, ua[a + k] + ub[a + k], y[k]);
@@ -735,8 +747,8 @@ struct Solver {
 
   // CVXOPT-style start: (Q + G'G) x + A'y = -q + G'h, A x = b; z = G x - h, s = -z, shifted.
   // With m = 0 this is the exact solution of the equality-constrained QP.
-  __device__ __noinline__ bool initialize() {
-    const FLayout& L = st->L;
+  static __device__ __noinline__ bool initialize() {
+    const FLayout& L = fwd_state.L;
     const int m = L.m, p = L.p, t = threadIdx.x;
     QP_ARR(bz); QP_ARR(bs); QP_ARR(ua); QP_ARR(b); QP_ARR(h); QP_ARR(R); QP_ARR(G); QP_ARR(col);
     QP_ARR(q); QP_ARR(x); QP_ARR(y); QP_ARR(z); QP_ARR(s); QP_ARR(red);
@@ -764,7 +776,7 @@ struct Solver {
       mx[1] = fmaxf(mx[1], -zr);  // -min(z)
       mx[2] = fmaxf(mx[2], fabsf(zr));
     }
-    block_reduce<NT, 3>(mx, red, parity, OpMax());
+    reduce<3>(mx, red, OpMax());
     const float thr = -1e-8f * fmaxf(1.0f, mx[2]);
     const bool shs = mx[0] >= thr, shz = mx[1] >= thr;
     for (int r = t; r < m; r += NT) {
@@ -776,11 +788,11 @@ struct Solver {
   }
 
   // ---- gradient cache: factors, W, active map and the point (Alg. 3 input) ----
-  __device__ __noinline__ void write_cache(const FwdParams& P, int bi) {
-    const FLayout& L = st->L;
+  static __device__ __noinline__ void write_cache(const FwdParams& P, int bi) {
+    const FLayout& L = fwd_state.L;
     QP_ARR(K); QP_ARR(Y); QP_ARR(C); QP_ARR(ea); QP_ARR(D); QP_ARR(x); QP_ARR(y); QP_ARR(z);
     QP_IARR(pos);
-    const int n = L.n, m = L.m, p = L.p, t = threadIdx.x, a = st->a, nf = st->nf;
+    const int n = L.n, m = L.m, p = L.p, t = threadIdx.x, a = fwd_state.a, nf = fwd_state.nf;
     const CacheLayout cl = cache_layout(n, m, p, L.amax);
     float* c = P.cache + (size_t)bi * (size_t)P.cache_stride;
     if (t == 0) {
@@ -816,8 +828,8 @@ struct Solver {
     __syncthreads();
   }
 
-  __device__ __noinline__ void write_solution(const FwdParams& P, int bi, bool good) {
-    const FLayout& L = st->L;
+  static __device__ __noinline__ void write_solution(const FwdParams& P, int bi, bool good) {
+    const FLayout& L = fwd_state.L;
     QP_ARR(x); QP_ARR(y); QP_ARR(z); QP_ARR(s);
     const int n = L.n, m = L.m, p = L.p, t = threadIdx.x;
     const float nanv = NAN;
@@ -830,8 +842,8 @@ struct Solver {
   }
 
   // ---- whole instance ----
-  __device__ __noinline__ void run(const FwdParams& P, int bi) {
-    const int n = st->L.n, m = st->L.m, p = st->L.p, t = threadIdx.x;
+  static __device__ __noinline__ void run(const FwdParams& P, int bi) {
+    const int n = fwd_state.L.n, m = fwd_state.L.m, p = fwd_state.L.p, t = threadIdx.x;
     const bool implicit = P.formulation == 0;
     int status = ST_SOLVED, iters = 0;
     float meas = NAN;
@@ -850,7 +862,7 @@ struct Solver {
           s[r] = P.s[(size_t)bi * m + r];
           mn[0] = fminf(mn[0], fminf(z[r], s[r]));
         }
-        block_reduce<NT, 1>(mn, red, parity, OpMin());
+        reduce<1>(mn, red, OpMin());
         warm = mn[0] > 0.f;
       }
       if (!warm && !initialize()) status = ST_NUMERICAL;
@@ -858,8 +870,7 @@ struct Solver {
         // equality-only QP: the start is the exact solve; Newton steps on the
         // linear KKT system refine it with the same factorisation
         for (int it = 0; status == ST_SOLVED; ++it) {
-          float kap;
-          meas = residuals(P, implicit, 0, kap);
+          meas = residuals(P, implicit, 0).x;
           if (!(meas == meas)) { status = ST_NUMERICAL; break; }
           if (meas < P.tol || it >= P.max_iter) break;
           QP_ARR(R); QP_ARR(rt); QP_ARR(ua); QP_ARR(re); QP_ARR(x); QP_ARR(y);
@@ -877,8 +888,9 @@ struct Solver {
         float best = INFINITY;
         int since_best = 0;
         for (int it = 0; status == ST_SOLVED; ++it) {
-          float kappa;
-          meas = residuals(P, implicit, 0, kappa);
+          const float2 rk = residuals(P, implicit, 0);
+          const float kappa = rk.y;
+          meas = rk.x;
           if (!(meas == meas)) { status = ST_NUMERICAL; break; }
           if (meas < P.tol) break;
           if (it >= P.max_iter) { status = ST_MAX_ITER; break; }
@@ -897,8 +909,8 @@ struct Solver {
       if (m > 0 && P.kappa_relax > 0.f && status != ST_NUMERICAL) {
         int rstatus = ST_MAX_ITER;
         for (int it = 0;; ++it) {
-          float kappa;
-          const float rm = residuals(P, true, 1, kappa);
+          const float2 rr = residuals(P, true, 1);
+          const float rm = rr.x, kappa = rr.y;
           if (!(rm == rm)) { rstatus = ST_NUMERICAL; break; }
           if (rm < P.relax_tol) {
             // one more (quadratically convergent) Newton step polishes the
@@ -927,7 +939,7 @@ struct Solver {
       // non-finite data: mark the slot unwritten (active count -1) so the
       // backward pass gives NaN gradients instead of reading stale contents
       int* hdr = reinterpret_cast<int*>(P.cache + (size_t)bi * (size_t)P.cache_stride +
-                                        cache_layout(n, m, p, st->L.amax).oHdr);
+                                        cache_layout(n, m, p, fwd_state.L.amax).oHdr);
       hdr[0] = -1;
       hdr[1] = -1;
       hdr[2] = 0;
@@ -950,19 +962,16 @@ template <> struct MinBlocks<256> { static constexpr int value = 3; };
 
 template <int NT>
 __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) qp_forward_kernel(const FwdParams P) {
-  extern __shared__ __align__(16) float sm[];
-  __shared__ SharedState st;
   // the phases take the parameters by reference: keep them in shared memory
   // rather than letting each thread copy the whole block to local memory
   __shared__ FwdParams sP;
   if (threadIdx.x == 0) sP = P;
-  Solver<NT> slv;
-  slv.bind(sm, &st, P.n, P.m, P.p, P.amax);  // ends with a barrier
+  Solver<NT>::init(P.n, P.m, P.p, P.amax);  // ends with a barrier
 #ifdef QP_PHASE_TIMERS
-  if (threadIdx.x == 0) st.timers = P.timers;
+  if (threadIdx.x == 0) fwd_state.timers = P.timers;
   __syncthreads();
 #endif
-  slv.run(sP, blockIdx.x);
+  Solver<NT>::run(sP, blockIdx.x);
 }
 
 }  // namespace fwd
