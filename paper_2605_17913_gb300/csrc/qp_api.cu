@@ -5,7 +5,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-#include "../../include/qp.h"
+#include "qp.h"
 #include "qp_internal.h"
 
 using namespace qpgpu;
