@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--tol", type=float, default=5e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    # implicit vs standard complementarity in FP32 over a tolerance sweep
+    # (one JSON line per formulation and tolerance instead of the bench line)
+    ap.add_argument("--ablation", action="store_true")
     return ap.parse_args()
 
 
@@ -360,8 +363,68 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- ablation sweep
+def run_ablation(args):
+    """Implicit vs standard complementarity, both in FP32, on one batch of the
+    workload, at solve tolerances 1e-2 .. 1e-8 (forward only, no relax).
+    Below the FP32 floor (about 1e-6 here) the sweep shows how each method
+    stops: stalled, iteration cap or numerical failure."""
+    import torch
+
+    from paper_2605_17913_gb300.metrics import kkt_report, rel_err_inf
+    from paper_2605_17913_gb300.solver import QPSolver
+    from qpgen import CONFIGS, make_batch
+
+    torch.cuda.set_device(0)
+    import __graft_entry__ as ge
+
+    ge.build()
+    B = args.batch or CONFIGS[args.workload]["batch"]
+    data = make_batch(args.workload, B, seed=0)
+    names = ("Q", "q", "A", "b", "G", "h")
+    T = {k: torch.from_numpy(getattr(data, k)).cuda() for k in names}
+    slv = QPSolver(B, data.n, data.p, data.m)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    for form in ("implicit", "standard"):
+        for tol in (1e-2, 1e-3, 1e-4, 1e-5, 1e-6, 1e-7, 1e-8):
+            ms = []
+            for rep in range(4):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                out = slv.solve(*(T[k] for k in names), tol=tol, formulation=form)
+                e1.record()
+                torch.cuda.synchronize()
+                if rep > 0:
+                    ms.append(e0.elapsed_time(e1))
+            r = {k: v.cpu().numpy() for k, v in out.items()}
+            st, it = r["status"], r["iters"]
+            rep = kkt_report(data.Q, data.q, data.A, data.b, data.G, data.h, r["x"], r["y"],
+                             r["z"], r["s"])
+            finite = np.isfinite(r["x"]).all(axis=1)
+            xerr = rel_err_inf(r["x"][finite], data.x0[finite]) if finite.any() else np.array([])
+            fwd = statistics.median(ms)
+            line = {
+                "ablation": "complementarity", "workload": args.workload, "batch": B,
+                "formulation": form, "tol": tol, "dtype": "f32",
+                "solved": float(np.mean(st == 0)), "stalled": float(np.mean(st == 2)),
+                "max_iter": float(np.mean(st == 1)), "numerical": float(np.mean(st == 3)),
+                "nan_rate": float(np.mean(~finite)),
+                "iters_median": float(np.median(it)), "iters_p95": float(np.percentile(it, 95)),
+                "kkt_scaled_median": float(np.median(rep["scaled"])),
+                "kkt_scaled_max": float(np.max(rep["scaled"])),
+                "x_err_median": float(np.median(xerr)) if xerr.size else None,
+                "x_err_max": float(np.max(xerr)) if xerr.size else None,
+                "forward_ms": fwd, "solves_per_s": float(np.sum(st == 0)) / (fwd / 1e3),
+            }
+            print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.ablation:
+        run_ablation(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

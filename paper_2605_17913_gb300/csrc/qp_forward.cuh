@@ -957,7 +957,7 @@ struct Solver {
 
 // minimum resident CTAs per SM the register budget is sized for
 template <int NT> struct MinBlocks { static constexpr int value = 1; };
-template <> struct MinBlocks<128> { static constexpr int value = 4; };
+template <> struct MinBlocks<128> { static constexpr int value = 3; };
 template <> struct MinBlocks<256> { static constexpr int value = 3; };
 
 template <int NT>
