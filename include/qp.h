@@ -6,11 +6,15 @@
  *   Problem (eq. 1):  minimise 1/2 x'Qx + q'x  subject to  A x = b,  G x <= h.
  *   Complementarity is kept on the manifold z .* s = kappa by the softplus
  *   retraction z = b_k(v), s = b_k(-v) (eq. 9-11, App. C); each Newton step
- *   solves eq. 14, here by eliminating dv into K = Q + G' diag(W) G with
- *   W = B_k(v)/B_k(-v), a Cholesky factor of K and the range-space Schur
- *   complement A K^-1 A' of the equality block (Alg. 1), then takes eq. 7's
- *   step length and retracts.  Gradients follow Alg. 2 (relax to kappa_relax)
- *   and Alg. 3 (implicit-function-theorem adjoint with the cached factor).
+ *   solves eq. 14 by a two-level elimination that keeps every pivot bounded:
+ *   rows with W = B_k(v)/B_k(-v) <= tau are eliminated into
+ *   K_I = Q + G_I' W_I G_I, the others stay as scaled multipliers beside the
+ *   equality rows; K_I and the Schur complement C = D + Y Y' (Y = F L^-T,
+ *   F = [G_A; A]) are Cholesky-factored in FP32.  The predictor and
+ *   corrector share that factorisation, eq. 7 gives the step length, and the
+ *   iterate is retracted (Alg. 1).  Gradients follow Alg. 2 (relax to
+ *   kappa_relax) and Alg. 3 (implicit-function-theorem adjoint with the
+ *   cached factors).
  *
  * Letters: n variables, n_eq equality rows (A, b), n_ineq inequality rows
  * (G, h).  (The paper writes m for the equality count and p for the
@@ -29,8 +33,11 @@
  *   - Return value: QP_OK or a negative QP_E* code.  Argument errors are
  *     detected on the host before anything is enqueued.  Per-instance
  *     outcomes are written to status[] on the device.
- *   - A handle holds only launch configuration for one problem size; it owns
- *     no device memory, so one handle may serve several streams at once.
+ *   - A handle holds launch configuration for one problem size.  Sizes that
+ *     fit one SM's shared memory need no other device memory, so one handle
+ *     may serve several streams at once.  Larger sizes (up to n = 256) run a
+ *     variant whose matrices live in a device workspace the handle owns
+ *     (qp_workspace_bytes); calls through such a handle must not overlap.
  *     The factor cache that the backward pass reuses is caller-owned device
  *     memory (qp_grad_cache_bytes), which keeps each forward/backward pair
  *     independent of any other.
@@ -89,7 +96,9 @@ typedef struct {
   float kappa_min;      /* floor on kappa_target (0: 1e-2 * tol)                    */
   float kappa_relax;    /* central-path parameter of the gradients (Alg. 2); 0:
                            gradients at the solution itself                         */
-  float relax_tol;      /* Alg. 2 stop tolerance (0: tol / 10)                      */
+  float relax_tol;      /* Alg. 2 stop tolerance (0: tol / 10); a relaxed measure
+                           below tol that has stopped decreasing for 3 iterations
+                           (the FP32 floor) also ends the relax                     */
   int32_t relax_max_iter; /* Alg. 2 iteration cap (0: max_iter)                     */
   int32_t formulation;  /* QP_IMPLICIT or QP_STANDARD                               */
   int32_t residual_norm; /* QP_NORM_*                                               */
@@ -109,22 +118,32 @@ typedef struct qp_handle qp_handle;
 void qp_settings_default(qp_settings* s);
 
 /* Create a solver handle for batches of the given size on the current
- * device.  Allocates no device memory.  Returns QP_EINVAL (bad dims),
- * QP_ENOTSUP (size too large for this build) or QP_ECUDA. */
+ * device.  Allocates device memory only for sizes beyond one SM's shared
+ * memory: the workspace of qp_workspace_bytes.  Supported: n <= 256.
+ * Returns QP_EINVAL (bad dims), QP_ENOTSUP (size too large for this build),
+ * QP_ENOMEM (workspace allocation failed) or QP_ECUDA. */
 int qp_handle_create(const qp_dims* dims, qp_handle** out);
 
-/* Free the handle (host memory only). */
+/* Free the handle and its workspace, if any. */
 int qp_handle_destroy(qp_handle* h);
 
 /* Bytes of device memory the gradient cache of one solve needs: per
- * instance n(n+1)/2 floats of the Cholesky factor L of Q + G'WG, n_eq*n of
- * U' = L^-1 A', n_eq(n_eq+1)/2 of the factor of U'U, n_ineq of W and the
- * relaxed point (x, y, z), each block padded to 16 bytes. */
+ * instance a header, the Cholesky factor L of K_I = Q + G_I'W_I G_I (packed
+ * lower; unpacked for the large-problem variant), Y = F L^-T with
+ * F = [G_A; A] (nf = active rows + n_eq rows), the factor of
+ * C = D + Y Y' (packed lower; unpacked for the large variant), W (or 1/W),
+ * the active-row map and the relaxed point (x, y, z), each block padded to
+ * 16 bytes. */
 size_t qp_grad_cache_bytes(const qp_dims* dims);
 
 /* Per-instance shared memory the solve kernel uses, in bytes (0 if the
  * size is unsupported); for capacity planning. */
 size_t qp_smem_bytes(int32_t n, int32_t n_eq, int32_t n_ineq);
+
+/* Bytes of device workspace a handle of these dims allocates: 0 when the
+ * problem fits one SM's shared memory, else batch x (K, G, A, Y, C of one
+ * instance) for the large-problem variant. */
+size_t qp_workspace_bytes(const qp_dims* dims);
 
 /* Solve the batch (Alg. 1).  If grad_cache is not NULL (device memory of
  * qp_grad_cache_bytes, 16-byte aligned), also relax each solution to

@@ -76,6 +76,8 @@ def lib() -> ctypes.CDLL:
     L.qp_handle_create.argtypes = [ctypes.POINTER(Dims), ctypes.POINTER(vp)]
     L.qp_grad_cache_bytes.restype = ctypes.c_size_t
     L.qp_grad_cache_bytes.argtypes = [ctypes.POINTER(Dims)]
+    L.qp_workspace_bytes.restype = ctypes.c_size_t
+    L.qp_workspace_bytes.argtypes = [ctypes.POINTER(Dims)]
     L.qp_handle_destroy.restype = ctypes.c_int
     L.qp_handle_destroy.argtypes = [vp]
     L.qp_solve_batch.restype = ctypes.c_int

@@ -20,6 +20,9 @@ struct qp_handle {
   size_t bwd_smem;
   int amax;
   long long cache_stride;  // floats per instance in the gradient cache
+  bool split;              // large-problem variant (matrices in a global workspace)
+  float* ws;               // its workspace, batch * ws_stride floats (owned)
+  long long ws_stride;
 };
 
 static bool aligned4(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 3) == 0; }
@@ -85,6 +88,13 @@ size_t qp_smem_bytes(int32_t n, int32_t n_eq, int32_t n_ineq) {
   return forward_config(n, n_ineq, n_eq, nullptr, nullptr);
 }
 
+size_t qp_workspace_bytes(const qp_dims* dims) {
+  if (!dims_ok(dims)) return 0;
+  long long ws = 0;
+  if (forward_config(dims->n, dims->n_ineq, dims->n_eq, nullptr, nullptr, &ws) == 0) return 0;
+  return (size_t)dims->batch * (size_t)ws * sizeof(float);
+}
+
 int qp_handle_create(const qp_dims* dims, qp_handle** out) {
   if (!out || !dims_ok(dims)) return QP_EINVAL;
   *out = nullptr;
@@ -92,9 +102,10 @@ int qp_handle_create(const qp_dims* dims, qp_handle** out) {
   if (!h) return QP_ENOMEM;
   h->dims = *dims;
   const int n = dims->n, m = dims->n_ineq, p = dims->n_eq;
-  h->fwd_smem = forward_config(n, m, p, &h->fwd_threads, &h->amax);
-  h->bwd_smem = backward_smem_bytes(n, m, p, h->amax, &h->bwd_threads);
-  h->cache_stride = cache_layout(n, m, p, h->amax).stride;
+  h->fwd_smem = forward_config(n, m, p, &h->fwd_threads, &h->amax, &h->ws_stride);
+  h->split = h->ws_stride > 0;
+  h->bwd_smem = backward_smem_bytes(n, m, p, h->amax, h->split, &h->bwd_threads);
+  h->cache_stride = cache_layout(n, m, p, h->amax, h->split).stride;
   if (h->fwd_smem == 0 || h->bwd_smem == 0) {
     free(h);
     return QP_ENOTSUP;
@@ -106,11 +117,19 @@ int qp_handle_create(const qp_dims* dims, qp_handle** out) {
     free(h);
     return QP_ECUDA;
   }
-  h->fwd_blocks_per_sm = forward_blocks_per_sm(h->fwd_threads, h->fwd_smem);
+  h->fwd_blocks_per_sm = forward_blocks_per_sm(h->fwd_threads, h->fwd_smem, h->split);
   if (h->fwd_blocks_per_sm < 1) {
     cudaGetLastError();
     free(h);
     return QP_ENOTSUP;
+  }
+  if (h->split && dims->batch > 0) {
+    const size_t bytes = (size_t)dims->batch * (size_t)h->ws_stride * sizeof(float);
+    if (cudaMalloc((void**)&h->ws, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      free(h);
+      return QP_ENOMEM;
+    }
   }
   *out = h;
   return QP_OK;
@@ -118,6 +137,7 @@ int qp_handle_create(const qp_dims* dims, qp_handle** out) {
 
 int qp_handle_destroy(qp_handle* h) {
   if (!h) return QP_EINVAL;
+  if (h->ws) cudaFree(h->ws);
   free(h);
   return QP_OK;
 }
@@ -125,9 +145,11 @@ int qp_handle_destroy(qp_handle* h) {
 size_t qp_grad_cache_bytes(const qp_dims* dims) {
   if (!dims_ok(dims)) return 0;
   int amax = 0;
-  if (forward_config(dims->n, dims->n_ineq, dims->n_eq, nullptr, &amax) == 0) return 0;
+  long long ws = 0;
+  if (forward_config(dims->n, dims->n_ineq, dims->n_eq, nullptr, &amax, &ws) == 0) return 0;
   return (size_t)dims->batch *
-         (size_t)cache_layout(dims->n, dims->n_ineq, dims->n_eq, amax).stride * sizeof(float);
+         (size_t)cache_layout(dims->n, dims->n_ineq, dims->n_eq, amax, ws > 0).stride *
+         sizeof(float);
 }
 
 int qp_solve_batch(qp_handle* h, const qp_settings* st, const float* Q, const float* q,
@@ -171,6 +193,8 @@ int qp_solve_batch(qp_handle* h, const qp_settings* st, const float* Q, const fl
   P.refine_steps = st->refine_steps;
   P.cache = grad_cache;
   P.cache_stride = h->cache_stride;
+  P.ws = h->ws;
+  P.ws_stride = h->ws_stride;
 #ifdef QP_PHASE_TIMERS
   P.timers = g_phase_counters;
 #endif
@@ -197,6 +221,7 @@ int qp_backward_batch(qp_handle* h, const float* grad_cache, const float* Q, con
     if (ptr && !aligned4(ptr)) return QP_EINVAL;
   BwdParams P;
   P.batch = B; P.n = n; P.m = m; P.p = p; P.amax = h->amax;
+  P.split = h->split ? 1 : 0;
   P.Q = Q; P.A = A; P.G = G; P.g = dl_dx; P.cache = grad_cache; P.cache_stride = h->cache_stride;
   P.dQ = dQ; P.dq = dq; P.dA = p > 0 ? dA : nullptr; P.db = p > 0 ? db : nullptr;
   P.dG = m > 0 ? dG : nullptr; P.dh = m > 0 ? dh : nullptr;

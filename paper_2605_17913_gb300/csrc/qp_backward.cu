@@ -20,6 +20,8 @@
 //   dG = dz x' + z dx',     dh = -dz.
 // One CTA per instance: Q, A, G and the factors are staged in shared memory
 // once; the gradient blocks go out as coalesced 16-byte streaming stores.
+#include <mutex>
+
 #include "qp_device.cuh"
 #include "qp_internal.h"
 
@@ -34,8 +36,10 @@ struct BLayout {
 };
 
 // kStage: Q, G, A copied to shared memory (when they fit), else read from global.
+// global: the large-problem variant, whose factors are read in place from the
+// (unpacked) gradient cache, so K, Y, C take no shared memory.
 __host__ __device__ inline BLayout make_blayout(int n, int m, int p, int amax, int nthreads,
-                                                bool stage) {
+                                                bool stage, bool global = false) {
   BLayout B;
   const int f = amax + p;
   B.ldk = ld_odd(n);
@@ -46,9 +50,9 @@ __host__ __device__ inline BLayout make_blayout(int n, int m, int p, int amax, i
   B.fv = round4(f > 0 ? f : 1);
   int o = 0;
   auto take = [&](int c) -> int { int r = o; o += round4(c); return r; };
-  B.oK = take(n * B.ldk);
-  B.oY = take(f * B.ldk);
-  B.oC = take(f * B.ldc);
+  B.oK = take(global ? 0 : n * B.ldk);
+  B.oY = take(global ? 0 : f * B.ldk);
+  B.oC = take(global ? 0 : f * B.ldc);
   B.oQ = take(stage ? n * B.ldg : 0);
   B.oG = take(stage ? m * B.ldg : 0);
   B.oA = take(stage ? p * B.ldg : 0);
@@ -132,13 +136,14 @@ __device__ void warp_rows_dot(const float* M, int ld, int rows, int cols, const 
 }
 
 // Solve [K_I F'; F -D] (d, t) = (r1, r2) with the cached factors: r1 in R
-// (row 0), r2 in t; the solution overwrites both.
-template <int NT>
+// (row 0), r2 in t; the solution overwrites both.  kMaxS: warp-solve length
+// bound in units of 32 rows (4 on chip, 8 for the large variant).
+template <int NT, int kMaxS>
 __device__ void two_level_solve(const float* K, int ldk, const float* dinv, const float* Y,
                                 const float* C, int ldc, const float* cdinv, int n, int nf,
                                 float* R, int ldx, float* t) {
   const int tid = threadIdx.x;
-  solve_rows<NT, false>(K, ldk, dinv, n, R, ldx, 0, 1);
+  solve_rows<NT, false, kMaxS>(K, ldk, dinv, n, R, ldx, 0, 1);
   if (nf > 0) {
     for (int k = tid; k < nf; k += NT) {
       float acc = 0.f;
@@ -150,7 +155,13 @@ __device__ void two_level_solve(const float* K, int ldk, const float* dinv, cons
       if (nf <= 32) small_chol_solve<1>(C, ldc, cdinv, nf, t);
       else if (nf <= 64) small_chol_solve<2>(C, ldc, cdinv, nf, t);
       else if (nf <= 96) small_chol_solve<3>(C, ldc, cdinv, nf, t);
-      else small_chol_solve<4>(C, ldc, cdinv, nf, t);
+      else if (kMaxS <= 4 || nf <= 128) small_chol_solve<4>(C, ldc, cdinv, nf, t);
+      else if constexpr (kMaxS > 4) {
+        if (nf <= 160) small_chol_solve<5>(C, ldc, cdinv, nf, t);
+        else if (nf <= 192) small_chol_solve<6>(C, ldc, cdinv, nf, t);
+        else if (nf <= 224) small_chol_solve<7>(C, ldc, cdinv, nf, t);
+        else small_chol_solve<8>(C, ldc, cdinv, nf, t);
+      }
     }
     __syncthreads();
     for (int i = tid; i < n; i += NT) {
@@ -160,20 +171,23 @@ __device__ void two_level_solve(const float* K, int ldk, const float* dinv, cons
     }
     __syncthreads();
   }
-  solve_rows<NT, true>(K, ldk, dinv, n, R, ldx, 0, 1);
+  solve_rows<NT, true, kMaxS>(K, ldk, dinv, n, R, ldx, 0, 1);
 }
 
-template <int NT, bool kStage>
+template <int NT, bool kStage, bool kGlobal>
 __global__ void __launch_bounds__(NT) qp_backward_kernel(const BwdParams P) {
   extern __shared__ __align__(16) float sm[];
   const int n = P.n, m = P.m, p = P.p, t = threadIdx.x;
   const int bi = blockIdx.x;
-  const BLayout B = make_blayout(n, m, p, P.amax, NT, kStage);
-  const CacheLayout cl = cache_layout(n, m, p, P.amax);
+  const BLayout B = make_blayout(n, m, p, P.amax, NT, kStage, kGlobal);
+  const CacheLayout cl = cache_layout(n, m, p, P.amax, kGlobal);
   const float* c = P.cache + (size_t)bi * (size_t)P.cache_stride;
-  float* K = sm + B.oK;
-  float* Y = sm + B.oY;
-  float* C = sm + B.oC;
+  // the factors: staged in shared memory, or (large variant) read in place
+  float* K = kGlobal ? const_cast<float*>(c + cl.oL) : sm + B.oK;
+  float* Y = kGlobal ? const_cast<float*>(c + cl.oY) : sm + B.oY;
+  float* C = kGlobal ? const_cast<float*>(c + cl.oLC) : sm + B.oC;
+  const int ldk = kGlobal ? cl.ldk : B.ldk;
+  const int ldc = kGlobal ? cl.ldc : B.ldc;
   float* Qs = sm + B.oQ;
   float* Gs = sm + B.oG;
   float* As = sm + B.oA;
@@ -227,24 +241,30 @@ __global__ void __launch_bounds__(NT) qp_backward_kernel(const BwdParams P) {
   const float* Gm = kStage ? Gs : gG;
   const float* Am = kStage ? As : gA;
   const int ldm = kStage ? B.ldg : n;
-  const int nl = n * (n + 1) / 2;
-  for (int e2 = t; e2 < nl; e2 += NT) {
-    const int i = tri_row(e2), j = e2 - i * (i + 1) / 2;
-    const float v = __ldg(c + cl.oL + e2);
-    K[i * B.ldk + j] = v;
-    if (i == j) dinv[i] = 1.0f / v;
-  }
   const int nfl = valid ? nf : 0;
-  for (int e2 = t; e2 < nfl * n; e2 += NT) {
-    const int k = e2 / n, i = e2 - k * n;
-    Y[k * B.ldk + i] = __ldg(c + cl.oY + e2);
-  }
-  const int fl = nfl * (nfl + 1) / 2;
-  for (int e2 = t; e2 < fl; e2 += NT) {
-    const int i = tri_row(e2), j = e2 - i * (i + 1) / 2;
-    const float v = __ldg(c + cl.oLC + e2);
-    C[i * B.ldc + j] = v;
-    if (i == j) cdinv[i] = 1.0f / v;
+  if (kGlobal) {
+    // factors stay in the cache: only the reciprocal pivots go to shared memory
+    for (int i = t; i < n; i += NT) dinv[i] = 1.0f / __ldg(c + cl.oL + i * ldk + i);
+    for (int i = t; i < nfl; i += NT) cdinv[i] = 1.0f / __ldg(c + cl.oLC + i * ldc + i);
+  } else {
+    const int nl = n * (n + 1) / 2;
+    for (int e2 = t; e2 < nl; e2 += NT) {
+      const int i = tri_row(e2), j = e2 - i * (i + 1) / 2;
+      const float v = __ldg(c + cl.oL + e2);
+      K[i * ldk + j] = v;
+      if (i == j) dinv[i] = 1.0f / v;
+    }
+    for (int e2 = t; e2 < nfl * n; e2 += NT) {
+      const int k = e2 / n, i = e2 - k * n;
+      Y[k * ldk + i] = __ldg(c + cl.oY + e2);
+    }
+    const int fl = nfl * (nfl + 1) / 2;
+    for (int e2 = t; e2 < fl; e2 += NT) {
+      const int i = tri_row(e2), j = e2 - i * (i + 1) / 2;
+      const float v = __ldg(c + cl.oLC + e2);
+      C[i * ldc + j] = v;
+      if (i == j) cdinv[i] = 1.0f / v;
+    }
   }
   for (int i = t; i < n; i += NT) {
     xs[i] = __ldg(c + cl.ox + i);
@@ -273,7 +293,7 @@ __global__ void __launch_bounds__(NT) qp_backward_kernel(const BwdParams P) {
     return;
   }
   // ---- adjoint solve, then refinement against the bounded system ----
-  two_level_solve<NT>(K, B.ldk, dinv, Y, C, B.ldc, cdinv, n, nf, R, B.ldx, mu);
+  two_level_solve<NT, kGlobal ? 8 : 4>(K, ldk, dinv, Y, C, ldc, cdinv, n, nf, R, B.ldx, mu);
   float* dx = R + B.ldx;  // accumulated solution; R row 0 is the work row
   for (int i = t; i < n; i += NT) dx[i] = R[i];
   __syncthreads();
@@ -303,7 +323,7 @@ __global__ void __launch_bounds__(NT) qp_backward_kernel(const BwdParams P) {
       }
     }
     __syncthreads();
-    two_level_solve<NT>(K, B.ldk, dinv, Y, C, B.ldc, cdinv, n, nf, R, B.ldx, dmu);
+    two_level_solve<NT, kGlobal ? 8 : 4>(K, ldk, dinv, Y, C, ldc, cdinv, n, nf, R, B.ldx, dmu);
     for (int i = t; i < n; i += NT) dx[i] += R[i];
     for (int k = t; k < nf; k += NT) mu[k] += dmu[k];
     __syncthreads();
@@ -339,8 +359,14 @@ __global__ void __launch_bounds__(NT) qp_backward_kernel(const BwdParams P) {
 
 }  // namespace
 
-size_t backward_smem_bytes(int n, int m, int p, int amax, int* nthreads) {
+size_t backward_smem_bytes(int n, int m, int p, int amax, bool split, int* nthreads) {
   if (nthreads) *nthreads = 256;
+  if (split) {
+    if (n > 256 || amax + p > 256) return 0;
+    const size_t bytes =
+        (size_t)make_blayout(n, m, p, amax, 256, false, true).total * sizeof(float);
+    return bytes <= 227 * 1024 ? bytes : 0;
+  }
   if (n > 128 || amax + p > 128) return 0;
   const size_t staged = (size_t)make_blayout(n, m, p, amax, 256, true).total * sizeof(float);
   if (staged <= 227 * 1024) return staged;
@@ -348,26 +374,26 @@ size_t backward_smem_bytes(int n, int m, int p, int amax, int* nthreads) {
   return direct <= 227 * 1024 ? direct : 0;
 }
 
+template <bool kStage, bool kGlobal>
+cudaError_t launch_backward_v(const BwdParams& P, size_t smem, cudaStream_t st) {
+  static std::once_flag once;
+  static cudaError_t set = cudaSuccess;
+  std::call_once(once, [] {
+    set = cudaFuncSetAttribute(qp_backward_kernel<256, kStage, kGlobal>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  });
+  if (set != cudaSuccess) return set;
+  qp_backward_kernel<256, kStage, kGlobal><<<P.batch, 256, smem, st>>>(P);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_backward(const BwdParams& P, int nthreads, size_t smem, cudaStream_t st) {
   if (nthreads != 256) return cudaErrorInvalidValue;
+  if (P.split) return launch_backward_v<false, true>(P, smem, st);
   const bool stage =
       (size_t)make_blayout(P.n, P.m, P.p, P.amax, 256, true).total * sizeof(float) == smem;
-  static bool configured[2] = {false, false};
-  if (!configured[stage]) {
-    cudaError_t e = stage ? cudaFuncSetAttribute(qp_backward_kernel<256, true>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 227 * 1024)
-                          : cudaFuncSetAttribute(qp_backward_kernel<256, false>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 227 * 1024);
-    if (e != cudaSuccess) return e;
-    configured[stage] = true;
-  }
-  if (stage)
-    qp_backward_kernel<256, true><<<P.batch, 256, smem, st>>>(P);
-  else
-    qp_backward_kernel<256, false><<<P.batch, 256, smem, st>>>(P);
-  return cudaGetLastError();
+  return stage ? launch_backward_v<true, false>(P, smem, st)
+               : launch_backward_v<false, false>(P, smem, st);
 }
 
 }  // namespace qpgpu

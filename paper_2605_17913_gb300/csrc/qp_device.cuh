@@ -577,7 +577,9 @@ __device__ void solve_rows_S(const float* L, int ldk, const float* dinv, int n, 
   }
 }
 
-template <int NT, bool kUpper>
+// kMaxS: 4 (n <= 128) or 8 (n <= 256; only the large-problem variant
+// instantiates the longer register arrays).
+template <int NT, bool kUpper, int kMaxS = 4>
 __device__ void solve_rows(const float* L, int ldk, const float* dinv, int n, float* X, int ldx,
                            int row0, int nrows) {
   if (n <= 32)
@@ -586,8 +588,18 @@ __device__ void solve_rows(const float* L, int ldk, const float* dinv, int n, fl
     solve_rows_S<NT, 2, kUpper>(L, ldk, dinv, n, X, ldx, row0, nrows);
   else if (n <= 96)
     solve_rows_S<NT, 3, kUpper>(L, ldk, dinv, n, X, ldx, row0, nrows);
-  else
+  else if (kMaxS <= 4 || n <= 128)
     solve_rows_S<NT, 4, kUpper>(L, ldk, dinv, n, X, ldx, row0, nrows);
+  else if constexpr (kMaxS > 4) {
+    if (n <= 160)
+      solve_rows_S<NT, 5, kUpper>(L, ldk, dinv, n, X, ldx, row0, nrows);
+    else if (n <= 192)
+      solve_rows_S<NT, 6, kUpper>(L, ldk, dinv, n, X, ldx, row0, nrows);
+    else if (n <= 224)
+      solve_rows_S<NT, 7, kUpper>(L, ldk, dinv, n, X, ldx, row0, nrows);
+    else
+      solve_rows_S<NT, 8, kUpper>(L, ldk, dinv, n, X, ldx, row0, nrows);
+  }
   __syncthreads();
 }
 

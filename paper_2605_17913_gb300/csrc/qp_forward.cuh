@@ -43,6 +43,8 @@
 // Register budget: the layout lives in shared memory and each method forms
 // only the addresses it uses, so that no pointer stays live across phases.
 #pragma once
+#include <mutex>
+
 #include "qp_device.cuh"
 #include "qp_internal.h"
 
@@ -57,6 +59,8 @@ constexpr int kStaticSmem = 1024;  // upper bound of the kernel's static shared 
 struct FLayout {
   int n, m, p, amax, fmax;
   int ldk, ldg, ldx, ldc, nv, mv, pv, fv;
+  int split;      // K, G, A, Y, C in a global workspace (large problems)
+  int big_total;  // floats of K, G, A, Y, C
   int o_K, o_qd, o_G, o_A, o_Y, o_C, o_R, o_col, o_red, o_Pb;
   int o_q, o_x, o_rt, o_dinv, o_tn;
   int o_b, o_y, o_re;
@@ -70,7 +74,8 @@ struct FLayout {
 // are dead there.
 // Y and C carry two extra rows: the right-hand sides folded into the
 // factorisation of an implicit step.
-__host__ __device__ inline FLayout make_fwd_layout(int n, int m, int p, int amax, int nthreads) {
+__host__ __device__ inline FLayout make_fwd_layout(int n, int m, int p, int amax, int nthreads,
+                                                   bool split = false) {
   FLayout L;
   L.n = n; L.m = m; L.p = p; L.amax = amax; L.fmax = amax + p;
   L.ldk = ld_odd(n);
@@ -81,12 +86,17 @@ __host__ __device__ inline FLayout make_fwd_layout(int n, int m, int p, int amax
   L.fv = round4(L.fmax > 0 ? L.fmax : 1);
   int o = 0;
   auto take = [&](int cnt) -> int { int r = o; o += round4(cnt); return r; };
+  // the five matrices: first in shared memory, or (split) at the start of
+  // the instance's global workspace, with the rest in shared memory from 0
   L.o_K = take(n * L.ldk);
-  L.o_qd = take(L.nv);
   L.o_G = take(m * L.ldg);
   L.o_A = take(p * L.ldg);
   L.o_Y = take((L.fmax + 2) * L.ldk);
   L.o_C = take((L.fmax + 2) * L.ldc);
+  L.split = split ? 1 : 0;
+  L.big_total = o;
+  if (split) o = 0;
+  L.o_qd = take(L.nv);
   L.o_R = take(2 * L.ldx);
   L.o_red = take(2 * (nthreads / 32) * kRedK);
   {
@@ -120,6 +130,7 @@ struct SharedState {
   unsigned long long* timers;      // phase timers only
   int a, nf;         // active rows, rows of F = a + p (set by partition())
   int ni;            // inactive rows (listed in ina)
+  float* gbase;      // base of K, G, A, Y, C: the dynamic shared memory or the workspace
   float qn, bn, hn;  // |q|, |b|, |h| (infinity norms)
 };
 
@@ -149,15 +160,18 @@ extern __shared__ __align__(16) float fwd_dyn[];   // the per-instance layout
 static __shared__ SharedState fwd_state;
 static __shared__ unsigned char fwd_parity[512];   // block_reduce buffer parity, per thread
 
-// address of array `name` in the per-instance shared-memory layout
+// address of array `name` in the per-instance shared-memory layout; QP_BIG for
+// the five matrices, which the large-problem variant keeps in global memory
 #define QP_ARR(name) float* const name = fwd_dyn + fwd_state.L.o_##name
+#define QP_BIG(name) float* const name = (kBig ? fwd_state.gbase : fwd_dyn) + fwd_state.L.o_##name
 #define QP_IARR(name) int* const name = reinterpret_cast<int*>(fwd_dyn + fwd_state.L.o_##name)
 
-template <int NT>
+template <int NT, bool kBig>
 struct Solver {
-  static __device__ void init(int n, int m, int p, int amax) {
+  static __device__ void init(int n, int m, int p, int amax, float* ws) {
     if (threadIdx.x == 0) {
-      fwd_state.L = make_fwd_layout(n, m, p, amax, NT);
+      fwd_state.L = make_fwd_layout(n, m, p, amax, NT, kBig);
+      fwd_state.gbase = kBig ? ws : fwd_dyn;
       fwd_state.a = 0;
       fwd_state.nf = p;
       fwd_state.t_mark = clock64();
@@ -180,8 +194,10 @@ struct Solver {
   static __device__ __noinline__ bool load(const FwdParams& P, int bi) {
     const FLayout& L = fwd_state.L;
     const int n = L.n, m = L.m, p = L.p, t = threadIdx.x;
-    QP_ARR(K); QP_ARR(qd); QP_ARR(G); QP_ARR(A); QP_ARR(q); QP_ARR(b); QP_ARR(h); QP_ARR(red);
+    QP_BIG(K); QP_ARR(qd); QP_BIG(G); QP_BIG(A); QP_ARR(q); QP_ARR(b); QP_ARR(h); QP_ARR(red);
     for (int i = t; i < L.total; i += NT) fwd_dyn[i] = 0.0f;
+    if (kBig)
+      for (int i = t; i < L.big_total; i += NT) fwd_state.gbase[i] = 0.0f;
     __syncthreads();
     const float* gQ = P.Q + (size_t)bi * n * n;
     const float* gG = P.G + (size_t)bi * m * n;
@@ -232,8 +248,8 @@ struct Solver {
   static __device__ __noinline__ void partition() {
     const FLayout& L = fwd_state.L;
     const int m = L.m, p = L.p, n = L.n, t = threadIdx.x, w = t >> 5, lane = t & 31;
-    QP_ARR(bz); QP_ARR(bs); QP_ARR(red); QP_ARR(G); QP_ARR(A); QP_ARR(Y);
-    QP_ARR(C); QP_ARR(D); QP_ARR(ea); QP_IARR(act); QP_IARR(pos); QP_IARR(ina);
+    QP_ARR(bz); QP_ARR(bs); QP_ARR(red); QP_BIG(G); QP_BIG(A); QP_BIG(Y);
+    QP_BIG(C); QP_ARR(D); QP_ARR(ea); QP_IARR(act); QP_IARR(pos); QP_IARR(ina);
     float tau = 1.0f;
     for (int round = 0; round < 40; ++round) {
       float cnt[1] = {0.f};
@@ -285,7 +301,7 @@ struct Solver {
   // the factorisation leaves u = L^-1 r1 in Y and w = L_C^-1 (Y u - rhs2) in C.
   static __device__ void fold_rhs() {
     const FLayout& L = fwd_state.L;
-    QP_ARR(R); QP_ARR(Y); QP_ARR(C); QP_ARR(ua); QP_ARR(ub);
+    QP_ARR(R); QP_BIG(Y); QP_BIG(C); QP_ARR(ua); QP_ARR(ub);
     const int n = L.n, nf = fwd_state.nf, t = threadIdx.x;
     for (int e = t; e < 2 * n; e += NT) {
       const int c = e / n, i = e - c * n;
@@ -303,7 +319,7 @@ struct Solver {
   // nfold = 2): the elimination overwrites them. ----
   static __device__ __noinline__ bool factor_once(float creg, int nfold) {
     const FLayout& L = fwd_state.L;
-    QP_ARR(K); QP_ARR(qd); QP_ARR(G); QP_ARR(ea); QP_ARR(Y); QP_ARR(C); QP_ARR(dinv);
+    QP_BIG(K); QP_ARR(qd); QP_BIG(G); QP_ARR(ea); QP_BIG(Y); QP_BIG(C); QP_ARR(dinv);
     QP_ARR(cdinv); QP_ARR(Pb); QP_ARR(red); QP_IARR(ina);
     const int nf = fwd_state.nf;
     syrk_gwg<NT>(K, L.ldk, qd, G, L.ldg, ea, ina, fwd_state.ni, L.n);
@@ -348,7 +364,7 @@ struct Solver {
   // columns; dx returned in R rows 0, 1 and mu in ua / ub ----
   static __device__ void solve_folded() {
     const FLayout& L = fwd_state.L;
-    QP_ARR(K); QP_ARR(dinv); QP_ARR(R); QP_ARR(Y); QP_ARR(C); QP_ARR(cdinv); QP_ARR(ua);
+    QP_BIG(K); QP_ARR(dinv); QP_ARR(R); QP_BIG(Y); QP_BIG(C); QP_ARR(cdinv); QP_ARR(ua);
     QP_ARR(ub);
     const int n = L.n, t = threadIdx.x, w = t >> 5, nf = fwd_state.nf;
     if (nf > 0) {
@@ -357,10 +373,7 @@ struct Solver {
         const float* wrow = C + (nf + w) * L.ldc;
         for (int k = t & 31; k < nf; k += 32) u[k] = wrow[k];
         __syncwarp();
-        if (nf <= 32) c_solve<1>(u, nf, true);
-        else if (nf <= 64) c_solve<2>(u, nf, true);
-        else if (nf <= 96) c_solve<3>(u, nf, true);
-        else c_solve<4>(u, nf, true);
+        c_solve_n(u, nf, true);
       }
       __syncthreads();
     }
@@ -372,14 +385,28 @@ struct Solver {
       R[c * L.ldx + i] = acc;
     }
     __syncthreads();
-    solve_rows<NT, true>(K, L.ldk, dinv, n, R, L.ldx, 0, 2);
+    solve_rows<NT, true, kBig ? 8 : 4>(K, L.ldk, dinv, n, R, L.ldx, 0, 2);
     QP_MARK(PH_SOLVE);
+  }
+
+  // warp solve with C for nf rows (up to 128 on chip, 256 in the large variant)
+  static __device__ void c_solve_n(float* u, int nf, bool upper_only) {
+    if (nf <= 32) c_solve<1>(u, nf, upper_only);
+    else if (nf <= 64) c_solve<2>(u, nf, upper_only);
+    else if (nf <= 96) c_solve<3>(u, nf, upper_only);
+    else if (!kBig || nf <= 128) c_solve<4>(u, nf, upper_only);
+    else if constexpr (kBig) {
+      if (nf <= 160) c_solve<5>(u, nf, upper_only);
+      else if (nf <= 192) c_solve<6>(u, nf, upper_only);
+      else if (nf <= 224) c_solve<7>(u, nf, upper_only);
+      else c_solve<8>(u, nf, upper_only);
+    }
   }
 
   template <int SP>
   static __device__ void c_solve(float* v, int nf, bool upper_only = false) {
     const FLayout& L = fwd_state.L;
-    QP_ARR(C); QP_ARR(cdinv);
+    QP_BIG(C); QP_ARR(cdinv);
     const int lane = threadIdx.x & 31;
     float r[1][SP];
 #pragma unroll
@@ -400,9 +427,9 @@ struct Solver {
   // rhs1 in R rows, rhs2 in ua (column 0) / ub (column 1); dx returned in R, mu in ua / ub.
   static __device__ __noinline__ void solve(int slot0, int nrhs) {
     const FLayout& L = fwd_state.L;
-    QP_ARR(K); QP_ARR(dinv); QP_ARR(R); QP_ARR(Y); QP_ARR(ua); QP_ARR(ub);
+    QP_BIG(K); QP_ARR(dinv); QP_ARR(R); QP_BIG(Y); QP_ARR(ua); QP_ARR(ub);
     const int n = L.n, t = threadIdx.x, w = t >> 5, nf = fwd_state.nf;
-    solve_rows<NT, false>(K, L.ldk, dinv, n, R, L.ldx, slot0, nrhs);
+    solve_rows<NT, false, kBig ? 8 : 4>(K, L.ldk, dinv, n, R, L.ldx, slot0, nrhs);
     if (nf > 0) {
       for (int e = t; e < nf * nrhs; e += NT) {
         const int k = e % nf, cc = slot0 + e / nf;
@@ -416,10 +443,7 @@ struct Solver {
       __syncthreads();
       if (w < nrhs) {
         float* u = (slot0 + w) == 0 ? ua : ub;
-        if (nf <= 32) c_solve<1>(u, nf);
-        else if (nf <= 64) c_solve<2>(u, nf);
-        else if (nf <= 96) c_solve<3>(u, nf);
-        else c_solve<4>(u, nf);
+        c_solve_n(u, nf, false);
       }
       __syncthreads();
       for (int e = t; e < n * nrhs; e += NT) {
@@ -431,14 +455,14 @@ struct Solver {
       }
       __syncthreads();
     }
-    solve_rows<NT, true>(K, L.ldk, dinv, n, R, L.ldx, slot0, nrhs);
+    solve_rows<NT, true, kBig ? 8 : 4>(K, L.ldk, dinv, n, R, L.ldx, slot0, nrhs);
     QP_MARK(PH_SOLVE);
   }
 
   // e = G dx for the solved columns (ea for column 0, eb for column 1)
   static __device__ __noinline__ void g_times_dx(int slot0, int nrhs) {
     const FLayout& L = fwd_state.L;
-    QP_ARR(G); QP_ARR(R); QP_ARR(ea); QP_ARR(eb);
+    QP_BIG(G); QP_ARR(R); QP_ARR(ea); QP_ARR(eb);
     for (int r = threadIdx.x; r < L.m; r += NT) {
       if (nrhs == 2) {
         float u, v;
@@ -459,7 +483,7 @@ struct Solver {
   static __device__ __noinline__ float2 residuals(const FwdParams& P, bool implicit, int mode) {
     const FLayout& L = fwd_state.L;
     const int n = L.n, m = L.m, p = L.p, t = threadIdx.x;
-    QP_ARR(K); QP_ARR(qd); QP_ARR(G); QP_ARR(A); QP_ARR(q); QP_ARR(b); QP_ARR(h); QP_ARR(x);
+    QP_BIG(K); QP_ARR(qd); QP_BIG(G); QP_BIG(A); QP_ARR(q); QP_ARR(b); QP_ARR(h); QP_ARR(x);
     QP_ARR(y); QP_ARR(z); QP_ARR(s); QP_ARR(rt); QP_ARR(re); QP_ARR(ri);
     QP_ARR(bz); QP_ARR(bs); QP_ARR(tn); QP_ARR(red); QP_ARR(col);
     float ks[1] = {0.f};
@@ -535,7 +559,7 @@ struct Solver {
   static __device__ __noinline__ void implicit_rhs() {
     const FLayout& L = fwd_state.L;
     QP_ARR(bz); QP_ARR(bs); QP_ARR(z); QP_ARR(s); QP_ARR(ri); QP_ARR(re); QP_ARR(ta);
-    QP_ARR(tb); QP_ARR(ua); QP_ARR(ub); QP_ARR(R); QP_ARR(G); QP_ARR(rt); QP_ARR(col);
+    QP_ARR(tb); QP_ARR(ua); QP_ARR(ub); QP_ARR(R); QP_BIG(G); QP_ARR(rt); QP_ARR(col);
     QP_IARR(pos); QP_IARR(act);
     const int m = L.m, t = threadIdx.x, a = fwd_state.a, nf = fwd_state.nf;
     for (int r = t; r < m; r += NT) {
@@ -668,7 +692,7 @@ struct Solver {
     const int m = L.m, p = L.p, t = threadIdx.x;
     partition();
     QP_ARR(z); QP_ARR(s); QP_ARR(ri); QP_ARR(re); QP_ARR(ta); QP_ARR(tb);
-    QP_ARR(ua); QP_ARR(ub); QP_ARR(ea); QP_ARR(eb); QP_ARR(R); QP_ARR(G); QP_ARR(rt);
+    QP_ARR(ua); QP_ARR(ub); QP_ARR(ea); QP_ARR(eb); QP_ARR(R); QP_BIG(G); QP_ARR(rt);
     QP_ARR(col); QP_ARR(red); QP_ARR(x); QP_ARR(y); QP_IARR(pos); QP_IARR(act);
     const int a = fwd_state.a, nf = fwd_state.nf;
     // predictor (slot 0): r_c = z.*s
@@ -750,7 +774,7 @@ struct Solver {
   static __device__ __noinline__ bool initialize() {
     const FLayout& L = fwd_state.L;
     const int m = L.m, p = L.p, t = threadIdx.x;
-    QP_ARR(bz); QP_ARR(bs); QP_ARR(ua); QP_ARR(b); QP_ARR(h); QP_ARR(R); QP_ARR(G); QP_ARR(col);
+    QP_ARR(bz); QP_ARR(bs); QP_ARR(ua); QP_ARR(b); QP_ARR(h); QP_ARR(R); QP_BIG(G); QP_ARR(col);
     QP_ARR(q); QP_ARR(x); QP_ARR(y); QP_ARR(z); QP_ARR(s); QP_ARR(red);
     for (int r = t; r < m; r += NT) { bz[r] = 1.0f; bs[r] = 1.0f; }
     __syncthreads();
@@ -790,28 +814,43 @@ struct Solver {
   // ---- gradient cache: factors, W, active map and the point (Alg. 3 input) ----
   static __device__ __noinline__ void write_cache(const FwdParams& P, int bi) {
     const FLayout& L = fwd_state.L;
-    QP_ARR(K); QP_ARR(Y); QP_ARR(C); QP_ARR(ea); QP_ARR(D); QP_ARR(x); QP_ARR(y); QP_ARR(z);
+    QP_BIG(K); QP_BIG(Y); QP_BIG(C); QP_ARR(ea); QP_ARR(D); QP_ARR(x); QP_ARR(y); QP_ARR(z);
     QP_IARR(pos);
     const int n = L.n, m = L.m, p = L.p, t = threadIdx.x, a = fwd_state.a, nf = fwd_state.nf;
-    const CacheLayout cl = cache_layout(n, m, p, L.amax);
+    const CacheLayout cl = cache_layout(n, m, p, L.amax, kBig);
     float* c = P.cache + (size_t)bi * (size_t)P.cache_stride;
     if (t == 0) {
       reinterpret_cast<int*>(c + cl.oHdr)[0] = a;
       reinterpret_cast<int*>(c + cl.oHdr)[1] = nf;
       reinterpret_cast<int*>(c + cl.oHdr)[2] = P.refine_steps;
     }
-    const int nl = n * (n + 1) / 2;
+    if (kBig) {
+      // unpacked, with the workspace strides (cl.ldk == L.ldk, cl.ldc == L.ldc)
+      for (int e = t; e < n * n; e += NT) {
+        const int i = e / n, j = e - i * n;
+        if (j <= i) c[cl.oL + i * cl.ldk + j] = K[i * L.ldk + j];
+      }
+      for (int e = t; e < nf * n; e += NT) {
+        const int k = e / n, i = e - k * n;
+        c[cl.oY + k * cl.ldk + i] = Y[k * L.ldk + i];
+      }
+      for (int e = t; e < nf * nf; e += NT) {
+        const int i = e / nf, j = e - i * nf;
+        if (j <= i) c[cl.oLC + i * cl.ldc + j] = C[i * L.ldc + j];
+      }
+    }
+    const int nl = kBig ? 0 : n * (n + 1) / 2;
     for (int e = t; e < nl; e += NT) {
       int i = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
       while ((i + 1) * (i + 2) / 2 <= e) ++i;
       while (i * (i + 1) / 2 > e) --i;
       c[cl.oL + e] = K[i * L.ldk + (e - i * (i + 1) / 2)];
     }
-    for (int e = t; e < nf * n; e += NT) {
+    for (int e = t; e < (kBig ? 0 : nf * n); e += NT) {
       const int k = e / n, i = e - k * n;
       c[cl.oY + e] = Y[k * L.ldk + i];
     }
-    const int fl = nf * (nf + 1) / 2;
+    const int fl = kBig ? 0 : nf * (nf + 1) / 2;
     for (int e = t; e < fl; e += NT) {
       int i = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
       while ((i + 1) * (i + 2) / 2 <= e) ++i;
@@ -908,11 +947,16 @@ struct Solver {
       QP_ARR(z); QP_ARR(s); QP_ARR(bz); QP_ARR(bs);
       if (m > 0 && P.kappa_relax > 0.f && status != ST_NUMERICAL) {
         int rstatus = ST_MAX_ITER;
+        float rbest = INFINITY;
+        int rsince = 0;
         for (int it = 0;; ++it) {
           const float2 rr = residuals(P, true, 1);
           const float rm = rr.x, kappa = rr.y;
           if (!(rm == rm)) { rstatus = ST_NUMERICAL; break; }
-          if (rm < P.relax_tol) {
+          if (rm < 0.9f * rbest) { rbest = rm; rsince = 0; } else { ++rsince; }
+          // relax_tol where FP32 reaches it; otherwise its floor, once the
+          // measure is below the solve tolerance and has stopped decreasing
+          if (rm < P.relax_tol || (rm < P.tol && rsince >= 3)) {
             // one more (quadratically convergent) Newton step polishes the
             // relaxed point the gradients are taken at
             rstatus = ST_SOLVED;
@@ -939,7 +983,7 @@ struct Solver {
       // non-finite data: mark the slot unwritten (active count -1) so the
       // backward pass gives NaN gradients instead of reading stale contents
       int* hdr = reinterpret_cast<int*>(P.cache + (size_t)bi * (size_t)P.cache_stride +
-                                        cache_layout(n, m, p, fwd_state.L.amax).oHdr);
+                                        cache_layout(n, m, p, fwd_state.L.amax, kBig).oHdr);
       hdr[0] = -1;
       hdr[1] = -1;
       hdr[2] = 0;
@@ -954,50 +998,61 @@ struct Solver {
 
 #undef QP_ARR
 #undef QP_IARR
+#undef QP_BIG
 
 // minimum resident CTAs per SM the register budget is sized for
 template <int NT> struct MinBlocks { static constexpr int value = 1; };
 template <> struct MinBlocks<128> { static constexpr int value = 3; };
 template <> struct MinBlocks<256> { static constexpr int value = 3; };
 
-template <int NT>
+// kBig: the large-problem variant, K, G, A, Y, C in the instance's slice of
+// the global workspace P.ws (L1/L2-cached) instead of shared memory.
+template <int NT, bool kBig>
 __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) qp_forward_kernel(const FwdParams P) {
   // the phases take the parameters by reference: keep them in shared memory
   // rather than letting each thread copy the whole block to local memory
   __shared__ FwdParams sP;
   if (threadIdx.x == 0) sP = P;
-  Solver<NT>::init(P.n, P.m, P.p, P.amax);  // ends with a barrier
+  float* const ws = kBig ? P.ws + (size_t)blockIdx.x * (size_t)P.ws_stride : nullptr;
+  Solver<NT, kBig>::init(P.n, P.m, P.p, P.amax, ws);  // ends with a barrier
 #ifdef QP_PHASE_TIMERS
   if (threadIdx.x == 0) fwd_state.timers = P.timers;
   __syncthreads();
 #endif
-  Solver<NT>::run(sP, blockIdx.x);
+  Solver<NT, kBig>::run(sP, blockIdx.x);
 }
 
 }  // namespace fwd
 
-// Instantiated once per block size in qp_forward_<NT>.cu.
-template <int NT>
+// Raise (never lower) the kernel's dynamic shared-memory limit to `smem`; the
+// attribute is per function and per process, shared by every handle.
+template <int NT, bool kBig>
+cudaError_t ensure_forward_smem(size_t smem) {
+  static std::mutex mu;
+  static size_t configured = 0;
+  std::lock_guard<std::mutex> lock(mu);
+  if (smem <= configured) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(fwd::qp_forward_kernel<NT, kBig>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) configured = smem;
+  return e;
+}
+
+// Instantiated once per (block size, variant) in qp_forward_<NT>[w].cu.
+template <int NT, bool kBig>
 cudaError_t launch_forward_nt(const FwdParams& P, size_t smem, int grid, cudaStream_t st) {
-  static size_t configured = 0;  // the attribute is per function and per process
-  if (smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(fwd::qp_forward_kernel<NT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = smem;
-  }
-  fwd::qp_forward_kernel<NT><<<grid, NT, smem, st>>>(P);
+  const cudaError_t e = ensure_forward_smem<NT, kBig>(smem);
+  if (e != cudaSuccess) return e;
+  fwd::qp_forward_kernel<NT, kBig><<<grid, NT, smem, st>>>(P);
   return cudaGetLastError();
 }
 
-template <int NT>
+template <int NT, bool kBig>
 int forward_blocks_per_sm_nt(size_t smem) {
   int nb = 0;
-  if (cudaFuncSetAttribute(fwd::qp_forward_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem) != cudaSuccess)
-    return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fwd::qp_forward_kernel<NT>, NT, smem) !=
-      cudaSuccess)
+  if (ensure_forward_smem<NT, kBig>(smem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fwd::qp_forward_kernel<NT, kBig>, NT,
+                                                    smem) != cudaSuccess)
     return 0;
   return nb;
 }

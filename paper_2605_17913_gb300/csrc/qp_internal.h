@@ -23,6 +23,10 @@ struct FwdParams {
   // gradient cache (nullptr: no relax, no cache)
   float* cache;
   long long cache_stride;
+  // per-instance global workspace of the large-problem variant (K, G, A, Y, C
+  // outside shared memory); nullptr for sizes that fit on chip
+  float* ws;
+  long long ws_stride;
 #ifdef QP_PHASE_TIMERS
   unsigned long long* timers;  // device counters of the phase timers (tracing build)
 #endif
@@ -30,6 +34,7 @@ struct FwdParams {
 
 struct BwdParams {
   int batch, n, m, p, amax;
+  int split;  // cache in the unpacked (large-problem) layout
   const float *Q, *A, *G;
   const float* g;
   const float* cache;
@@ -44,19 +49,26 @@ struct BwdParams {
 // C = D + Y Y' (packed lower), W of the inactive rows and 1/W of the active
 // rows, the row -> position map
 // (int32, -1 for inactive rows) and the point (x, y, z).
+// Large-problem variant (split): L, Y and L_C are stored unpacked with the
+// forward kernel's strides ldk = n | 1 (L, Y) and ldc = (amax + p + 2) | 1
+// (L_C), so that the backward pass reads them in place.
 struct CacheLayout {
   int oHdr, oL, oY, oLC, oW, oPos, ox, oy, oz, stride;
+  int ldk, ldc;  // strides of L / Y and of L_C (split layout; 0 when packed)
 };
 
-__host__ __device__ inline CacheLayout cache_layout(int n, int m, int p, int amax) {
+__host__ __device__ inline CacheLayout cache_layout(int n, int m, int p, int amax,
+                                                    bool split = false) {
   auto r4 = [](long long v) -> int { return (int)((v + 3) & ~3LL); };
   const long long f = (long long)amax + p;
   CacheLayout c;
   int o = 0;
+  c.ldk = split ? (n | 1) : 0;
+  c.ldc = split ? (int)((f + 2) | 1) : 0;
   c.oHdr = o; o += 4;
-  c.oL = o; o += r4((long long)n * (n + 1) / 2);
-  c.oY = o; o += r4(f * n);
-  c.oLC = o; o += r4(f * (f + 1) / 2);
+  c.oL = o; o += r4(split ? (long long)n * c.ldk : (long long)n * (n + 1) / 2);
+  c.oY = o; o += r4(split ? f * c.ldk : f * n);
+  c.oLC = o; o += r4(split ? f * c.ldc : f * (f + 1) / 2);
   c.oW = o; o += r4(m);
   c.oPos = o; o += r4(m);
   c.ox = o; o += r4(n);
@@ -67,13 +79,16 @@ __host__ __device__ inline CacheLayout cache_layout(int n, int m, int p, int ama
 }
 
 // Launch configuration of the forward kernel for a size: shared-memory bytes
-// (0 if unsupported), threads per CTA and the active-row cap amax.
-size_t forward_config(int n, int m, int p, int* nthreads, int* amax);
+// (0 if unsupported), threads per CTA, the active-row cap amax and, for the
+// large-problem variant, the global workspace floats per instance (0 when
+// everything fits in shared memory).
+size_t forward_config(int n, int m, int p, int* nthreads, int* amax,
+                      long long* ws_floats = nullptr);
 cudaError_t launch_forward(const FwdParams& P, int nthreads, size_t smem, int grid,
                            cudaStream_t stream);
-int forward_blocks_per_sm(int nthreads, size_t smem);
+int forward_blocks_per_sm(int nthreads, size_t smem, bool split);
 
-size_t backward_smem_bytes(int n, int m, int p, int amax, int* nthreads);
+size_t backward_smem_bytes(int n, int m, int p, int amax, bool split, int* nthreads);
 cudaError_t launch_backward(const BwdParams& P, int nthreads, size_t smem, cudaStream_t stream);
 
 // Problem sizes of a handle (struct qp_handle is private to qp_api.cu).

@@ -153,6 +153,27 @@ def test_ragged_and_edge_sizes(n, m, p):
     check_grads(res, ref)
 
 
+@pytest.mark.parametrize("workload,B,sizes", [
+    ("small", 5, dict(n=130, m=200, p=10)),   # beyond the on-chip n limit
+    ("small", 5, dict(n=100, m=400, p=8)),    # n fits, shared memory does not
+    ("precision", 3, {}),                      # n=256, m=512, p=32, cond(Q) = 1e4
+])
+def test_large_variant_parity(workload, B, sizes):
+    """The large-problem variant (matrices in a device workspace) against the
+    oracle: forward bars and gradients."""
+    from paper_2605_17913_gb300 import _lib
+    import ctypes
+
+    batch = make_batch(workload, B, seed=0, **sizes)
+    dims = _lib.Dims(B, batch.n, batch.p, batch.m)
+    assert _lib.lib().qp_workspace_bytes(ctypes.byref(dims)) > 0
+    res = gpu_run(batch, grad=True)
+    ref = oracle_run(batch, grad=True)
+    check_forward(batch, res, O.solve(batch.Q, batch.q, batch.A, batch.b, batch.G, batch.h,
+                                      tol=1e-12, nthreads=B))
+    check_grads(res, ref)
+
+
 def test_unconstrained_closed_form():
     batch = make_batch("small", 5, seed=2, m=0, p=0)
     res = gpu_run(batch, grad=True)
