@@ -205,6 +205,88 @@ int qp_solve_backward_static(qp_handle* h, const qp_settings* settings, const fl
                              float* dQ, float* dq, float* dA, float* db, float* dG, float* dh,
                              void* stream);
 
+/* ---- serving: continuous batching of single requests ------------------- */
+
+/* A server owns a device arena, a pinned host mirror of it, max_inflight
+ * CUDA streams and a scheduler thread.  Requests of any supported size are
+ * submitted one at a time; the scheduler groups waiting requests into
+ * launches (the oldest request first, requests of its kernel class in
+ * arrival order, up to max_batch and up to the free arena memory) and keeps
+ * up to max_inflight launches on the GPU at once, so requests that arrive
+ * while others run start as soon as a stream and memory free up; a kernel
+ * class takes the last free stream only while it has fewer than
+ * max(1, max_inflight / 3) launches in flight.  Each
+ * request is solved (Alg. 1; with want_grad also relaxed and differentiated,
+ * Alg. 2-3) by one CTA with the same arithmetic as qp_solve_batch of its
+ * size: results equal solo results bit for bit.  Every wait is bounded. */
+typedef struct qp_server qp_server;
+
+typedef struct {
+  size_t hbm_budget_bytes; /* device arena for resident requests (>= 1 MiB)     */
+  int32_t max_inflight;    /* launches on the GPU at once, one stream each (1-64) */
+  int32_t max_batch;       /* requests per launch                                */
+  int32_t max_queue;       /* requests waiting on the host before QP_EAGAIN       */
+  qp_settings settings;    /* solver settings of every request (no warm start)    */
+} qp_serve_config;
+
+typedef struct {
+  int32_t n, n_eq, n_ineq; /* sizes of this request                             */
+  int32_t want_grad;       /* 1: relax and return the gradients of <dl_dx, x>    */
+  /* HOST inputs, copied during qp_serve_submit (layout as qp_solve_batch, one
+   * instance); dl_dx[n] when want_grad */
+  const float *Q, *q, *A, *b, *G, *h, *dl_dx;
+  /* HOST outputs, written by the qp_serve_poll* / qp_serve_wait call that
+   * returns this request; each may be NULL; they must stay valid until then */
+  float *x, *y, *z, *s;
+  float *dQ, *dq, *dA, *db, *dG, *dh;
+} qp_request;
+
+typedef struct {
+  uint64_t ticket;
+  int32_t status;          /* per-instance status (QP_SOLVED, ...)               */
+  int32_t iters;
+  float kkt_res;
+  double t_submit_ms;      /* server clock (ms since qp_serve_create): submitted */
+  double t_launch_ms;      /* its launch was issued                              */
+  double t_done_ms;        /* its launch's results reached host memory           */
+} qp_result;
+
+/* Defaults: 1 GiB arena, 8 launches in flight, 1024 requests per launch,
+ * 2^20 queued requests, qp_settings_default. */
+void qp_serve_config_default(qp_serve_config* c);
+
+/* Arena bytes one request occupies while resident (data, outputs, gradient
+ * outputs and factor cache when want_grad, workspace of the large variant);
+ * 0 if the size is unsupported.  The admission unit of the server. */
+size_t qp_serve_footprint_bytes(int32_t n, int32_t n_eq, int32_t n_ineq, int32_t want_grad);
+
+/* Allocate the arena and mirror, create the streams and start the scheduler on
+ * the current device.  QP_EINVAL (bad config), QP_ENOMEM, QP_ECUDA. */
+int qp_serve_create(const qp_serve_config* cfg, qp_server** out);
+
+/* Queue one request (non-blocking: its inputs are copied, the GPU work is
+ * issued by the scheduler).  QP_OK with *ticket; QP_EAGAIN if max_queue
+ * requests are waiting; QP_ENOTSUP if the size is unsupported or larger than
+ * the arena; QP_EINVAL for bad arguments; QP_ECUDA after a device error. */
+int qp_serve_submit(qp_server* s, const qp_request* r, uint64_t* ticket);
+
+/* QP_PENDING while the request is queued or running; otherwise writes its
+ * outputs, fills *res, retires the ticket and returns QP_OK (or the error
+ * code of a failed launch).  QP_EINVAL for an unknown ticket. */
+int qp_serve_poll(qp_server* s, uint64_t ticket, qp_result* res);
+
+/* As qp_serve_poll for the earliest completed request not yet collected;
+ * QP_PENDING if none has completed. */
+int qp_serve_poll_any(qp_server* s, qp_result* res);
+
+/* Wait at most timeout_ms for the request, then as qp_serve_poll;
+ * QP_ETIMEOUT if it has not completed by then. */
+int qp_serve_wait(qp_server* s, uint64_t ticket, int32_t timeout_ms, qp_result* res);
+
+/* Stop the scheduler, drain the streams and free everything; tickets not yet
+ * collected are dropped. */
+int qp_serve_destroy(qp_server* s);
+
 /* Human-readable name of a return or status code. */
 const char* qp_status_string(int code);
 

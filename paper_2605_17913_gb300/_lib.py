@@ -54,6 +54,26 @@ class Settings(ctypes.Structure):
     ]
 
 
+class ServeConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int32),
+                ("max_batch", ctypes.c_int32), ("max_queue", ctypes.c_int32),
+                ("settings", Settings)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("n_eq", ctypes.c_int32), ("n_ineq", ctypes.c_int32),
+                ("want_grad", ctypes.c_int32)] + [
+        (k, ctypes.c_void_p) for k in ("Q", "q", "A", "b", "G", "h", "dl_dx", "x", "y", "z", "s",
+                                       "dQ", "dq", "dA", "db", "dG", "dh")]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("status", ctypes.c_int32),
+                ("iters", ctypes.c_int32), ("kkt_res", ctypes.c_float),
+                ("t_submit_ms", ctypes.c_double), ("t_launch_ms", ctypes.c_double),
+                ("t_done_ms", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -84,6 +104,22 @@ def lib() -> ctypes.CDLL:
     L.qp_solve_batch.argtypes = [vp, ctypes.POINTER(Settings)] + [vp] * 14 + [vp]
     L.qp_backward_batch.restype = ctypes.c_int
     L.qp_backward_batch.argtypes = [vp] * 13
+    L.qp_serve_config_default.restype = None
+    L.qp_serve_config_default.argtypes = [ctypes.POINTER(ServeConfig)]
+    L.qp_serve_footprint_bytes.restype = ctypes.c_size_t
+    L.qp_serve_footprint_bytes.argtypes = [i32, i32, i32, i32]
+    L.qp_serve_create.restype = ctypes.c_int
+    L.qp_serve_create.argtypes = [ctypes.POINTER(ServeConfig), ctypes.POINTER(vp)]
+    L.qp_serve_submit.restype = ctypes.c_int
+    L.qp_serve_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
+    L.qp_serve_poll.restype = ctypes.c_int
+    L.qp_serve_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(Result)]
+    L.qp_serve_poll_any.restype = ctypes.c_int
+    L.qp_serve_poll_any.argtypes = [vp, ctypes.POINTER(Result)]
+    L.qp_serve_wait.restype = ctypes.c_int
+    L.qp_serve_wait.argtypes = [vp, ctypes.c_uint64, i32, ctypes.POINTER(Result)]
+    L.qp_serve_destroy.restype = ctypes.c_int
+    L.qp_serve_destroy.argtypes = [vp]
     L.qp_solve_backward_static.restype = ctypes.c_int
     L.qp_solve_backward_static.argtypes = [vp, ctypes.POINTER(Settings)] + [vp] * 21
     _lib = L

@@ -37,6 +37,30 @@ static unsigned long long* g_phase_counters = nullptr;
 
 namespace qpgpu {
 qp_dims handle_dims(const qp_handle* h) { return h->dims; }
+
+int settings_to_params(const qp_settings* st, FwdParams* P) {
+  if (!(st->tol > 0.0f) || st->max_iter < 0 || st->formulation < 0 || st->formulation > 1 ||
+      st->sigma_mode < 0 || st->sigma_mode > 1 || !(st->kappa_relax >= 0.0f) ||
+      st->residual_norm < 0 || st->residual_norm > 1 || st->refine_steps < 0)
+    return QP_EINVAL;
+  if (st->gwg_precision != QP_GWG_FP32) return QP_ENOTSUP;
+  if (st->sigma_mode == QP_SIGMA_CONSTANT && !(st->sigma >= 0.0f && st->sigma <= 1.0f))
+    return QP_EINVAL;
+  P->tol = st->tol;
+  P->sigma = st->sigma;
+  P->kappa_min = st->kappa_min > 0.0f ? st->kappa_min : 1e-2f * st->tol;
+  P->kappa_relax = st->kappa_relax;
+  P->relax_tol = st->relax_tol > 0.0f ? st->relax_tol : 0.1f * st->tol;
+  P->step_frac = 1.0f;
+  P->max_iter = st->max_iter;
+  P->relax_max_iter = st->relax_max_iter > 0 ? st->relax_max_iter : st->max_iter;
+  P->sigma_mode = st->sigma_mode;
+  P->formulation = st->formulation;
+  P->norm_abs = st->residual_norm == QP_NORM_ABS;
+  P->warm_start = st->warm_start;
+  P->refine_steps = st->refine_steps;
+  return QP_OK;
+}
 }  // namespace qpgpu
 
 extern "C" {
@@ -165,32 +189,14 @@ int qp_solve_batch(qp_handle* h, const qp_settings* st, const float* Q, const fl
   for (const void* ptr : ptrs)
     if (ptr && !aligned4(ptr)) return QP_EINVAL;
   if (grad_cache && (reinterpret_cast<uintptr_t>(grad_cache) & 15)) return QP_EINVAL;
-  if (!(st->tol > 0.0f) || st->max_iter < 0 || st->formulation < 0 || st->formulation > 1 ||
-      st->sigma_mode < 0 || st->sigma_mode > 1 || !(st->kappa_relax >= 0.0f) ||
-      st->residual_norm < 0 || st->residual_norm > 1 || st->refine_steps < 0)
-    return QP_EINVAL;
-  if (st->gwg_precision != QP_GWG_FP32) return QP_ENOTSUP;
-  if (st->sigma_mode == QP_SIGMA_CONSTANT && !(st->sigma >= 0.0f && st->sigma <= 1.0f))
-    return QP_EINVAL;
   FwdParams P;
   memset(&P, 0, sizeof(P));
+  const int rc = settings_to_params(st, &P);
+  if (rc != QP_OK) return rc;
   P.batch = B; P.n = n; P.m = m; P.p = p; P.amax = h->amax;
   P.Q = Q; P.q = q; P.A = A; P.b = b; P.G = G; P.h = hv;
   P.x = x; P.y = y; P.z = z; P.s = s;
   P.status = status; P.iters = iters; P.kkt = kkt_res;
-  P.tol = st->tol;
-  P.sigma = st->sigma;
-  P.kappa_min = st->kappa_min > 0.0f ? st->kappa_min : 1e-2f * st->tol;
-  P.kappa_relax = st->kappa_relax;
-  P.relax_tol = st->relax_tol > 0.0f ? st->relax_tol : 0.1f * st->tol;
-  P.step_frac = 1.0f;
-  P.max_iter = st->max_iter;
-  P.relax_max_iter = st->relax_max_iter > 0 ? st->relax_max_iter : st->max_iter;
-  P.sigma_mode = st->sigma_mode;
-  P.formulation = st->formulation;
-  P.norm_abs = st->residual_norm == QP_NORM_ABS;
-  P.warm_start = st->warm_start;
-  P.refine_steps = st->refine_steps;
   P.cache = grad_cache;
   P.cache_stride = h->cache_stride;
   P.ws = h->ws;
@@ -220,6 +226,7 @@ int qp_backward_batch(qp_handle* h, const float* grad_cache, const float* Q, con
   for (const void* ptr : ptrs)
     if (ptr && !aligned4(ptr)) return QP_EINVAL;
   BwdParams P;
+  memset(&P, 0, sizeof(P));
   P.batch = B; P.n = n; P.m = m; P.p = p; P.amax = h->amax;
   P.split = h->split ? 1 : 0;
   P.Q = Q; P.A = A; P.G = G; P.g = dl_dx; P.cache = grad_cache; P.cache_stride = h->cache_stride;

@@ -175,10 +175,9 @@ __device__ void two_level_solve(const float* K, int ldk, const float* dinv, cons
 }
 
 template <int NT, bool kStage, bool kGlobal>
-__global__ void __launch_bounds__(NT) qp_backward_kernel(const BwdParams P) {
+__device__ __forceinline__ void backward_body(const BwdParams& P, int bi) {
   extern __shared__ __align__(16) float sm[];
   const int n = P.n, m = P.m, p = P.p, t = threadIdx.x;
-  const int bi = blockIdx.x;
   const BLayout B = make_blayout(n, m, p, P.amax, NT, kStage, kGlobal);
   const CacheLayout cl = cache_layout(n, m, p, P.amax, kGlobal);
   const float* c = P.cache + (size_t)bi * (size_t)P.cache_stride;
@@ -357,34 +356,80 @@ __global__ void __launch_bounds__(NT) qp_backward_kernel(const BwdParams P) {
     for (int r = t; r < m; r += NT) __stcs(P.dh + (size_t)bi * m + r, -dz[r]);
 }
 
+template <int NT, bool kStage, bool kGlobal>
+__global__ void __launch_bounds__(NT) qp_backward_kernel(const BwdParams P) {
+  // parameters in shared memory (the body takes them by reference); a ragged
+  // launch substitutes this CTA's request, addressed as instance 0
+  __shared__ BwdParams sP;
+  if (threadIdx.x == 0) {
+    sP = P;
+    if (P.desc) {
+      const ReqDesc& d = P.desc[blockIdx.x];
+      sP.batch = 1; sP.n = d.n; sP.m = d.m; sP.p = d.p; sP.amax = d.amax;
+      sP.Q = d.Q; sP.A = d.A; sP.G = d.G; sP.g = d.g;
+      sP.cache = d.cache; sP.cache_stride = 0;
+      sP.dQ = d.dQ; sP.dq = d.dq;
+      sP.dA = d.p > 0 ? d.dA : nullptr; sP.db = d.p > 0 ? d.db : nullptr;
+      sP.dG = d.m > 0 ? d.dG : nullptr; sP.dh = d.m > 0 ? d.dh : nullptr;
+    }
+  }
+  __syncthreads();
+  backward_body<NT, kStage, kGlobal>(sP, P.desc ? 0 : blockIdx.x);
+}
+
 }  // namespace
+
+// dynamic shared memory left beside the kernel's static parameter copy
+constexpr size_t kBwdBudget = 227 * 1024 - 512;
+
+size_t backward_direct_smem_bytes(int n, int m, int p, int amax, bool split) {
+  if (split ? (n > 256 || amax + p > 256) : (n > 128 || amax + p > 128)) return 0;
+  const size_t bytes =
+      (size_t)make_blayout(n, m, p, amax, 256, false, split).total * sizeof(float);
+  return bytes <= kBwdBudget ? bytes : 0;
+}
 
 size_t backward_smem_bytes(int n, int m, int p, int amax, bool split, int* nthreads) {
   if (nthreads) *nthreads = 256;
-  if (split) {
-    if (n > 256 || amax + p > 256) return 0;
-    const size_t bytes =
-        (size_t)make_blayout(n, m, p, amax, 256, false, true).total * sizeof(float);
-    return bytes <= 227 * 1024 ? bytes : 0;
-  }
+  if (split) return backward_direct_smem_bytes(n, m, p, amax, true);
   if (n > 128 || amax + p > 128) return 0;
   const size_t staged = (size_t)make_blayout(n, m, p, amax, 256, true).total * sizeof(float);
-  if (staged <= 227 * 1024) return staged;
-  const size_t direct = (size_t)make_blayout(n, m, p, amax, 256, false).total * sizeof(float);
-  return direct <= 227 * 1024 ? direct : 0;
+  if (staged <= kBwdBudget) return staged;
+  return backward_direct_smem_bytes(n, m, p, amax, false);
 }
 
+// The dynamic shared-memory limit is set once per variant, to the largest
+// layout (setting it can wait for running kernels: not on the launch path).
 template <bool kStage, bool kGlobal>
-cudaError_t launch_backward_v(const BwdParams& P, size_t smem, cudaStream_t st) {
+cudaError_t configure_backward_v() {
   static std::once_flag once;
   static cudaError_t set = cudaSuccess;
   std::call_once(once, [] {
     set = cudaFuncSetAttribute(qp_backward_kernel<256, kStage, kGlobal>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBwdBudget);
   });
+  return set;
+}
+
+template <bool kStage, bool kGlobal>
+cudaError_t launch_backward_v(const BwdParams& P, size_t smem, cudaStream_t st) {
+  const cudaError_t set = configure_backward_v<kStage, kGlobal>();
   if (set != cudaSuccess) return set;
   qp_backward_kernel<256, kStage, kGlobal><<<P.batch, 256, smem, st>>>(P);
   return cudaGetLastError();
+}
+
+// Load every variant's module and set its limit now (kernels load lazily).
+void preload_backward_kernels() {
+  configure_backward_v<true, false>();
+  configure_backward_v<false, false>();
+  configure_backward_v<false, true>();
+  cudaGetLastError();
+}
+
+cudaError_t launch_backward_ragged(const BwdParams& P, size_t smem, cudaStream_t st) {
+  return P.split ? launch_backward_v<false, true>(P, smem, st)
+                 : launch_backward_v<false, false>(P, smem, st);
 }
 
 cudaError_t launch_backward(const BwdParams& P, int nthreads, size_t smem, cudaStream_t st) {

@@ -63,6 +63,15 @@ cudaError_t launch_forward(const FwdParams& P, int nthreads, size_t smem, int gr
   }
 }
 
+// Load every variant's module now (the runtime loads kernels lazily, on
+// first use), so that no later launch pays for it.
+void preload_forward_kernels() {
+  forward_blocks_per_sm_nt<128, false>(1024);
+  forward_blocks_per_sm_nt<512, false>(1024);
+  forward_blocks_per_sm_nt<512, true>(1024);
+  cudaGetLastError();
+}
+
 int forward_blocks_per_sm(int nthreads, size_t smem, bool split) {
   if (split) return nthreads == 512 ? forward_blocks_per_sm_nt<512, true>(smem) : 0;
   switch (nthreads) {

@@ -1012,30 +1012,49 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) qp_forward_kernel(co
   // the phases take the parameters by reference: keep them in shared memory
   // rather than letting each thread copy the whole block to local memory
   __shared__ FwdParams sP;
-  if (threadIdx.x == 0) sP = P;
-  float* const ws = kBig ? P.ws + (size_t)blockIdx.x * (size_t)P.ws_stride : nullptr;
-  Solver<NT, kBig>::init(P.n, P.m, P.p, P.amax, ws);  // ends with a barrier
+  if (threadIdx.x == 0) {
+    sP = P;
+    if (P.desc) {
+      // ragged launch: this CTA's request, addressed as instance 0
+      const ReqDesc& d = P.desc[blockIdx.x];
+      sP.batch = 1; sP.n = d.n; sP.m = d.m; sP.p = d.p; sP.amax = d.amax;
+      sP.Q = d.Q; sP.q = d.q; sP.A = d.A; sP.b = d.b; sP.G = d.G; sP.h = d.h;
+      sP.x = d.x; sP.y = d.y; sP.z = d.z; sP.s = d.s;
+      sP.status = d.status; sP.iters = d.iters; sP.kkt = d.kkt;
+      sP.cache = d.cache; sP.cache_stride = 0;
+      sP.ws = d.ws; sP.ws_stride = 0;
+    }
+  }
+  __syncthreads();
+  const int bi = P.desc ? 0 : blockIdx.x;
+  float* const ws = kBig ? sP.ws + (size_t)bi * (size_t)sP.ws_stride : nullptr;
+  Solver<NT, kBig>::init(sP.n, sP.m, sP.p, sP.amax, ws);  // ends with a barrier
 #ifdef QP_PHASE_TIMERS
   if (threadIdx.x == 0) fwd_state.timers = P.timers;
   __syncthreads();
 #endif
-  Solver<NT, kBig>::run(sP, blockIdx.x);
+  Solver<NT, kBig>::run(sP, bi);
 }
 
 }  // namespace fwd
 
-// Raise (never lower) the kernel's dynamic shared-memory limit to `smem`; the
-// attribute is per function and per process, shared by every handle.
+// The kernel's dynamic shared-memory limit is set once, to the largest
+// request any size can make: the attribute is per function and per process,
+// and setting it can wait for kernels already running on the device, so it
+// must not happen on the launch path.
 template <int NT, bool kBig>
 cudaError_t ensure_forward_smem(size_t smem) {
   static std::mutex mu;
   static size_t configured = 0;
   std::lock_guard<std::mutex> lock(mu);
-  if (smem <= configured) return cudaSuccess;
-  const cudaError_t e = cudaFuncSetAttribute(fwd::qp_forward_kernel<NT, kBig>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess) configured = smem;
-  return e;
+  if (configured == 0) {
+    const size_t maxdyn = 227 * 1024 - fwd::kStaticSmem;
+    const cudaError_t e = cudaFuncSetAttribute(
+        fwd::qp_forward_kernel<NT, kBig>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)maxdyn);
+    if (e != cudaSuccess) return e;
+    configured = maxdyn;
+  }
+  return smem <= configured ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 // Instantiated once per (block size, variant) in qp_forward_<NT>[w].cu.

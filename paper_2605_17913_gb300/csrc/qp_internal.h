@@ -9,6 +9,21 @@
 
 namespace qpgpu {
 
+// One request of a ragged launch (serving): its sizes and device pointers.
+// A CTA that finds a descriptor table uses its own entry in place of the
+// launch's uniform sizes and batch-strided pointers, with instance index 0.
+struct ReqDesc {
+  int n, m, p, amax;
+  const float *Q, *q, *A, *b, *G, *h;
+  float *x, *y, *z, *s;
+  int32_t *status, *iters;
+  float* kkt;
+  float* cache;     // gradient cache (nullptr: no relax, no cache)
+  float* ws;        // workspace of the large-problem variant
+  const float* g;   // dl/dx for the backward pass
+  float *dQ, *dq, *dA, *db, *dG, *dh;
+};
+
 // Parameters of one forward launch (all device pointers).
 struct FwdParams {
   int batch, n, m, p;
@@ -27,6 +42,7 @@ struct FwdParams {
   // outside shared memory); nullptr for sizes that fit on chip
   float* ws;
   long long ws_stride;
+  const ReqDesc* desc;  // ragged launch: one descriptor per CTA (nullptr: uniform batch)
 #ifdef QP_PHASE_TIMERS
   unsigned long long* timers;  // device counters of the phase timers (tracing build)
 #endif
@@ -40,6 +56,7 @@ struct BwdParams {
   const float* cache;
   long long cache_stride;
   float *dQ, *dq, *dA, *db, *dG, *dh;
+  const ReqDesc* desc;  // ragged launch: one descriptor per CTA (nullptr: uniform batch)
 };
 
 // Per-instance layout of the gradient cache, in floats (offsets multiples of
@@ -89,9 +106,23 @@ cudaError_t launch_forward(const FwdParams& P, int nthreads, size_t smem, int gr
 int forward_blocks_per_sm(int nthreads, size_t smem, bool split);
 
 size_t backward_smem_bytes(int n, int m, int p, int amax, bool split, int* nthreads);
+// Shared memory of the backward kernel reading Q, G, A from global memory
+// (the variant of ragged launches; same arithmetic as the staged one).
+size_t backward_direct_smem_bytes(int n, int m, int p, int amax, bool split);
 cudaError_t launch_backward(const BwdParams& P, int nthreads, size_t smem, cudaStream_t stream);
+// Ragged backward launch over P.desc[0 .. P.batch): Q, G, A read from global memory.
+cudaError_t launch_backward_ragged(const BwdParams& P, size_t smem, cudaStream_t stream);
+
+// Load the kernels' modules ahead of their first launch (the runtime loads
+// lazily); for callers whose launches must not pay for loading.
+void preload_forward_kernels();
+void preload_backward_kernels();
 
 // Problem sizes of a handle (struct qp_handle is private to qp_api.cu).
 qp_dims handle_dims(const qp_handle* h);
+
+// Validate solver settings and copy them into launch parameters (QP_OK,
+// QP_EINVAL or QP_ENOTSUP).
+int settings_to_params(const qp_settings* st, FwdParams* P);
 
 }  // namespace qpgpu

@@ -81,3 +81,24 @@ def test_sizes(L):
     assert L.qp_grad_cache_bytes(ctypes.byref(dims)) == 3 * per
     for c in (0, 1, 2, 3, 4, -1, -6):
         assert isinstance(_lib.status_string(c), str)
+
+
+def test_serve_footprint_and_config_validation(L):
+    from paper_2605_17913_gb300 import _lib
+
+    f0 = L.qp_serve_footprint_bytes(50, 5, 100, 0)
+    f1 = L.qp_serve_footprint_bytes(50, 5, 100, 1)
+    assert 0 < f0 < f1 and f0 % 256 == 0
+    # data + outputs at least, gradients and the factor cache on top
+    assert f0 >= 4 * (50 * 50 + 50 + 5 * 50 + 5 + 100 * 50 + 100)
+    assert f1 - f0 >= 4 * (50 * 50 + 100 * 50)
+    assert L.qp_serve_footprint_bytes(300, 5, 10, 0) == 0  # beyond n = 256
+    assert L.qp_serve_footprint_bytes(10, 11, 5, 0) == 0  # n_eq > n
+    cfg = _lib.ServeConfig()
+    L.qp_serve_config_default(ctypes.byref(cfg))
+    assert cfg.hbm_budget_bytes == 1 << 30 and cfg.max_inflight == 8
+    h = ctypes.c_void_p()
+    cfg.max_inflight = 0
+    assert L.qp_serve_create(ctypes.byref(cfg), ctypes.byref(h)) == _lib.QP_EINVAL
+    assert L.qp_serve_submit(None, None, None) == _lib.QP_EINVAL
+    assert L.qp_serve_poll_any(None, None) == _lib.QP_EINVAL
