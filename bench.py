@@ -53,6 +53,12 @@ def parse():
     # implicit vs standard complementarity in FP32 over a tolerance sweep
     # (one JSON line per formulation and tolerance instead of the bench line)
     ap.add_argument("--ablation", action="store_true")
+    # serving (continuous batching) on the uneven-size request stream: the full
+    # study prints one JSON line per load; the bench line carries a short run
+    ap.add_argument("--serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=None)
+    ap.add_argument("--serve-pool", type=int, default=2048)
+    ap.add_argument("--no-serve", action="store_true")
     return ap.parse_args()
 
 
@@ -331,6 +337,19 @@ def run_ours(args, rank, world, local_rank):
         e2e_value = total_passed / float(te.item())
     if rank != 0:
         return
+    serve = None
+    if world == 1 and not args.no_serve and args.workload == "degenerate":
+        # a short run of the serving study (uneven-size stream at 0.8 of the
+        # padded baseline's saturated rate); `--serve` runs the full study
+        s = run_serve_study(args, lines=False, requests=3000, fracs=(0.8,))[0]
+        serve = {"requests": s["requests"], "rate_per_s": s["rate_per_s"],
+                 "load_vs_padded_saturation": s["load_vs_padded_saturation"],
+                 "p50_ms": s["latency_ms"]["p50"], "p99_ms": s["latency_ms"]["p99"],
+                 "solves_per_s": s["solves_per_s"], "solved": s["solved"],
+                 "padded_p50_ms": s["padded_baseline"]["latency_ms"]["p50"],
+                 "padded_p99_ms": s["padded_baseline"]["latency_ms"]["p99"],
+                 "note": "n log-uniform in [8, 256], m = 2n, p = n // 10, 30 % with "
+                         "gradients; latency = poll completion - submit"}
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         rate, cores, sample = cpu_oracle_rate(args.workload, args.cpu_seconds,
@@ -359,8 +378,222 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clk,
         "wall_s_timed_region": wall,
         "cpu_baseline": cpu,
+        "serve": serve,
     }
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- serving
+def _serve_pool(count, seed=0):
+    """Seeded serving requests (uneven sizes), FP32, with their gradient flag."""
+    from qpgen import make_instance, serving_sizes
+
+    flags = serving_sizes(count, seed=seed)
+    pool = []
+    for i in range(count):
+        d = make_instance("serving", i, seed=seed)
+        d = {k: np.ascontiguousarray(v, dtype=np.float32) for k, v in d.items()}
+        d["grad"] = bool(flags[i][3])
+        pool.append(d)
+    return pool
+
+
+def _pad_group(reqs):
+    """One padded batch of the baseline: every request padded to the group's
+    largest n (m = 2n, p = n // 10).  Padded variables: Q = I, q = 0 and zero
+    columns elsewhere; padded inequality rows 0 . x <= 1; padded equality rows
+    pin one padded variable each to 0 (keeps A full rank)."""
+    nmax = max(r["q"].size for r in reqs)
+    mmax, pmax = 2 * nmax, nmax // 10
+    B = len(reqs)
+    Q = np.zeros((B, nmax, nmax), np.float32)
+    q = np.zeros((B, nmax), np.float32)
+    A = np.zeros((B, pmax, nmax), np.float32)
+    b = np.zeros((B, pmax), np.float32)
+    G = np.zeros((B, mmax, nmax), np.float32)
+    h = np.ones((B, mmax), np.float32)
+    g = np.zeros((B, nmax), np.float32)
+    for k, r in enumerate(reqs):
+        n, p, m = r["q"].size, r["b"].size, r["h"].size
+        Q[k, :n, :n] = r["Q"]
+        Q[k, range(n, nmax), range(n, nmax)] = 1.0
+        q[k, :n] = r["q"]
+        A[k, :p, :n] = r["A"]
+        b[k, :p] = r["b"]
+        for j in range(pmax - p):
+            A[k, p + j, n + j] = 1.0
+        G[k, :m, :n] = r["G"]
+        h[k, :m] = r["h"]
+        g[k, :n] = r["g"]
+    return dict(Q=Q, q=q, A=A, b=b, G=G, h=h, g=g)
+
+
+def _padded_group_times(pool, order, group, tol):
+    """Device time of each padded batch (solve + relax + backward) of the
+    baseline, in arrival order."""
+    import torch
+
+    from paper_2605_17913_gb300.solver import QPSolver
+
+    times = []
+    for g0 in range(0, len(order), group):
+        reqs = [pool[i] for i in order[g0:g0 + group]]
+        d = _pad_group(reqs)
+        T = {k: torch.from_numpy(v).cuda() for k, v in d.items()}
+        B, n, p, m = d["Q"].shape[0], d["Q"].shape[1], d["A"].shape[1], d["G"].shape[1]
+        slv = QPSolver(B, n, p, m)
+        cache = slv.new_grad_cache()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        slv.solve(T["Q"], T["q"], T["A"], T["b"], T["G"], T["h"], grad_cache=cache, tol=tol)
+        slv.backward(cache, T["Q"], T["A"], T["G"], T["g"])
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+        slv.close()
+    return times
+
+
+def _padded_latency(arrivals, times, group):
+    """Queueing of the padded baseline: a batch starts when its last request
+    has arrived and the previous batch is done."""
+    lat, free = [], 0.0
+    for k, t in enumerate(times):
+        idx = range(k * group, min(len(arrivals), (k + 1) * group))
+        start = max(free, max(arrivals[i] for i in idx))
+        free = start + t
+        lat.extend(free - arrivals[i] for i in idx)
+    return np.array(lat)
+
+
+def _serve_run(srv, pool, order, arrivals, verify=0):
+    """Submit request order[i] at arrivals[i] (seconds from start, host clock);
+    collect with poll_any.  Returns per-request latency (poll completion -
+    submit, and the server's own done - submit), the makespan and statuses."""
+    import threading
+
+    N = len(order)
+    sub_t = np.zeros(N)
+    done_t = np.zeros(N)
+    srv_lat = np.zeros(N)
+    status = np.zeros(N, np.int32)
+    ticket_of = {}
+    results = {}
+    lock = threading.Lock()
+    finished = threading.Event()
+
+    def collect():
+        got = 0
+        while got < N:
+            r = srv.poll_any()
+            if r is None:
+                time.sleep(0.0001)
+                continue
+            t = time.perf_counter()
+            with lock:
+                i = ticket_of.get(r["ticket"])
+            while i is None:  # the submitter records the ticket right after submit returns
+                time.sleep(0.00005)
+                with lock:
+                    i = ticket_of.get(r["ticket"])
+            done_t[i] = t
+            srv_lat[i] = (r["t_done_ms"] - r["t_submit_ms"]) / 1e3
+            status[i] = r["status"]
+            if verify and i < verify:
+                results[i] = r
+            got += 1
+        finished.set()
+
+    th = threading.Thread(target=collect, daemon=True)
+    th.start()
+    t0 = time.perf_counter()
+    for k in range(N):
+        target = t0 + arrivals[k]
+        while True:
+            dt = target - time.perf_counter()
+            if dt <= 0:
+                break
+            time.sleep(dt if dt > 2e-4 else 0)
+        d = pool[order[k]]
+        sub_t[k] = time.perf_counter()
+        tk = srv.submit(d["Q"], d["q"], d["A"], d["b"], d["G"], d["h"],
+                        dl_dx=d["g"] if d["grad"] else None)
+        with lock:
+            ticket_of[tk] = k
+    finished.wait(timeout=600)
+    th.join(timeout=5)
+    makespan = float(done_t.max() - t0)
+    return done_t - sub_t, srv_lat, makespan, status, results
+
+
+def _pctl(a, q):
+    return float(np.percentile(a, q) * 1e3)
+
+
+def run_serve_study(args, lines=True, requests=None, fracs=(0.5, 0.8, 0.95)):
+    """Config 5: Poisson stream of uneven QPs (n log-uniform in [8, 256],
+    m = 2n, p = n // 10, 30 % with gradients) through the continuous-batching
+    server vs the padded-batch baseline (groups of 256 in arrival order,
+    padded to the group's largest n)."""
+    import sys as _sys
+
+    import torch
+
+    from paper_2605_17913_gb300.metrics import kkt_report
+    from paper_2605_17913_gb300.serve import QPServer
+
+    _sys.setswitchinterval(1e-4)
+    torch.cuda.set_device(0)
+    import __graft_entry__ as ge
+
+    ge.build()
+    N = requests or args.serve_requests or 20000
+    P = min(args.serve_pool, N)
+    pool = _serve_pool(P)
+    order = np.arange(N) % P
+    rng = np.random.default_rng(12345)
+    srv = QPServer(hbm_budget_bytes=4 << 30, max_inflight=8, tol=args.tol)
+    # warm the kernels and the arena with one pass over a few requests
+    _serve_run(srv, pool, order[:64], np.zeros(64))
+    # saturated throughput of the server: everything submitted at once
+    lat0, slat0, mk0, st0, _ = _serve_run(srv, pool, order, np.zeros(N))
+    served_sat = N / mk0
+    # padded baseline: device time of each batch of 256 in arrival order
+    group = 256
+    times = _padded_group_times(pool, order, group, args.tol)
+    pad_sat = N / sum(times)
+    out = []
+    for frac in fracs:
+        lam = frac * pad_sat
+        arrivals = np.cumsum(rng.exponential(1.0 / lam, N))
+        arrivals -= arrivals[0]
+        lat, slat, mk, st, res = _serve_run(srv, pool, order, arrivals, verify=256)
+        plat = _padded_latency(arrivals, times, group)
+        # FP64 check of a sample of the served results
+        kmax = 0.0
+        for i, r in res.items():
+            d = pool[order[i]]
+            rep = kkt_report(d["Q"][None], d["q"][None], d["A"][None], d["b"][None],
+                             d["G"][None], d["h"][None], r["x"][None], r["y"][None],
+                             r["z"][None], r["s"][None])
+            kmax = max(kmax, float(rep["scaled"][0]))
+        line = {
+            "serve": "continuous batching", "requests": N, "distinct_instances": P,
+            "arrival": "poisson", "rate_per_s": lam, "load_vs_padded_saturation": frac,
+            "latency_ms": {"p50": _pctl(lat, 50), "p99": _pctl(lat, 99),
+                           "mean": float(lat.mean() * 1e3)},
+            "server_latency_ms": {"p50": _pctl(slat, 50), "p99": _pctl(slat, 99)},
+            "solves_per_s": N / mk, "solved": float(np.mean(st == 0)),
+            "kkt_scaled_max_sample": kmax,
+            "padded_baseline": {"latency_ms": {"p50": _pctl(plat, 50), "p99": _pctl(plat, 99)},
+                                "group": group, "saturated_solves_per_s": pad_sat},
+            "served_saturated_solves_per_s": served_sat,
+        }
+        out.append(line)
+        if lines:
+            print(json.dumps(line), flush=True)
+    srv.close()
+    return out
 
 
 # ---------------------------------------------------------------- ablation sweep
@@ -424,6 +657,9 @@ def main():
     args = parse()
     if args.ablation:
         run_ablation(args)
+        return
+    if args.serve:
+        run_serve_study(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
