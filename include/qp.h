@@ -102,7 +102,10 @@ typedef struct {
   int32_t relax_max_iter; /* Alg. 2 iteration cap (0: max_iter)                     */
   int32_t formulation;  /* QP_IMPLICIT or QP_STANDARD                               */
   int32_t residual_norm; /* QP_NORM_*                                               */
-  int32_t gwg_precision; /* QP_GWG_* (only QP_GWG_FP32 for n that fits on chip)      */
+  int32_t gwg_precision; /* QP_GWG_*: TF32 / BF16 put the G'WG products on the tensor
+                            cores (FP32 sums) in the large-problem variant; sizes that
+                            run on chip accept only QP_GWG_FP32 (QP_ENOTSUP); the
+                            server applies it to large-variant requests only         */
   int32_t refine_steps;  /* iterative-refinement sweeps of the adjoint solve of
                             Alg. 3 against the bounded system (default 3)           */
   int32_t warm_start;    /* 1: start from the x, y, z, s passed in (z, s > 0)       */

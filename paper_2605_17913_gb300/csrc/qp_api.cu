@@ -43,7 +43,7 @@ int settings_to_params(const qp_settings* st, FwdParams* P) {
       st->sigma_mode < 0 || st->sigma_mode > 1 || !(st->kappa_relax >= 0.0f) ||
       st->residual_norm < 0 || st->residual_norm > 1 || st->refine_steps < 0)
     return QP_EINVAL;
-  if (st->gwg_precision != QP_GWG_FP32) return QP_ENOTSUP;
+  if (st->gwg_precision < QP_GWG_FP32 || st->gwg_precision > QP_GWG_BF16) return QP_EINVAL;
   if (st->sigma_mode == QP_SIGMA_CONSTANT && !(st->sigma >= 0.0f && st->sigma <= 1.0f))
     return QP_EINVAL;
   P->tol = st->tol;
@@ -59,6 +59,7 @@ int settings_to_params(const qp_settings* st, FwdParams* P) {
   P->norm_abs = st->residual_norm == QP_NORM_ABS;
   P->warm_start = st->warm_start;
   P->refine_steps = st->refine_steps;
+  P->gwg = st->gwg_precision;
   return QP_OK;
 }
 }  // namespace qpgpu
@@ -193,6 +194,8 @@ int qp_solve_batch(qp_handle* h, const qp_settings* st, const float* Q, const fl
   memset(&P, 0, sizeof(P));
   const int rc = settings_to_params(st, &P);
   if (rc != QP_OK) return rc;
+  // tensor-core G'WG exists in the large-problem variant only
+  if (P.gwg != QP_GWG_FP32 && !h->split) return QP_ENOTSUP;
   P.batch = B; P.n = n; P.m = m; P.p = p; P.amax = h->amax;
   P.Q = Q; P.q = q; P.A = A; P.b = b; P.G = G; P.h = hv;
   P.x = x; P.y = y; P.z = z; P.s = s;

@@ -47,6 +47,7 @@
 
 #include "qp_device.cuh"
 #include "qp_internal.h"
+#include "qp_tc.cuh"
 
 namespace qpgpu {
 
@@ -54,7 +55,7 @@ namespace fwd {
 
 constexpr int ST_SOLVED = 0, ST_MAX_ITER = 1, ST_STALLED = 2, ST_NUMERICAL = 3, ST_BAD_INPUT = 4;
 constexpr float kCReg = 1e-7f;  // relative diagonal shift of C
-constexpr int kStaticSmem = 1024;  // upper bound of the kernel's static shared memory (state + params)
+constexpr int kStaticSmem = 1152;  // upper bound of the kernel's static shared memory (state + params)
 
 struct FLayout {
   int n, m, p, amax, fmax;
@@ -100,9 +101,12 @@ __host__ __device__ inline FLayout make_fwd_layout(int n, int m, int p, int amax
   L.o_R = take(2 * L.ldx);
   L.o_red = take(2 * (nthreads / 32) * kRedK);
   {
-    // union: Pb | (col, ta, tb, eb, tn)
+    // union: Pb | (col, ta, tb, eb, tn) | (large variant) the two tensor-core
+    // staging buffers of G'WG, 128-byte aligned
+    if (split) o = (o + 31) & ~31;
     const int base = o;
-    const int pb = round4(pb_floats(n + L.fmax + 2 + 4));
+    int pb = round4(pb_floats(n + L.fmax + 2 + 4));
+    if (split && pb < 2 * tc::stage_bytes(n, 4) / 4) pb = 2 * tc::stage_bytes(n, 4) / 4;
     L.o_Pb = base;
     L.o_col = take(2 * nthreads);
     L.o_ta = take(L.mv); L.o_tb = take(L.mv); L.o_eb = take(L.mv);
@@ -131,6 +135,11 @@ struct SharedState {
   int a, nf;         // active rows, rows of F = a + p (set by partition())
   int ni;            // inactive rows (listed in ina)
   float* gbase;      // base of K, G, A, Y, C: the dynamic shared memory or the workspace
+  uint64_t mbar[2];  // tensor-core G'WG: completion of the two staging buffers
+  uint32_t tmem;     // its TMEM base (large variant with gwg != 0)
+  int tc_flag;       // a bounded wait ran out in the current G'WG
+  int tc_bad;        // sticky: G'WG falls back to FP32 for the rest of the solve
+  int gwg;           // 0 FP32, 1 TF32, 2 BF16 (tensor-core products, large variant)
   float qn, bn, hn;  // |q|, |b|, |h| (infinity norms)
 };
 
@@ -168,10 +177,14 @@ static __shared__ unsigned char fwd_parity[512];   // block_reduce buffer parity
 
 template <int NT, bool kBig>
 struct Solver {
-  static __device__ void init(int n, int m, int p, int amax, float* ws) {
+  static __device__ void init(int n, int m, int p, int amax, float* ws, int gwg) {
     if (threadIdx.x == 0) {
       fwd_state.L = make_fwd_layout(n, m, p, amax, NT, kBig);
       fwd_state.gbase = kBig ? ws : fwd_dyn;
+      fwd_state.gwg = kBig ? gwg : 0;
+      fwd_state.tc_flag = 0;
+      fwd_state.tc_bad = 0;
+      fwd_state.tmem = 0;
       fwd_state.a = 0;
       fwd_state.nf = p;
       fwd_state.t_mark = clock64();
@@ -322,7 +335,21 @@ struct Solver {
     QP_BIG(K); QP_ARR(qd); QP_BIG(G); QP_ARR(ea); QP_BIG(Y); QP_BIG(C); QP_ARR(dinv);
     QP_ARR(cdinv); QP_ARR(Pb); QP_ARR(red); QP_IARR(ina);
     const int nf = fwd_state.nf;
-    syrk_gwg<NT>(K, L.ldk, qd, G, L.ldg, ea, ina, fwd_state.ni, L.n);
+    bool tc_done = false;
+    if constexpr (kBig) {
+      if (fwd_state.gwg != 0 && !fwd_state.tc_bad) {
+        char* stage = reinterpret_cast<char*>(fwd_dyn + L.o_Pb);  // dead during the factorisation
+        const int ni = fwd_state.ni;
+        const uint32_t tm = fwd_state.tmem;
+        tc_done = fwd_state.gwg == 2
+                      ? tc::syrk_gwg_tc<NT, true>(K, L.ldk, qd, G, L.ldg, ea, ina, ni, L.n, stage,
+                                                  fwd_state.mbar, tm, &fwd_state.tc_flag)
+                      : tc::syrk_gwg_tc<NT, false>(K, L.ldk, qd, G, L.ldg, ea, ina, ni, L.n,
+                                                   stage, fwd_state.mbar, tm, &fwd_state.tc_flag);
+        if (!tc_done && threadIdx.x == 0) fwd_state.tc_bad = 1;
+      }
+    }
+    if (!tc_done) syrk_gwg<NT>(K, L.ldk, qd, G, L.ldg, ea, ina, fwd_state.ni, L.n);
     QP_MARK(PH_SYRK);
 #ifdef QP_PHASE_TIMERS
     unsigned long long* const sub = fwd_state.timers ? fwd_state.timers + PH_COUNT : nullptr;
@@ -1028,12 +1055,33 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) qp_forward_kernel(co
   __syncthreads();
   const int bi = P.desc ? 0 : blockIdx.x;
   float* const ws = kBig ? sP.ws + (size_t)bi * (size_t)sP.ws_stride : nullptr;
-  Solver<NT, kBig>::init(sP.n, sP.m, sP.p, sP.amax, ws);  // ends with a barrier
+  Solver<NT, kBig>::init(sP.n, sP.m, sP.p, sP.amax, ws, sP.gwg);  // ends with a barrier
 #ifdef QP_PHASE_TIMERS
   if (threadIdx.x == 0) fwd_state.timers = P.timers;
   __syncthreads();
 #endif
+  if constexpr (kBig) {
+    // tensor-core G'WG: this CTA's TMEM for the whole solve (one CTA per SM:
+    // the variant uses the whole register file)
+    if (sP.gwg != 0) {
+      if (threadIdx.x < 32) {
+        tc::tmem_alloc(&fwd_state.tmem, tc::kTmemCols);
+        tc::tmem_relinquish();
+      }
+      tc::fence_before_sync();
+      __syncthreads();
+      tc::fence_after_sync();
+    }
+  }
   Solver<NT, kBig>::run(sP, bi);
+  if constexpr (kBig) {
+    if (sP.gwg != 0) {
+      tc::fence_before_sync();
+      __syncthreads();
+      tc::fence_after_sync();
+      if (threadIdx.x < 32) tc::tmem_dealloc(fwd_state.tmem, tc::kTmemCols);
+    }
+  }
 }
 
 }  // namespace fwd

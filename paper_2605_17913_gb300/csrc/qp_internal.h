@@ -35,6 +35,7 @@ struct FwdParams {
   // settings
   float tol, sigma, kappa_min, kappa_relax, relax_tol, step_frac;
   int max_iter, relax_max_iter, sigma_mode, formulation, norm_abs, warm_start, refine_steps;
+  int gwg;  // G'WG products: 0 FP32, 1 TF32, 2 BF16 (tensor cores, large variant only)
   // gradient cache (nullptr: no relax, no cache)
   float* cache;
   long long cache_stride;

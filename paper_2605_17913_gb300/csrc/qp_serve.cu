@@ -329,6 +329,7 @@ cudaError_t qp_server::issue(Launch& L) {
     P.desc = L.ddesc;
     const SizeCfg& c0 = take[0]->cfg;
     P.ws = c0.split ? db : nullptr;  // selects the large variant; CTAs use their descriptor's
+    if (!c0.split) P.gwg = 0;  // tensor-core G'WG: large variant only
     e = launch_forward(P, c0.nt, fsmem, R, L.stream);
   }
   if (e == cudaSuccess && nb > 0) {

@@ -174,6 +174,39 @@ def test_large_variant_parity(workload, B, sizes):
     check_grads(res, ref)
 
 
+@pytest.mark.parametrize("mode", ["tf32", "bf16"])
+def test_tensor_core_gwg_parity(mode):
+    """G'WG on the tensor cores (TF32 / BF16 products, FP32 sums) in the
+    large variant, n = 256, cond(Q) = 1e4: the IPM's FP32 residuals and the
+    backward's refinement hold the FP32 bars."""
+    batch = make_batch("precision", 3, seed=0)
+    res = gpu_run(batch, grad=True, gwg_precision=mode)
+    ref = oracle_run(batch, grad=True)
+    check_forward(batch, res, O.solve(batch.Q, batch.q, batch.A, batch.b, batch.G, batch.h,
+                                      tol=1e-12, nthreads=3))
+    check_grads(res, ref)
+
+
+def test_tensor_core_gwg_one_newton_step():
+    """One Newton step from the same start: the tensor-core contraction moves
+    x by no more than its input rounding (TF32: 2^-11, BF16: 2^-8 relative,
+    amplified by the conditioning of one step) and is not the FP32 result."""
+    batch = make_batch("precision", 2, seed=2)
+    x32 = gpu_run(batch, max_iter=1)["x"].astype(np.float64)
+    for mode, bound in (("tf32", 2e-2), ("bf16", 2e-1)):
+        x = gpu_run(batch, max_iter=1, gwg_precision=mode)["x"].astype(np.float64)
+        d = np.abs(x - x32).max() / np.abs(x32).max()
+        assert 0 < d < bound, (mode, d)
+
+
+def test_tensor_core_gwg_refused_on_chip():
+    from paper_2605_17913_gb300 import _lib
+
+    batch = make_batch("small", 2, seed=0)
+    with pytest.raises(_lib.QPError, match="QP_ENOTSUP"):
+        gpu_run(batch, gwg_precision="tf32")
+
+
 def test_unconstrained_closed_form():
     batch = make_batch("small", 5, seed=2, m=0, p=0)
     res = gpu_run(batch, grad=True)
