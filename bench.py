@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=None)
     ap.add_argument("--serve-pool", type=int, default=2048)
     ap.add_argument("--no-serve", action="store_true")
+    # G'WG in FP32 vs TF32 / BF16 tensor cores on the n = 256 workload
+    # (one JSON line per mode instead of the bench line)
+    ap.add_argument("--precision", action="store_true")
     return ap.parse_args()
 
 
@@ -596,6 +599,71 @@ def run_serve_study(args, lines=True, requests=None, fracs=(0.5, 0.8, 0.95)):
     return out
 
 
+# ---------------------------------------------------------------- precision study
+def run_precision(args):
+    """Config 4: 256 QPs, n = 256, m = 512, p = 32, cond(Q) = 1e4; solve +
+    relax + backward with G'WG in FP32, TF32 or BF16 (tensor cores, FP32
+    sums).  Errors against FP64: the KKT measure of every instance, x and the
+    gradients against the oracle on a sample."""
+    import torch
+
+    from oracle import oracle as O
+    from paper_2605_17913_gb300.metrics import kkt_report, rel_err_2, rel_err_inf
+    from paper_2605_17913_gb300.solver import QPSolver
+    from qpgen import make_batch
+
+    torch.cuda.set_device(0)
+    import __graft_entry__ as ge
+
+    ge.build()
+    B = args.batch or 256
+    data = make_batch("precision", B, seed=0)
+    names = ("Q", "q", "A", "b", "G", "h", "g")
+    T = {k: torch.from_numpy(getattr(data, k)).cuda() for k in names}
+    slv = QPSolver(B, data.n, data.p, data.m)
+    cache = slv.new_grad_cache()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    sample = [0, 1, 2, 3]
+    sub = make_batch("precision", len(sample), seed=0)
+    ref = O.solve(sub.Q, sub.q, sub.A, sub.b, sub.G, sub.h, tol=1e-12,
+                  kappa_relax=args.kappa_relax, g=sub.g, nthreads=len(sample))
+    for mode in ("fp32", "tf32", "bf16"):
+        ms = []
+        for rep_ in range(args.warmup + args.steps):
+            flush.zero_()
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record()
+            out = slv.solve(T["Q"], T["q"], T["A"], T["b"], T["G"], T["h"], grad_cache=cache,
+                            tol=args.tol, kappa_relax=args.kappa_relax, gwg_precision=mode)
+            e[1].record()
+            gr = slv.backward(cache, T["Q"], T["A"], T["G"], T["g"])
+            e[2].record()
+            torch.cuda.synchronize()
+            if rep_ >= args.warmup:
+                ms.append((e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])))
+        r = {k: v.cpu().numpy() for k, v in out.items()}
+        gg = {k: v.cpu().numpy() for k, v in gr.items()}
+        rep = kkt_report(data.Q, data.q, data.A, data.b, data.G, data.h, r["x"], r["y"], r["z"],
+                         r["s"])
+        fwd = statistics.median(m[0] for m in ms)
+        bwd = statistics.median(m[1] for m in ms)
+        ok = (r["status"] == 0) & (rep["scaled"] <= 1e-5)
+        line = {
+            "precision": "G'WG products", "gwg": mode, "workload": "precision", "batch": B,
+            "n": data.n, "m_ineq": data.m, "p_eq": data.p, "cond_Q": 1e4,
+            "forward_ms": fwd, "backward_ms": bwd,
+            "solves_grads_per_s": float(ok.sum()) / ((fwd + bwd) / 1e3),
+            "solved": float(np.mean(r["status"] == 0)),
+            "iters_mean": float(np.mean(r["iters"])),
+            "kkt_scaled_max": float(rep["scaled"].max()),
+            "x_err_vs_fp64_max": float(rel_err_inf(r["x"][sample], ref["x"]).max()),
+            "grad_err_vs_fp64_max": {k: float(rel_err_2(gg[k][sample], ref[k]).max())
+                                     for k in ("dQ", "dq", "dA", "db", "dG", "dh")},
+            "error_sample": f"instances {sample} against the FP64 oracle (relaxed point)",
+        }
+        print(json.dumps(line), flush=True)
+
+
 # ---------------------------------------------------------------- ablation sweep
 def run_ablation(args):
     """Implicit vs standard complementarity, both in FP32, on one batch of the
@@ -660,6 +728,9 @@ def main():
         return
     if args.serve:
         run_serve_study(args)
+        return
+    if args.precision:
+        run_precision(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
