@@ -35,7 +35,8 @@ def _stale(target: str, deps) -> bool:
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     os.makedirs(OBJ, exist_ok=True)
     sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    headers = sorted(glob.glob(os.path.join(CSRC, "*.h*")) +
+    headers = sorted(glob.glob(os.path.join(CSRC, "*.h")) +
+                     glob.glob(os.path.join(CSRC, "*.cuh")) +
                      glob.glob(os.path.join(INCLUDE, "*.h")))
     procs, objs = [], []
     for src in sources:

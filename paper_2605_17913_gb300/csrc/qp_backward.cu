@@ -137,7 +137,8 @@ __device__ void warp_rows_dot(const float* M, int ld, int rows, int cols, const 
 
 // Solve [K_I F'; F -D] (d, t) = (r1, r2) with the cached factors: r1 in R
 // (row 0), r2 in t; the solution overwrites both.  kMaxS: warp-solve length
-// bound in units of 32 rows (4 on chip, 8 for the large variant).
+// bound of the K part in units of 32 rows (4 on chip, 8 for the large
+// variant, whose C part goes to 320 rows).
 template <int NT, int kMaxS>
 __device__ void two_level_solve(const float* K, int ldk, const float* dinv, const float* Y,
                                 const float* C, int ldc, const float* cdinv, int n, int nf,
@@ -160,7 +161,9 @@ __device__ void two_level_solve(const float* K, int ldk, const float* dinv, cons
         if (nf <= 160) small_chol_solve<5>(C, ldc, cdinv, nf, t);
         else if (nf <= 192) small_chol_solve<6>(C, ldc, cdinv, nf, t);
         else if (nf <= 224) small_chol_solve<7>(C, ldc, cdinv, nf, t);
-        else small_chol_solve<8>(C, ldc, cdinv, nf, t);
+        else if (nf <= 256) small_chol_solve<8>(C, ldc, cdinv, nf, t);
+        else if (nf <= 288) small_chol_solve<9>(C, ldc, cdinv, nf, t);
+        else small_chol_solve<10>(C, ldc, cdinv, nf, t);
       }
     }
     __syncthreads();
@@ -383,7 +386,7 @@ __global__ void __launch_bounds__(NT) qp_backward_kernel(const BwdParams P) {
 constexpr size_t kBwdBudget = 227 * 1024 - 512;
 
 size_t backward_direct_smem_bytes(int n, int m, int p, int amax, bool split) {
-  if (split ? (n > 256 || amax + p > 256) : (n > 128 || amax + p > 128)) return 0;
+  if (split ? (n > 256 || amax + p > 318) : (n > 128 || amax + p > 128)) return 0;
   const size_t bytes =
       (size_t)make_blayout(n, m, p, amax, 256, false, split).total * sizeof(float);
   return bytes <= kBwdBudget ? bytes : 0;

@@ -8,16 +8,16 @@ cudaError_t launch_forward_nt(const FwdParams& P, size_t smem, int grid, cudaStr
 template <int NT, bool kBig>
 int forward_blocks_per_sm_nt(size_t smem);
 
-// Threads per CTA and the active-row cap amax by size.  On chip (n <= 128,
-// everything in shared memory): 128 threads up to n = 72 (fewer warps per
-// barrier, no register cap; 5 % faster than 256 threads at n = 50), else 512;
-// amax = rows kept as multipliers, at most min(m, n) (at a non-degenerate
-// solution at most n - p rows are active), lowered to fit shared memory but
-// not more than 4 below min(m, n - p); amax + p <= 126 (warp solves hold at
-// most 128 rows, two of them folded right-hand sides).  Otherwise the large
-// variant (n <= 256): 512 threads, K, G, A, Y, C in a global workspace,
-// amax + p <= 254.  Rows beyond amax with W > 1 go to K_I with the smallest W
-// first (tau grows).
+// Threads per CTA and the active-row cap amax by size.  amax = rows kept as
+// multipliers: min(m, n) where possible (at a non-degenerate solution at most
+// n - p rows are active, at a degenerate one up to n); rows beyond it with
+// W > 1 would have to go to K_I (tau grows), which FP32 may not factor.  On
+// chip (n <= 128, everything in shared memory): 128 threads up to n = 72
+// (fewer warps per barrier, no register cap; 5 % faster than 256 threads at
+// n = 50), else 512; amax lowered to fit shared memory but not below
+// min(m, n - p), and amax + p <= 126 (warp solves hold at most 128 rows, two
+// of them folded right-hand sides).  Otherwise the large variant (n <= 256):
+// 512 threads, K, G, A, Y, C in a global workspace, amax + p <= 318.
 size_t forward_config(int n, int m, int p, int* nthreads, int* amax_out, long long* ws_floats) {
   if (nthreads) *nthreads = 0;
   if (amax_out) *amax_out = 0;
@@ -28,7 +28,7 @@ size_t forward_config(int n, int m, int p, int* nthreads, int* amax_out, long lo
     const int nt = n <= 72 ? 128 : 512;
     int amax0 = m < n ? m : n;
     if (amax0 + p > 126) amax0 = 126 - p;
-    int floor_a = (m < n - p ? m : n - p) - 4;
+    int floor_a = m < n - p ? m : n - p;
     if (floor_a < 0) floor_a = 0;
     for (int amax = amax0; amax >= floor_a && amax >= 0; --amax) {
       const fwd::FLayout L = fwd::make_fwd_layout(n, m, p, amax, nt);
@@ -41,7 +41,7 @@ size_t forward_config(int n, int m, int p, int* nthreads, int* amax_out, long lo
     }
   }
   int amax = m < n ? m : n;
-  if (amax + p > 254) amax = 254 - p;
+  if (amax + p > 318) amax = 318 - p;
   if (amax < 0) return 0;
   const fwd::FLayout L = fwd::make_fwd_layout(n, m, p, amax, 512, true);
   const size_t bytes = (size_t)L.total * sizeof(float);

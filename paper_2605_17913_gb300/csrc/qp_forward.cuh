@@ -60,9 +60,9 @@ constexpr int kStaticSmem = 1152;  // upper bound of the kernel's static shared 
 struct FLayout {
   int n, m, p, amax, fmax;
   int ldk, ldg, ldx, ldc, nv, mv, pv, fv;
-  int split;      // K, G, A, Y, C in a global workspace (large problems)
-  int big_total;  // floats of K, G, A, Y, C
-  int o_K, o_qd, o_G, o_A, o_Y, o_C, o_R, o_col, o_red, o_Pb;
+  int split;      // K, G, Y, C in a global workspace (large problems)
+  int big_total;  // floats of K, G, Y, C
+  int o_K, o_qd, o_G, o_Y, o_C, o_R, o_col, o_red, o_Pb;
   int o_q, o_x, o_rt, o_dinv, o_tn;
   int o_b, o_y, o_re;
   int o_cdinv, o_D, o_ua, o_ub, o_act;
@@ -87,11 +87,11 @@ __host__ __device__ inline FLayout make_fwd_layout(int n, int m, int p, int amax
   L.fv = round4(L.fmax > 0 ? L.fmax : 1);
   int o = 0;
   auto take = [&](int cnt) -> int { int r = o; o += round4(cnt); return r; };
-  // the five matrices: first in shared memory, or (split) at the start of
-  // the instance's global workspace, with the rest in shared memory from 0
+  // the four matrices: first in shared memory, or (split) at the start of
+  // the instance's global workspace, with the rest in shared memory from 0.
+  // A (p x n) is read where the caller keeps it (L1 / L2), row stride n.
   L.o_K = take(n * L.ldk);
   L.o_G = take(m * L.ldg);
-  L.o_A = take(p * L.ldg);
   L.o_Y = take((L.fmax + 2) * L.ldk);
   L.o_C = take((L.fmax + 2) * L.ldc);
   L.split = split ? 1 : 0;
@@ -134,7 +134,8 @@ struct SharedState {
   unsigned long long* timers;      // phase timers only
   int a, nf;         // active rows, rows of F = a + p (set by partition())
   int ni;            // inactive rows (listed in ina)
-  float* gbase;      // base of K, G, A, Y, C: the dynamic shared memory or the workspace
+  float* gbase;      // base of K, G, Y, C: the dynamic shared memory or the workspace
+  const float* gA;   // this instance's A in the caller's memory (row stride n)
   uint64_t mbar[2];  // tensor-core G'WG: completion of the two staging buffers
   uint32_t tmem;     // its TMEM base (large variant with gwg != 0)
   int tc_flag;       // a bounded wait ran out in the current G'WG
@@ -207,7 +208,7 @@ struct Solver {
   static __device__ __noinline__ bool load(const FwdParams& P, int bi) {
     const FLayout& L = fwd_state.L;
     const int n = L.n, m = L.m, p = L.p, t = threadIdx.x;
-    QP_BIG(K); QP_ARR(qd); QP_BIG(G); QP_BIG(A); QP_ARR(q); QP_ARR(b); QP_ARR(h); QP_ARR(red);
+    QP_BIG(K); QP_ARR(qd); QP_BIG(G); QP_ARR(q); QP_ARR(b); QP_ARR(h); QP_ARR(red);
     for (int i = t; i < L.total; i += NT) fwd_dyn[i] = 0.0f;
     if (kBig)
       for (int i = t; i < L.big_total; i += NT) fwd_state.gbase[i] = 0.0f;
@@ -229,12 +230,8 @@ struct Solver {
       chk = isfinite(v) ? chk : 1.0f;
       G[r * L.ldg + c] = v;
     }
-    for (int e = t; e < p * n; e += NT) {
-      const int r = e / n, c = e - r * n;
-      const float v = gA[e];
-      chk = isfinite(v) ? chk : 1.0f;
-      A[r * L.ldg + c] = v;
-    }
+    for (int e = t; e < p * n; e += NT) chk = isfinite(gA[e]) ? chk : 1.0f;
+    if (t == 0) fwd_state.gA = gA;  // A stays in the caller's memory
     float lq = 0.f, lb = 0.f, lh = 0.f;
     for (int i = t; i < n; i += NT) {
       const float v = P.q[(size_t)bi * n + i];
@@ -261,7 +258,8 @@ struct Solver {
   static __device__ __noinline__ void partition() {
     const FLayout& L = fwd_state.L;
     const int m = L.m, p = L.p, n = L.n, t = threadIdx.x, w = t >> 5, lane = t & 31;
-    QP_ARR(bz); QP_ARR(bs); QP_ARR(red); QP_BIG(G); QP_BIG(A); QP_BIG(Y);
+    QP_ARR(bz); QP_ARR(bs); QP_ARR(red); QP_BIG(G); QP_BIG(Y);
+    const float* const A = fwd_state.gA;
     QP_BIG(C); QP_ARR(D); QP_ARR(ea); QP_IARR(act); QP_IARR(pos); QP_IARR(ina);
     float tau = 1.0f;
     for (int round = 0; round < 40; ++round) {
@@ -297,7 +295,7 @@ struct Solver {
     __syncthreads();
     const int a = fwd_state.a, nf = fwd_state.nf;
     for (int k = w; k < nf; k += NT / 32) {
-      const float* src = k < a ? G + act[k] * L.ldg : A + (k - a) * L.ldg;
+      const float* src = k < a ? G + act[k] * L.ldg : A + (k - a) * n;
       for (int c = lane; c < n; c += 32) Y[k * L.ldk + c] = src[c];
       for (int c = lane; c <= k; c += 32) C[k * L.ldc + c] = 0.f;
     }
@@ -416,7 +414,7 @@ struct Solver {
     QP_MARK(PH_SOLVE);
   }
 
-  // warp solve with C for nf rows (up to 128 on chip, 256 in the large variant)
+  // warp solve with C for nf rows (up to 128 on chip, 320 in the large variant)
   static __device__ void c_solve_n(float* u, int nf, bool upper_only) {
     if (nf <= 32) c_solve<1>(u, nf, upper_only);
     else if (nf <= 64) c_solve<2>(u, nf, upper_only);
@@ -426,7 +424,9 @@ struct Solver {
       if (nf <= 160) c_solve<5>(u, nf, upper_only);
       else if (nf <= 192) c_solve<6>(u, nf, upper_only);
       else if (nf <= 224) c_solve<7>(u, nf, upper_only);
-      else c_solve<8>(u, nf, upper_only);
+      else if (nf <= 256) c_solve<8>(u, nf, upper_only);
+      else if (nf <= 288) c_solve<9>(u, nf, upper_only);
+      else c_solve<10>(u, nf, upper_only);
     }
   }
 
@@ -510,7 +510,8 @@ struct Solver {
   static __device__ __noinline__ float2 residuals(const FwdParams& P, bool implicit, int mode) {
     const FLayout& L = fwd_state.L;
     const int n = L.n, m = L.m, p = L.p, t = threadIdx.x;
-    QP_BIG(K); QP_ARR(qd); QP_BIG(G); QP_BIG(A); QP_ARR(q); QP_ARR(b); QP_ARR(h); QP_ARR(x);
+    QP_BIG(K); QP_ARR(qd); QP_BIG(G); QP_ARR(q); QP_ARR(b); QP_ARR(h); QP_ARR(x);
+    const float* const A = fwd_state.gA;
     QP_ARR(y); QP_ARR(z); QP_ARR(s); QP_ARR(rt); QP_ARR(re); QP_ARR(ri);
     QP_ARR(bz); QP_ARR(bs); QP_ARR(tn); QP_ARR(red); QP_ARR(col);
     float ks[1] = {0.f};
@@ -534,7 +535,7 @@ struct Solver {
         for (int j = 0; j < i; ++j) qx = fmaf(K[j * L.ldk + i], x[j], qx);
         for (int j = i + 1; j < n; ++j) qx = fmaf(K[i * L.ldk + j], x[j], qx);
         float aty = 0.f;
-        for (int k = 0; k < p; ++k) aty = fmaf(A[k * L.ldg + i], y[k], aty);
+        for (int k = 0; k < p; ++k) aty = fmaf(__ldg(A + k * n + i), y[k], aty);
         const float r = qx + q[i] + tn[i] + aty;
         rt[i] = r;
         mx[12] += isfinite(r) ? 0.f : 1.f;
@@ -560,7 +561,8 @@ struct Solver {
         }
       } else {
         const int k = u - n - m;
-        const float ax = row_dot(A, L.ldg, k, x, L.nv);
+        float ax = 0.f;
+        for (int j = 0; j < n; ++j) ax = fmaf(__ldg(A + k * n + j), x[j], ax);
         const float r = ax - b[k];
         re[k] = r;
         mx[12] += isfinite(r) ? 0.f : 1.f;
