@@ -94,6 +94,36 @@ def fp32_alu_peak_tflops(sms=152, lanes=128, mhz=2070.0):
     return sms * lanes * 2 * mhz * 1e6 / 1e12
 
 
+# ---------------------------------------------------------------- multi-rank (replicas)
+def shard_start(rank: int, per_rank: int) -> int:
+    """Weak scaling by instance: rank r solves instances [r * per_rank,
+    (r + 1) * per_rank) of the seeded workload; the ranks share no data and
+    exchange nothing on the data path."""
+    return rank * per_rank
+
+
+def combine_ranks(ms: float, passed: int, device=None):
+    """Whole-job figures over the default process group: the slowest rank's
+    step time and the total of instances that passed."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    tp = torch.tensor([passed], dtype=torch.float64, device=device)
+    dist.all_reduce(tp)
+    return float(t.item()), int(tp.item())
+
+
+def max_over_ranks(x: float, device=None) -> float:
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ---------------------------------------------------------------- clocks sampler
 class Clocks:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -223,7 +253,7 @@ def run_ours(args, rank, world, local_rank):
     cfg = CONFIGS[args.workload]
     B = args.batch or cfg["batch"]
     # weak scaling: every rank solves its own shard of B instances
-    data = make_batch(args.workload, B, seed=0, start=rank * B)
+    data = make_batch(args.workload, B, seed=0, start=shard_start(rank, B))
     n, m, p = data.n, data.m, data.p
     names = ("Q", "q", "A", "b", "G", "h", "g")
     T = {k: torch.from_numpy(getattr(data, k)).to(dev) for k in names}
@@ -288,12 +318,7 @@ def run_ours(args, rank, world, local_rank):
     passed = int(ok.sum())
     local = {"ms": step_ms / args.steps, "passed": passed}
     if world > 1:
-        t = torch.tensor([local["ms"], -passed], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_max = float(t[0])
-        tp = torch.tensor([passed], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tp)
-        total_passed = int(tp.item())
+        ms_max, total_passed = combine_ranks(local["ms"], passed, dev)
     else:
         ms_max, total_passed = local["ms"], passed
     value = total_passed / (ms_max / 1e3)
@@ -335,9 +360,7 @@ def run_ours(args, rank, world, local_rank):
     e2e_dt = (time.perf_counter() - t0) / e2e_steps
     e2e_value = total_passed / e2e_dt if world == 1 else None
     if world > 1:
-        te = torch.tensor([e2e_dt], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
-        e2e_value = total_passed / float(te.item())
+        e2e_value = total_passed / max_over_ranks(e2e_dt, dev)
     if rank != 0:
         return
     serve = None
