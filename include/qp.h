@@ -135,8 +135,9 @@ int qp_handle_destroy(qp_handle* h);
  * lower; unpacked for the large-problem variant), Y = F L^-T with
  * F = [G_A; A] (nf = active rows + n_eq rows), the factor of
  * C = D + Y Y' (packed lower; unpacked for the large variant), W (or 1/W),
- * the active-row map and the relaxed point (x, y, z), each block padded to
- * 16 bytes. */
+ * the active-row map, the relaxed point (x, y, z) and one more m-block (the
+ * solve keeps the iterate the relax starts from in this slot), each block
+ * padded to 16 bytes. */
 size_t qp_grad_cache_bytes(const qp_dims* dims);
 
 /* Per-instance shared memory the solve kernel uses, in bytes (0 if the
@@ -179,7 +180,7 @@ int qp_backward_batch(qp_handle* h, const float* grad_cache, const float* Q, con
  *      counterpart) -------------------------------------------------------- */
 
 /* Size of the library's fixed device array that holds the factor cache of
- * qp_solve_backward_static: 16 MiB per device (for example 647 instances of
+ * qp_solve_backward_static: 16 MiB per device (for example 637 instances of
  * n = 50, n_eq = 10, n_ineq = 100; compare qp_grad_cache_bytes). */
 #define QP_STATIC_CACHE_BYTES (16 * 1024 * 1024)
 

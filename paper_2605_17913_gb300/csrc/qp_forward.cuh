@@ -896,6 +896,26 @@ struct Solver {
     __syncthreads();
   }
 
+  // save (restore = false) or restore the iterate (x, y, z, s) in the
+  // instance's gradient-cache slot (its x, y, z blocks and the s block)
+  static __device__ __noinline__ void snapshot(const FwdParams& P, int bi, bool restore) {
+    const FLayout& L = fwd_state.L;
+    QP_ARR(x); QP_ARR(y); QP_ARR(z); QP_ARR(s);
+    const int n = L.n, m = L.m, p = L.p, t = threadIdx.x;
+    const CacheLayout cl = cache_layout(n, m, p, L.amax, kBig);
+    float* c = P.cache + (size_t)bi * (size_t)P.cache_stride;
+    if (restore) {
+      for (int i = t; i < n; i += NT) x[i] = c[cl.ox + i];
+      for (int k = t; k < p; k += NT) y[k] = c[cl.oy + k];
+      for (int r = t; r < m; r += NT) { z[r] = c[cl.oz + r]; s[r] = c[cl.os + r]; }
+    } else {
+      for (int i = t; i < n; i += NT) c[cl.ox + i] = x[i];
+      for (int k = t; k < p; k += NT) c[cl.oy + k] = y[k];
+      for (int r = t; r < m; r += NT) { c[cl.oz + r] = z[r]; c[cl.os + r] = s[r]; }
+    }
+    __syncthreads();
+  }
+
   static __device__ __noinline__ void write_solution(const FwdParams& P, int bi, bool good) {
     const FLayout& L = fwd_state.L;
     QP_ARR(x); QP_ARR(y); QP_ARR(z); QP_ARR(s);
@@ -915,6 +935,7 @@ struct Solver {
     const bool implicit = P.formulation == 0;
     int status = ST_SOLVED, iters = 0;
     float meas = NAN;
+    bool snap = false;  // a snapshot for Alg. 2 is in the cache slot
     const bool good = load(P, bi);
     if (!good) {
       status = ST_BAD_INPUT;
@@ -955,11 +976,17 @@ struct Solver {
         // ---- Alg. 1 ----
         float best = INFINITY;
         int since_best = 0;
+        const bool snap_on = implicit && P.cache && P.kappa_relax > 0.f;
         for (int it = 0; status == ST_SOLVED; ++it) {
           const float2 rk = residuals(P, implicit, 0);
           const float kappa = rk.y;
           meas = rk.x;
           if (!(meas == meas)) { status = ST_NUMERICAL; break; }
+          // the last iterate with kappa >= kappa_relax is where Alg. 2 starts
+          if (snap_on && kappa >= P.kappa_relax) {
+            snapshot(P, bi, false);
+            snap = true;
+          }
           if (meas < P.tol) break;
           if (it >= P.max_iter) { status = ST_MAX_ITER; break; }
           if (meas < 0.9f * best) { best = meas; since_best = 0; }
@@ -975,6 +1002,12 @@ struct Solver {
     if (P.cache && status != ST_BAD_INPUT) {
       QP_ARR(z); QP_ARR(s); QP_ARR(bz); QP_ARR(bs);
       if (m > 0 && P.kappa_relax > 0.f && status != ST_NUMERICAL) {
+        // Alg. 2 targets the central-path point x(kappa_relax), which does
+        // not depend on where the Newton iteration starts; from the solve's
+        // last iterate with kappa >= kappa_relax it is a few steps away,
+        // from the converged solution (kappa << kappa_relax) about twice as
+        // many (eq. 7 limits how fast kappa can grow back).
+        if (snap) snapshot(P, bi, true);
         int rstatus = ST_MAX_ITER;
         float rbest = INFINITY;
         int rsince = 0;

@@ -66,12 +66,13 @@ struct BwdParams {
 // K_I = Q + G_I'W_I G_I (packed lower), Y = F L^-T (nf rows of n), L_C of
 // C = D + Y Y' (packed lower), W of the inactive rows and 1/W of the active
 // rows, the row -> position map
-// (int32, -1 for inactive rows) and the point (x, y, z).
+// (int32, -1 for inactive rows) and the point (x, y, z); s completes the
+// solve's snapshot (x, y, z, s) that the relax starts from.
 // Large-problem variant (split): L, Y and L_C are stored unpacked with the
 // forward kernel's strides ldk = n | 1 (L, Y) and ldc = (amax + p + 2) | 1
 // (L_C), so that the backward pass reads them in place.
 struct CacheLayout {
-  int oHdr, oL, oY, oLC, oW, oPos, ox, oy, oz, stride;
+  int oHdr, oL, oY, oLC, oW, oPos, ox, oy, oz, os, stride;
   int ldk, ldc;  // strides of L / Y and of L_C (split layout; 0 when packed)
 };
 
@@ -92,6 +93,7 @@ __host__ __device__ inline CacheLayout cache_layout(int n, int m, int p, int ama
   c.ox = o; o += r4(n);
   c.oy = o; o += r4(p);
   c.oz = o; o += r4(m);
+  c.os = o; o += r4(m);
   c.stride = o;
   return c;
 }

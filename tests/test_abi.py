@@ -77,7 +77,7 @@ def test_sizes(L):
     dims = _lib.Dims(3, 10, 2, 20)
     # padded blocks: header, L (55), Y (12 x 10: amax = min(m, n) = 10 plus p = 2 rows),
     # L_C (78), W, row map, x, y, z
-    per = (4 + 56 + 120 + 80 + 20 + 20 + 12 + 4 + 20) * 4
+    per = (4 + 56 + 120 + 80 + 20 + 20 + 12 + 4 + 20 + 20) * 4
     assert L.qp_grad_cache_bytes(ctypes.byref(dims)) == 3 * per
     for c in (0, 1, 2, 3, 4, -1, -6):
         assert isinstance(_lib.status_string(c), str)
