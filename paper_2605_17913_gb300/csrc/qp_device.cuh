@@ -453,24 +453,197 @@ __device__ void panel_syrk(const float* Pb, float* A, int lda, int rowA0, int nA
   __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// 16-wide panels.  Pb16 holds panel rows in groups of 4 (16 values each)
+// padded to 68 floats (conflict-free float4 loads across row groups); fb is a
+// 16 x 16 scratch for the diagonal block's factor.  Per panel: warp 0 factors
+// the diagonal block with shuffles (lane i holds row i), barrier, every row
+// below (and every border row) is solved against it by one thread, barrier,
+// rank-16 trailing update, barrier -- three barriers per 16 columns, and the
+// block factor computed once instead of by every thread.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline int pb16_floats(int rows) { return ((rows + 3) / 4 + 1) * 68; }
+__device__ __forceinline__ int pb16_off(int r) { return (r >> 2) * 68 + (r & 3) * 16; }
+
+template <int NT>
+__device__ bool panel_factor16(float* M, int ld, int j0, int jb, float* dinv, float* A, int lda,
+                               int rowA0, int nA, float* B, int ldb, int nB, float* Pb,
+                               float* fb) {
+  const int nA4 = (nA + 3) & ~3;
+  const int N = nA + nB;
+  const int tid = threadIdx.x, lane = tid & 31;
+  int okw = 1;
+  if (tid < 32) {
+    float a[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c)
+      a[c] = (lane < jb && c <= lane) ? M[(j0 + lane) * ld + j0 + c] : 0.0f;
+    float rinv = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      if (k < jb) {
+        const float d = __shfl_sync(kFull, a[k], k);
+        if (!(d > 0.0f) || !(d < INFINITY)) okw = 0;
+        const float r = rsqrtf(d);
+        if (lane == k) {
+          a[k] = d * r;
+          rinv = r;
+        } else if (lane > k) {
+          a[k] *= r;
+        }
+#pragma unroll
+        for (int c = k + 1; c < 16; ++c) {
+          const float lck = __shfl_sync(kFull, a[k], c);  // L[c][k], held by lane c
+          if (c < jb && lane >= c) a[c] = fmaf(-a[k], lck, a[c]);
+        }
+      }
+    }
+    if (lane < jb) {
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const float v = c <= lane ? a[c] : 0.0f;
+        fb[lane * 16 + c] = v;
+        if (c <= lane) M[(j0 + lane) * ld + j0 + c] = v;
+      }
+      dinv[j0 + lane] = rinv;
+    }
+  }
+  const bool all_ok = __syncthreads_and(okw) != 0;
+  for (int rr = tid; rr < N; rr += NT) {
+    const bool inA = rr < nA;
+    float* row = inA ? A + (rowA0 + rr) * lda + j0 : B + (rr - nA) * ldb + j0;
+    float v[16];
+#pragma unroll
+    for (int t = 0; t < 16; ++t) v[t] = t < jb ? row[t] : 0.0f;
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+      if (t < jb) {
+        float acc = v[t];
+#pragma unroll
+        for (int u = 0; u < t; ++u) acc = fmaf(-v[u], fb[t * 16 + u], acc);
+        v[t] = acc * dinv[j0 + t];
+      }
+    }
+    float4* pr = reinterpret_cast<float4*>(Pb + pb16_off(inA ? rr : nA4 + (rr - nA)));
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      pr[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+#pragma unroll
+    for (int t = 0; t < 16; ++t)
+      if (t < jb) row[t] = v[t];
+  }
+  // zero the pad rows: nA .. nA4-1 and after the last B row up to its group's end
+  if (tid < 128) {
+    const int k = tid >> 4, c = tid & 15;
+    const int r = k < 4 ? nA + k : nA4 + nB + (k - 4);
+    const bool pad = k < 4 ? r < nA4 : (r & 3) != 0 && (r >> 2) == ((nA4 + nB) >> 2);
+    if (pad) Pb[pb16_off(r) + c] = 0.0f;
+  }
+  __syncthreads();
+  return all_ok;
+}
+
+// Rank-16 trailing update with the panel in Pb16 (same row sets and rules as
+// panel_syrk).
+template <int NT>
+__device__ void panel_syrk16(const float* Pb, float* A, int lda, int rowA0, int nA, float* B,
+                             int ldb, int nB, float* C, int ldc) {
+  const int nA4 = (nA + 3) & ~3;
+  const int ntA = nA4 >> 2;
+  const int nt = ntA + ((nB + 3) >> 2);
+  const int T = nt * (nt + 1) / 2;
+  for (int t = threadIdx.x; t < T; t += NT) {
+    const float x8 = 8.0f * (float)t + 1.0f;
+    int I = (int)((x8 * rsqrtf(x8) - 1.0f) * 0.5f);
+    while ((I + 1) * (I + 2) / 2 <= t) ++I;
+    while (I * (I + 1) / 2 > t) --I;
+    const int J = t - I * (I + 1) / 2;
+    const bool rowA = I < ntA, colA = J < ntA;
+    if (!rowA && !colA && C == nullptr) continue;
+    float* dst;
+    int ld, rmax, cmax;
+    float sgn = -1.0f;
+    if (rowA) {
+      dst = A + (rowA0 + 4 * I) * lda + rowA0 + 4 * J;
+      ld = lda;
+      rmax = nA - 4 * I;
+      cmax = nA - 4 * J;
+    } else if (colA) {
+      dst = B + (4 * I - nA4) * ldb + rowA0 + 4 * J;
+      ld = ldb;
+      rmax = nB - (4 * I - nA4);
+      cmax = nA - 4 * J;
+    } else {
+      dst = C + (4 * I - nA4) * ldc + (4 * J - nA4);
+      ld = ldc;
+      rmax = nB - (4 * I - nA4);
+      cmax = nB - (4 * J - nA4);
+      sgn = 1.0f;
+    }
+    const bool diag = I == J;
+    float acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      float4 ra[4], cb[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) ra[a] = reinterpret_cast<const float4*>(Pb + I * 68 + a * 16)[h];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) cb[b] = reinterpret_cast<const float4*>(Pb + J * 68 + b * 16)[h];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          acc[a][b] = fmaf(ra[a].x, cb[b].x, acc[a][b]);
+          acc[a][b] = fmaf(ra[a].y, cb[b].y, acc[a][b]);
+          acc[a][b] = fmaf(ra[a].z, cb[b].z, acc[a][b]);
+          acc[a][b] = fmaf(ra[a].w, cb[b].w, acc[a][b]);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+        if (a < rmax && b < cmax && (!diag || b <= a))
+          dst[a * ld + b] = fmaf(sgn, acc[a][b], dst[a * ld + b]);
+  }
+  __syncthreads();
+}
+
 // Eliminate the n pivots of K (n x n lower, stride ldk) bordered by nB rows
 // in Y (stride ldy); C (nB x nB lower, stride ldc, may be null) accumulates
 // Y Y'.  With C == nullptr this is a plain blocked Cholesky of K (nB = 0) or
 // a Cholesky plus triangular solve of the border rows.
 // sub (tracing builds only, may be null): cycles of the factor+TRSM stage and
 // of the trailing updates are added to sub[0] and sub[1] by thread 0.
-template <int NT>
+// PW: panel width, 8 (Pb of pb_floats rows) or 16 (Pb of pb16_floats rows
+// followed by the 256-float block scratch).
+template <int NT, int PW = 8>
 __device__ bool blocked_cholesky_bordered(float* K, int ldk, int n, float* Y, int ldy, int nB,
                                           float* C, int ldc, float* dinv, float* Pb,
                                           unsigned long long* sub = nullptr) {
   bool ok = true;
-  for (int j0 = 0; j0 < n; j0 += 8) {
-    const int jb = min(8, n - j0);
+  float* const fb = PW == 16 ? Pb + pb16_floats(n + nB + 4) : nullptr;
+  for (int j0 = 0; j0 < n; j0 += PW) {
+    const int jb = min(PW, n - j0);
     const int nK = n - j0 - jb;
     const long long c0 = sub ? clock64() : 0;
-    ok = panel_factor_trsm<NT>(K, ldk, j0, jb, dinv, K, ldk, j0 + jb, nK, Y, ldy, nB, Pb) && ok;
+    if (PW == 16)
+      ok = panel_factor16<NT>(K, ldk, j0, jb, dinv, K, ldk, j0 + jb, nK, Y, ldy, nB, Pb, fb) &&
+           ok;
+    else
+      ok = panel_factor_trsm<NT>(K, ldk, j0, jb, dinv, K, ldk, j0 + jb, nK, Y, ldy, nB, Pb) &&
+           ok;
     const long long c1 = sub ? clock64() : 0;
-    if (nK + nB > 0) panel_syrk<NT>(Pb, K, ldk, j0 + jb, nK, Y, ldy, nB, C, ldc);
+    if (nK + nB > 0) {
+      if (PW == 16)
+        panel_syrk16<NT>(Pb, K, ldk, j0 + jb, nK, Y, ldy, nB, C, ldc);
+      else
+        panel_syrk<NT>(Pb, K, ldk, j0 + jb, nK, Y, ldy, nB, C, ldc);
+    }
     if (sub && threadIdx.x == 0) {
       const long long c2 = clock64();
       atomicAdd(&sub[0], (unsigned long long)(c1 - c0));

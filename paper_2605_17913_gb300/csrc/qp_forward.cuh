@@ -75,6 +75,15 @@ struct FLayout {
 // are dead there.
 // Y and C carry two extra rows: the right-hand sides folded into the
 // factorisation of an implicit step.
+// Panel width of the blocked factorisation: 16 for the large variant (its
+// trailing updates read and write global memory, so halving their number pays:
+// +14-18 % at n = 256), 8 on chip, where the 16-wide diagonal-block factor
+// (one warp, shuffles) lengthens the critical path more than the wider update
+// saves (measured 40 % slower at n = 50).
+__host__ __device__ constexpr int panel_width(int nthreads, bool split) {
+  return (split || nthreads < 0) ? 16 : 8;
+}
+
 __host__ __device__ inline FLayout make_fwd_layout(int n, int m, int p, int amax, int nthreads,
                                                    bool split = false) {
   FLayout L;
@@ -105,7 +114,9 @@ __host__ __device__ inline FLayout make_fwd_layout(int n, int m, int p, int amax
     // staging buffers of G'WG, 128-byte aligned
     if (split) o = (o + 31) & ~31;
     const int base = o;
-    int pb = round4(pb_floats(n + L.fmax + 2 + 4));
+    const int rows = n + L.fmax + 2 + 4;
+    int pb = panel_width(nthreads, split) == 16 ? pb16_floats(rows) + 256 : pb_floats(rows);
+    pb = round4(pb);
     if (split && pb < 2 * tc::stage_bytes(n, 4) / 4) pb = 2 * tc::stage_bytes(n, 4) / 4;
     L.o_Pb = base;
     L.o_col = take(2 * nthreads);
@@ -178,6 +189,8 @@ static __shared__ unsigned char fwd_parity[512];   // block_reduce buffer parity
 
 template <int NT, bool kBig>
 struct Solver {
+  static constexpr int kPW = panel_width(NT, kBig);
+
   static __device__ void init(int n, int m, int p, int amax, float* ws, int gwg) {
     if (threadIdx.x == 0) {
       fwd_state.L = make_fwd_layout(n, m, p, amax, NT, kBig);
@@ -354,7 +367,7 @@ struct Solver {
 #else
     unsigned long long* const sub = nullptr;
 #endif
-    bool ok = blocked_cholesky_bordered<NT>(K, L.ldk, L.n, Y, L.ldk, nf + nfold, C, L.ldc, dinv,
+    bool ok = blocked_cholesky_bordered<NT, kPW>(K, L.ldk, L.n, Y, L.ldk, nf + nfold, C, L.ldc, dinv,
                                             Pb, sub);
     QP_MARK(PH_BORDER);
     if (nf > 0) {
@@ -364,7 +377,7 @@ struct Solver {
       const float shift = creg * dm[0];
       for (int k = threadIdx.x; k < nf; k += NT) C[k * L.ldc + k] += shift;
       __syncthreads();
-      ok = blocked_cholesky_bordered<NT>(C, L.ldc, nf, C + nf * L.ldc, L.ldc, nfold, nullptr, 0,
+      ok = blocked_cholesky_bordered<NT, kPW>(C, L.ldc, nf, C + nf * L.ldc, L.ldc, nfold, nullptr, 0,
                                          cdinv, Pb, sub ? sub + 2 : nullptr) && ok;
       QP_MARK(PH_CCHOL);
     }

@@ -6,10 +6,13 @@ Bars (stated by the method's accuracy targets):
   |grad - grad*|_2 / max(|grad*|_2, 1e-6) <= 1e-3 per block (Q, q, A, b, G, h).
 The solver runs at tol 5e-6: its stopping test is evaluated in FP32, and the
 margin keeps the FP64 evaluation of the returned point within 1e-5.
-The degenerate workload (m/2 + p > n active rows) is the exception for the
-gradient bar: there the FP64 gradient itself moves by up to ~8e-3 when the
-data are perturbed at 1e-7 relative (FP32 rounding), so no FP32 computation
-can be held to 1e-3; its bar is 1e-2.
+The degenerate workload (m/2 + p > n active rows, LICQ fails) is the
+exception for the gradient bar: there the FP64 gradient itself moves by up to
+~1.6e-2 (median ~4e-3) when the data are perturbed at 1e-7 relative -- the
+size of FP32 input rounding -- so no FP32 computation can be held to 1e-3
+there.  Its bar is per instance: max(1e-3, 3 x that instance's FP64
+sensitivity), measured with the oracle on perturbed copies of the data (an
+FP32 result is the exact result for data perturbed by a few ulps).
 """
 import numpy as np
 import pytest
@@ -22,7 +25,7 @@ from qpgen import make_batch
 pytestmark = pytest.mark.gpu
 
 TOL_KKT, TOL_X, TOL_F, TOL_G = 1e-5, 1e-4, 1e-4, 1e-3
-TOL_G_DEGENERATE = 1e-2
+SENS_FACTOR = 3.0
 SOLVER_TOL = 5e-6
 GRAD_KEYS = ("dQ", "dq", "dA", "db", "dG", "dh")
 
@@ -84,12 +87,34 @@ def check_forward(batch, res, ref, tol_kkt=TOL_KKT):
     return rep
 
 
-def check_grads(res, ref, tol=TOL_G):
+def fp64_sensitivity(batch, ref, trials=2, rel=1e-7, seed=0):
+    """Per instance, the largest relative change of the oracle's gradient
+    blocks when the data are perturbed by `rel` relative noise (FP32 input
+    rounding size): the accuracy any FP32 computation can be held to."""
+    rng = np.random.default_rng(seed)
+    worst = np.zeros(batch.batch)
+    for _ in range(trials):
+        pert = {k: getattr(batch, k).astype(np.float64) for k in ("Q", "q", "A", "b", "G", "h")}
+        for k in pert:
+            pert[k] = pert[k] * (1.0 + rel * rng.standard_normal(pert[k].shape))
+        pert["Q"] = 0.5 * (pert["Q"] + np.swapaxes(pert["Q"], 1, 2))
+        r2 = O.solve(pert["Q"], pert["q"], pert["A"], pert["b"], pert["G"], pert["h"], tol=1e-12,
+                     kappa_relax=1e-4, g=batch.g, nthreads=8)
+        for k in GRAD_KEYS:
+            if ref[k].size:
+                worst = np.maximum(worst, rel_err_2(r2[k], ref[k]))
+    return worst
+
+
+def check_grads(res, ref, tol=TOL_G, sens=None):
+    """Per block, |g - g*| / |g*| <= tol, or per instance
+    max(tol, SENS_FACTOR * sens) when the FP64 sensitivity is given."""
+    bar = tol if sens is None else np.maximum(tol, SENS_FACTOR * sens)
     for k in GRAD_KEYS:
         if ref[k].size == 0:
             continue
         e = rel_err_2(res[k], ref[k])
-        assert e.max() <= tol, (k, e.max())
+        assert np.all(e <= bar), (k, e.max(), np.argmax(e / bar))
 
 
 # ---------------------------------------------------------------- forward parity
@@ -130,7 +155,7 @@ def test_degenerate_subset_parity():
     assert ex0.max() <= TOL_X, ex0.max()
     check_forward(batch, res, O.solve(batch.Q, batch.q, batch.A, batch.b, batch.G, batch.h,
                                       tol=1e-12, nthreads=8))
-    check_grads(res, ref, TOL_G_DEGENERATE)
+    check_grads(res, ref, TOL_G, fp64_sensitivity(batch, ref))
 
 
 def test_diff_workload_parity():
@@ -324,9 +349,8 @@ def test_degenerate_full_size_sampled():
     assert rep["scaled"].max() <= TOL_KKT
     assert rel_err_inf(res["x"], batch.x0).max() <= TOL_X
     idx = [0, 1, 777, 2048, 4095]
-    sub = make_batch("degenerate", 1, seed=0, start=idx[0])
     for i in idx:
         sub = make_batch("degenerate", 1, seed=0, start=i)
         ref = oracle_run(sub, grad=True)
-        for k in GRAD_KEYS:
-            assert rel_err_2(res[k][i:i + 1], ref[k]).max() <= TOL_G_DEGENERATE, (i, k)
+        check_grads({k: res[k][i:i + 1] for k in GRAD_KEYS}, ref, TOL_G,
+                    fp64_sensitivity(sub, ref))
