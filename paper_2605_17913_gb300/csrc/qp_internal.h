@@ -113,8 +113,12 @@ size_t backward_smem_bytes(int n, int m, int p, int amax, bool split, int* nthre
 // (the variant of ragged launches; same arithmetic as the staged one).
 size_t backward_direct_smem_bytes(int n, int m, int p, int amax, bool split);
 cudaError_t launch_backward(const BwdParams& P, int nthreads, size_t smem, cudaStream_t stream);
-// Ragged backward launch over P.desc[0 .. P.batch): Q, G, A read from global memory.
-cudaError_t launch_backward_ragged(const BwdParams& P, size_t smem, cudaStream_t stream);
+// Ragged backward launch over P.desc[0 .. P.batch): Q, G, A read from global
+// memory; nthreads = backward_threads of the launch's size class.
+cudaError_t launch_backward_ragged(const BwdParams& P, int nthreads, size_t smem,
+                                   cudaStream_t stream);
+// Threads per CTA of the backward kernel for a size.
+int backward_threads(int n, bool split);
 
 // Load the kernels' modules ahead of their first launch (the runtime loads
 // lazily); for callers whose launches must not pay for loading.

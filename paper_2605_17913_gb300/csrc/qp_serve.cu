@@ -338,7 +338,8 @@ cudaError_t qp_server::issue(Launch& L) {
     B.batch = nb;
     B.split = take[0]->cfg.split ? 1 : 0;
     B.desc = L.ddesc + R;
-    e = launch_backward_ragged(B, bsmem, L.stream);
+    e = launch_backward_ragged(B, backward_threads(take[0]->n, take[0]->cfg.split), bsmem,
+                               L.stream);
   }
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(hb + in_f, db + in_f, (size_t)out_f * sizeof(float),
