@@ -62,6 +62,9 @@ def parse():
     # G'WG in FP32 vs TF32 / BF16 tensor cores on the n = 256 workload
     # (one JSON line per mode instead of the bench line)
     ap.add_argument("--precision", action="store_true")
+    # App. D: gradients of the polytope projection against the exact
+    # hard-projection Jacobian (kappa_relax and size sweeps)
+    ap.add_argument("--projection", action="store_true")
     return ap.parse_args()
 
 
@@ -687,6 +690,88 @@ def run_precision(args):
         print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- projection study
+def _projection_batch(n, m, m_act, seeds, per_seed, ds):
+    """Stacked App. D instances: per seed `per_seed` polytopes, each queried
+    at every displacement d; plus their exact gradients J_hard v."""
+    from qpgen import make_instance
+
+    insts = [make_instance("projection", i, seed=sd, n=n, m=m, m_act=m_act, d=float(d))
+             for sd in seeds for i in range(per_seed) for d in ds]
+    st = lambda k: np.stack([np.asarray(x[k], dtype=np.float32) for x in insts])  # noqa: E731
+    ghard = []
+    for x in insts:
+        Ga = x["G"][:x["n_active"]]
+        J = np.eye(n) - Ga.T @ np.linalg.solve(Ga @ Ga.T, Ga)
+        ghard.append(J @ x["g"])
+    return {k: st(k) for k in ("Q", "q", "G", "h", "g")}, np.array(ghard)
+
+
+def run_projection(args):
+    """App. D on the GPU: phi(x) = v' Pi(x), the projection of x onto a
+    polytope (Q = I, q = -x, G y <= h); its gradient from the solve + relax +
+    backward (dphi/dx = -dphi/dq) against J_hard v.  kappa sweep: n = 20, 25
+    inequalities, 10/12/15 active, kappa_relax 1e-2 .. 1e-9, tol =
+    min(kappa_relax, 1e-4); size sweep: n = 2 .. 38, 1.25 n inequalities,
+    active fraction 0.2/0.6/0.8, kappa_relax = tol = 1e-4.  Seeds 0-2, d in
+    logspace(-2, 2, 21), 8 polytopes per seed: 504 instances per point.
+    Errors |g - J_hard v| / |v|."""
+    import torch
+
+    from paper_2605_17913_gb300.solver import QPSolver
+
+    torch.cuda.set_device(0)
+    import __graft_entry__ as ge
+
+    ge.build()
+    ds = np.logspace(-2, 2, 21)
+    seeds, per_seed = (0, 1, 2), 8
+
+    def point(n, m, m_act, kr, tol):
+        data, ghard = _projection_batch(n, m, m_act, seeds, per_seed, ds)
+        B = data["Q"].shape[0]
+        T = {k: torch.from_numpy(v).cuda() for k, v in data.items()}
+        A = torch.zeros(B, 0, n, device="cuda")
+        b = torch.zeros(B, 0, device="cuda")
+        slv = QPSolver(B, n, 0, m)
+        cache = slv.new_grad_cache()
+        out = slv.solve(T["Q"], T["q"], A, b, T["G"], T["h"], grad_cache=cache, tol=tol,
+                        kappa_relax=kr, max_iter=100)
+        gr = slv.backward(cache, T["Q"], A, T["G"], T["g"])
+        g = -gr["dq"].cpu().numpy().astype(np.float64)  # q = -x
+        st = out["status"].cpu().numpy()
+        finite = np.isfinite(g).all(axis=1)
+        # relative to |v|, which bounds |J_hard v| (J_hard is an orthogonal
+        # projector, zero when n rows are active)
+        err = np.linalg.norm(g - ghard, axis=1) / np.linalg.norm(data["g"].astype(np.float64),
+                                                                 axis=1)
+        e = err[finite]
+        return {"instances": B, "nan_rate": float(np.mean(~finite)),
+                "solved": float(np.mean(st == 0)),
+                "grad_err_median": float(np.median(e)) if e.size else None,
+                "grad_err_p90": float(np.percentile(e, 90)) if e.size else None,
+                "grad_err_max": float(e.max()) if e.size else None}
+
+    for m_act in (10, 12, 15):
+        for kr in (1e-2, 1e-3, 1e-4, 1e-5, 1e-6, 1e-7, 1e-8, 1e-9):
+            r = point(20, 25, m_act, kr, min(kr, 1e-4))
+            print(json.dumps({"projection": "kappa sweep", "n": 20, "m_ineq": 25,
+                              "active": m_act, "kappa_relax": kr, "tol": min(kr, 1e-4),
+                              "dtype": "f32", **r}), flush=True)
+    for n in (2, 6, 10, 14, 18, 22, 26, 30, 34, 38):
+        done = set()
+        for mr in (0.2, 0.6, 0.8):
+            m = int(round(1.25 * n))
+            m_act = max(1, int(round(mr * n)))
+            if m_act in done:
+                continue
+            done.add(m_act)
+            r = point(n, m, m_act, 1e-4, 1e-4)
+            print(json.dumps({"projection": "size sweep", "n": n, "m_ineq": m, "active": m_act,
+                              "active_ratio": mr, "kappa_relax": 1e-4, "tol": 1e-4,
+                              "dtype": "f32", **r}), flush=True)
+
+
 # ---------------------------------------------------------------- ablation sweep
 def run_ablation(args):
     """Implicit vs standard complementarity, both in FP32, on one batch of the
@@ -754,6 +839,9 @@ def main():
         return
     if args.precision:
         run_precision(args)
+        return
+    if args.projection:
+        run_projection(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -232,6 +232,27 @@ def test_tensor_core_gwg_refused_on_chip():
         gpu_run(batch, gwg_precision="tf32")
 
 
+def test_projection_gradients_vs_oracle():
+    """App. D polytope projections (Q = I, q = -x, no equalities; a prescribed
+    active face): gradients of <v, x(kappa_relax)> against the oracle's relaxed
+    point, over near and far query points."""
+    from qpgen import make_instance
+
+    insts = [make_instance("projection", i, seed=0, n=20, m=25, m_act=12, d=float(d))
+             for i in range(3) for d in (0.01, 1.0, 100.0)]
+    from qpgen.workloads import QPBatch
+
+    st = lambda k: np.stack([np.asarray(x[k], dtype=np.float32) for x in insts])  # noqa: E731
+    batch = QPBatch(Q=st("Q"), q=st("q"), A=np.zeros((len(insts), 0, 20), np.float32),
+                    b=np.zeros((len(insts), 0), np.float32), G=st("G"), h=st("h"),
+                    x0=st("x0"), g=st("g"), workload="projection", seed=0, start=0)
+    res = gpu_run(batch, grad=True)
+    ref = oracle_run(batch, grad=True)
+    check_forward(batch, res, O.solve(batch.Q, batch.q, batch.A, batch.b, batch.G, batch.h,
+                                      tol=1e-12, nthreads=8))
+    check_grads(res, ref)
+
+
 def test_unconstrained_closed_form():
     batch = make_batch("small", 5, seed=2, m=0, p=0)
     res = gpu_run(batch, grad=True)
