@@ -274,16 +274,20 @@ struct Solver {
     QP_ARR(bz); QP_ARR(bs); QP_ARR(red); QP_BIG(G); QP_BIG(Y);
     const float* const A = fwd_state.gA;
     QP_BIG(C); QP_ARR(D); QP_ARR(ea); QP_IARR(act); QP_IARR(pos); QP_IARR(ina);
-    float tau = 1.0f;
-    for (int round = 0; round < 40; ++round) {
-      float cnt[1] = {0.f};
-      for (int r = t; r < m; r += NT) cnt[0] += (bz[r] > tau * bs[r]) ? 1.f : 0.f;
-      reduce<1>(cnt, red, OpSum());
-      if ((int)cnt[0] <= L.amax) break;
-      tau *= 10.0f;
-    }
-    // ordered compaction of the active rows: one warp scans all rows
+    (void)red;
+    // one warp: tau = 1 unless more than amax rows have W > tau (then tau
+    // grows tenfold until they fit), and the ordered compaction of the rows
     if (w == 0) {
+      float tau = 1.0f;
+      for (int round = 0; round < 40; ++round) {
+        int cnt = 0;
+        for (int r0 = 0; r0 < m; r0 += 32) {
+          const int r = r0 + lane;
+          cnt += __popc(__ballot_sync(kFull, r < m && bz[r] > tau * bs[r]));
+        }
+        if (cnt <= L.amax) break;
+        tau *= 10.0f;
+      }
       int base = 0, ibase = 0;
       for (int r0 = 0; r0 < m; r0 += 32) {
         const int r = r0 + lane;
@@ -309,13 +313,12 @@ struct Solver {
     const int a = fwd_state.a, nf = fwd_state.nf;
     for (int k = w; k < nf; k += NT / 32) {
       const float* src = k < a ? G + act[k] * L.ldg : A + (k - a) * n;
+      const float dk = k < a ? bs[act[k]] / bz[act[k]] : 0.f;
       for (int c = lane; c < n; c += 32) Y[k * L.ldk + c] = src[c];
-      for (int c = lane; c <= k; c += 32) C[k * L.ldc + c] = 0.f;
+      for (int c = lane; c <= k; c += 32) C[k * L.ldc + c] = c == k ? dk : 0.f;
+      if (lane == 0) D[k] = dk;
     }
-    for (int k = t; k < nf; k += NT) D[k] = k < a ? bs[act[k]] / bz[act[k]] : 0.f;
     for (int r = t; r < m; r += NT) ea[r] = pos[r] < 0 ? bz[r] / bs[r] : 0.f;
-    __syncthreads();
-    for (int k = t; k < nf; k += NT) C[k * L.ldc + k] = D[k];
     __syncthreads();
     QP_MARK(PH_PART);
   }
