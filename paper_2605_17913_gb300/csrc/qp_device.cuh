@@ -662,11 +662,29 @@ template <int S, int R>
 __device__ __forceinline__ void warp_lower_solve(const float* L, int ldk, const float* dinv, int n,
                                                  float (&x)[R][S]) {
   const int lane = threadIdx.x & 31;
+  // column j of L for this lane's rows, loaded one step ahead (the loads do
+  // not depend on the solve, so their latency overlaps the previous step)
+  float lc[S];
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int i = lane + 32 * s;
+    lc[s] = (i > 0 && i < n) ? L[i * ldk] : 0.f;
+  }
 #pragma unroll
   for (int sl = 0; sl < S; ++sl) {
     const int jend = min(32, n - 32 * sl);
     for (int jj = 0; jj < jend; ++jj) {
       const int j = 32 * sl + jj;
+      float cur[S];
+#pragma unroll
+      for (int s = 0; s < S; ++s) cur[s] = lc[s];
+      if (j + 1 < n) {
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+          const int i = lane + 32 * s;
+          lc[s] = (i > j + 1 && i < n) ? L[i * ldk + j + 1] : 0.f;
+        }
+      }
       const float dj = dinv[j];
       float xj[R];
 #pragma unroll
@@ -678,9 +696,8 @@ __device__ __forceinline__ void warp_lower_solve(const float* L, int ldk, const 
       for (int s = sl; s < S; ++s) {
         const int i = lane + 32 * s;
         if (i > j && i < n) {
-          const float lij = L[i * ldk + j];
 #pragma unroll
-          for (int r = 0; r < R; ++r) x[r][s] = fmaf(-lij, xj[r], x[r][s]);
+          for (int r = 0; r < R; ++r) x[r][s] = fmaf(-cur[s], xj[r], x[r][s]);
         }
       }
     }
@@ -692,11 +709,28 @@ template <int S, int R>
 __device__ __forceinline__ void warp_upper_solve(const float* L, int ldk, const float* dinv, int n,
                                                  float (&x)[R][S]) {
   const int lane = threadIdx.x & 31;
+  // row j of L for this lane's columns, loaded one step ahead
+  float lr[S];
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int i = lane + 32 * s;
+    lr[s] = (n > 0 && i < n - 1) ? L[(n - 1) * ldk + i] : 0.f;
+  }
 #pragma unroll
   for (int sl = S - 1; sl >= 0; --sl) {
     const int jend = min(32, n - 32 * sl);
     for (int jj = jend - 1; jj >= 0; --jj) {
       const int j = 32 * sl + jj;
+      float cur[S];
+#pragma unroll
+      for (int s = 0; s < S; ++s) cur[s] = lr[s];
+      if (j >= 1) {
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+          const int i = lane + 32 * s;
+          lr[s] = (i < j - 1) ? L[(j - 1) * ldk + i] : 0.f;
+        }
+      }
       const float dj = dinv[j];
       float xj[R];
 #pragma unroll
@@ -708,9 +742,8 @@ __device__ __forceinline__ void warp_upper_solve(const float* L, int ldk, const 
       for (int s = 0; s <= sl; ++s) {
         const int i = lane + 32 * s;
         if (i < j) {
-          const float lji = L[j * ldk + i];
 #pragma unroll
-          for (int r = 0; r < R; ++r) x[r][s] = fmaf(-lji, xj[r], x[r][s]);
+          for (int r = 0; r < R; ++r) x[r][s] = fmaf(-cur[s], xj[r], x[r][s]);
         }
       }
     }
