@@ -454,33 +454,40 @@ __device__ void panel_syrk(const float* Pb, float* A, int lda, int rowA0, int nA
 }
 
 // ---------------------------------------------------------------------------
-// 16-wide panels.  Pb16 holds panel rows in groups of 4 (16 values each)
-// padded to 68 floats (conflict-free float4 loads across row groups); fb is a
-// 16 x 16 scratch for the diagonal block's factor.  Per panel: warp 0 factors
-// the diagonal block with shuffles (lane i holds row i), barrier, every row
-// below (and every border row) is solved against it by one thread, barrier,
-// rank-16 trailing update, barrier -- three barriers per 16 columns, and the
-// block factor computed once instead of by every thread.
+// Wide panels (PW = 16 or 32).  Pbw holds panel rows in groups of 4 (PW
+// values each) padded to 4 PW + 4 floats (conflict-free float4 loads across
+// row groups); fb is a PW x PW scratch for the diagonal block's factor.  Per
+// panel: warp 0 factors the diagonal block with shuffles (lane i holds row
+// i), barrier, every row below (and every border row) is solved against it
+// by one thread, barrier, rank-PW trailing update, barrier -- three barriers
+// per PW columns, and the block factor computed once instead of by every
+// thread.
 // ---------------------------------------------------------------------------
-__host__ __device__ inline int pb16_floats(int rows) { return ((rows + 3) / 4 + 1) * 68; }
-__device__ __forceinline__ int pb16_off(int r) { return (r >> 2) * 68 + (r & 3) * 16; }
+__host__ __device__ constexpr int pbw_group(int pw) { return 4 * pw + 4; }
+__host__ __device__ inline int pbw_floats(int rows, int pw) {
+  return ((rows + 3) / 4 + 1) * pbw_group(pw);
+}
+template <int PW>
+__device__ __forceinline__ int pbw_off(int r) {
+  return (r >> 2) * pbw_group(PW) + (r & 3) * PW;
+}
 
-template <int NT>
-__device__ bool panel_factor16(float* M, int ld, int j0, int jb, float* dinv, float* A, int lda,
-                               int rowA0, int nA, float* B, int ldb, int nB, float* Pb,
-                               float* fb) {
+template <int NT, int PW>
+__device__ bool panel_factor_wide(float* M, int ld, int j0, int jb, float* dinv, float* A,
+                                  int lda, int rowA0, int nA, float* B, int ldb, int nB,
+                                  float* Pb, float* fb) {
   const int nA4 = (nA + 3) & ~3;
   const int N = nA + nB;
   const int tid = threadIdx.x, lane = tid & 31;
   int okw = 1;
   if (tid < 32) {
-    float a[16];
+    float a[PW];
 #pragma unroll
-    for (int c = 0; c < 16; ++c)
+    for (int c = 0; c < PW; ++c)
       a[c] = (lane < jb && c <= lane) ? M[(j0 + lane) * ld + j0 + c] : 0.0f;
     float rinv = 0.0f;
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
+    for (int k = 0; k < PW; ++k) {
       if (k < jb) {
         const float d = __shfl_sync(kFull, a[k], k);
         if (!(d > 0.0f) || !(d < INFINITY)) okw = 0;
@@ -492,7 +499,7 @@ __device__ bool panel_factor16(float* M, int ld, int j0, int jb, float* dinv, fl
           a[k] *= r;
         }
 #pragma unroll
-        for (int c = k + 1; c < 16; ++c) {
+        for (int c = k + 1; c < PW; ++c) {
           const float lck = __shfl_sync(kFull, a[k], c);  // L[c][k], held by lane c
           if (c < jb && lane >= c) a[c] = fmaf(-a[k], lck, a[c]);
         }
@@ -500,9 +507,9 @@ __device__ bool panel_factor16(float* M, int ld, int j0, int jb, float* dinv, fl
     }
     if (lane < jb) {
 #pragma unroll
-      for (int c = 0; c < 16; ++c) {
+      for (int c = 0; c < PW; ++c) {
         const float v = c <= lane ? a[c] : 0.0f;
-        fb[lane * 16 + c] = v;
+        fb[lane * PW + c] = v;
         if (c <= lane) M[(j0 + lane) * ld + j0 + c] = v;
       }
       dinv[j0 + lane] = rinv;
@@ -512,42 +519,43 @@ __device__ bool panel_factor16(float* M, int ld, int j0, int jb, float* dinv, fl
   for (int rr = tid; rr < N; rr += NT) {
     const bool inA = rr < nA;
     float* row = inA ? A + (rowA0 + rr) * lda + j0 : B + (rr - nA) * ldb + j0;
-    float v[16];
+    float v[PW];
 #pragma unroll
-    for (int t = 0; t < 16; ++t) v[t] = t < jb ? row[t] : 0.0f;
+    for (int t = 0; t < PW; ++t) v[t] = t < jb ? row[t] : 0.0f;
 #pragma unroll
-    for (int t = 0; t < 16; ++t) {
+    for (int t = 0; t < PW; ++t) {
       if (t < jb) {
         float acc = v[t];
 #pragma unroll
-        for (int u = 0; u < t; ++u) acc = fmaf(-v[u], fb[t * 16 + u], acc);
+        for (int u = 0; u < t; ++u) acc = fmaf(-v[u], fb[t * PW + u], acc);
         v[t] = acc * dinv[j0 + t];
       }
     }
-    float4* pr = reinterpret_cast<float4*>(Pb + pb16_off(inA ? rr : nA4 + (rr - nA)));
+    float4* pr = reinterpret_cast<float4*>(Pb + pbw_off<PW>(inA ? rr : nA4 + (rr - nA)));
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
+    for (int q = 0; q < PW / 4; ++q)
       pr[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
 #pragma unroll
-    for (int t = 0; t < 16; ++t)
+    for (int t = 0; t < PW; ++t)
       if (t < jb) row[t] = v[t];
   }
   // zero the pad rows: nA .. nA4-1 and after the last B row up to its group's end
-  if (tid < 128) {
-    const int k = tid >> 4, c = tid & 15;
+  for (int e = tid; e < 8 * PW; e += NT) {
+    const int k = e / PW, c = e - k * PW;
     const int r = k < 4 ? nA + k : nA4 + nB + (k - 4);
     const bool pad = k < 4 ? r < nA4 : (r & 3) != 0 && (r >> 2) == ((nA4 + nB) >> 2);
-    if (pad) Pb[pb16_off(r) + c] = 0.0f;
+    if (pad) Pb[pbw_off<PW>(r) + c] = 0.0f;
   }
   __syncthreads();
   return all_ok;
 }
 
-// Rank-16 trailing update with the panel in Pb16 (same row sets and rules as
+// Rank-PW trailing update with the panel in Pbw (same row sets and rules as
 // panel_syrk).
-template <int NT>
-__device__ void panel_syrk16(const float* Pb, float* A, int lda, int rowA0, int nA, float* B,
-                             int ldb, int nB, float* C, int ldc) {
+template <int NT, int PW>
+__device__ void panel_syrk_wide(const float* Pb, float* A, int lda, int rowA0, int nA, float* B,
+                                int ldb, int nB, float* C, int ldc) {
+  constexpr int GS = pbw_group(PW);
   const int nA4 = (nA + 3) & ~3;
   const int ntA = nA4 >> 2;
   const int nt = ntA + ((nB + 3) >> 2);
@@ -587,12 +595,12 @@ __device__ void panel_syrk16(const float* Pb, float* A, int lda, int rowA0, int 
 #pragma unroll
       for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
 #pragma unroll
-    for (int h = 0; h < 4; ++h) {
+    for (int h = 0; h < PW / 4; ++h) {
       float4 ra[4], cb[4];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) ra[a] = reinterpret_cast<const float4*>(Pb + I * 68 + a * 16)[h];
+      for (int a = 0; a < 4; ++a) ra[a] = reinterpret_cast<const float4*>(Pb + I * GS + a * PW)[h];
 #pragma unroll
-      for (int b = 0; b < 4; ++b) cb[b] = reinterpret_cast<const float4*>(Pb + J * 68 + b * 16)[h];
+      for (int b = 0; b < 4; ++b) cb[b] = reinterpret_cast<const float4*>(Pb + J * GS + b * PW)[h];
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -619,28 +627,29 @@ __device__ void panel_syrk16(const float* Pb, float* A, int lda, int rowA0, int 
 // a Cholesky plus triangular solve of the border rows.
 // sub (tracing builds only, may be null): cycles of the factor+TRSM stage and
 // of the trailing updates are added to sub[0] and sub[1] by thread 0.
-// PW: panel width, 8 (Pb of pb_floats rows) or 16 (Pb of pb16_floats rows
-// followed by the 256-float block scratch).
+// PW: panel width, 8 (Pb of pb_floats rows) or 16 / 32 (Pb of pbw_floats
+// rows followed by the PW x PW block scratch).
 template <int NT, int PW = 8>
 __device__ bool blocked_cholesky_bordered(float* K, int ldk, int n, float* Y, int ldy, int nB,
                                           float* C, int ldc, float* dinv, float* Pb,
                                           unsigned long long* sub = nullptr) {
   bool ok = true;
-  float* const fb = PW == 16 ? Pb + pb16_floats(n + nB + 4) : nullptr;
+  float* const fb = PW > 8 ? Pb + pbw_floats(n + nB + 4, PW) : nullptr;
   for (int j0 = 0; j0 < n; j0 += PW) {
     const int jb = min(PW, n - j0);
     const int nK = n - j0 - jb;
     const long long c0 = sub ? clock64() : 0;
-    if (PW == 16)
-      ok = panel_factor16<NT>(K, ldk, j0, jb, dinv, K, ldk, j0 + jb, nK, Y, ldy, nB, Pb, fb) &&
+    if constexpr (PW > 8)
+      ok = panel_factor_wide<NT, PW>(K, ldk, j0, jb, dinv, K, ldk, j0 + jb, nK, Y, ldy, nB, Pb,
+                                     fb) &&
            ok;
     else
       ok = panel_factor_trsm<NT>(K, ldk, j0, jb, dinv, K, ldk, j0 + jb, nK, Y, ldy, nB, Pb) &&
            ok;
     const long long c1 = sub ? clock64() : 0;
     if (nK + nB > 0) {
-      if (PW == 16)
-        panel_syrk16<NT>(Pb, K, ldk, j0 + jb, nK, Y, ldy, nB, C, ldc);
+      if constexpr (PW > 8)
+        panel_syrk_wide<NT, PW>(Pb, K, ldk, j0 + jb, nK, Y, ldy, nB, C, ldc);
       else
         panel_syrk<NT>(Pb, K, ldk, j0 + jb, nK, Y, ldy, nB, C, ldc);
     }

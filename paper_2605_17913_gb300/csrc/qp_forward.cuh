@@ -75,13 +75,13 @@ struct FLayout {
 // are dead there.
 // Y and C carry two extra rows: the right-hand sides folded into the
 // factorisation of an implicit step.
-// Panel width of the blocked factorisation: 16 for the large variant (its
-// trailing updates read and write global memory, so halving their number pays:
-// +14-18 % at n = 256), 8 on chip, where the 16-wide diagonal-block factor
-// (one warp, shuffles) lengthens the critical path more than the wider update
-// saves (measured 40 % slower at n = 50).
+// Panel width of the blocked factorisation: 32 for the large variant (its
+// trailing updates read and write global memory, so fewer passes pay: 16-wide
+// +14-18 % over 8-wide at n = 256, 32-wide another 7 %), 8 on chip, where the
+// wide diagonal-block factor (one warp, shuffles) lengthens the critical path
+// more than the wider update saves (16-wide measured 40 % slower at n = 50).
 __host__ __device__ constexpr int panel_width(int nthreads, bool split) {
-  return (split || nthreads < 0) ? 16 : 8;
+  return (split || nthreads < 0) ? 32 : 8;
 }
 
 __host__ __device__ inline FLayout make_fwd_layout(int n, int m, int p, int amax, int nthreads,
@@ -115,7 +115,8 @@ __host__ __device__ inline FLayout make_fwd_layout(int n, int m, int p, int amax
     if (split) o = (o + 31) & ~31;
     const int base = o;
     const int rows = n + L.fmax + 2 + 4;
-    int pb = panel_width(nthreads, split) == 16 ? pb16_floats(rows) + 256 : pb_floats(rows);
+    const int pw = panel_width(nthreads, split);
+    int pb = pw > 8 ? pbw_floats(rows, pw) + pw * pw : pb_floats(rows);
     pb = round4(pb);
     if (split && pb < 2 * tc::stage_bytes(n, 4) / 4) pb = 2 * tc::stage_bytes(n, 4) / 4;
     L.o_Pb = base;
