@@ -232,38 +232,6 @@ __device__ void syrk_gwg(float* K, int ldk, const float* qd, const float* G, int
   }
 }
 
-// ---------------------------------------------------------------------------
-// Right-looking Cholesky of the lower triangle of K (n x n, stride ldk, odd).
-// On exit K's lower triangle holds L (K = L L') and dinv[j] = 1 / L[j][j].
-// Returns false if a pivot is not positive and finite.  Ends with a barrier.
-// ---------------------------------------------------------------------------
-template <int NT>
-__device__ bool cholesky(float* K, int ldk, int n, float* dinv) {
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  constexpr int nw = NT / 32;
-  bool ok = true;
-  for (int j = 0; j < n; ++j) {
-    const float d = K[j * ldk + j];
-    if (!(d > 0.0f) || !(d < INFINITY)) ok = false;
-    const float inv = 1.0f / d;
-    for (int r = j + 1 + w; r < n; r += nw) {
-      const float lrj = K[r * ldk + j] * inv;
-      for (int c = j + 1 + l; c <= r; c += 32) K[r * ldk + c] = fmaf(-lrj, K[c * ldk + j], K[r * ldk + c]);
-    }
-    __syncthreads();
-  }
-  for (int j = threadIdx.x; j < n; j += NT) {
-    const float sd = sqrtf(K[j * ldk + j]);
-    dinv[j] = 1.0f / sd;
-  }
-  __syncthreads();
-  for (int r = w; r < n; r += nw) {
-    for (int c = l; c < r; c += 32) K[r * ldk + c] *= dinv[c];
-    if (l == 0) K[r * ldk + r] = 1.0f / dinv[r];
-  }
-  __syncthreads();
-  return ok;
-}
 
 
 // ---------------------------------------------------------------------------

@@ -406,8 +406,7 @@ struct Solver {
   // columns; dx returned in R rows 0, 1 and mu in ua / ub ----
   static __device__ void solve_folded() {
     const FLayout& L = fwd_state.L;
-    QP_BIG(K); QP_ARR(dinv); QP_ARR(R); QP_BIG(Y); QP_BIG(C); QP_ARR(cdinv); QP_ARR(ua);
-    QP_ARR(ub);
+    QP_BIG(K); QP_ARR(dinv); QP_ARR(R); QP_BIG(Y); QP_BIG(C); QP_ARR(ua); QP_ARR(ub);
     const int n = L.n, t = threadIdx.x, w = t >> 5, nf = fwd_state.nf;
     if (nf > 0) {
       if (w < 2) {
