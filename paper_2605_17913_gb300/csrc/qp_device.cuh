@@ -599,8 +599,11 @@ __device__ void panel_syrk_wide(const float* Pb, float* A, int lda, int rowA0, i
 // of the trailing updates are added to sub[0] and sub[1] by thread 0.
 // PW: panel width, 8 (Pb of pb_floats rows) or 16 / 32 (Pb of pbw_floats
 // rows followed by the PW x PW block scratch).
+// Not inlined: the forward factors K_I and C with it, and one shared copy
+// of the unrolled panel code keeps the hot loop within the instruction cache
+// (two inlined copies made the forward 11 % slower).
 template <int NT, int PW = 8>
-__device__ bool blocked_cholesky_bordered(float* K, int ldk, int n, float* Y, int ldy, int nB,
+__device__ __noinline__ bool blocked_cholesky_bordered(float* K, int ldk, int n, float* Y, int ldy, int nB,
                                           float* C, int ldc, float* dinv, float* Pb,
                                           unsigned long long* sub = nullptr) {
   bool ok = true;
