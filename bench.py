@@ -65,6 +65,9 @@ def parse():
     # App. D: gradients of the polytope projection against the exact
     # hard-projection Jacobian (kappa_relax and size sweeps)
     ap.add_argument("--projection", action="store_true")
+    ap.add_argument("--chord", action="store_true",
+                    help="Alg. 2 with chord steps vs refactoring: time, iterations, "
+                         "gradient error against FP64")
     return ap.parse_args()
 
 
@@ -690,6 +693,68 @@ def run_precision(args):
         print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- chord relax study
+def run_chord(args):
+    """Alg. 2 refactoring at every relax iterate (default) vs chord steps (one
+    factorisation at the relax's first iterate, reused until the polishing
+    step).  Per workload: forward / backward time, mean Newton iterations
+    (Alg. 1 + Alg. 2; Alg. 1 is the same in both), and the gradient error
+    against the FP64 oracle at the relaxed point on a sample."""
+    import torch
+
+    from oracle import oracle as O
+    from paper_2605_17913_gb300.metrics import rel_err_2
+    from paper_2605_17913_gb300.solver import QPSolver
+    from qpgen import make_batch
+
+    torch.cuda.set_device(0)
+    import __graft_entry__ as ge
+
+    ge.build()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    keys = ("dQ", "dq", "dA", "db", "dG", "dh")
+    for wl, B, ns in (("degenerate", 4096, 16), ("diff", 1024, 8), ("small", 4096, 32)):
+        data = make_batch(wl, args.batch or B, seed=0)
+        B = data.batch
+        T = {k: torch.from_numpy(getattr(data, k)).cuda() for k in ("Q", "q", "A", "b", "G", "h", "g")}
+        slv = QPSolver(B, data.n, data.p, data.m)
+        cache = slv.new_grad_cache()
+        sample = list(range(min(ns, B)))
+        sub = make_batch(wl, len(sample), seed=0)
+        ref = O.solve(sub.Q, sub.q, sub.A, sub.b, sub.G, sub.h, tol=1e-12,
+                      kappa_relax=args.kappa_relax, g=sub.g, nthreads=min(16, len(sample)))
+        for chord in (0, 1):
+            ms = []
+            for rep_ in range(args.warmup + args.steps):
+                flush.zero_()
+                e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                e[0].record()
+                out = slv.solve(T["Q"], T["q"], T["A"], T["b"], T["G"], T["h"], grad_cache=cache,
+                                tol=args.tol, kappa_relax=args.kappa_relax, relax_chord=chord)
+                e[1].record()
+                gr = slv.backward(cache, T["Q"], T["A"], T["G"], T["g"])
+                e[2].record()
+                torch.cuda.synchronize()
+                if rep_ >= args.warmup:
+                    ms.append((e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])))
+            st = out["status"].cpu().numpy()
+            it = out["iters"].cpu().numpy()
+            gg = {k: v.cpu().numpy() for k, v in gr.items()}
+            errs = {k: rel_err_2(gg[k][sample], ref[k]) for k in keys if ref[k].size}
+            print(json.dumps({
+                "study": "chord relax", "relax": "chord" if chord else "refactor",
+                "workload": wl, "batch": B, "n": data.n, "m_ineq": data.m, "p_eq": data.p,
+                "kappa_relax": args.kappa_relax, "tol": args.tol,
+                "forward_ms": statistics.median(m[0] for m in ms),
+                "backward_ms": statistics.median(m[1] for m in ms),
+                "solved": float(np.mean(st == 0)),
+                "iters_mean": float(it.mean()), "iters_max": int(it.max()),
+                "grad_err_vs_fp64_median": {k: float(np.median(v)) for k, v in errs.items()},
+                "grad_err_vs_fp64_max": {k: float(v.max()) for k, v in errs.items()},
+                "error_sample": f"instances 0..{len(sample) - 1} against the FP64 oracle",
+            }), flush=True)
+
+
 # ---------------------------------------------------------------- projection study
 def _projection_batch(n, m, m_act, seeds, per_seed, ds):
     """Stacked App. D instances: per seed `per_seed` polytopes, each queried
@@ -839,6 +904,9 @@ def main():
         return
     if args.precision:
         run_precision(args)
+        return
+    if args.chord:
+        run_chord(args)
         return
     if args.projection:
         run_projection(args)

@@ -109,6 +109,11 @@ typedef struct {
   int32_t refine_steps;  /* iterative-refinement sweeps of the adjoint solve of
                             Alg. 3 against the bounded system (default 3)           */
   int32_t warm_start;    /* 1: start from the x, y, z, s passed in (z, s > 0)       */
+  int32_t relax_chord;   /* 1: Alg. 2 factors its first iterate only and reuses that
+                            factorisation for the following Newton steps (chord
+                            steps; Alg. 2's "if not cached"); its polishing step and
+                            the factor cached for Alg. 3 are fresh.  0: refactor at
+                            every relax iterate (default)                            */
 } qp_settings;
 
 typedef struct qp_handle qp_handle;
@@ -116,7 +121,7 @@ typedef struct qp_handle qp_handle;
 /* Fill `s` with the defaults: tol 1e-5, max_iter 100, Mehrotra sigma,
  * sigma 0.1, kappa_min 0 (-> 1e-2 tol), kappa_relax 1e-4, relax_tol 0
  * (-> tol / 10), relax_max_iter 0, implicit, scaled norm, FP32 G'WG, 3
- * refinement sweeps, cold start.  (Defaults follow the paper's ablation settings where it states
+ * refinement sweeps, cold start, relax refactors every iterate.  (Defaults follow the paper's ablation settings where it states
  * them: max_iter 100, kappa_relax 1e-4.) */
 void qp_settings_default(qp_settings* s);
 

@@ -51,6 +51,7 @@ class Settings(ctypes.Structure):
         ("gwg_precision", ctypes.c_int32),
         ("refine_steps", ctypes.c_int32),
         ("warm_start", ctypes.c_int32),
+        ("relax_chord", ctypes.c_int32),
     ]
 
 

@@ -41,7 +41,8 @@ qp_dims handle_dims(const qp_handle* h) { return h->dims; }
 int settings_to_params(const qp_settings* st, FwdParams* P) {
   if (!(st->tol > 0.0f) || st->max_iter < 0 || st->formulation < 0 || st->formulation > 1 ||
       st->sigma_mode < 0 || st->sigma_mode > 1 || !(st->kappa_relax >= 0.0f) ||
-      st->residual_norm < 0 || st->residual_norm > 1 || st->refine_steps < 0)
+      st->residual_norm < 0 || st->residual_norm > 1 || st->refine_steps < 0 ||
+      st->relax_chord < 0 || st->relax_chord > 1)
     return QP_EINVAL;
   if (st->gwg_precision < QP_GWG_FP32 || st->gwg_precision > QP_GWG_BF16) return QP_EINVAL;
   if (st->sigma_mode == QP_SIGMA_CONSTANT && !(st->sigma >= 0.0f && st->sigma <= 1.0f))
@@ -60,6 +61,7 @@ int settings_to_params(const qp_settings* st, FwdParams* P) {
   P->warm_start = st->warm_start;
   P->refine_steps = st->refine_steps;
   P->gwg = st->gwg_precision;
+  P->chord = st->relax_chord;
   return QP_OK;
 }
 }  // namespace qpgpu
@@ -88,6 +90,7 @@ void qp_settings_default(qp_settings* s) {
   s->gwg_precision = QP_GWG_FP32;
   s->refine_steps = 3;
   s->warm_start = 0;
+  s->relax_chord = 0;
 }
 
 const char* qp_status_string(int code) {

@@ -55,6 +55,10 @@ namespace fwd {
 
 constexpr int ST_SOLVED = 0, ST_MAX_ITER = 1, ST_STALLED = 2, ST_NUMERICAL = 3, ST_BAD_INPUT = 4;
 constexpr float kCReg = 1e-7f;  // relative diagonal shift of C
+// Alg. 2 chord steps reuse a factorisation while each step cuts the relax
+// measure at least this much (4x); a slower step means the frozen Newton
+// matrix (W moves like z^2 / kappa on active rows) has drifted too far
+constexpr float kChordRate = 0.25f;
 constexpr int kStaticSmem = 1152;  // upper bound of the kernel's static shared memory (state + params)
 
 struct FLayout {
@@ -153,6 +157,7 @@ struct SharedState {
   int tc_flag;       // a bounded wait ran out in the current G'WG
   int tc_bad;        // sticky: G'WG falls back to FP32 for the rest of the solve
   int gwg;           // 0 FP32, 1 TF32, 2 BF16 (tensor-core products, large variant)
+  float chord_kappa;  // kappa of the factorisation that Alg. 2's chord steps reuse
   float qn, bn, hn;  // |q|, |b|, |h| (infinity norms)
 };
 
@@ -202,6 +207,7 @@ struct Solver {
       fwd_state.tmem = 0;
       fwd_state.a = 0;
       fwd_state.nf = p;
+      fwd_state.chord_kappa = 0.f;
       fwd_state.t_mark = clock64();
       fwd_state.timers = nullptr;
     }
@@ -600,7 +606,27 @@ struct Solver {
         fmaxf(fmaxf(fmaxf(mx[0] / dt, mx[4] / de), fmaxf(mx[6] / di, comp)), mx[10] / dz), kappa);
   }
 
+  // b_k(v), b_k(-v) of row r in the Newton matrix: those of the current
+  // point, or (kChord) those frozen with the factorisation that chord steps
+  // reuse -- b_k(v) kept in `ina` (read only while factoring), b_k(-v) =
+  // kappa / b_k(v) (the retraction keeps b_k(v) b_k(-v) = kappa)
+  template <bool kChord>
+  static __device__ __forceinline__ void newton_diag(int r, float& jz, float& js) {
+    if constexpr (kChord) {
+      QP_ARR(ina);
+      jz = ina[r];
+      js = fwd_state.chord_kappa / jz;
+    } else {
+      QP_ARR(bz); QP_ARR(bs);
+      jz = bz[r];
+      js = bs[r];
+    }
+  }
+
   // ---- implicit right-hand sides, two columns (r_kappa = 0 and d/dr_kappa) ----
+  // The residuals r_z = z - bz, r_s = s - bs are the current point's; the
+  // elimination's diagonals are the Newton matrix's (newton_diag).
+  template <bool kChord>
   static __device__ __noinline__ void implicit_rhs() {
     const FLayout& L = fwd_state.L;
     QP_ARR(bz); QP_ARR(bs); QP_ARR(z); QP_ARR(s); QP_ARR(ri); QP_ARR(re); QP_ARR(ta);
@@ -608,19 +634,23 @@ struct Solver {
     QP_IARR(pos); QP_IARR(act);
     const int m = L.m, t = threadIdx.x, a = fwd_state.a, nf = fwd_state.nf;
     for (int r = t; r < m; r += NT) {
-      const float rho = bz[r] + bs[r];
+      float jz, js;
+      newton_diag<kChord>(r, jz, js);
+      const float rho = jz + js;
       const bool inact = pos[r] < 0;
       const float rzr = z[r] - bz[r], rsr = s[r] - bs[r];
       const float dri = ri[r] - rsr;
-      ta[r] = ri[r] + rzr - rsr - (inact ? dri * rho / bs[r] : 0.f);
-      tb[r] = inact ? 1.0f / bs[r] : 0.f;
+      ta[r] = ri[r] + rzr - rsr - (inact ? dri * rho / js : 0.f);
+      tb[r] = inact ? 1.0f / js : 0.f;
     }
     for (int k = t; k < nf; k += NT) {
       if (k < a) {
         const int r = act[k];
-        const float rho = bz[r] + bs[r];
-        ua[k] = -(ri[r] - (s[r] - bs[r])) * rho / bz[r];
-        ub[k] = 1.0f / bz[r];
+        float jz, js;
+        newton_diag<kChord>(r, jz, js);
+        const float rho = jz + js;
+        ua[k] = -(ri[r] - (s[r] - bs[r])) * rho / jz;
+        ub[k] = 1.0f / jz;
       } else {
         ua[k] = -re[k - a];
         ub[k] = 0.f;
@@ -634,31 +664,35 @@ struct Solver {
   }
 
   // ds, dz, dv of the implicit direction for r_kappa = rk on row r
+  template <bool kChord>
   static __device__ __forceinline__ void implicit_dir(int r, float rk, float& dsr, float& dzr,
                                                       float& dvr) {
     QP_ARR(bz); QP_ARR(bs); QP_ARR(ea); QP_ARR(eb); QP_ARR(ri); QP_ARR(z); QP_ARR(s);
     QP_ARR(ua); QP_ARR(ub); QP_IARR(pos);
+    float jz, js;
+    newton_diag<kChord>(r, jz, js);
     const float rzr = z[r] - bz[r], rsr = s[r] - bs[r];
-    const float rho = bz[r] + bs[r];
+    const float rho = jz + js;
     const float c = 1.0f / rho;
     const float e = fmaf(rk, eb[r], ea[r]);
     const int k = pos[r];
     if (k < 0) {
       const float rho2 = ri[r] - rsr - c * rk;
-      dvr = (e + rho2) * rho / bs[r];
+      dvr = (e + rho2) * rho / js;
     } else {
       dvr = fmaf(rk, ub[k], ua[k]) + e;
     }
-    dzr = -rzr + (bz[r] * c) * dvr - c * rk;
-    dsr = -rsr - (bs[r] * c) * dvr - c * rk;
+    dzr = -rzr + (jz * c) * dvr - c * rk;
+    dsr = -rsr - (js * c) * dvr - c * rk;
   }
 
+  template <bool kChord>
   static __device__ __noinline__ float implicit_alpha(float rk, bool store) {
     QP_ARR(s); QP_ARR(z); QP_ARR(tb); QP_ARR(red);
     float amin[1] = {1.0f};
     for (int r = threadIdx.x; r < fwd_state.L.m; r += NT) {
       float dsr, dzr, dvr;
-      implicit_dir(r, rk, dsr, dzr, dvr);
+      implicit_dir<kChord>(r, rk, dsr, dzr, dvr);
       if (dsr < 0.f) amin[0] = fminf(amin[0], -s[r] / dsr);
       if (dzr < 0.f) amin[0] = fminf(amin[0], -z[r] / dzr);
       if (store) tb[r] = dvr;
@@ -672,7 +706,7 @@ struct Solver {
     float acc[1] = {0.f};
     for (int r = threadIdx.x; r < fwd_state.L.m; r += NT) {
       float dsr, dzr, dvr;
-      implicit_dir(r, rk, dsr, dzr, dvr);
+      implicit_dir<false>(r, rk, dsr, dzr, dvr);
       acc[0] = fmaf(fmaf(alpha, dsr, s[r]), fmaf(alpha, dzr, z[r]), acc[0]);
     }
     reduce<1>(acc, red, OpSum());
@@ -700,7 +734,7 @@ struct Solver {
   // kt_fixed >= 0).  Returns false on a factorisation failure.
   static __device__ __noinline__ bool implicit_step(const FwdParams& P, float kappa, float kt_fixed) {
     partition();
-    implicit_rhs();
+    implicit_rhs<false>();
     fold_rhs();
     if (!factor(2)) return false;
     solve_folded();
@@ -713,7 +747,7 @@ struct Solver {
       if (P.sigma_mode == 1) {
         sigma = P.sigma;
       } else {
-        const float aa = implicit_alpha(kappa, false);
+        const float aa = implicit_alpha<false>(kappa, false);
         const float mua = implicit_mu_aff(kappa, aa);
         const float ratio = mua / kappa;
         sigma = ratio * ratio * ratio;
@@ -723,10 +757,34 @@ struct Solver {
       kt = fmaxf(sigma * kappa, P.kappa_min);
     }
     const float rk = kappa - kt;
-    const float alpha = P.step_frac * implicit_alpha(rk, true);
+    const float alpha = P.step_frac * implicit_alpha<false>(rk, true);
     implicit_update(alpha, rk, kappa);
     QP_MARK(PH_STEP);
     return true;
+  }
+
+  // ---- Alg. 2 chord step: the Newton step to kt with the factorisation of an
+  // earlier iterate (its partition, factors and Newton-matrix diagonals, see
+  // freeze_newton_matrix) and the residuals of the current one.  Its fixed
+  // point is the relaxed point itself; convergence is linear instead of
+  // quadratic. ----
+  static __device__ __noinline__ void chord_step(const FwdParams& P, float kappa, float kt) {
+    implicit_rhs<true>();
+    solve(0, 2);
+    g_times_dx(0, 2);
+    const float rk = kappa - kt;
+    const float alpha = P.step_frac * implicit_alpha<true>(rk, true);
+    implicit_update(alpha, rk, kappa);
+    QP_MARK(PH_STEP);
+  }
+
+  // Right after an implicit step: keep its Newton matrix's b_k(v) (bz, not yet
+  // recomputed at the new point) and kappa for the chord steps that follow.
+  static __device__ void freeze_newton_matrix(float kappa) {
+    QP_ARR(bz); QP_ARR(ina);
+    for (int r = threadIdx.x; r < fwd_state.L.m; r += NT) ina[r] = bz[r];
+    if (threadIdx.x == 0) fwd_state.chord_kappa = kappa;
+    __syncthreads();
   }
 
   // ---- explicit complementarity (ablation): Mehrotra predictor-corrector on
@@ -1028,9 +1086,17 @@ struct Solver {
         int rstatus = ST_MAX_ITER;
         float rbest = INFINITY;
         int rsince = 0;
+        bool chord = false;  // a factorisation of an earlier relax iterate is current
+        float rprev = INFINITY;
         for (int it = 0;; ++it) {
           const float2 rr = residuals(P, true, 1);
           const float rm = rr.x, kappa = rr.y;
+          // chord steps continue while each cuts the measure at least
+          // kChordRate-fold and it is above tol; otherwise the next step
+          // refactors (linear convergence would end the relax on its floor
+          // rule, short of relax_tol)
+          if (chord && !(rm <= kChordRate * rprev && rm >= P.tol)) chord = false;
+          rprev = rm;
           if (!(rm == rm)) { rstatus = ST_NUMERICAL; break; }
           if (rm < 0.9f * rbest) { rbest = rm; rsince = 0; } else { ++rsince; }
           // relax_tol where FP32 reaches it; otherwise its floor, once the
@@ -1046,7 +1112,12 @@ struct Solver {
             break;
           }
           if (it >= P.relax_max_iter) break;
-          if (!implicit_step(P, kappa, P.kappa_relax)) { rstatus = ST_NUMERICAL; break; }
+          if (chord) {
+            chord_step(P, kappa, P.kappa_relax);
+          } else {
+            if (!implicit_step(P, kappa, P.kappa_relax)) { rstatus = ST_NUMERICAL; break; }
+            if (P.chord) { freeze_newton_matrix(kappa); chord = true; }
+          }
           ++iters;
         }
         if (status == ST_SOLVED) status = rstatus;

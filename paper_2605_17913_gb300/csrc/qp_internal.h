@@ -36,6 +36,7 @@ struct FwdParams {
   float tol, sigma, kappa_min, kappa_relax, relax_tol, step_frac;
   int max_iter, relax_max_iter, sigma_mode, formulation, norm_abs, warm_start, refine_steps;
   int gwg;  // G'WG products: 0 FP32, 1 TF32, 2 BF16 (tensor cores, large variant only)
+  int chord;  // Alg. 2 reuses the factorisation of its first iterate (chord steps)
   // gradient cache (nullptr: no relax, no cache)
   float* cache;
   long long cache_stride;

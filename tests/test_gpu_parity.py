@@ -199,6 +199,36 @@ def test_large_variant_parity(workload, B, sizes):
     check_grads(res, ref)
 
 
+@pytest.mark.parametrize("workload,B,sizes", [
+    ("small", 48, {}),
+    ("degenerate", 64, {}),
+    ("diff", 8, {}),
+    ("small", 4, dict(n=130, m=200, p=10)),   # large variant
+])
+def test_chord_relax_vs_oracle(workload, B, sizes):
+    """Alg. 2 with chord steps (the relax factors its first iterate only and
+    reuses that factorisation): the same relaxed point, so the gradients meet
+    the same bars against the oracle as the refactoring default.  The
+    solution is written before the relax and is bitwise the default's."""
+    batch = make_batch(workload, B, seed=2, **sizes)
+    res = gpu_run(batch, grad=True, relax_chord=1)
+    base = gpu_run(batch, grad=True)
+    ref = oracle_run(batch, grad=True)
+    assert np.all(res["status"] == 0), np.unique(res["status"], return_counts=True)
+    for k in ("x", "y", "z", "s"):
+        assert np.array_equal(res[k], base[k]), k
+    sens = fp64_sensitivity(batch, ref) if workload == "degenerate" else None
+    check_grads(res, ref, TOL_G, sens)
+
+
+def test_chord_relax_setting_validated():
+    from paper_2605_17913_gb300 import _lib
+
+    batch = make_batch("small", 2, seed=0)
+    with pytest.raises(_lib.QPError):
+        gpu_run(batch, grad=True, relax_chord=2)
+
+
 @pytest.mark.parametrize("mode", ["tf32", "bf16"])
 def test_tensor_core_gwg_parity(mode):
     """G'WG on the tensor cores (TF32 / BF16 products, FP32 sums) in the
