@@ -65,6 +65,8 @@ def parse():
     # App. D: gradients of the polytope projection against the exact
     # hard-projection Jacobian (kappa_relax and size sweeps)
     ap.add_argument("--projection", action="store_true")
+    ap.add_argument("--safety", action="store_true",
+                    help="safety-filter-shaped QPs in large batches: one warp vs 128 threads per QP")
     ap.add_argument("--chord", action="store_true",
                     help="Alg. 2 with chord steps vs refactoring: time, iterations, "
                          "gradient error against FP64")
@@ -693,6 +695,65 @@ def run_precision(args):
         print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- safety-filter shapes
+def run_safety(args):
+    """Safety-filter-shaped QPs (k agents: n = 2k, m = 7k + k(k-1)/2, Q = I)
+    in large batches, solve + relax + backward, with one warp per QP (the
+    default from 2048 QPs on) against 128 threads per QP.  Every instance is
+    checked (status and FP64 scaled KKT <= 1e-5); solves+grads/s counts those
+    that pass."""
+    import torch
+
+    from paper_2605_17913_gb300.metrics import kkt_report
+    from paper_2605_17913_gb300.solver import QPSolver
+    from qpgen import make_batch
+
+    torch.cuda.set_device(0)
+    import __graft_entry__ as ge
+
+    ge.build()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    B = args.batch or 65536
+    for k in (2, 5, 7, 9):
+        data = make_batch("safety", B, seed=0, agents=k)
+        T = {n_: torch.from_numpy(getattr(data, n_)).cuda()
+             for n_ in ("Q", "q", "A", "b", "G", "h", "g")}
+        for tpq in (32, 128):
+            slv = QPSolver(B, data.n, data.p, data.m, tpq)
+            info = slv.info()
+            cache = slv.new_grad_cache()
+            ms = []
+            for rep_ in range(args.warmup + args.steps):
+                flush.zero_()
+                e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                e[0].record()
+                out = slv.solve(T["Q"], T["q"], T["A"], T["b"], T["G"], T["h"], grad_cache=cache,
+                                tol=args.tol, kappa_relax=args.kappa_relax)
+                e[1].record()
+                gr = slv.backward(cache, T["Q"], T["A"], T["G"], T["g"])
+                e[2].record()
+                torch.cuda.synchronize()
+                if rep_ >= args.warmup:
+                    ms.append((e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])))
+            r = {n_: v.cpu().numpy() for n_, v in out.items()}
+            rep = kkt_report(data.Q, data.q, data.A, data.b, data.G, data.h, r["x"], r["y"],
+                             r["z"], r["s"])
+            finite = torch.isfinite(gr["dq"]).all(dim=1).cpu().numpy()
+            ok = (r["status"] == 0) & (rep["scaled"] <= 1e-5) & finite
+            fwd = statistics.median(m_[0] for m_ in ms)
+            bwd = statistics.median(m_[1] for m_ in ms)
+            print(json.dumps({
+                "study": "safety-filter shapes", "agents": k, "n": data.n, "m_ineq": data.m,
+                "p_eq": data.p, "batch": B, "threads_per_qp": info["fwd_threads"],
+                "ctas_per_sm": info["fwd_blocks_per_sm"], "smem_bytes": info["fwd_smem_bytes"],
+                "forward_ms": fwd, "backward_ms": bwd,
+                "solves_grads_per_s": float(ok.sum()) / ((fwd + bwd) / 1e3),
+                "passed": float(ok.mean()), "iters_mean": float(r["iters"].mean()),
+                "kkt_scaled_max": float(rep["scaled"].max()),
+            }), flush=True)
+            del slv, cache, out, gr
+
+
 # ---------------------------------------------------------------- chord relax study
 def run_chord(args):
     """Alg. 2 refactoring at every relax iterate (default) vs chord steps (one
@@ -904,6 +965,9 @@ def main():
         return
     if args.precision:
         run_precision(args)
+        return
+    if args.safety:
+        run_safety(args)
         return
     if args.chord:
         run_chord(args)

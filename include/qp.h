@@ -132,8 +132,32 @@ void qp_settings_default(qp_settings* s);
  * QP_ENOMEM (workspace allocation failed) or QP_ECUDA. */
 int qp_handle_create(const qp_dims* dims, qp_handle** out);
 
+/* As qp_handle_create, with the threads per QP of the forward kernel chosen
+ * by the caller: 0 automatic (as qp_handle_create: one warp per QP for
+ * n <= 32 in batches of 2048 or more, else 128 up to n = 72, else 512), 32
+ * (one warp per QP; n <= 32) or 128 (n <= 72).  Sizes whose data do not fit
+ * one SM's shared memory at the requested width, and other widths, return
+ * QP_ENOTSUP.  Results are the same up to FP32 rounding order. */
+int qp_handle_create_threads(const qp_dims* dims, int32_t threads_per_qp, qp_handle** out);
+
 /* Free the handle and its workspace, if any. */
 int qp_handle_destroy(qp_handle* h);
+
+/* Launch configuration a handle chose (capacity planning, tests).  Problems
+ * with n <= 32 in batches of 2048 or more run one warp (32 threads) per QP,
+ * so that many QPs share an SM; other sizes up to n = 72 use 128 threads per
+ * QP, larger ones 512. */
+typedef struct {
+  int32_t fwd_threads;        /* threads per CTA (one CTA per QP) of the forward kernel */
+  int32_t fwd_blocks_per_sm;  /* resident forward CTAs per SM                          */
+  int32_t bwd_threads;        /* threads per CTA of the backward kernel                 */
+  int32_t max_active;         /* amax: inequality rows kept as multipliers at most      */
+  int32_t large_variant;      /* 1: matrices in the handle's device workspace           */
+  size_t fwd_smem_bytes;      /* dynamic shared memory per forward CTA                  */
+} qp_handle_info;
+
+/* Fill `out`.  Returns QP_EINVAL for a null argument. */
+int qp_handle_query(const qp_handle* h, qp_handle_info* out);
 
 /* Bytes of device memory the gradient cache of one solve needs: per
  * instance a header, the Cholesky factor L of K_I = Q + G_I'W_I G_I (packed

@@ -36,6 +36,12 @@ class Dims(ctypes.Structure):
                 ("n_ineq", ctypes.c_int32)]
 
 
+class HandleInfo(ctypes.Structure):
+    _fields_ = [("fwd_threads", ctypes.c_int32), ("fwd_blocks_per_sm", ctypes.c_int32),
+                ("bwd_threads", ctypes.c_int32), ("max_active", ctypes.c_int32),
+                ("large_variant", ctypes.c_int32), ("fwd_smem_bytes", ctypes.c_size_t)]
+
+
 class Settings(ctypes.Structure):
     _fields_ = [
         ("tol", ctypes.c_float),
@@ -95,12 +101,16 @@ def lib() -> ctypes.CDLL:
     L.qp_smem_bytes.argtypes = [i32, i32, i32]
     L.qp_handle_create.restype = ctypes.c_int
     L.qp_handle_create.argtypes = [ctypes.POINTER(Dims), ctypes.POINTER(vp)]
+    L.qp_handle_create_threads.restype = ctypes.c_int
+    L.qp_handle_create_threads.argtypes = [ctypes.POINTER(Dims), i32, ctypes.POINTER(vp)]
     L.qp_grad_cache_bytes.restype = ctypes.c_size_t
     L.qp_grad_cache_bytes.argtypes = [ctypes.POINTER(Dims)]
     L.qp_workspace_bytes.restype = ctypes.c_size_t
     L.qp_workspace_bytes.argtypes = [ctypes.POINTER(Dims)]
     L.qp_handle_destroy.restype = ctypes.c_int
     L.qp_handle_destroy.argtypes = [vp]
+    L.qp_handle_query.restype = ctypes.c_int
+    L.qp_handle_query.argtypes = [vp, ctypes.POINTER(HandleInfo)]
     L.qp_solve_batch.restype = ctypes.c_int
     L.qp_solve_batch.argtypes = [vp, ctypes.POINTER(Settings)] + [vp] * 14 + [vp]
     L.qp_backward_batch.restype = ctypes.c_int

@@ -124,13 +124,24 @@ size_t qp_workspace_bytes(const qp_dims* dims) {
 }
 
 int qp_handle_create(const qp_dims* dims, qp_handle** out) {
+  return qp_handle_create_threads(dims, 0, out);
+}
+
+int qp_handle_create_threads(const qp_dims* dims, int32_t threads_per_qp, qp_handle** out) {
   if (!out || !dims_ok(dims)) return QP_EINVAL;
   *out = nullptr;
+  if (threads_per_qp != 0 && threads_per_qp != 32 && threads_per_qp != 128) return QP_ENOTSUP;
   qp_handle* h = (qp_handle*)calloc(1, sizeof(qp_handle));
   if (!h) return QP_ENOMEM;
   h->dims = *dims;
   const int n = dims->n, m = dims->n_ineq, p = dims->n_eq;
-  h->fwd_smem = forward_config(n, m, p, &h->fwd_threads, &h->amax, &h->ws_stride);
+  const bool warp = threads_per_qp == 32 ||
+                    (threads_per_qp == 0 && dims->batch >= kWarpPerQpMinBatch);
+  h->fwd_smem = forward_config(n, m, p, &h->fwd_threads, &h->amax, &h->ws_stride, warp);
+  if (threads_per_qp != 0 && h->fwd_threads != threads_per_qp) {
+    free(h);
+    return QP_ENOTSUP;
+  }
   h->split = h->ws_stride > 0;
   h->bwd_smem = backward_smem_bytes(n, m, p, h->amax, h->split, &h->bwd_threads);
   h->cache_stride = cache_layout(n, m, p, h->amax, h->split).stride;
@@ -160,6 +171,17 @@ int qp_handle_create(const qp_dims* dims, qp_handle** out) {
     }
   }
   *out = h;
+  return QP_OK;
+}
+
+int qp_handle_query(const qp_handle* h, qp_handle_info* out) {
+  if (!h || !out) return QP_EINVAL;
+  out->fwd_threads = h->fwd_threads;
+  out->fwd_blocks_per_sm = h->fwd_blocks_per_sm;
+  out->bwd_threads = h->bwd_threads;
+  out->max_active = h->amax;
+  out->large_variant = h->split ? 1 : 0;
+  out->fwd_smem_bytes = h->fwd_smem;
   return QP_OK;
 }
 

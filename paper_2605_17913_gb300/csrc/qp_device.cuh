@@ -17,7 +17,6 @@ namespace qpgpu {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kRedK = 16;  // maximum quantities reduced by one block_reduce call
-constexpr int kMaxWarps = 16;  // blocks have at most 512 threads
 
 __host__ __device__ inline int round4(int v) { return (v + 3) & ~3; }
 __host__ __device__ inline int ld_vec(int n) {
@@ -54,11 +53,13 @@ struct OpSum { __device__ float operator()(float a, float b) const { return a + 
 template <int NT, int K, class Op>
 __device__ __forceinline__ void block_reduce(float (&v)[K], float* red, int& parity, Op op) {
   static_assert(K <= kRedK, "too many reduced values");
+  static_assert(NT % 32 == 0 && NT <= 512, "whole warps, at most 16");
 #pragma unroll
   for (int k = 0; k < K; ++k)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v[k] = op(v[k], __shfl_xor_sync(kFull, v[k], o));
-  float* buf = red + parity * (kMaxWarps * kRedK);
+  // two buffers of (NT / 32) * kRedK floats: red holds 2 * (NT / 32) * kRedK
+  float* buf = red + parity * ((NT / 32) * kRedK);
   parity ^= 1;
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   if (l == 0) {
@@ -325,8 +326,8 @@ __device__ bool panel_factor_trsm(float* M, int ld, int j0, int jb, float* dinv,
     }
   }
   // zero the pad rows: nA .. nA4-1 and after the last B row up to the group end
-  if (tid < 64) {
-    const int k = tid >> 3, c = tid & 7;
+  for (int e = tid; e < 64; e += NT) {
+    const int k = e >> 3, c = e & 7;
     const int r = k < 4 ? nA + k : nA4 + nB + (k - 4);
     const bool pad = k < 4 ? r < nA4 : (r & 3) != 0 && (r >> 2) == ((nA4 + nB) >> 2);
     if (pad) Pb[pb_off(r) + c] = 0.0f;

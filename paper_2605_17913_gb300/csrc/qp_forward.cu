@@ -18,7 +18,8 @@ int forward_blocks_per_sm_nt(size_t smem);
 // min(m, n - p), and amax + p <= 126 (warp solves hold at most 128 rows, two
 // of them folded right-hand sides).  Otherwise the large variant (n <= 256):
 // 512 threads, K, G, A, Y, C in a global workspace, amax + p <= 318.
-size_t forward_config(int n, int m, int p, int* nthreads, int* amax_out, long long* ws_floats) {
+size_t forward_config(int n, int m, int p, int* nthreads, int* amax_out, long long* ws_floats,
+                      bool warp_per_qp) {
   if (nthreads) *nthreads = 0;
   if (amax_out) *amax_out = 0;
   if (ws_floats) *ws_floats = 0;
@@ -32,9 +33,16 @@ size_t forward_config(int n, int m, int p, int* nthreads, int* amax_out, long lo
     if (floor_a < 0) floor_a = 0;
     for (int amax = amax0; amax >= floor_a && amax >= 0; --amax) {
       const fwd::FLayout L = fwd::make_fwd_layout(n, m, p, amax, nt);
-      const size_t bytes = (size_t)L.total * sizeof(float);
+      size_t bytes = (size_t)L.total * sizeof(float);
       if (bytes <= budget) {
-        if (nthreads) *nthreads = nt;
+        int nt_used = nt;
+        // one warp per QP: the same amax (its layout is no larger), so the
+        // gradient cache and every size query are unchanged
+        if (warp_per_qp && n <= 32) {
+          nt_used = 32;
+          bytes = (size_t)fwd::make_fwd_layout(n, m, p, amax, 32).total * sizeof(float);
+        }
+        if (nthreads) *nthreads = nt_used;
         if (amax_out) *amax_out = amax;
         return bytes;
       }
@@ -57,6 +65,7 @@ cudaError_t launch_forward(const FwdParams& P, int nthreads, size_t smem, int gr
   if (P.ws) return nthreads == 512 ? launch_forward_nt<512, true>(P, smem, grid, st)
                                    : cudaErrorInvalidValue;
   switch (nthreads) {
+    case 32: return launch_forward_nt<32, false>(P, smem, grid, st);
     case 128: return launch_forward_nt<128, false>(P, smem, grid, st);
     case 512: return launch_forward_nt<512, false>(P, smem, grid, st);
     default: return cudaErrorInvalidValue;
@@ -66,6 +75,7 @@ cudaError_t launch_forward(const FwdParams& P, int nthreads, size_t smem, int gr
 // Load every variant's module now (the runtime loads kernels lazily, on
 // first use), so that no later launch pays for it.
 void preload_forward_kernels() {
+  forward_blocks_per_sm_nt<32, false>(1024);
   forward_blocks_per_sm_nt<128, false>(1024);
   forward_blocks_per_sm_nt<512, false>(1024);
   forward_blocks_per_sm_nt<512, true>(1024);
@@ -75,6 +85,7 @@ void preload_forward_kernels() {
 int forward_blocks_per_sm(int nthreads, size_t smem, bool split) {
   if (split) return nthreads == 512 ? forward_blocks_per_sm_nt<512, true>(smem) : 0;
   switch (nthreads) {
+    case 32: return forward_blocks_per_sm_nt<32, false>(smem);
     case 128: return forward_blocks_per_sm_nt<128, false>(smem);
     case 512: return forward_blocks_per_sm_nt<512, false>(smem);
     default: return 0;

@@ -55,6 +55,7 @@ namespace fwd {
 
 constexpr int ST_SOLVED = 0, ST_MAX_ITER = 1, ST_STALLED = 2, ST_NUMERICAL = 3, ST_BAD_INPUT = 4;
 constexpr float kCReg = 1e-7f;  // relative diagonal shift of C
+constexpr float kStallMeasure = 1e-4f;  // Alg. 1 may end STALLED only below this measure
 // Alg. 2 chord steps reuse a factorisation while each step cuts the relax
 // measure at least this much (4x); a slower step means the frozen Newton
 // matrix (W moves like z^2 / kappa on active rows) has drifted too far
@@ -415,9 +416,10 @@ struct Solver {
     QP_BIG(K); QP_ARR(dinv); QP_ARR(R); QP_BIG(Y); QP_BIG(C); QP_ARR(ua); QP_ARR(ub);
     const int n = L.n, t = threadIdx.x, w = t >> 5, nf = fwd_state.nf;
     if (nf > 0) {
-      if (w < 2) {
-        float* u = w == 0 ? ua : ub;
-        const float* wrow = C + (nf + w) * L.ldc;
+      // one warp per column (both columns in turn with a single warp)
+      for (int c = w; c < 2; c += NT / 32) {
+        float* u = c == 0 ? ua : ub;
+        const float* wrow = C + (nf + c) * L.ldc;
         for (int k = t & 31; k < nf; k += 32) u[k] = wrow[k];
         __syncwarp();
         c_solve_n(u, nf, true);
@@ -490,8 +492,8 @@ struct Solver {
         u[k] = acc - u[k];
       }
       __syncthreads();
-      if (w < nrhs) {
-        float* u = (slot0 + w) == 0 ? ua : ub;
+      for (int c = w; c < nrhs; c += NT / 32) {
+        float* u = (slot0 + c) == 0 ? ua : ub;
         c_solve_n(u, nf, false);
       }
       __syncthreads();
@@ -1064,8 +1066,12 @@ struct Solver {
           }
           if (meas < P.tol) break;
           if (it >= P.max_iter) { status = ST_MAX_ITER; break; }
+          // stalled: the measure has reached its FP32 floor (~1e-7 scaled)
+          // without reaching tol -- below kStallMeasure and no 10 % better
+          // in 10 iterations.  Above it the iteration is still far from the
+          // solution (short steps) and continues to max_iter, as in Alg. 1.
           if (meas < 0.9f * best) { best = meas; since_best = 0; }
-          else if (++since_best >= 10) { status = ST_STALLED; break; }
+          else if (++since_best >= 10 && best < kStallMeasure) { status = ST_STALLED; break; }
           const bool ok = implicit ? implicit_step(P, kappa, -1.0f) : standard_step(P, kappa);
           if (!ok) { status = ST_NUMERICAL; break; }
           iters = it + 1;
@@ -1170,6 +1176,7 @@ struct Solver {
 
 // minimum resident CTAs per SM the register budget is sized for
 template <int NT> struct MinBlocks { static constexpr int value = 1; };
+template <> struct MinBlocks<32> { static constexpr int value = 12; };
 template <> struct MinBlocks<128> { static constexpr int value = 3; };
 template <> struct MinBlocks<256> { static constexpr int value = 3; };
 

@@ -102,9 +102,13 @@ __host__ __device__ inline CacheLayout cache_layout(int n, int m, int p, int ama
 // Launch configuration of the forward kernel for a size: shared-memory bytes
 // (0 if unsupported), threads per CTA, the active-row cap amax and, for the
 // large-problem variant, the global workspace floats per instance (0 when
-// everything fits in shared memory).
+// everything fits in shared memory).  warp_per_qp: one warp per CTA for
+// n <= 32 (throughput of large batches; the amax is the same either way).
 size_t forward_config(int n, int m, int p, int* nthreads, int* amax,
-                      long long* ws_floats = nullptr);
+                      long long* ws_floats = nullptr, bool warp_per_qp = false);
+
+// Batches from this size up run problems with n <= 32 one warp per QP.
+constexpr int kWarpPerQpMinBatch = 2048;
 cudaError_t launch_forward(const FwdParams& P, int nthreads, size_t smem, int grid,
                            cudaStream_t stream);
 int forward_blocks_per_sm(int nthreads, size_t smem, bool split);

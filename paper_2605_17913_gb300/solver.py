@@ -22,14 +22,16 @@ def _stream_handle(stream: Optional[torch.cuda.Stream]) -> int:
 
 class QPSolver:
     """Handle for batches of ``batch`` QPs with ``n`` variables, ``n_eq``
-    equality rows and ``n_ineq`` inequality rows (eq. 1)."""
+    equality rows and ``n_ineq`` inequality rows (eq. 1).  ``threads_per_qp``:
+    0 chooses by size and batch; 32 (one warp per QP, n <= 32) or 128 force
+    a width (qp_handle_create_threads)."""
 
-    def __init__(self, batch: int, n: int, n_eq: int, n_ineq: int):
+    def __init__(self, batch: int, n: int, n_eq: int, n_ineq: int, threads_per_qp: int = 0):
         self.batch, self.n, self.n_eq, self.n_ineq = int(batch), int(n), int(n_eq), int(n_ineq)
         self._dims = _lib.Dims(self.batch, self.n, self.n_eq, self.n_ineq)
         h = ctypes.c_void_p()
-        check(_lib.lib().qp_handle_create(ctypes.byref(self._dims), ctypes.byref(h)),
-              "qp_handle_create")
+        check(_lib.lib().qp_handle_create_threads(ctypes.byref(self._dims), int(threads_per_qp),
+                                                  ctypes.byref(h)), "qp_handle_create_threads")
         self._h = h
         self.device = torch.device("cuda", torch.cuda.current_device())
 
@@ -43,6 +45,12 @@ class QPSolver:
             self.close()
         except Exception:
             pass
+
+    def info(self) -> dict:
+        """The launch configuration this handle chose (qp_handle_query)."""
+        out = _lib.HandleInfo()
+        check(_lib.lib().qp_handle_query(self._h, ctypes.byref(out)), "qp_handle_query")
+        return {k: getattr(out, k) for k, _ in _lib.HandleInfo._fields_}
 
     @property
     def grad_cache_bytes(self) -> int:

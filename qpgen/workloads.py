@@ -37,6 +37,20 @@ Workloads (one per named configuration):
                 rows active at y0 (h = G y0 there), the others inactive with
                 h = G y0 + U(0.1, 1); x_query = y0 + G_A^T (d * xi),
                 xi ~ U(0.5, 1.5).  Then the projection of x_query is y0.
+``safety``      the centralised CBF safety-filter QP of k planar agents (the
+                paper's App. E shapes; default k = 7: n = 14, m = 70, p = 0).
+                u in R^{2k}; Q = I, q = -u_nom; rows: the box -u_max <= u_c
+                <= u_max (4k rows, u_max = 2), one zeroing-CBF row per agent
+                and obstacle (3 obstacles: -2 (p_i - c_o)' u_i <= alpha h_obs,
+                h_obs = |p_i - c_o|^2 - r_o^2) and one per agent pair
+                (-2 (p_i - p_j)' (u_i - u_j) <= alpha h_pair, h_pair =
+                |p_i - p_j|^2 - (2 r_agent)^2, r_agent = 0.35).  Positions,
+                goals and obstacle centres ~ U(-3, 3)^2, radii ~ U(0.3, 0.8),
+                each agent redrawn until it is safe (every h >= 0.05); gains
+                alpha ~ U(0.5, 2); u_nom = 3 (g_i - p_i) / max(|g_i - p_i|, 0.1)
+                (the goal-seeking law, not clipped, so box rows can bind).
+                u = 0 is strictly feasible (x0 = 0).  Shapes and structure
+                only: no rollouts, no learned gains.
 """
 from __future__ import annotations
 
@@ -55,6 +69,7 @@ _WORKLOAD_CODE = {
     "serving": 5,
     "projection": 6,
     "custom": 7,
+    "safety": 8,
 }
 
 CONFIGS: Dict[str, dict] = {
@@ -66,7 +81,14 @@ CONFIGS: Dict[str, dict] = {
                  q_mode="gauss", s0_mode="uniform"),
     "precision": dict(n=256, m=512, p=32, batch=256, Q_mode="logspec", reg=1e-3,
                       cond=1e4, q_mode="gauss", s0_mode="uniform"),
+    "safety": dict(n=14, m=70, p=0, batch=65536, agents=7),
 }
+
+
+def safety_size(agents: int):
+    """(n, m, p) of the k-agent safety-filter QP: 2k, 4k + 3k + k(k-1)/2, 0."""
+    k = int(agents)
+    return 2 * k, 4 * k + 3 * k + k * (k - 1) // 2, 0
 
 
 @dataclasses.dataclass
@@ -138,6 +160,8 @@ def make_instance(workload: str, index: int, seed: int = 0, *, n: Optional[int] 
         cfg.update(n=n_, m=m_, p=p_)
     elif workload == "projection":
         return _projection_instance(index, seed, n=n, m=m, **overrides)
+    elif workload == "safety":
+        return _safety_instance(index, seed, **overrides)
     else:
         cfg = dict(CONFIGS.get(workload, CONFIGS["small"]))
         rng = instance_rng(seed, workload, index)
@@ -234,3 +258,49 @@ def _projection_instance(index: int, seed: int, *, n=None, m=None, m_act=None, d
     probe = rng.standard_normal(n_)
     return dict(Q=np.eye(n_), q=-xq, A=np.zeros((0, n_)), b=np.zeros(0), G=G, h=h,
                 x0=y0, g=probe, x_query=xq, n_active=ma)
+
+
+def _safety_instance(index: int, seed: int, *, agents: int = 7, u_max: float = 2.0,
+                     n_obs: int = 3, r_agent: float = 0.35, **_):
+    k = int(agents)
+    n_, m_, _p = safety_size(k)
+    rng = instance_rng(seed, "safety", index)
+    c = rng.uniform(-3.0, 3.0, (n_obs, 2))
+    r = rng.uniform(0.3, 0.8, n_obs)
+    pos = np.zeros((k, 2))
+    for i in range(k):
+        for _try in range(1000):
+            pi = rng.uniform(-3.0, 3.0, 2)
+            ok = np.all(np.sum((pi - c) ** 2, axis=1) - r ** 2 >= 0.05)
+            ok = ok and all(np.sum((pi - pos[j]) ** 2) - (2 * r_agent) ** 2 >= 0.05
+                            for j in range(i))
+            if ok:
+                break
+        pos[i] = pi
+    goal = rng.uniform(-3.0, 3.0, (k, 2))
+    d = goal - pos
+    u_nom = (3.0 * d / np.maximum(np.linalg.norm(d, axis=1, keepdims=True), 0.1)).reshape(-1)
+    G = np.zeros((m_, n_))
+    h = np.zeros(m_)
+    row = 0
+    for cc in range(n_):                     # box
+        G[row, cc], h[row] = 1.0, u_max
+        G[row + 1, cc], h[row + 1] = -1.0, u_max
+        row += 2
+    for i in range(k):                       # obstacles
+        for o in range(n_obs):
+            dp = pos[i] - c[o]
+            G[row, 2 * i:2 * i + 2] = -2.0 * dp
+            h[row] = rng.uniform(0.5, 2.0) * (dp @ dp - r[o] ** 2)
+            row += 1
+    for i in range(k):                       # agent pairs
+        for j in range(i + 1, k):
+            dp = pos[i] - pos[j]
+            G[row, 2 * i:2 * i + 2] = -2.0 * dp
+            G[row, 2 * j:2 * j + 2] = 2.0 * dp
+            h[row] = rng.uniform(0.5, 2.0) * (dp @ dp - (2 * r_agent) ** 2)
+            row += 1
+    assert row == m_
+    g = rng.standard_normal(n_)
+    return dict(Q=np.eye(n_), q=-u_nom, A=np.zeros((0, n_)), b=np.zeros(0), G=G, h=h,
+                x0=np.zeros(n_), g=g)

@@ -102,3 +102,9 @@ def test_serve_footprint_and_config_validation(L):
     assert L.qp_serve_create(ctypes.byref(cfg), ctypes.byref(h)) == _lib.QP_EINVAL
     assert L.qp_serve_submit(None, None, None) == _lib.QP_EINVAL
     assert L.qp_serve_poll_any(None, None) == _lib.QP_EINVAL
+    assert L.qp_handle_query(None, None) == _lib.QP_EINVAL
+    # forced widths that cannot run are refused before any device call
+    h2 = ctypes.c_void_p()
+    for tpq, dims in ((64, (8, 10, 0, 20)), (32, (8, 40, 0, 20)), (128, (8, 100, 0, 20))):
+        d = _lib.Dims(*dims)
+        assert L.qp_handle_create_threads(ctypes.byref(d), tpq, ctypes.byref(h2)) == _lib.QP_ENOTSUP

@@ -51,3 +51,39 @@ def test_serving_sizes_range():
 def test_empty_batch():
     b = make_batch("small", 0)
     assert b.Q.shape == (0, 10, 10)
+
+
+def test_safety_filter_structure():
+    from qpgen.workloads import safety_size
+
+    for k in (1, 2, 7, 9):
+        n, m, p = safety_size(k)
+        assert (n, m, p) == (2 * k, 4 * k + 3 * k + k * (k - 1) // 2, 0)
+        d = make_instance("safety", 3, seed=1, agents=k)
+        G, h = d["G"], d["h"]
+        np.testing.assert_array_equal(d["Q"], np.eye(n))
+        assert G.shape == (m, n) and d["A"].shape == (0, n)
+        assert np.all(h > 0)  # u = 0 strictly feasible (safe state, positive gains)
+        # box rows: +e_c and -e_c with bound u_max = 2
+        for c in range(n):
+            np.testing.assert_array_equal(G[2 * c], np.eye(n)[c])
+            np.testing.assert_array_equal(G[2 * c + 1], -np.eye(n)[c])
+        np.testing.assert_array_equal(h[:4 * k], 2.0)
+        # obstacle rows touch one agent's two controls
+        obs = G[4 * k:7 * k]
+        for r, row in enumerate(obs):
+            nz = np.flatnonzero(row)
+            assert len(nz) == 2 and nz[0] == 2 * (r // 3) and nz[1] == nz[0] + 1
+        # pair rows: opposite gradients on the two agents' blocks
+        pair = G[7 * k:]
+        rr = 0
+        for i in range(k):
+            for j in range(i + 1, k):
+                row = pair[rr]
+                np.testing.assert_array_equal(row[2 * i:2 * i + 2], -row[2 * j:2 * j + 2])
+                assert np.count_nonzero(row) == 4
+                rr += 1
+    # the nominal control has length 3 (goal-seeking gain) unless within 0.1 of the goal
+    d = make_instance("safety", 0, seed=0)
+    speeds = np.linalg.norm(-d["q"].reshape(-1, 2), axis=1)
+    assert np.all(speeds <= 3.0 + 1e-12) and np.median(speeds) > 2.0

@@ -43,11 +43,11 @@ def _dev(batch):
             for k in ("Q", "q", "A", "b", "G", "h", "g")}
 
 
-def gpu_run(batch, grad=False, **settings):
+def gpu_run(batch, grad=False, threads_per_qp=0, **settings):
     from paper_2605_17913_gb300.solver import QPSolver
 
     T = _dev(batch)
-    slv = QPSolver(batch.batch, batch.n, batch.p, batch.m)
+    slv = QPSolver(batch.batch, batch.n, batch.p, batch.m, threads_per_qp)
     cache = slv.new_grad_cache() if grad else None
     settings.setdefault("tol", SOLVER_TOL)
     out = slv.solve(T["Q"], T["q"], T["A"], T["b"], T["G"], T["h"], grad_cache=cache, **settings)
@@ -219,6 +219,78 @@ def test_chord_relax_vs_oracle(workload, B, sizes):
         assert np.array_equal(res[k], base[k]), k
     sens = fp64_sensitivity(batch, ref) if workload == "degenerate" else None
     check_grads(res, ref, TOL_G, sens)
+
+
+@pytest.mark.parametrize("agents", [1, 2, 7, 9])
+def test_safety_filter_one_warp_per_qp_vs_oracle(agents):
+    """Safety-filter-shaped QPs of k agents (n = 2k, m = 7k + k(k-1)/2, Q = I)
+    with one warp per QP: forward bars and gradients against the oracle, and
+    the same solution as the 128-thread kernel."""
+    batch = make_batch("safety", 96, seed=0, agents=agents)
+    res = gpu_run(batch, grad=True, threads_per_qp=32)
+    ref = oracle_run(batch, grad=True)
+    check_forward(batch, res, O.solve(batch.Q, batch.q, batch.A, batch.b, batch.G, batch.h,
+                                      tol=1e-12, nthreads=8))
+    check_grads(res, ref)
+    res128 = gpu_run(batch, grad=True, threads_per_qp=128)
+    assert rel_err_inf(res["x"], res128["x"]).max() <= TOL_X
+
+
+@pytest.mark.parametrize("n,m,p", [(10, 20, 2), (1, 3, 0), (5, 0, 2), (7, 12, 0), (3, 1, 1),
+                                   (32, 64, 4), (17, 150, 3)])
+def test_one_warp_per_qp_edge_sizes(n, m, p):
+    """The one-warp kernel on ragged and degenerate sizes (equality-only,
+    a single row, n = 32 and m > 4 x 32 rows) against the oracle."""
+    batch = make_batch("small", 9, seed=6, n=n, m=m, p=p)
+    res = gpu_run(batch, grad=True, threads_per_qp=32)
+    ref = oracle_run(batch, grad=True)
+    check_forward(batch, res, O.solve(batch.Q, batch.q, batch.A, batch.b, batch.G, batch.h,
+                                      tol=1e-12, nthreads=8))
+    check_grads(res, ref)
+
+
+def test_one_warp_per_qp_chosen_for_large_batches():
+    """Batches of 2048 or more QPs with n <= 32 run one warp per QP unless
+    told otherwise; every instance passes, a sample matches the oracle."""
+    import dataclasses
+
+    from paper_2605_17913_gb300.solver import QPSolver
+
+    B = 2048
+    batch = make_batch("safety", B, seed=1)
+    assert QPSolver(B, batch.n, batch.p, batch.m).info()["fwd_threads"] == 32
+    assert QPSolver(B - 1, batch.n, batch.p, batch.m).info()["fwd_threads"] == 128
+    assert QPSolver(B, 40, 0, 80).info()["fwd_threads"] == 128
+    res = gpu_run(batch, grad=True)
+    assert np.all(res["status"] == 0)
+    rep = kkt_report(batch.Q, batch.q, batch.A, batch.b, batch.G, batch.h, res["x"], res["y"],
+                     res["z"], res["s"])
+    assert rep["scaled"].max() <= TOL_KKT
+    idx = np.arange(0, B, 64)
+    sub = dataclasses.replace(batch, **{k: getattr(batch, k)[idx] for k in
+                                        ("Q", "q", "A", "b", "G", "h", "x0", "g")})
+    ref = oracle_run(sub, grad=True)
+    picked = {k: v[idx] for k, v in res.items()}
+    check_forward(sub, picked, O.solve(sub.Q, sub.q, sub.A, sub.b, sub.G, sub.h, tol=1e-12,
+                                       nthreads=8))
+    check_grads(picked, ref)
+
+
+def test_slow_start_is_not_stalled():
+    """A safety-filter instance (2 agents, instance 1122 of seed 0) whose FP32
+    iteration takes short steps for its first ten iterations while the
+    scaled measure stays near 1: it must run on (Alg. 1 has no stall exit;
+    the kernel's exists only for the FP32 floor) and reach the oracle's x*."""
+    import dataclasses
+
+    full = make_batch("safety", 1, seed=0, start=1122, agents=2)
+    batch = dataclasses.replace(full)
+    for tpq in (32, 128):
+        res = gpu_run(batch, grad=True, threads_per_qp=tpq)
+        ref = oracle_run(batch, grad=True)
+        check_forward(batch, res, O.solve(batch.Q, batch.q, batch.A, batch.b, batch.G, batch.h,
+                                          tol=1e-12, nthreads=1))
+        check_grads(res, ref)
 
 
 def test_chord_relax_setting_validated():
