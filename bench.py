@@ -33,7 +33,7 @@ L2_BYTES = 129 * 1024 * 1024
 # DRAM bytes per launch of the forward kernel on the default workload (4096
 # instances), scaled by instance count from the ncu capture of 1024 instances
 # summarised in profiles/forward_degenerate_n50.md; None once the kernel changes.
-FORWARD_TRAFFIC_BYTES = None
+FORWARD_TRAFFIC_BYTES = 4 * 33063168
 
 
 def parse():
