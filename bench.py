@@ -342,20 +342,18 @@ def run_ours(args, rank, world, local_rank):
                if FORWARD_TRAFFIC_BYTES is not None and args.workload == "degenerate" else None)
     bwd_avg = sum(bwd_ms) / len(bwd_ms)
     bwd_gbs = backward_bytes(n, m, p, B) / (bwd_avg / 1e3) / 1e9
-    # ---- end to end through the public API with pinned host buffers ----
+    # ---- end to end: qp_solve_backward_host, the C-ABI call on host buffers
+    # (page-locked): every step copies the inputs in and the solution, status
+    # and gradients out, chunked on the library's two streams ----
     H = {k: torch.from_numpy(getattr(data, k)).pin_memory() for k in names}
     Hout = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in
-            list(gout.items()) + [("x", out["x"]), ("status", out["status"])]}
+            list(out.items()) + list(gout.items())}
     h2d = sum(v.numel() * v.element_size() for v in H.values())
     d2h = sum(v.numel() * v.element_size() for v in Hout.values())
 
     def e2e_step():
-        for k in names:
-            T[k].copy_(H[k], non_blocking=True)
-        step()
-        for k, v in Hout.items():
-            v.copy_(gout[k] if k in gout else out[k], non_blocking=True)
-        torch.cuda.synchronize()
+        slv.solve_backward_host(H["Q"], H["q"], H["A"], H["b"], H["G"], H["h"], dl_dx=H["g"],
+                                settings=settings, out=Hout)
 
     for _ in range(2):
         e2e_step()
@@ -366,6 +364,10 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(e2e_steps):
         e2e_step()
     e2e_dt = (time.perf_counter() - t0) / e2e_steps
+    # the host path's results are the device path's, bit for bit (so the same
+    # instances pass)
+    e2e_same = all(torch.equal(Hout[k], v.cpu()) for k, v in
+                   list(out.items()) + list(gout.items()))
     e2e_value = total_passed / e2e_dt if world == 1 else None
     if world > 1:
         e2e_value = total_passed / max_over_ranks(e2e_dt, dev)
@@ -407,7 +409,8 @@ def run_ours(args, rank, world, local_rank):
                     "backward_algorithmic_gbs": bwd_gbs,
                     "mean_iters": float(np.mean(iters)), "max_iters": int(np.max(iters))},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h)},
+                "d2h_bytes_per_step": int(d2h), "call": "qp_solve_backward_host",
+                "host_memory": "page-locked", "matches_device_outputs": bool(e2e_same)},
         "gpu_launches": 2 * args.steps,
         "clocks": clk,
         "wall_s_timed_region": wall,

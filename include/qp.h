@@ -159,6 +159,25 @@ typedef struct {
 /* Fill `out`.  Returns QP_EINVAL for a null argument. */
 int qp_handle_query(const qp_handle* h, qp_handle_info* out);
 
+/* Solve + relax + backward of a batch held in HOST memory: the library copies
+ * the data in, runs the kernels and copies the results out, in chunks of
+ * about a quarter of the batch (whole waves of resident CTAs) on two
+ * streams of its own, so that a chunk's
+ * copies overlap the kernels of its neighbours (with page-locked host memory;
+ * pageable memory works but serialises the copies).  Blocks until done.
+ * Arrays and layouts as qp_solve_batch / qp_backward_batch, all in host
+ * memory.  dl_dx NULL: solve only (no relax, no gradients; dQ..dh ignored).
+ * y, status, iters, kkt_res and the gradient outputs may be NULL (not
+ * copied back).  The first call allocates the handle's device arena for two
+ * chunks (inputs, outputs, gradient cache) and the two streams; they are
+ * kept until qp_handle_destroy.  Calls through one handle must not overlap.
+ * Returns QP_EINVAL / QP_ENOTSUP as qp_solve_batch, QP_ENOMEM, QP_ECUDA. */
+int qp_solve_backward_host(qp_handle* h, const qp_settings* settings, const float* Q,
+                           const float* q, const float* A, const float* b, const float* G,
+                           const float* h_, const float* dl_dx, float* x, float* y, float* z,
+                           float* s, int32_t* status, int32_t* iters, float* kkt_res, float* dQ,
+                           float* dq, float* dA, float* db, float* dG, float* dh);
+
 /* Bytes of device memory the gradient cache of one solve needs: per
  * instance a header, the Cholesky factor L of K_I = Q + G_I'W_I G_I (packed
  * lower; unpacked for the large-problem variant), Y = F L^-T with

@@ -133,6 +133,8 @@ def lib() -> ctypes.CDLL:
     L.qp_serve_destroy.argtypes = [vp]
     L.qp_solve_backward_static.restype = ctypes.c_int
     L.qp_solve_backward_static.argtypes = [vp, ctypes.POINTER(Settings)] + [vp] * 21
+    L.qp_solve_backward_host.restype = ctypes.c_int
+    L.qp_solve_backward_host.argtypes = [vp, ctypes.POINTER(Settings)] + [vp] * 20
     _lib = L
     return L
 

@@ -23,6 +23,12 @@ struct qp_handle {
   bool split;              // large-problem variant (matrices in a global workspace)
   float* ws;               // its workspace, batch * ws_stride floats (owned)
   long long ws_stride;
+  // qp_solve_backward_host: two streams and a two-slot device arena (owned,
+  // created on its first call)
+  cudaStream_t hstream[2];
+  float* hbuf;
+  size_t hbuf_bytes;
+  int hchunk;
 };
 
 static bool aligned4(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 3) == 0; }
@@ -188,6 +194,9 @@ int qp_handle_query(const qp_handle* h, qp_handle_info* out) {
 int qp_handle_destroy(qp_handle* h) {
   if (!h) return QP_EINVAL;
   if (h->ws) cudaFree(h->ws);
+  if (h->hbuf) cudaFree(h->hbuf);
+  for (cudaStream_t s : h->hstream)
+    if (s) cudaStreamDestroy(s);
   free(h);
   return QP_OK;
 }
@@ -202,12 +211,43 @@ size_t qp_grad_cache_bytes(const qp_dims* dims) {
          sizeof(float);
 }
 
+namespace {
+// The forward kernel over B instances (B <= the handle's batch) of the given
+// arrays; ws: the large variant's workspace for them.
+int solve_impl(qp_handle* h, const qp_settings* st, int B, float* ws, const float* Q,
+               const float* q, const float* A, const float* b, const float* G, const float* hv,
+               float* x, float* y, float* z, float* s, int32_t* status, int32_t* iters,
+               float* kkt_res, float* grad_cache, cudaStream_t stream);
+int backward_impl(qp_handle* h, int B, const float* grad_cache, const float* Q, const float* A,
+                  const float* G, const float* dl_dx, float* dQ, float* dq, float* dA, float* db,
+                  float* dG, float* dh, cudaStream_t stream);
+}  // namespace
+
 int qp_solve_batch(qp_handle* h, const qp_settings* st, const float* Q, const float* q,
                    const float* A, const float* b, const float* G, const float* hv, float* x,
                    float* y, float* z, float* s, int32_t* status, int32_t* iters, float* kkt_res,
                    float* grad_cache, void* stream) {
   if (!h || !st) return QP_EINVAL;
-  const int B = h->dims.batch, n = h->dims.n, m = h->dims.n_ineq, p = h->dims.n_eq;
+  return solve_impl(h, st, h->dims.batch, h->ws, Q, q, A, b, G, hv, x, y, z, s, status, iters,
+                    kkt_res, grad_cache, (cudaStream_t)stream);
+}
+
+int qp_backward_batch(qp_handle* h, const float* grad_cache, const float* Q, const float* A,
+                      const float* G, const float* dl_dx, float* dQ, float* dq, float* dA,
+                      float* db, float* dG, float* dh, void* stream) {
+  if (!h) return QP_EINVAL;
+  return backward_impl(h, h->dims.batch, grad_cache, Q, A, G, dl_dx, dQ, dq, dA, db, dG, dh,
+                       (cudaStream_t)stream);
+}
+
+}  // extern "C"
+
+namespace {
+int solve_impl(qp_handle* h, const qp_settings* st, int B, float* ws, const float* Q,
+               const float* q, const float* A, const float* b, const float* G, const float* hv,
+               float* x, float* y, float* z, float* s, int32_t* status, int32_t* iters,
+               float* kkt_res, float* grad_cache, cudaStream_t stream) {
+  const int n = h->dims.n, m = h->dims.n_ineq, p = h->dims.n_eq;
   if (B == 0) return QP_OK;
   if (!Q || !q || !x || (p > 0 && (!A || !b || !y)) || (m > 0 && (!G || !hv || !z || !s)))
     return QP_EINVAL;
@@ -227,14 +267,14 @@ int qp_solve_batch(qp_handle* h, const qp_settings* st, const float* Q, const fl
   P.status = status; P.iters = iters; P.kkt = kkt_res;
   P.cache = grad_cache;
   P.cache_stride = h->cache_stride;
-  P.ws = h->ws;
+  P.ws = ws;
   P.ws_stride = h->ws_stride;
 #ifdef QP_PHASE_TIMERS
   P.timers = g_phase_counters;
 #endif
   // one CTA per instance: the block scheduler hands a new instance to an SM
   // as soon as one finishes, which balances uneven iteration counts
-  cudaError_t e = launch_forward(P, h->fwd_threads, h->fwd_smem, B, (cudaStream_t)stream);
+  cudaError_t e = launch_forward(P, h->fwd_threads, h->fwd_smem, B, stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return QP_ECUDA;
@@ -242,11 +282,10 @@ int qp_solve_batch(qp_handle* h, const qp_settings* st, const float* Q, const fl
   return QP_OK;
 }
 
-int qp_backward_batch(qp_handle* h, const float* grad_cache, const float* Q, const float* A,
-                      const float* G, const float* dl_dx, float* dQ, float* dq, float* dA,
-                      float* db, float* dG, float* dh, void* stream) {
-  if (!h) return QP_EINVAL;
-  const int B = h->dims.batch, n = h->dims.n, m = h->dims.n_ineq, p = h->dims.n_eq;
+int backward_impl(qp_handle* h, int B, const float* grad_cache, const float* Q, const float* A,
+                  const float* G, const float* dl_dx, float* dQ, float* dq, float* dA, float* db,
+                  float* dG, float* dh, cudaStream_t stream) {
+  const int n = h->dims.n, m = h->dims.n_ineq, p = h->dims.n_eq;
   if (B == 0) return QP_OK;
   if (!grad_cache || !dl_dx || !Q || (m > 0 && !G) || (p > 0 && !A)) return QP_EINVAL;
   if (reinterpret_cast<uintptr_t>(grad_cache) & 15) return QP_EINVAL;
@@ -260,12 +299,142 @@ int qp_backward_batch(qp_handle* h, const float* grad_cache, const float* Q, con
   P.Q = Q; P.A = A; P.G = G; P.g = dl_dx; P.cache = grad_cache; P.cache_stride = h->cache_stride;
   P.dQ = dQ; P.dq = dq; P.dA = p > 0 ? dA : nullptr; P.db = p > 0 ? db : nullptr;
   P.dG = m > 0 ? dG : nullptr; P.dh = m > 0 ? dh : nullptr;
-  cudaError_t e = launch_backward(P, h->bwd_threads, h->bwd_smem, (cudaStream_t)stream);
+  cudaError_t e = launch_backward(P, h->bwd_threads, h->bwd_smem, stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return QP_ECUDA;
   }
   return QP_OK;
+}
+// Floats per instance of the host path's device arrays, each region of a
+// slot rounded up to 64 floats (the cache needs 16-byte alignment).
+struct HostLayout {
+  long long Q, q, A, b, G, h, g, x, y, z, s, st, it, kkt, dQ, dq, dA, db, dG, dh, cache, total;
+};
+
+long long r64(long long v) { return (v + 63) & ~63LL; }
+
+HostLayout host_layout(const qp_handle* h, long long C) {
+  const long long n = h->dims.n, m = h->dims.n_ineq, p = h->dims.n_eq;
+  HostLayout L;
+  long long o = 0;
+  auto take = [&](long long per) { const long long r = o; o += r64(C * per); return r; };
+  L.Q = take(n * n); L.q = take(n); L.A = take(p * n); L.b = take(p); L.G = take(m * n);
+  L.h = take(m); L.g = take(n);
+  L.x = take(n); L.y = take(p); L.z = take(m); L.s = take(m);
+  L.st = take(1); L.it = take(1); L.kkt = take(1);
+  L.dQ = take(n * n); L.dq = take(n); L.dA = take(p * n); L.db = take(p); L.dG = take(m * n);
+  L.dh = take(m);
+  L.cache = take(h->cache_stride);
+  L.total = o;
+  return L;
+}
+}  // namespace
+
+extern "C" {
+
+int qp_solve_backward_host(qp_handle* h, const qp_settings* st, const float* Q, const float* q,
+                           const float* A, const float* b, const float* G, const float* hv,
+                           const float* dl_dx, float* x, float* y, float* z, float* s,
+                           int32_t* status, int32_t* iters, float* kkt_res, float* dQ, float* dq,
+                           float* dA, float* db, float* dG, float* dh) {
+  if (!h || !st) return QP_EINVAL;
+  const int B = h->dims.batch, n = h->dims.n, m = h->dims.n_ineq, p = h->dims.n_eq;
+  if (B == 0) return QP_OK;
+  if (!Q || !q || !x || (p > 0 && (!A || !b || !y)) || (m > 0 && (!G || !hv || !z || !s)))
+    return QP_EINVAL;
+  const bool grad = dl_dx != nullptr;
+  FwdParams chk;
+  memset(&chk, 0, sizeof(chk));
+  int rc = settings_to_params(st, &chk);
+  if (rc != QP_OK) return rc;
+  if (chk.gwg != QP_GWG_FP32 && !h->split) return QP_ENOTSUP;
+  // about four chunks per batch, each a whole number of waves of resident
+  // CTAs: a partial last wave per chunk left SMs idle (chunks of 1024 at
+  // 456 resident: 5 % slower than 912)
+  if (h->hchunk == 0) {
+    const long long resident = (long long)h->fwd_blocks_per_sm * h->num_sms;
+    long long waves = (B + 2 * resident) / (4 * resident);
+    if (waves < 1) waves = 1;
+    long long C = waves * resident;
+    if (C > B) C = B;
+    h->hchunk = (int)C;
+  }
+  if (!h->hbuf) {
+    const size_t bytes = 2 * (size_t)host_layout(h, h->hchunk).total * sizeof(float);
+    if (cudaMalloc((void**)&h->hbuf, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      h->hbuf = nullptr;
+      return QP_ENOMEM;
+    }
+    h->hbuf_bytes = bytes;
+  }
+  for (cudaStream_t& sm : h->hstream) {
+    if (!sm && cudaStreamCreateWithFlags(&sm, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      sm = nullptr;
+      return QP_ECUDA;
+    }
+  }
+  const long long C = h->hchunk;
+  const HostLayout L = host_layout(h, C);
+  bool ok = true;
+  auto h2d = [&](float* dst, const void* src, long long count, cudaStream_t sm) {
+    if (ok && count > 0 && src)
+      ok = cudaMemcpyAsync(dst, src, (size_t)count * 4, cudaMemcpyHostToDevice, sm) == cudaSuccess;
+  };
+  auto d2h = [&](void* dst, const float* src, long long count, cudaStream_t sm) {
+    if (ok && count > 0 && dst)
+      ok = cudaMemcpyAsync(dst, src, (size_t)count * 4, cudaMemcpyDeviceToHost, sm) == cudaSuccess;
+  };
+  // chunk i runs on stream i % 2 in slot i % 2: the slot's previous chunk is
+  // earlier on the same stream, so reuse needs no further synchronisation
+  for (long long c0 = 0, i = 0; c0 < B && ok && rc == QP_OK; c0 += C, ++i) {
+    const long long nb = (B - c0) < C ? (B - c0) : C;
+    cudaStream_t sm = h->hstream[i & 1];
+    float* d = h->hbuf + (i & 1) * L.total;
+    h2d(d + L.Q, Q + c0 * n * n, nb * n * n, sm);
+    h2d(d + L.q, q + c0 * n, nb * n, sm);
+    if (p > 0) { h2d(d + L.A, A + c0 * p * n, nb * p * n, sm); h2d(d + L.b, b + c0 * p, nb * p, sm); }
+    if (m > 0) { h2d(d + L.G, G + c0 * m * n, nb * m * n, sm); h2d(d + L.h, hv + c0 * m, nb * m, sm); }
+    if (grad) h2d(d + L.g, dl_dx + c0 * n, nb * n, sm);
+    if (!ok) break;
+    float* ws = h->ws ? h->ws + c0 * h->ws_stride : nullptr;
+    rc = solve_impl(h, st, (int)nb, ws, d + L.Q, d + L.q, d + L.A, d + L.b, d + L.G, d + L.h,
+                    d + L.x, d + L.y, d + L.z, d + L.s, reinterpret_cast<int32_t*>(d + L.st),
+                    reinterpret_cast<int32_t*>(d + L.it), d + L.kkt, grad ? d + L.cache : nullptr,
+                    sm);
+    if (rc == QP_OK && grad)
+      rc = backward_impl(h, (int)nb, d + L.cache, d + L.Q, d + L.A, d + L.G, d + L.g, d + L.dQ,
+                         d + L.dq, d + L.dA, d + L.db, d + L.dG, d + L.dh, sm);
+    if (rc != QP_OK) break;
+    d2h(x + c0 * n, d + L.x, nb * n, sm);
+    if (p > 0) d2h(y + c0 * p, d + L.y, nb * p, sm);
+    if (m > 0) { d2h(z + c0 * m, d + L.z, nb * m, sm); d2h(s + c0 * m, d + L.s, nb * m, sm); }
+    d2h(status ? status + c0 : nullptr, d + L.st, nb, sm);
+    d2h(iters ? iters + c0 : nullptr, d + L.it, nb, sm);
+    d2h(kkt_res ? kkt_res + c0 : nullptr, d + L.kkt, nb, sm);
+    if (grad) {
+      d2h(dQ ? dQ + c0 * n * n : nullptr, d + L.dQ, nb * n * n, sm);
+      d2h(dq ? dq + c0 * n : nullptr, d + L.dq, nb * n, sm);
+      if (p > 0) {
+        d2h(dA ? dA + c0 * p * n : nullptr, d + L.dA, nb * p * n, sm);
+        d2h(db ? db + c0 * p : nullptr, d + L.db, nb * p, sm);
+      }
+      if (m > 0) {
+        d2h(dG ? dG + c0 * m * n : nullptr, d + L.dG, nb * m * n, sm);
+        d2h(dh ? dh + c0 * m : nullptr, d + L.dh, nb * m, sm);
+      }
+    }
+  }
+  // wait for everything enqueued, also after an error
+  for (cudaStream_t sm : h->hstream)
+    if (cudaStreamSynchronize(sm) != cudaSuccess) ok = false;
+  if (!ok) {
+    cudaGetLastError();
+    return QP_ECUDA;
+  }
+  return rc;
 }
 
 }  // extern "C"

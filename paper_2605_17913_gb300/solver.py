@@ -1,14 +1,16 @@
 """PyTorch-facing API: batched solves, gradients and a torch.autograd.Function.
 
 Tensors must be float32, contiguous and on the CUDA device current when the
-solver is created.  PyTorch only allocates memory and supplies the stream;
-the arithmetic is in libqpgpu's kernels.
+solver is created (``solve_backward_host``: in host memory).  PyTorch only
+allocates memory and supplies the stream; the arithmetic is in libqpgpu's
+kernels.
 """
 from __future__ import annotations
 
 import ctypes
 from typing import Dict, Optional
 
+import numpy as np
 import torch
 
 from . import _lib
@@ -70,6 +72,52 @@ class QPSolver:
         if tuple(t.shape) != tuple(shape):
             raise QPError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
         return t
+
+    def _host(self, name, t, shape):
+        if t is None:
+            if int(torch.tensor(shape).prod()) == 0:
+                return None
+            raise QPError(f"{name} is required")
+        if not isinstance(t, torch.Tensor):
+            t = torch.from_numpy(np.ascontiguousarray(t, dtype=np.float32))
+        if t.dtype != torch.float32 or t.is_cuda or not t.is_contiguous():
+            raise QPError(f"{name} must be a contiguous float32 host tensor or array")
+        if tuple(t.shape) != tuple(shape):
+            raise QPError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+        return t
+
+    def solve_backward_host(self, Q, q, A, b, G, h, dl_dx=None,
+                            settings: Optional[_lib.Settings] = None, out: Optional[Dict] = None,
+                            **overrides) -> Dict[str, torch.Tensor]:
+        """Solve, relax and backward pass of a batch in host memory in one
+        call (qp_solve_backward_host): the library moves chunks of the batch
+        to the device and back on two streams, overlapping the copies with
+        the kernels when the host tensors are page-locked (``pin_memory()``).
+        Without ``dl_dx``: the solve only.  Returns host tensors (``out``,
+        if given, is filled instead)."""
+        B, n, p, m = self.batch, self.n, self.n_eq, self.n_ineq
+        Q = self._host("Q", Q, (B, n, n))
+        q = self._host("q", q, (B, n))
+        A = self._host("A", A, (B, p, n))
+        b = self._host("b", b, (B, p))
+        G = self._host("G", G, (B, m, n))
+        h = self._host("h", h, (B, m))
+        g = self._host("dl_dx", dl_dx, (B, n)) if dl_dx is not None else None
+        st = settings if settings is not None else default_settings(**overrides)
+        if out is None:
+            out = dict(x=torch.empty(B, n), y=torch.empty(B, p), z=torch.empty(B, m),
+                       s=torch.empty(B, m), status=torch.empty(B, dtype=torch.int32),
+                       iters=torch.empty(B, dtype=torch.int32), kkt=torch.empty(B))
+            if g is not None:
+                out.update(dQ=torch.empty(B, n, n), dq=torch.empty(B, n), dA=torch.empty(B, p, n),
+                           db=torch.empty(B, p), dG=torch.empty(B, m, n), dh=torch.empty(B, m))
+        o = lambda k: ptr(out.get(k))  # noqa: E731
+        rc = _lib.lib().qp_solve_backward_host(
+            self._h, ctypes.byref(st), ptr(Q), ptr(q), ptr(A), ptr(b), ptr(G), ptr(h), ptr(g),
+            o("x"), o("y"), o("z"), o("s"), o("status"), o("iters"), o("kkt"), o("dQ"), o("dq"),
+            o("dA"), o("db"), o("dG"), o("dh"))
+        check(rc, "qp_solve_backward_host")
+        return out
 
     def solve(self, Q, q, A, b, G, h, settings: Optional[_lib.Settings] = None,
               grad_cache: Optional[torch.Tensor] = None, out: Optional[Dict] = None,

@@ -293,6 +293,37 @@ def test_slow_start_is_not_stalled():
         check_grads(res, ref)
 
 
+@pytest.mark.parametrize("workload,B,sizes", [
+    ("small", 1000, {}),                       # three chunks, both slots reused
+    ("degenerate", 700, {}),
+    ("small", 5, dict(n=130, m=200, p=10)),   # large variant: workspace per chunk
+])
+def test_host_buffer_call_matches_device_calls(workload, B, sizes):
+    """qp_solve_backward_host on host arrays (chunked copies on two streams)
+    gives bit for bit what qp_solve_batch + qp_backward_batch give on device
+    arrays; pinned and pageable host memory alike; solve-only without dl_dx."""
+    from paper_2605_17913_gb300.solver import QPSolver
+
+    batch = make_batch(workload, B, seed=3, **sizes)
+    dev = gpu_run(batch, grad=True)
+    slv = QPSolver(B, batch.n, batch.p, batch.m)
+    for pin in (True, False):
+        H = {k: torch.from_numpy(np.ascontiguousarray(getattr(batch, k))) for k in
+             ("Q", "q", "A", "b", "G", "h", "g")}
+        if pin:
+            H = {k: v.pin_memory() for k, v in H.items()}
+        out = slv.solve_backward_host(H["Q"], H["q"], H["A"], H["b"], H["G"], H["h"],
+                                      dl_dx=H["g"], tol=SOLVER_TOL)
+        for k in ("x", "y", "z", "s", "status", "iters", "kkt") + GRAD_KEYS:
+            assert np.array_equal(out[k].numpy(), dev[k]), (k, pin)
+    solo = gpu_run(batch, grad=False)
+    out = slv.solve_backward_host(batch.Q, batch.q, batch.A, batch.b, batch.G, batch.h,
+                                  tol=SOLVER_TOL)
+    for k in ("x", "y", "z", "s", "status", "iters", "kkt"):
+        assert np.array_equal(out[k].numpy(), solo[k]), k
+    assert "dQ" not in out
+
+
 def test_chord_relax_setting_validated():
     from paper_2605_17913_gb300 import _lib
 
