@@ -18,8 +18,12 @@
 // in Alg. 3
 //   dQ = (dx x' + x dx')/2, dq = dx, dA = dy x' + y dx', db = -dy,
 //   dG = dz x' + z dx',     dh = -dz.
-// One CTA per instance: Q, A, G and the factors are staged in shared memory
-// once; the gradient blocks go out as coalesced 16-byte streaming stores.
+// One CTA per instance: the factors are staged in shared memory once (the
+// large variant reads them in place); Q, G, A are read where the caller keeps
+// them, through L1 / L2, so that the small shared-memory layout lets five
+// CTAs share an SM (staging Q, G, A too gave three per SM at n = 50 and took
+// 1.6x as long); the gradient blocks go out as coalesced 16-byte streaming
+// stores.
 #include <mutex>
 
 #include "qp_device.cuh"
@@ -31,15 +35,14 @@ namespace {
 
 struct BLayout {
   int ldk, ldc, ldx, ldg, nv, mv, pv, fv;
-  int oK, oY, oC, oQ, oG, oA, oR, oCol, o_dinv, o_cdinv, o_mu, o_dmu, o_g, o_x, o_y, o_z, o_W,
+  int oK, oY, oC, oR, oCol, o_dinv, o_cdinv, o_mu, o_dmu, o_g, o_x, o_y, o_z, o_W,
       o_pos, o_act, o_e, o_tv, o_dz, o_qdx, o_adx, total;
 };
 
-// kStage: Q, G, A copied to shared memory (when they fit), else read from global.
 // global: the large-problem variant, whose factors are read in place from the
 // (unpacked) gradient cache, so K, Y, C take no shared memory.
 __host__ __device__ inline BLayout make_blayout(int n, int m, int p, int amax, int nthreads,
-                                                bool stage, bool global = false) {
+                                                bool global) {
   BLayout B;
   const int f = amax + p;
   B.ldk = ld_odd(n);
@@ -53,9 +56,6 @@ __host__ __device__ inline BLayout make_blayout(int n, int m, int p, int amax, i
   B.oK = take(global ? 0 : n * B.ldk);
   B.oY = take(global ? 0 : f * B.ldk);
   B.oC = take(global ? 0 : f * B.ldc);
-  B.oQ = take(stage ? n * B.ldg : 0);
-  B.oG = take(stage ? m * B.ldg : 0);
-  B.oA = take(stage ? p * B.ldg : 0);
   B.oR = take(2 * B.ldx);
   B.oCol = take(2 * nthreads);
   B.o_dinv = take(B.nv); B.o_cdinv = take(B.fv); B.o_mu = take(B.fv); B.o_dmu = take(B.fv);
@@ -177,11 +177,11 @@ __device__ void two_level_solve(const float* K, int ldk, const float* dinv, cons
   solve_rows<NT, true, kMaxS>(K, ldk, dinv, n, R, ldx, 0, 1);
 }
 
-template <int NT, bool kStage, bool kGlobal>
+template <int NT, bool kGlobal>
 __device__ __forceinline__ void backward_body(const BwdParams& P, int bi) {
   extern __shared__ __align__(16) float sm[];
   const int n = P.n, m = P.m, p = P.p, t = threadIdx.x;
-  const BLayout B = make_blayout(n, m, p, P.amax, NT, kStage, kGlobal);
+  const BLayout B = make_blayout(n, m, p, P.amax, NT, kGlobal);
   const CacheLayout cl = cache_layout(n, m, p, P.amax, kGlobal);
   const float* c = P.cache + (size_t)bi * (size_t)P.cache_stride;
   // the factors: staged in shared memory, or (large variant) read in place
@@ -190,9 +190,6 @@ __device__ __forceinline__ void backward_body(const BwdParams& P, int bi) {
   float* C = kGlobal ? const_cast<float*>(c + cl.oLC) : sm + B.oC;
   const int ldk = kGlobal ? cl.ldk : B.ldk;
   const int ldc = kGlobal ? cl.ldc : B.ldc;
-  float* Qs = sm + B.oQ;
-  float* Gs = sm + B.oG;
-  float* As = sm + B.oA;
   float* R = sm + B.oR;
   float* col = sm + B.oCol;
   float* dinv = sm + B.o_dinv;
@@ -218,31 +215,14 @@ __device__ __forceinline__ void backward_body(const BwdParams& P, int bi) {
   // a cache that was not written by a forward solve of this size cannot index
   // out of bounds: its gradients come out NaN instead
   const bool valid = a >= 0 && a <= P.amax && nf == a + p;
-  // ---- stage the data, the cached factors and the point ----
+  // ---- stage the cached factors and the point ----
   for (int i = t; i < B.total; i += NT) sm[i] = 0.0f;
   __syncthreads();
-  const float* gQ = P.Q + (size_t)bi * n * n;
-  const float* gG = P.G + (size_t)bi * m * n;
-  const float* gA = P.A + (size_t)bi * p * n;
-  if (kStage) {
-    for (int e2 = t; e2 < n * n; e2 += NT) {
-      const int r = e2 / n;
-      Qs[r * B.ldg + (e2 - r * n)] = __ldg(gQ + e2);
-    }
-    for (int e2 = t; e2 < m * n; e2 += NT) {
-      const int r = e2 / n;
-      Gs[r * B.ldg + (e2 - r * n)] = __ldg(gG + e2);
-    }
-    for (int e2 = t; e2 < p * n; e2 += NT) {
-      const int r = e2 / n;
-      As[r * B.ldg + (e2 - r * n)] = __ldg(gA + e2);
-    }
-  }
-  // generic pointers: shared-memory copies, or the caller's global arrays
-  const float* Qm = kStage ? Qs : gQ;
-  const float* Gm = kStage ? Gs : gG;
-  const float* Am = kStage ? As : gA;
-  const int ldm = kStage ? B.ldg : n;
+  // the data stay in the caller's memory (row stride n)
+  const float* const Qm = P.Q + (size_t)bi * n * n;
+  const float* const Gm = P.G + (size_t)bi * m * n;
+  const float* const Am = P.A + (size_t)bi * p * n;
+  const int ldm = n;
   const int nfl = valid ? nf : 0;
   if (kGlobal) {
     // factors stay in the cache: only the reciprocal pivots go to shared memory
@@ -359,8 +339,12 @@ __device__ __forceinline__ void backward_body(const BwdParams& P, int bi) {
     for (int r = t; r < m; r += NT) __stcs(P.dh + (size_t)bi * m + r, -dz[r]);
 }
 
-template <int NT, bool kStage, bool kGlobal>
-__global__ void __launch_bounds__(NT) qp_backward_kernel(const BwdParams P) {
+// On chip: at most 102 registers with 128 threads, so that five CTAs fit an
+// SM (the shared-memory layout is 42.8 KB at n = 50, m = 100, p = 10), and 128
+// with 256 threads (two CTAs where shared memory allows).
+template <int NT, bool kGlobal>
+__global__ void __launch_bounds__(NT, kGlobal ? 1 : (NT == 128 ? 5 : 2))
+    qp_backward_kernel(const BwdParams P) {
   // parameters in shared memory (the body takes them by reference); a ragged
   // launch substitutes this CTA's request, addressed as instance 0
   __shared__ BwdParams sP;
@@ -377,7 +361,7 @@ __global__ void __launch_bounds__(NT) qp_backward_kernel(const BwdParams P) {
     }
   }
   __syncthreads();
-  backward_body<NT, kStage, kGlobal>(sP, P.desc ? 0 : blockIdx.x);
+  backward_body<NT, kGlobal>(sP, P.desc ? 0 : blockIdx.x);
 }
 
 }  // namespace
@@ -389,71 +373,47 @@ constexpr size_t kBwdBudget = 227 * 1024 - 512;
 // 256 above (33 % faster than 128 at n = 100) and for the large variant.
 int backward_threads(int n, bool split) { return (!split && n <= 72) ? 128 : 256; }
 
-size_t backward_direct_smem_bytes(int n, int m, int p, int amax, bool split) {
-  if (split ? (n > 256 || amax + p > 318) : (n > 128 || amax + p > 128)) return 0;
-  const int nt = backward_threads(n, split);
-  const size_t bytes = (size_t)make_blayout(n, m, p, amax, nt, false, split).total * sizeof(float);
-  return bytes <= kBwdBudget ? bytes : 0;
-}
-
 size_t backward_smem_bytes(int n, int m, int p, int amax, bool split, int* nthreads) {
   const int nt = backward_threads(n, split);
   if (nthreads) *nthreads = nt;
-  if (split) return backward_direct_smem_bytes(n, m, p, amax, true);
-  if (n > 128 || amax + p > 128) return 0;
-  const size_t staged = (size_t)make_blayout(n, m, p, amax, nt, true).total * sizeof(float);
-  if (staged <= kBwdBudget) return staged;
-  return backward_direct_smem_bytes(n, m, p, amax, false);
+  if (split ? (n > 256 || amax + p > 318) : (n > 128 || amax + p > 128)) return 0;
+  const size_t bytes = (size_t)make_blayout(n, m, p, amax, nt, split).total * sizeof(float);
+  return bytes <= kBwdBudget ? bytes : 0;
 }
 
 // The dynamic shared-memory limit is set once per variant, to the largest
 // layout (setting it can wait for running kernels: not on the launch path).
-template <int NT, bool kStage, bool kGlobal>
+template <int NT, bool kGlobal>
 cudaError_t configure_backward_v() {
   static std::once_flag once;
   static cudaError_t set = cudaSuccess;
   std::call_once(once, [] {
-    set = cudaFuncSetAttribute(qp_backward_kernel<NT, kStage, kGlobal>,
+    set = cudaFuncSetAttribute(qp_backward_kernel<NT, kGlobal>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBwdBudget);
   });
   return set;
 }
 
-template <int NT, bool kStage, bool kGlobal>
+template <int NT, bool kGlobal>
 cudaError_t launch_backward_v(const BwdParams& P, size_t smem, cudaStream_t st) {
-  const cudaError_t set = configure_backward_v<NT, kStage, kGlobal>();
+  const cudaError_t set = configure_backward_v<NT, kGlobal>();
   if (set != cudaSuccess) return set;
-  qp_backward_kernel<NT, kStage, kGlobal><<<P.batch, NT, smem, st>>>(P);
+  qp_backward_kernel<NT, kGlobal><<<P.batch, NT, smem, st>>>(P);
   return cudaGetLastError();
 }
 
 // Load every variant's module and set its limit now (kernels load lazily).
 void preload_backward_kernels() {
-  configure_backward_v<128, true, false>();
-  configure_backward_v<128, false, false>();
-  configure_backward_v<256, true, false>();
-  configure_backward_v<256, false, false>();
-  configure_backward_v<256, false, true>();
+  configure_backward_v<128, false>();
+  configure_backward_v<256, false>();
+  configure_backward_v<256, true>();
   cudaGetLastError();
 }
 
-cudaError_t launch_backward_ragged(const BwdParams& P, int nthreads, size_t smem,
-                                   cudaStream_t st) {
-  if (P.split) return launch_backward_v<256, false, true>(P, smem, st);
-  return nthreads == 128 ? launch_backward_v<128, false, false>(P, smem, st)
-                         : launch_backward_v<256, false, false>(P, smem, st);
-}
-
 cudaError_t launch_backward(const BwdParams& P, int nthreads, size_t smem, cudaStream_t st) {
-  if (P.split) return launch_backward_v<256, false, true>(P, smem, st);
-  const bool stage =
-      (size_t)make_blayout(P.n, P.m, P.p, P.amax, nthreads, true).total * sizeof(float) == smem;
-  if (nthreads == 128)
-    return stage ? launch_backward_v<128, true, false>(P, smem, st)
-                 : launch_backward_v<128, false, false>(P, smem, st);
-  if (nthreads == 256)
-    return stage ? launch_backward_v<256, true, false>(P, smem, st)
-                 : launch_backward_v<256, false, false>(P, smem, st);
+  if (P.split) return launch_backward_v<256, true>(P, smem, st);
+  if (nthreads == 128) return launch_backward_v<128, false>(P, smem, st);
+  if (nthreads == 256) return launch_backward_v<256, false>(P, smem, st);
   return cudaErrorInvalidValue;
 }
 

@@ -113,15 +113,12 @@ cudaError_t launch_forward(const FwdParams& P, int nthreads, size_t smem, int gr
                            cudaStream_t stream);
 int forward_blocks_per_sm(int nthreads, size_t smem, bool split);
 
+// Dynamic shared memory of the backward kernel (0: size not supported) and
+// its threads per CTA.
 size_t backward_smem_bytes(int n, int m, int p, int amax, bool split, int* nthreads);
-// Shared memory of the backward kernel reading Q, G, A from global memory
-// (the variant of ragged launches; same arithmetic as the staged one).
-size_t backward_direct_smem_bytes(int n, int m, int p, int amax, bool split);
+// Uniform batch over P.batch instances, or (P.desc set) a ragged launch over
+// P.desc[0 .. P.batch) with nthreads = backward_threads of its size class.
 cudaError_t launch_backward(const BwdParams& P, int nthreads, size_t smem, cudaStream_t stream);
-// Ragged backward launch over P.desc[0 .. P.batch): Q, G, A read from global
-// memory; nthreads = backward_threads of the launch's size class.
-cudaError_t launch_backward_ragged(const BwdParams& P, int nthreads, size_t smem,
-                                   cudaStream_t stream);
 // Threads per CTA of the backward kernel for a size.
 int backward_threads(int n, bool split);
 

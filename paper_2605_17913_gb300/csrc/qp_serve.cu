@@ -68,7 +68,7 @@ bool size_cfg(int n, int m, int p, SizeCfg* c) {
   if (c->fsmem == 0) return false;
   c->split = ws > 0;
   c->ws = ws;
-  c->bsmem = backward_direct_smem_bytes(n, m, p, c->amax, c->split);
+  c->bsmem = backward_smem_bytes(n, m, p, c->amax, c->split, nullptr);
   if (c->bsmem == 0) return false;
   c->cache = cache_layout(n, m, p, c->amax, c->split).stride;
   return true;
@@ -338,8 +338,8 @@ cudaError_t qp_server::issue(Launch& L) {
     B.batch = nb;
     B.split = take[0]->cfg.split ? 1 : 0;
     B.desc = L.ddesc + R;
-    e = launch_backward_ragged(B, backward_threads(take[0]->n, take[0]->cfg.split), bsmem,
-                               L.stream);
+    e = launch_backward(B, backward_threads(take[0]->n, take[0]->cfg.split), bsmem,
+                        L.stream);
   }
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(hb + in_f, db + in_f, (size_t)out_f * sizeof(float),
