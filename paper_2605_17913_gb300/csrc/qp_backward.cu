@@ -35,8 +35,8 @@ namespace {
 
 struct BLayout {
   int ldk, ldc, ldx, ldg, nv, mv, pv, fv;
-  int oK, oY, oC, oR, oCol, o_dinv, o_cdinv, o_mu, o_dmu, o_g, o_x, o_y, o_z, o_W,
-      o_pos, o_act, o_e, o_tv, o_dz, o_qdx, o_adx, total;
+  int oK, oY, oC, oR, oPart, o_dinv, o_cdinv, o_mu, o_dmu, o_g, o_x, o_y, o_z, o_W,
+      o_pos, o_act, o_e, o_dz, o_qdx, o_adx, total;
 };
 
 // global: the large-problem variant, whose factors are read in place from the
@@ -57,11 +57,11 @@ __host__ __device__ inline BLayout make_blayout(int n, int m, int p, int amax, i
   B.oY = take(global ? 0 : f * B.ldk);
   B.oC = take(global ? 0 : f * B.ldc);
   B.oR = take(2 * B.ldx);
-  B.oCol = take(2 * nthreads);
+  B.oPart = take((nthreads / 32) * B.nv);
   B.o_dinv = take(B.nv); B.o_cdinv = take(B.fv); B.o_mu = take(B.fv); B.o_dmu = take(B.fv);
   B.o_g = take(B.nv); B.o_x = take(B.nv); B.o_y = take(B.pv); B.o_z = take(B.mv);
   B.o_W = take(B.mv); B.o_pos = take(B.mv); B.o_act = take(B.fv); B.o_e = take(B.mv);
-  B.o_tv = take(B.mv); B.o_dz = take(B.mv); B.o_qdx = take(B.nv); B.o_adx = take(B.pv);
+  B.o_dz = take(B.mv); B.o_qdx = take(B.nv); B.o_adx = take(B.pv);
   B.total = o;
   return B;
 }
@@ -118,21 +118,113 @@ __device__ void small_chol_solve(const float* C, int ldc, const float* cdinv, in
   }
 }
 
-// out[r] = M[r][:] . v for r < rows: one warp per row, lanes over columns
-// (coalesced from global memory, conflict-free from shared memory).  Ends
-// with a barrier.
-template <int NT>
-__device__ void warp_rows_dot(const float* M, int ld, int rows, int cols, const float* v,
-                              float* out) {
+// One pass over the rows of [G; Q; A] (each row of the caller's arrays, row
+// stride n) with v = dx held in registers (lane owns columns lane + 32 s):
+//   e = G dx,  qdx = Q dx,  adx = A dx,
+// and, when `accumulate`, the per-warp column sums of
+//   G' t + A' mu_y,   t_r = W_r e_r (inactive rows), mu_pos(r) (active rows),
+// written to part[w][0 .. n) (summed over warps by the caller, in warp order).
+// Each warp takes U consecutive rows at a time, so U x S loads are in flight
+// per lane; every element of G, Q, A is read once per pass.  with_qa = false:
+// G rows only (e = G dx).  Ends with a barrier.
+template <int NT, int S, int U>
+__device__ __forceinline__ void rows_pass_S(const float* G, const float* Q, const float* A, int m,
+                                            int n, int p, int a, const float* dx, const float* W,
+                                            const int* pos, const float* mu, float* e, float* qdx,
+                                            float* adx, float* part, int ldp, bool accumulate,
+                                            bool with_qa) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int r = w; r < rows; r += NT / 32) {
-    float acc = 0.f;
-    for (int j = lane; j < cols; j += 32) acc = fmaf(M[(size_t)r * ld + j], v[j], acc);
+  constexpr int nw = NT / 32;
+  float xr[S], acc[S];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-    if (lane == 0) out[r] = acc;
+  for (int s2 = 0; s2 < S; ++s2) {
+    const int c = lane + 32 * s2;
+    xr[s2] = c < n ? dx[c] : 0.f;
+    acc[s2] = 0.f;
+  }
+  const int nrows = with_qa ? m + n + p : m;
+  for (int r0 = w * U; r0 < nrows; r0 += nw * U) {
+    float v[U][S];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int r = r0 + u;
+      const float* row = r < m ? G + (size_t)r * n
+                               : (r < m + n ? Q + (size_t)(r - m) * n : A + (size_t)(r - m - n) * n);
+#pragma unroll
+      for (int s2 = 0; s2 < S; ++s2) {
+        const int c = lane + 32 * s2;
+        v[u][s2] = (r < nrows && c < n) ? __ldg(row + c) : 0.f;
+      }
+    }
+    float d[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      d[u] = 0.f;
+#pragma unroll
+      for (int s2 = 0; s2 < S; ++s2) d[u] = fmaf(v[u][s2], xr[s2], d[u]);
+    }
+    // butterfly: every lane ends with the same sum (addition commutes)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int u = 0; u < U; ++u) d[u] += __shfl_xor_sync(kFull, d[u], o);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int r = r0 + u;
+      if (r >= nrows) break;
+      float coef = 0.f;
+      if (r < m) {
+        if (lane == 0) e[r] = d[u];
+        const int k = pos[r];
+        coef = k < 0 ? W[r] * d[u] : mu[k];
+      } else if (r < m + n) {
+        if (lane == 0) qdx[r - m] = d[u];
+      } else {
+        if (lane == 0) adx[r - m - n] = d[u];
+        coef = mu[a + (r - m - n)];
+      }
+      if (accumulate) {
+#pragma unroll
+        for (int s2 = 0; s2 < S; ++s2) acc[s2] = fmaf(coef, v[u][s2], acc[s2]);
+      }
+    }
+  }
+  if (accumulate) {
+#pragma unroll
+    for (int s2 = 0; s2 < S; ++s2) {
+      const int c = lane + 32 * s2;
+      if (c < n) part[w * ldp + c] = acc[s2];
+    }
   }
   __syncthreads();
+}
+
+template <int NT, bool kGlobal>
+__device__ __forceinline__ void rows_pass(const float* G, const float* Q, const float* A, int m,
+                                          int n, int p, int a, const float* dx, const float* W,
+                                          const int* pos, const float* mu, float* e, float* qdx,
+                                          float* adx, float* part, int ldp, bool accumulate,
+                                          bool with_qa) {
+  if (n <= 32)
+    rows_pass_S<NT, 1, 4>(G, Q, A, m, n, p, a, dx, W, pos, mu, e, qdx, adx, part, ldp, accumulate,
+                          with_qa);
+  else if (n <= 64)
+    rows_pass_S<NT, 2, 4>(G, Q, A, m, n, p, a, dx, W, pos, mu, e, qdx, adx, part, ldp, accumulate,
+                          with_qa);
+  else if (n <= 96)
+    rows_pass_S<NT, 3, 4>(G, Q, A, m, n, p, a, dx, W, pos, mu, e, qdx, adx, part, ldp, accumulate,
+                          with_qa);
+  else if (!kGlobal || n <= 128)
+    rows_pass_S<NT, 4, 4>(G, Q, A, m, n, p, a, dx, W, pos, mu, e, qdx, adx, part, ldp, accumulate,
+                          with_qa);
+  else if constexpr (kGlobal) {
+    if (n <= 192)
+      rows_pass_S<NT, 6, 2>(G, Q, A, m, n, p, a, dx, W, pos, mu, e, qdx, adx, part, ldp,
+                            accumulate, with_qa);
+    else
+      rows_pass_S<NT, 8, 2>(G, Q, A, m, n, p, a, dx, W, pos, mu, e, qdx, adx, part, ldp,
+                            accumulate, with_qa);
+  }
 }
 
 // Solve [K_I F'; F -D] (d, t) = (r1, r2) with the cached factors: r1 in R
@@ -191,7 +283,7 @@ __device__ __forceinline__ void backward_body(const BwdParams& P, int bi) {
   const int ldk = kGlobal ? cl.ldk : B.ldk;
   const int ldc = kGlobal ? cl.ldc : B.ldc;
   float* R = sm + B.oR;
-  float* col = sm + B.oCol;
+  float* part = sm + B.oPart;  // per-warp column sums of the row pass
   float* dinv = sm + B.o_dinv;
   float* cdinv = sm + B.o_cdinv;
   float* mu = sm + B.o_mu;
@@ -204,7 +296,6 @@ __device__ __forceinline__ void backward_body(const BwdParams& P, int bi) {
   int* pos = reinterpret_cast<int*>(sm + B.o_pos);
   int* act = reinterpret_cast<int*>(sm + B.o_act);
   float* e = sm + B.o_e;
-  float* tv = sm + B.o_tv;
   float* dz = sm + B.o_dz;
   float* qdx = sm + B.o_qdx;  // Q dx (n)
   float* adx = sm + B.o_adx;  // A dx (p)
@@ -222,7 +313,6 @@ __device__ __forceinline__ void backward_body(const BwdParams& P, int bi) {
   const float* const Qm = P.Q + (size_t)bi * n * n;
   const float* const Gm = P.G + (size_t)bi * m * n;
   const float* const Am = P.A + (size_t)bi * p * n;
-  const int ldm = n;
   const int nfl = valid ? nf : 0;
   if (kGlobal) {
     // factors stay in the cache: only the reciprocal pivots go to shared memory
@@ -279,22 +369,19 @@ __device__ __forceinline__ void backward_body(const BwdParams& P, int bi) {
   float* dx = R + B.ldx;  // accumulated solution; R row 0 is the work row
   for (int i = t; i < n; i += NT) dx[i] = R[i];
   __syncthreads();
-  for (int it = 0; it < refine; ++it) {
-    // e = G dx;  tv = W_I e_I on inactive rows, lambda on active rows
-    warp_rows_dot<NT>(Gm, ldm, m, n, dx, e);
-    for (int r = t; r < m; r += NT) tv[r] = pos[r] < 0 ? Ws[r] * e[r] : mu[pos[r]];
-    __syncthreads();
-    {
-      const float* vv[1] = {tv};
-      float* oo[1] = {R};
-      col_dot<NT, 1>(Gm, ldm, m, n, vv, oo, col);  // R = G' tv
-    }
-    warp_rows_dot<NT>(Qm, ldm, n, n, dx, qdx);
-    warp_rows_dot<NT>(Am, ldm, p, n, dx, adx);
+  // Sweep it < refine: one row pass gives e = G dx, Q dx, A dx and the column
+  // sums of G' t + A' mu_y; r1 = -g - (K_I dx + F' mu) = -g - (Q dx + G' t +
+  // A' mu_y), r2 = -(F dx - D mu).  The last pass (it == refine) only forms
+  // e = G dx for dz.
+  for (int it = 0;; ++it) {
+    const bool last = it == refine;
+    rows_pass<NT, kGlobal>(Gm, Qm, Am, m, n, p, a, dx, Ws, pos, mu, e, qdx, adx, part, B.nv, !last,
+                           !last);
+    if (last) break;
     for (int i = t; i < n; i += NT) {
-      float acc = qdx[i] + R[i];
-      for (int k = 0; k < p; ++k) acc = fmaf(Am[(size_t)k * ldm + i], mu[a + k], acc);
-      R[i] = -gv[i] - acc;  // r1 = -g - (K_I dx + F' mu)
+      float acc = qdx[i];
+      for (int w2 = 0; w2 < NT / 32; ++w2) acc += part[w2 * B.nv + i];
+      R[i] = -gv[i] - acc;
     }
     for (int k = t; k < nf; k += NT) {
       if (k < a) {
@@ -312,7 +399,6 @@ __device__ __forceinline__ void backward_body(const BwdParams& P, int bi) {
   }
   const float* dy = mu + a;
   // ---- dz: active rows from the multipliers, inactive rows W (G dx) ----
-  warp_rows_dot<NT>(Gm, ldm, m, n, dx, e);
   for (int r = t; r < m; r += NT) {
     const int k = pos[r];
     dz[r] = k >= 0 ? mu[k] : Ws[r] * e[r];
