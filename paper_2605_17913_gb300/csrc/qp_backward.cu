@@ -21,9 +21,10 @@
 // One CTA per instance: the factors are staged in shared memory once (the
 // large variant reads them in place); Q, G, A are read where the caller keeps
 // them, through L1 / L2, so that the small shared-memory layout lets five
-// CTAs share an SM (staging Q, G, A too gave three per SM at n = 50 and took
-// 1.6x as long); the gradient blocks go out as coalesced 16-byte streaming
-// stores.
+// CTAs share an SM at n = 50 (copying Q, G, A as well left room for three).
+// Each refinement residual takes one pass over the rows of [G; Q; A] with
+// several rows' loads in flight per warp; the gradient blocks go out as
+// coalesced 16-byte streaming stores.
 #include <mutex>
 
 #include "qp_device.cuh"
