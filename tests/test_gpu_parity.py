@@ -168,7 +168,7 @@ def test_diff_workload_parity():
 
 
 @pytest.mark.parametrize("n,m,p", [(37, 53, 3), (1, 3, 0), (5, 0, 2), (7, 12, 0), (64, 128, 6),
-                                   (3, 1, 1)])
+                                   (3, 1, 1), (80, 150, 8)])
 def test_ragged_and_edge_sizes(n, m, p):
     batch = make_batch("small", 9, seed=5, n=n, m=m, p=p)
     res = gpu_run(batch, grad=True)
