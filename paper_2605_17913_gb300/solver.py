@@ -203,9 +203,8 @@ class QPFunction(torch.autograd.Function):
         Q, A, G = ctx.saved_tensors
         g = ctx.solver.backward(ctx.cache, Q.contiguous(), A.contiguous(), G.contiguous(),
                                 gx.contiguous())
-        p, m = ctx.solver.n_eq, ctx.solver.n_ineq
-        return (g["dQ"], g["dq"], g["dA"] if p else g["dA"], g["db"], g["dG"] if m else g["dG"],
-                g["dh"], None)
+        # with no equalities (inequalities) dA, db (dG, dh) are empty, like A, b (G, h)
+        return g["dQ"], g["dq"], g["dA"], g["db"], g["dG"], g["dh"], None
 
 
 def qp_layer(Q, q, A, b, G, h, **settings):
