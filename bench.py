@@ -36,7 +36,7 @@ L2_BYTES = 129 * 1024 * 1024
 FORWARD_TRAFFIC_BYTES = 4 * 33063168
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
@@ -70,7 +70,7 @@ def parse():
     ap.add_argument("--chord", action="store_true",
                     help="Alg. 2 with chord steps vs refactoring: time, iterations, "
                          "gradient error against FP64")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 # ---------------------------------------------------------------- algorithmic work

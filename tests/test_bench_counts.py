@@ -38,3 +38,23 @@ def test_backward_bytes_per_instance():
 
 def test_fp32_peak():
     assert abs(bench.fp32_alu_peak_tflops() - 152 * 128 * 2 * 2.07e-3) < 1e-9
+
+
+def test_profile_commands_are_valid_bench_invocations():
+    """Every `python bench.py ...` command quoted in profiles/ parses with the
+    bench's own argument parser (the summaries must name commands that run)."""
+    import glob
+    import os
+    import re
+    import shlex
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    files = sorted(glob.glob(os.path.join(root, "profiles", "*.md")))
+    assert files
+    found = 0
+    for path in files:
+        text = open(path).read().replace("\\\n", " ")
+        for cmd in re.findall(r"python bench\.py([^\n`]*)", text):
+            bench.parse(shlex.split(cmd))
+            found += 1
+    assert found >= len(files)
