@@ -117,3 +117,27 @@ def test_gpu_equality_closed_form(idx):
         assert np.abs(res["x"][i] - c["x"]).max() / max(1.0, np.abs(c["x"]).max()) <= X_TOL
         for k in ("dq", "dA", "db"):
             assert _rel(res[k][i], c[k]) <= GRAD_TOL, (k, i, _rel(res[k][i], c[k]))
+
+
+def test_fixtures_reject_planted_mistakes():
+    """The fixtures are sharp enough to catch the plausible slips in Alg. 3:
+    each variant below, built from the fixture's own dx = dq, dz = -dh and the
+    relaxed point, misses the stored gradient by far more than the FP32 bar."""
+    c = _cases("central_path_separable.json")[0]
+    x, z = np.array(c["x_relaxed"]), np.array(c["z_relaxed"])
+    dx, dz = np.array(c["dq"]), -np.array(c["dh"])
+    dG, dQ = np.array(c["dG"]), np.array(c["dQ"])
+    # the correct formulas reproduce the fixture (so the variants differ only by the slip)
+    assert _rel(np.outer(dz, x) + np.outer(z, dx), dG) < 1e-12
+    assert _rel(0.5 * (np.outer(dx, x) + np.outer(x, dx)), dQ) < 1e-12
+    planted = {
+        "dG without z dx'": np.outer(dz, x),
+        "dG without dz x'": np.outer(z, dx),
+        "dG transposed": (np.outer(dz, x) + np.outer(z, dx)).T,
+        "dG with dz sign flipped": np.outer(-dz, x) + np.outer(z, dx),
+        "dQ unsymmetrised": np.outer(dx, x),
+        "dQ doubled": np.outer(dx, x) + np.outer(x, dx),
+    }
+    for name, wrong in planted.items():
+        ref = dQ if name.startswith("dQ") else dG
+        assert _rel(wrong, ref) > 50 * GRAD_TOL, name
