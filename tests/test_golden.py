@@ -65,6 +65,17 @@ def test_oracle_central_path_closed_form(idx):
 
 
 @pytest.mark.parametrize("idx", [0, 1])
+def test_oracle_standard_formulation_reaches_the_same_optimum(idx):
+    """The explicit-complementarity ablation (eq. 6 / eq. 8) solves the same
+    problem: x* = min(-q, u) coordinate-wise."""
+    c = _cases("central_path_separable.json")[idx]
+    Q, q, A, b, G, h, g = _arrays(c)
+    r = O.solve(Q, q, A, b, G, h, tol=1e-12, formulation="standard")
+    assert r["status"] == O.SOLVED
+    np.testing.assert_allclose(r["x"], c["x_optimum"], atol=1e-10)
+
+
+@pytest.mark.parametrize("idx", [0, 1])
 def test_oracle_equality_closed_form(idx):
     c = _cases("equality_projection.json")[idx]
     Q, q, A, b, G, h, g = _arrays(c)
