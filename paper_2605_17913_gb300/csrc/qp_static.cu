@@ -12,8 +12,6 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include <mutex>
-
 #include "qp.h"
 #include "qp_internal.h"
 
@@ -28,32 +26,19 @@ static __device__ __align__(256) float g_static_cache[QP_STATIC_CACHE_BYTES / si
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;
-float* g_static_ptr[kMaxDevices];  // device address of g_static_cache per device
-
-// Set-up, once per device, with that device current: look up the array's
-// device address.  The first lookup on a device can load this library's
-// device code into the context, which is when the array's memory is
-// reserved; later calls only read the stored pointer.
+// The array's device address on the current device.  Looked up on every call
+// (cheap once this library's device code is loaded in the context): a cached
+// address could go stale when the context is destroyed and recreated
+// (cudaDeviceReset), which reloads the module, possibly elsewhere.  The first
+// lookup in a context loads the device code, which reserves the array.
 int static_cache_on_current_device(float** out) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess) {
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_static_cache);
+  if (e != cudaSuccess || !p) {
     cudaGetLastError();
     return QP_ECUDA;
   }
-  if (dev < 0 || dev >= kMaxDevices) return QP_ENOTSUP;
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_static_ptr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_cache);
-    if (e != cudaSuccess || !p) {
-      cudaGetLastError();
-      return QP_ECUDA;
-    }
-    g_static_ptr[dev] = static_cast<float*>(p);
-  }
-  *out = g_static_ptr[dev];
+  *out = static_cast<float*>(p);
   return QP_OK;
 }
 
