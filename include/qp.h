@@ -72,7 +72,14 @@ extern "C" {
 
 /* ---- options --------------------------------------------------------------- */
 #define QP_IMPLICIT 0     /* the paper's implicit complementarity (eq. 9-14)   */
-#define QP_STANDARD 1     /* explicit z .* s = kappa, Mehrotra (eq. 6, 8)      */
+#define QP_STANDARD 1     /* explicit z .* s = kappa, Mehrotra (eq. 6, 8), through
+                             the bounded two-level factorisation of QP_IMPLICIT   */
+#define QP_STANDARD_SCHUR 2 /* explicit z .* s = kappa, Mehrotra, with eq. 8's
+                             partially condensed matrix Q + G' diag(z ./ s) G
+                             Cholesky-factored in FP32 as it stands (equality rows
+                             by their Schur complement A K^-1 A', no shift, no
+                             retry): the standard method the paper compares with;
+                             a failed pivot ends the instance as QP_NUMERICAL   */
 #define QP_SIGMA_MEHROTRA 0 /* sigma = (mu_aff / kappa)^3 clipped to [0, 1]    */
 #define QP_SIGMA_CONSTANT 1 /* sigma = settings.sigma                          */
 #define QP_NORM_SCALED 0  /* scaled infinity-norm residual measure             */
@@ -80,6 +87,28 @@ extern "C" {
 #define QP_GWG_FP32 0     /* K = Q + G'WG formed in FP32                       */
 #define QP_GWG_TF32 1     /* G'WG on tensor cores, TF32 inputs, FP32 accumulate */
 #define QP_GWG_BF16 2     /* G'WG on tensor cores, BF16 inputs, FP32 accumulate */
+
+/* ---- per-instance diagnostics (qp_handle_set_diag) ------------------------ */
+/* bits 0-7: the first stage of the iteration at which a non-finite value (or a
+ * failed Cholesky pivot) appeared, in the order of the paper's NaN trace of
+ * the standard method (App. D, Table 1); 0 if none. */
+#define QP_STAGE_MASK 0xff
+#define QP_STAGE_NONE 0
+#define QP_STAGE_SCALING 1    /* the Newton matrix's diagonal W = z ./ s (or B_+/B_-) */
+#define QP_STAGE_PREDICTOR 2  /* the affine (predictor) solve, its factorisation included */
+#define QP_STAGE_CENTERING 3  /* alpha_aff, mu_aff, sigma                              */
+#define QP_STAGE_CORRECTOR 4  /* the corrector direction (dx, ds, dz, dy)              */
+#define QP_STAGE_LINESEARCH 5 /* the step length alpha and the updated iterate         */
+#define QP_STAGE_RELAX 6      /* anywhere in Alg. 2 or the factorisation cached for Alg. 3 */
+#define QP_STAGE_BACKWARD 7   /* the adjoint solve of Alg. 3 (qp_backward_batch)       */
+#define QP_STAGE_INIT 8       /* the starting point                                    */
+#define QP_DIAG_FACTOR_FAILED 0x100  /* a Cholesky pivot was not positive              */
+#define QP_DIAG_TC_FALLBACK 0x200    /* tensor-core G'WG ran out of a bounded wait and
+                                        the solve continued with FP32 products          */
+#define QP_DIAG_STAGE_FALLBACK 0x400 /* bulk-copy staging of G'WG ran out of a bounded
+                                        wait; the products were redone from global memory */
+#define QP_DIAG_ASYNC_LOST 0x800     /* copies may have been in flight after a bounded
+                                        wait: the instance is reported QP_NUMERICAL     */
 
 typedef struct {
   int32_t batch;  /* number of independent QPs (>= 0)        */
@@ -100,7 +129,7 @@ typedef struct {
                            below tol that has stopped decreasing for 3 iterations
                            (the FP32 floor) also ends the relax                     */
   int32_t relax_max_iter; /* Alg. 2 iteration cap (0: max_iter)                     */
-  int32_t formulation;  /* QP_IMPLICIT or QP_STANDARD                               */
+  int32_t formulation;  /* QP_IMPLICIT, QP_STANDARD or QP_STANDARD_SCHUR             */
   int32_t residual_norm; /* QP_NORM_*                                               */
   int32_t gwg_precision; /* QP_GWG_*: TF32 / BF16 put the G'WG products on the tensor
                             cores (FP32 sums) in the large-problem variant; sizes that
@@ -114,6 +143,12 @@ typedef struct {
                             steps; Alg. 2's "if not cached"); its polishing step and
                             the factor cached for Alg. 3 are fresh.  0: refactor at
                             every relax iterate (default)                            */
+  int32_t refine_forward; /* iterative-refinement sweeps of each Newton solve of Alg. 1
+                            and Alg. 2 in the large-problem variant: the residual of
+                            the bounded eq. 14 system is formed in FP32 from Q, G, A
+                            (no tensor-core products) and corrected with the same
+                            factors -- recovers the accuracy of TF32 / BF16 G'WG
+                            (default 0; sizes that run on chip ignore it)             */
 } qp_settings;
 
 typedef struct qp_handle qp_handle;
@@ -121,7 +156,8 @@ typedef struct qp_handle qp_handle;
 /* Fill `s` with the defaults: tol 1e-5, max_iter 100, Mehrotra sigma,
  * sigma 0.1, kappa_min 0 (-> 1e-2 tol), kappa_relax 1e-4, relax_tol 0
  * (-> tol / 10), relax_max_iter 0, implicit, scaled norm, FP32 G'WG, 3
- * refinement sweeps, cold start, relax refactors every iterate.  (Defaults follow the paper's ablation settings where it states
+ * refinement sweeps of the adjoint solve, cold start, relax refactors every
+ * iterate, no refinement of the forward Newton solves.  (Defaults follow the paper's ablation settings where it states
  * them: max_iter 100, kappa_relax 1e-4.) */
 void qp_settings_default(qp_settings* s);
 
@@ -158,6 +194,19 @@ typedef struct {
 
 /* Fill `out`.  Returns QP_EINVAL for a null argument. */
 int qp_handle_query(const qp_handle* h, qp_handle_info* out);
+
+/* Register a caller-owned DEVICE array diag[batch] (int32, 4-byte aligned)
+ * that later qp_solve_batch / qp_backward_batch calls through this handle
+ * fill with one diagnostics word per instance (QP_STAGE_* in bits 0-7, the
+ * first stage with a non-finite value; QP_DIAG_* flags above them).  The
+ * solve writes every word; the backward pass adds QP_STAGE_BACKWARD to words
+ * whose stage is still QP_STAGE_NONE when its adjoint solution is not finite
+ * or the instance's cache slot cannot be used (NaN gradients).
+ * With an array registered the solve also tests each stage's values for
+ * finiteness (a few block reductions per iteration); NULL (the default)
+ * turns both off.  Returns QP_EINVAL for a null handle or a misaligned
+ * pointer. */
+int qp_handle_set_diag(qp_handle* h, int32_t* diag);
 
 /* Solve + relax + backward of a batch held in HOST memory: the library copies
  * the data in, runs the kernels and copies the results out, in chunks of
@@ -244,9 +293,11 @@ int qp_backward_batch(qp_handle* h, const float* grad_cache, const float* Q, con
  * Limit: returns QP_ENOTSUP, with nothing enqueued, when
  * qp_grad_cache_bytes(dims) > QP_STATIC_CACHE_BYTES.  Other argument errors
  * return QP_EINVAL before anything that touches caller memory is enqueued.
- * The first call on each device does set-up (it looks up the array's device
- * address, which can load the library's device code into the context): make
- * it before any stream capture is begun.
+ * Every call looks up the array's device address in the current context (so
+ * a context that was destroyed and recreated gets the new address); the
+ * first call in a context can load the library's device code there, which
+ * is when the array is reserved: make that first call before any stream
+ * capture is begun.
  * Sharing: every call on a device uses the same array, so calls whose device
  * work can overlap (different streams, unsynchronised host threads) race on
  * it and give undefined results; calls ordered on one stream are safe. */

@@ -20,11 +20,17 @@ QP_EINVAL, QP_ENOMEM, QP_ECUDA, QP_EAGAIN, QP_ETIMEOUT, QP_ENOTSUP, QP_ESTATE = 
     -1, -2, -3, -4, -5, -6, -7)
 # per-instance status
 QP_SOLVED, QP_MAX_ITER, QP_STALLED, QP_NUMERICAL, QP_BAD_INPUT = 0, 1, 2, 3, 4
-QP_IMPLICIT, QP_STANDARD = 0, 1
+QP_IMPLICIT, QP_STANDARD, QP_STANDARD_SCHUR = 0, 1, 2
 QP_SIGMA_MEHROTRA, QP_SIGMA_CONSTANT = 0, 1
 QP_NORM_SCALED, QP_NORM_ABS = 0, 1
 QP_GWG_FP32, QP_GWG_TF32, QP_GWG_BF16 = 0, 1, 2
 QP_STATIC_CACHE_BYTES = 16 * 1024 * 1024
+# per-instance diagnostics word (qp_handle_set_diag)
+QP_STAGE_MASK = 0xFF
+QP_STAGE_NAMES = {0: "none", 1: "scaling", 2: "predictor", 3: "centering", 4: "corrector",
+                  5: "line search", 6: "relax", 7: "backward", 8: "init"}
+QP_DIAG_FACTOR_FAILED, QP_DIAG_TC_FALLBACK, QP_DIAG_STAGE_FALLBACK, QP_DIAG_ASYNC_LOST = (
+    0x100, 0x200, 0x400, 0x800)
 
 
 class QPError(RuntimeError):
@@ -58,6 +64,7 @@ class Settings(ctypes.Structure):
         ("refine_steps", ctypes.c_int32),
         ("warm_start", ctypes.c_int32),
         ("relax_chord", ctypes.c_int32),
+        ("refine_forward", ctypes.c_int32),
     ]
 
 
@@ -109,6 +116,8 @@ def lib() -> ctypes.CDLL:
     L.qp_workspace_bytes.argtypes = [ctypes.POINTER(Dims)]
     L.qp_handle_destroy.restype = ctypes.c_int
     L.qp_handle_destroy.argtypes = [vp]
+    L.qp_handle_set_diag.restype = ctypes.c_int
+    L.qp_handle_set_diag.argtypes = [vp, vp]
     L.qp_handle_query.restype = ctypes.c_int
     L.qp_handle_query.argtypes = [vp, ctypes.POINTER(HandleInfo)]
     L.qp_solve_batch.restype = ctypes.c_int
@@ -133,6 +142,8 @@ def lib() -> ctypes.CDLL:
     L.qp_serve_destroy.argtypes = [vp]
     L.qp_solve_backward_static.restype = ctypes.c_int
     L.qp_solve_backward_static.argtypes = [vp, ctypes.POINTER(Settings)] + [vp] * 21
+    L.qp_fma_probe.restype = ctypes.c_int
+    L.qp_fma_probe.argtypes = [i32, i32, i32, vp, vp]
     L.qp_solve_backward_host.restype = ctypes.c_int
     L.qp_solve_backward_host.argtypes = [vp, ctypes.POINTER(Settings)] + [vp] * 20
     _lib = L
@@ -153,7 +164,8 @@ def default_settings(**overrides) -> Settings:
     lib().qp_settings_default(ctypes.byref(s))
     for k, v in overrides.items():
         if k == "formulation" and isinstance(v, str):
-            v = {"implicit": QP_IMPLICIT, "standard": QP_STANDARD}[v]
+            v = {"implicit": QP_IMPLICIT, "standard": QP_STANDARD,
+                 "standard_schur": QP_STANDARD_SCHUR}[v]
         if k == "residual_norm" and isinstance(v, str):
             v = {"scaled": QP_NORM_SCALED, "abs": QP_NORM_ABS}[v]
         if k == "sigma_mode" and isinstance(v, str):

@@ -16,6 +16,8 @@ struct qp_handle {
   int num_sms;
   int fwd_threads, fwd_blocks_per_sm;
   size_t fwd_smem;
+  size_t fwd_smem_tc;       // large variant: shared memory of the 512-thread kernel that the
+                            // tensor-core G'WG runs in (one TMEM allocation per SM)
   int bwd_threads;
   size_t bwd_smem;
   int amax;
@@ -29,6 +31,7 @@ struct qp_handle {
   float* hbuf;
   size_t hbuf_bytes;
   int hchunk;
+  int32_t* diag;  // per-instance diagnostics words (caller's device memory) or nullptr
 };
 
 static bool aligned4(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 3) == 0; }
@@ -45,10 +48,11 @@ namespace qpgpu {
 qp_dims handle_dims(const qp_handle* h) { return h->dims; }
 
 int settings_to_params(const qp_settings* st, FwdParams* P) {
-  if (!(st->tol > 0.0f) || st->max_iter < 0 || st->formulation < 0 || st->formulation > 1 ||
+  if (!(st->tol > 0.0f) || st->max_iter < 0 || st->formulation < 0 || st->formulation > 2 ||
       st->sigma_mode < 0 || st->sigma_mode > 1 || !(st->kappa_relax >= 0.0f) ||
       st->residual_norm < 0 || st->residual_norm > 1 || st->refine_steps < 0 ||
-      st->relax_chord < 0 || st->relax_chord > 1)
+      st->relax_chord < 0 || st->relax_chord > 1 || st->refine_forward < 0 ||
+      st->refine_forward > 16)
     return QP_EINVAL;
   if (st->gwg_precision < QP_GWG_FP32 || st->gwg_precision > QP_GWG_BF16) return QP_EINVAL;
   if (st->sigma_mode == QP_SIGMA_CONSTANT && !(st->sigma >= 0.0f && st->sigma <= 1.0f))
@@ -68,6 +72,7 @@ int settings_to_params(const qp_settings* st, FwdParams* P) {
   P->refine_steps = st->refine_steps;
   P->gwg = st->gwg_precision;
   P->chord = st->relax_chord;
+  P->refine_fwd = st->refine_forward;
   return QP_OK;
 }
 }  // namespace qpgpu
@@ -97,6 +102,7 @@ void qp_settings_default(qp_settings* s) {
   s->refine_steps = 3;
   s->warm_start = 0;
   s->relax_chord = 0;
+  s->refine_forward = 0;
 }
 
 const char* qp_status_string(int code) {
@@ -136,19 +142,23 @@ int qp_handle_create(const qp_dims* dims, qp_handle** out) {
 int qp_handle_create_threads(const qp_dims* dims, int32_t threads_per_qp, qp_handle** out) {
   if (!out || !dims_ok(dims)) return QP_EINVAL;
   *out = nullptr;
-  if (threads_per_qp != 0 && threads_per_qp != 32 && threads_per_qp != 128) return QP_ENOTSUP;
+  if (threads_per_qp != 0 && threads_per_qp != 32 && threads_per_qp != 128 &&
+      threads_per_qp != 256 && threads_per_qp != 512)
+    return QP_ENOTSUP;
   qp_handle* h = (qp_handle*)calloc(1, sizeof(qp_handle));
   if (!h) return QP_ENOMEM;
   h->dims = *dims;
   const int n = dims->n, m = dims->n_ineq, p = dims->n_eq;
   const bool warp = threads_per_qp == 32 ||
                     (threads_per_qp == 0 && dims->batch >= kWarpPerQpMinBatch);
-  h->fwd_smem = forward_config(n, m, p, &h->fwd_threads, &h->amax, &h->ws_stride, warp);
+  h->fwd_smem = forward_config(n, m, p, &h->fwd_threads, &h->amax, &h->ws_stride, warp,
+                               threads_per_qp == 256 ? 256 : 512);
   if (threads_per_qp != 0 && h->fwd_threads != threads_per_qp) {
     free(h);
     return QP_ENOTSUP;
   }
   h->split = h->ws_stride > 0;
+  h->fwd_smem_tc = h->split ? forward_config(n, m, p, nullptr, nullptr, nullptr, false, 512) : 0;
   h->bwd_smem = backward_smem_bytes(n, m, p, h->amax, h->split, &h->bwd_threads);
   h->cache_stride = cache_layout(n, m, p, h->amax, h->split).stride;
   if (h->fwd_smem == 0 || h->bwd_smem == 0) {
@@ -188,6 +198,12 @@ int qp_handle_query(const qp_handle* h, qp_handle_info* out) {
   out->max_active = h->amax;
   out->large_variant = h->split ? 1 : 0;
   out->fwd_smem_bytes = h->fwd_smem;
+  return QP_OK;
+}
+
+int qp_handle_set_diag(qp_handle* h, int32_t* diag) {
+  if (!h || (diag && !aligned4(diag))) return QP_EINVAL;
+  h->diag = diag;
   return QP_OK;
 }
 
@@ -269,12 +285,18 @@ int solve_impl(qp_handle* h, const qp_settings* st, int B, float* ws, const floa
   P.cache_stride = h->cache_stride;
   P.ws = ws;
   P.ws_stride = h->ws_stride;
+  // the handle's diagnostics array covers its uniform batch (not the host
+  // path's chunks, which pass their own arrays)
+  P.diag = (B == h->dims.batch && ws == h->ws) ? h->diag : nullptr;
 #ifdef QP_PHASE_TIMERS
   P.timers = g_phase_counters;
 #endif
   // one CTA per instance: the block scheduler hands a new instance to an SM
   // as soon as one finishes, which balances uneven iteration counts
-  cudaError_t e = launch_forward(P, h->fwd_threads, h->fwd_smem, B, stream);
+  // the tensor-core G'WG runs in the 512-thread large variant
+  const bool tc512 = h->split && P.gwg != QP_GWG_FP32;
+  cudaError_t e = launch_forward(P, tc512 ? 512 : h->fwd_threads,
+                                 tc512 ? h->fwd_smem_tc : h->fwd_smem, B, stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return QP_ECUDA;
@@ -299,6 +321,7 @@ int backward_impl(qp_handle* h, int B, const float* grad_cache, const float* Q, 
   P.Q = Q; P.A = A; P.G = G; P.g = dl_dx; P.cache = grad_cache; P.cache_stride = h->cache_stride;
   P.dQ = dQ; P.dq = dq; P.dA = p > 0 ? dA : nullptr; P.db = p > 0 ? db : nullptr;
   P.dG = m > 0 ? dG : nullptr; P.dh = m > 0 ? dh : nullptr;
+  P.diag = B == h->dims.batch ? h->diag : nullptr;
   cudaError_t e = launch_backward(P, h->bwd_threads, h->bwd_smem, stream);
   if (e != cudaSuccess) {
     cudaGetLastError();

@@ -356,6 +356,12 @@ __device__ __forceinline__ void backward_body(const BwdParams& P, int bi) {
     if (k >= 0) act[k] = r;
   }
   if (__syncthreads_or(bad)) {
+    // a cache slot this call cannot use (never written, or overwritten):
+    // NaN gradients, recorded as the backward stage's
+    if (P.diag && t == 0) {
+      int32_t* dw = P.diag + bi;
+      if ((*dw & QP_STAGE_MASK) == QP_STAGE_NONE) *dw |= QP_STAGE_BACKWARD;
+    }
     const float nanv = NAN;
     if (P.dQ) for (int i = t; i < n * n; i += NT) P.dQ[(size_t)bi * n * n + i] = nanv;
     if (P.dq) for (int i = t; i < n; i += NT) P.dq[(size_t)bi * n + i] = nanv;
@@ -405,6 +411,18 @@ __device__ __forceinline__ void backward_body(const BwdParams& P, int bi) {
     dz[r] = k >= 0 ? mu[k] : Ws[r] * e[r];
   }
   __syncthreads();
+  if (P.diag) {
+    // diagnostics: a non-finite adjoint solution is the backward stage's,
+    // unless the solve already recorded an earlier stage
+    bool bad = false;
+    for (int i = t; i < n; i += NT) bad |= !isfinite(dx[i]);
+    for (int k = t; k < p; k += NT) bad |= !isfinite(dy[k]);
+    for (int r = t; r < m; r += NT) bad |= !isfinite(dz[r]);
+    if (__syncthreads_or(bad ? 1 : 0) && t == 0) {
+      int32_t* dw = P.diag + bi;
+      if ((*dw & QP_STAGE_MASK) == QP_STAGE_NONE) *dw |= QP_STAGE_BACKWARD;
+    }
+  }
   // ---- gradient blocks (Alg. 3) ----
   if (P.dQ)
     write_block<NT>(P.dQ + (size_t)bi * n * n, n, n, [&](int i, int j) {

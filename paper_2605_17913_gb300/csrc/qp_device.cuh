@@ -216,16 +216,24 @@ __device__ void syrk_gwg(float* K, int ldk, const float* qd, const float* G, int
     }
     for (int phase = 0; phase < ns; ++phase) {
       if (active && sp == phase) {
+        // every base value is read before the first store (a store to K may
+        // alias a later load from K, which would serialise the round trips)
+        float base[4][4];
 #pragma unroll
         for (int ii = 0; ii < 4; ++ii)
 #pragma unroll
           for (int jj = 0; jj < 4; ++jj) {
             const int i = 4 * I + ii, j = 4 * J + jj;
-            if (i < n && j <= i) {
-              float* dst = K + i * ldk + j;
-              const float base = phase != 0 ? *dst : (j == i ? qd[i] : K[j * ldk + i]);
-              *dst = base + acc[ii][jj];
-            }
+            base[ii][jj] = (i < n && j <= i)
+                               ? (phase != 0 ? K[i * ldk + j] : (j == i ? qd[i] : K[j * ldk + i]))
+                               : 0.f;
+          }
+#pragma unroll
+        for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) {
+            const int i = 4 * I + ii, j = 4 * J + jj;
+            if (i < n && j <= i) K[i * ldk + j] = base[ii][jj] + acc[ii][jj];
           }
       }
       __syncthreads();
@@ -429,10 +437,13 @@ __device__ void panel_syrk(const float* Pb, float* A, int lda, int rowA0, int nA
 // values each) padded to 4 PW + 4 floats (conflict-free float4 loads across
 // row groups); fb is a PW x PW scratch for the diagonal block's factor.  Per
 // panel: warp 0 factors the diagonal block with shuffles (lane i holds row
-// i), barrier, every row below (and every border row) is solved against it
-// by one thread, barrier, rank-PW trailing update, barrier -- three barriers
-// per PW columns, and the block factor computed once instead of by every
-// thread.
+// i) while, with PW = 32 (the large variant, matrices in global memory), the
+// other warps copy the panel's rows into Pbw one row per warp (coalesced);
+// barrier; every row below (and every border row) is solved against the
+// block by one thread, in shared memory; barrier; the solved rows go back to
+// global memory one row per warp, and the rank-PW trailing update follows
+// (barrier) -- three barriers per PW columns, the block factor computed once
+// instead of by every thread.
 // ---------------------------------------------------------------------------
 __host__ __device__ constexpr int pbw_group(int pw) { return 4 * pw + 4; }
 __host__ __device__ inline int pbw_floats(int rows, int pw) {
@@ -447,9 +458,10 @@ template <int NT, int PW>
 __device__ bool panel_factor_wide(float* M, int ld, int j0, int jb, float* dinv, float* A,
                                   int lda, int rowA0, int nA, float* B, int ldb, int nB,
                                   float* Pb, float* fb) {
+  static_assert(PW != 32 || NT >= 64, "the staged panel needs warps beside warp 0");
   const int nA4 = (nA + 3) & ~3;
   const int N = nA + nB;
-  const int tid = threadIdx.x, lane = tid & 31;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   int okw = 1;
   if (tid < 32) {
     float a[PW];
@@ -485,14 +497,32 @@ __device__ bool panel_factor_wide(float* M, int ld, int j0, int jb, float* dinv,
       }
       dinv[j0 + lane] = rinv;
     }
+  } else if (PW == 32) {
+    // meanwhile the other warps stage the panel's rows in Pb, one row per
+    // warp and lane = column: coalesced 128-byte reads of global memory
+    // (one row per thread would touch 32 rows per warp load)
+    for (int rr = w - 1; rr < N; rr += NT / 32 - 1) {
+      const bool inA = rr < nA;
+      const float* row = inA ? A + (rowA0 + rr) * lda + j0 : B + (rr - nA) * ldb + j0;
+      Pb[pbw_off<PW>(inA ? rr : nA4 + (rr - nA)) + lane] = lane < jb ? row[lane] : 0.0f;
+    }
   }
   const bool all_ok = __syncthreads_and(okw) != 0;
   for (int rr = tid; rr < N; rr += NT) {
     const bool inA = rr < nA;
     float* row = inA ? A + (rowA0 + rr) * lda + j0 : B + (rr - nA) * ldb + j0;
+    float4* pr = reinterpret_cast<float4*>(Pb + pbw_off<PW>(inA ? rr : nA4 + (rr - nA)));
     float v[PW];
+    if (PW == 32) {
 #pragma unroll
-    for (int t = 0; t < PW; ++t) v[t] = t < jb ? row[t] : 0.0f;
+      for (int q = 0; q < PW / 4; ++q) {
+        const float4 u = pr[q];
+        v[4 * q] = u.x; v[4 * q + 1] = u.y; v[4 * q + 2] = u.z; v[4 * q + 3] = u.w;
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < PW; ++t) v[t] = t < jb ? row[t] : 0.0f;
+    }
 #pragma unroll
     for (int t = 0; t < PW; ++t) {
       if (t < jb) {
@@ -502,13 +532,14 @@ __device__ bool panel_factor_wide(float* M, int ld, int j0, int jb, float* dinv,
         v[t] = acc * dinv[j0 + t];
       }
     }
-    float4* pr = reinterpret_cast<float4*>(Pb + pbw_off<PW>(inA ? rr : nA4 + (rr - nA)));
 #pragma unroll
     for (int q = 0; q < PW / 4; ++q)
       pr[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    if (PW != 32) {
 #pragma unroll
-    for (int t = 0; t < PW; ++t)
-      if (t < jb) row[t] = v[t];
+      for (int t = 0; t < PW; ++t)
+        if (t < jb) row[t] = v[t];
+    }
   }
   // zero the pad rows: nA .. nA4-1 and after the last B row up to its group's end
   for (int e = tid; e < 8 * PW; e += NT) {
@@ -518,6 +549,16 @@ __device__ bool panel_factor_wide(float* M, int ld, int j0, int jb, float* dinv,
     if (pad) Pb[pbw_off<PW>(r) + c] = 0.0f;
   }
   __syncthreads();
+  if (PW == 32) {
+    // write the solved rows back, one row per warp (coalesced); the trailing
+    // update that follows reads Pb only and writes other columns, so no
+    // barrier is needed before it
+    for (int rr = w; rr < N; rr += NT / 32) {
+      const bool inA = rr < nA;
+      float* row = inA ? A + (rowA0 + rr) * lda + j0 : B + (rr - nA) * ldb + j0;
+      if (lane < jb) row[lane] = Pb[pbw_off<PW>(inA ? rr : nA4 + (rr - nA)) + lane];
+    }
+  }
   return all_ok;
 }
 
@@ -560,6 +601,16 @@ __device__ void panel_syrk_wide(const float* Pb, float* A, int lda, int rowA0, i
       sgn = 1.0f;
     }
     const bool diag = I == J;
+    // the tile's current values, read before the product and before any
+    // store: a store through dst may alias a later load of dst, so loads
+    // interleaved with the stores would each wait for the one before (16
+    // serial round trips per tile, to L2 in the large variant)
+    float old[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+        old[a][b] = (a < rmax && b < cmax && (!diag || b <= a)) ? dst[a * ld + b] : 0.f;
     float acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -587,7 +638,7 @@ __device__ void panel_syrk_wide(const float* Pb, float* A, int lda, int rowA0, i
 #pragma unroll
       for (int b = 0; b < 4; ++b)
         if (a < rmax && b < cmax && (!diag || b <= a))
-          dst[a * ld + b] = fmaf(sgn, acc[a][b], dst[a * ld + b]);
+          dst[a * ld + b] = fmaf(sgn, acc[a][b], old[a][b]);
   }
   __syncthreads();
 }
@@ -730,6 +781,77 @@ __device__ __forceinline__ void warp_upper_solve(const float* L, int ldk, const 
         }
       }
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Blocked triangular solves for factors in global memory (large variant):
+// x_v <- L^-1 x_v (lower) or L^-T x_v (upper) for one or two vectors x0, x1
+// (x1 may be null) of length n in shared memory; L lower, stride ld;
+// dinv = 1 / diag(L).  32 indices per block: warp 0 loads the block's 32x32
+// diagonal part into registers (all 32 loads of a lane in flight at once) and
+// solves it with shuffles; then every thread applies the block to one of the
+// remaining entries (32 independent loads each).  Two barriers per block,
+// instead of n dependent round trips to L2 on a single warp.
+// ---------------------------------------------------------------------------
+template <int NT, bool kUpper>
+__device__ void block_trsv(const float* L, int ld, const float* dinv, int n, float* x0,
+                           float* x1) {
+  const int t = threadIdx.x, lane = t & 31;
+  const int nblk = (n + 31) >> 5;
+  for (int bk = 0; bk < nblk; ++bk) {
+    const int j0 = 32 * (kUpper ? nblk - 1 - bk : bk);
+    const int jb = min(32, n - j0);
+    if (t < 32) {
+      // lower: lane l holds row l of the block, a[k] = L[j0+l][j0+k] (k <= l);
+      // upper: lane l holds column l, a[k] = L[j0+k][j0+l] (k >= l)
+      float a[32];
+#pragma unroll
+      for (int k = 0; k < 32; ++k) {
+        const bool in = lane < jb && k < jb && (kUpper ? k >= lane : k <= lane);
+        a[k] = in ? (kUpper ? L[(j0 + k) * ld + j0 + lane] : L[(j0 + lane) * ld + j0 + k]) : 0.f;
+      }
+      float v0 = lane < jb ? x0[j0 + lane] : 0.f;
+      float v1 = (x1 && lane < jb) ? x1[j0 + lane] : 0.f;
+#pragma unroll
+      for (int kk = 0; kk < 32; ++kk) {
+        const int k = kUpper ? 31 - kk : kk;
+        if (k < jb) {
+          const float dk = dinv[j0 + k];
+          const float s0 = __shfl_sync(kFull, v0 * dk, k);
+          const float s1 = __shfl_sync(kFull, v1 * dk, k);
+          if (lane == k) { v0 = s0; v1 = s1; }
+          if (kUpper ? lane < k : lane > k) {
+            v0 = fmaf(-a[k], s0, v0);
+            v1 = fmaf(-a[k], s1, v1);
+          }
+        }
+      }
+      if (lane < jb) {
+        x0[j0 + lane] = v0;
+        if (x1) x1[j0 + lane] = v1;
+      }
+    }
+    __syncthreads();
+    // the rest: lower -> entries i >= j0 + jb, upper -> entries i < j0
+    const int r0 = kUpper ? 0 : j0 + jb, r1 = kUpper ? j0 : n;
+    for (int i = r0 + t; i < r1; i += NT) {
+      float l[32];
+#pragma unroll
+      for (int k = 0; k < 32; ++k)
+        l[k] = k < jb ? (kUpper ? L[(j0 + k) * ld + i] : L[i * ld + j0 + k]) : 0.f;
+      float acc0 = x0[i], acc1 = x1 ? x1[i] : 0.f;
+#pragma unroll
+      for (int k = 0; k < 32; ++k) {
+        if (k < jb) {
+          acc0 = fmaf(-l[k], x0[j0 + k], acc0);
+          if (x1) acc1 = fmaf(-l[k], x1[j0 + k], acc1);
+        }
+      }
+      x0[i] = acc0;
+      if (x1) x1[i] = acc1;
+    }
+    __syncthreads();
   }
 }
 

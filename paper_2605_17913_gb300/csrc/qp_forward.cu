@@ -19,7 +19,7 @@ int forward_blocks_per_sm_nt(size_t smem);
 // of them folded right-hand sides).  Otherwise the large variant (n <= 256):
 // 512 threads, K, G, A, Y, C in a global workspace, amax + p <= 318.
 size_t forward_config(int n, int m, int p, int* nthreads, int* amax_out, long long* ws_floats,
-                      bool warp_per_qp) {
+                      bool warp_per_qp, int large_threads) {
   if (nthreads) *nthreads = 0;
   if (amax_out) *amax_out = 0;
   if (ws_floats) *ws_floats = 0;
@@ -51,10 +51,11 @@ size_t forward_config(int n, int m, int p, int* nthreads, int* amax_out, long lo
   int amax = m < n ? m : n;
   if (amax + p > 318) amax = 318 - p;
   if (amax < 0) return 0;
-  const fwd::FLayout L = fwd::make_fwd_layout(n, m, p, amax, 512, true);
+  const int nt = large_threads == 256 ? 256 : 512;
+  const fwd::FLayout L = fwd::make_fwd_layout(n, m, p, amax, nt, true);
   const size_t bytes = (size_t)L.total * sizeof(float);
   if (bytes > budget) return 0;
-  if (nthreads) *nthreads = 512;
+  if (nthreads) *nthreads = nt;
   if (amax_out) *amax_out = amax;
   if (ws_floats) *ws_floats = round4(L.big_total);
   return bytes;
@@ -62,8 +63,9 @@ size_t forward_config(int n, int m, int p, int* nthreads, int* amax_out, long lo
 
 cudaError_t launch_forward(const FwdParams& P, int nthreads, size_t smem, int grid,
                            cudaStream_t st) {
-  if (P.ws) return nthreads == 512 ? launch_forward_nt<512, true>(P, smem, grid, st)
-                                   : cudaErrorInvalidValue;
+  if (P.ws) return nthreads == 512   ? launch_forward_nt<512, true>(P, smem, grid, st)
+                  : nthreads == 256 ? launch_forward_nt<256, true>(P, smem, grid, st)
+                                    : cudaErrorInvalidValue;
   switch (nthreads) {
     case 32: return launch_forward_nt<32, false>(P, smem, grid, st);
     case 128: return launch_forward_nt<128, false>(P, smem, grid, st);
@@ -79,11 +81,14 @@ void preload_forward_kernels() {
   forward_blocks_per_sm_nt<128, false>(1024);
   forward_blocks_per_sm_nt<512, false>(1024);
   forward_blocks_per_sm_nt<512, true>(1024);
+  forward_blocks_per_sm_nt<256, true>(1024);
   cudaGetLastError();
 }
 
 int forward_blocks_per_sm(int nthreads, size_t smem, bool split) {
-  if (split) return nthreads == 512 ? forward_blocks_per_sm_nt<512, true>(smem) : 0;
+  if (split) return nthreads == 512   ? forward_blocks_per_sm_nt<512, true>(smem)
+                  : nthreads == 256 ? forward_blocks_per_sm_nt<256, true>(smem)
+                                    : 0;
   switch (nthreads) {
     case 32: return forward_blocks_per_sm_nt<32, false>(smem);
     case 128: return forward_blocks_per_sm_nt<128, false>(smem);

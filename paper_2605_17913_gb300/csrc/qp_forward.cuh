@@ -72,6 +72,8 @@ struct FLayout {
   int o_b, o_y, o_re;
   int o_cdinv, o_D, o_ua, o_ub, o_act;
   int o_h, o_z, o_s, o_ri, o_bz, o_bs, o_ea, o_eb, o_ta, o_tb, o_pos, o_ina;
+  int o_rf;  // refinement of the folded solves (large variant): saved right-hand
+             // sides, the solution and G't for both columns (6 nv + 4 fv floats)
   int total;
 };
 
@@ -139,6 +141,7 @@ __host__ __device__ inline FLayout make_fwd_layout(int n, int m, int p, int amax
   L.o_ea = take(L.mv);
   L.o_pos = take(L.mv);
   L.o_ina = take(L.mv);
+  L.o_rf = take(split ? 6 * L.nv + 4 * L.fv : 0);
   L.total = o;
   return L;
 }
@@ -154,9 +157,17 @@ struct SharedState {
   float* gbase;      // base of K, G, Y, C: the dynamic shared memory or the workspace
   const float* gA;   // this instance's A in the caller's memory (row stride n)
   uint64_t mbar[2];  // tensor-core G'WG: completion of the two staging buffers
+  uint64_t mbar_g[2];  // FP32 G'WG (large variant): bulk copies of the two row buffers
+  uint32_t tc_chunks, g_chunks;  // chunks committed through mbar / mbar_g (phase parity)
   uint32_t tmem;     // its TMEM base (large variant with gwg != 0)
   int tc_flag;       // a bounded wait ran out in the current G'WG
   int tc_bad;        // sticky: G'WG falls back to FP32 for the rest of the solve
+  int async_lost;    // bulk copies may still be in flight after a bounded wait
+  int diag;          // diagnostic bits of this instance (QP_DIAG_*)
+  int nan_stage;     // first stage with a non-finite value (QP_STAGE_*), 0: none
+  int in_relax;      // Alg. 2 (or the factorisation cached for Alg. 3) is running
+  int all_inactive;  // eq. 8 as it stands: every row in K (QP_STANDARD_SCHUR)
+  int refine;        // refinement sweeps of each folded solve (large variant)
   int gwg;           // 0 FP32, 1 TF32, 2 BF16 (tensor-core products, large variant)
   float chord_kappa;  // kappa of the factorisation that Alg. 2's chord steps reuse
   float qn, bn, hn;  // |q|, |b|, |h| (infinity norms)
@@ -198,14 +209,31 @@ template <int NT, bool kBig>
 struct Solver {
   static constexpr int kPW = panel_width(NT, kBig);
 
-  static __device__ void init(int n, int m, int p, int amax, float* ws, int gwg) {
+  static __device__ void init(int n, int m, int p, int amax, float* ws, int gwg, int refine) {
     if (threadIdx.x == 0) {
       fwd_state.L = make_fwd_layout(n, m, p, amax, NT, kBig);
       fwd_state.gbase = kBig ? ws : fwd_dyn;
       fwd_state.gwg = kBig ? gwg : 0;
       fwd_state.tc_flag = 0;
       fwd_state.tc_bad = 0;
+      fwd_state.async_lost = 0;
+      fwd_state.diag = 0;
+      fwd_state.nan_stage = 0;
+      fwd_state.in_relax = 0;
+      fwd_state.all_inactive = 0;
+      fwd_state.refine = kBig ? refine : 0;
+      fwd_state.tc_chunks = 0;
+      fwd_state.g_chunks = 0;
       fwd_state.tmem = 0;
+      if (kBig) {
+        // the bulk-copy and tensor-core barriers, once per CTA (their phases
+        // follow from the chunk counts above)
+        tc::mbar_init(&fwd_state.mbar[0], 1);
+        tc::mbar_init(&fwd_state.mbar[1], 1);
+        tc::mbar_init(&fwd_state.mbar_g[0], 1);
+        tc::mbar_init(&fwd_state.mbar_g[1], 1);
+        tc::fence_mbar_init();
+      }
       fwd_state.a = 0;
       fwd_state.nf = p;
       fwd_state.chord_kappa = 0.f;
@@ -222,6 +250,51 @@ struct Solver {
     int parity = fwd_parity[threadIdx.x];
     block_reduce<NT, K>(v, red, parity, op);
     fwd_parity[threadIdx.x] = (unsigned char)parity;
+  }
+
+  // diagnostics: if any thread saw a non-finite value (`bad`), record `stage`
+  // as the instance's first such stage (Alg. 2 as a whole counts as the relax
+  // stage).  A block-wide vote, made only when the caller registered a
+  // diagnostics array (uniform over the CTA).
+  static __device__ void trace(const FwdParams& P, int stage, bool bad) {
+    if (!P.diag) return;
+    if (__syncthreads_or(bad ? 1 : 0) && threadIdx.x == 0 && fwd_state.nan_stage == 0)
+      fwd_state.nan_stage = fwd_state.in_relax ? QP_STAGE_RELAX : stage;
+  }
+
+  // bad = some entry of v[0 .. len) is not finite
+  static __device__ __forceinline__ bool any_nonfinite(const float* v, int len) {
+    bool bad = false;
+    for (int i = threadIdx.x; i < len; i += NT) bad |= !isfinite(v[i]);
+    return bad;
+  }
+
+  // trace the Newton matrix's diagonal (W of the inactive rows, 1/W of the
+  // active ones) right after partition()
+  static __device__ void trace_scaling(const FwdParams& P) {
+    if (!P.diag) return;
+    QP_ARR(ea); QP_ARR(D); QP_IARR(pos);
+    bool bad = false;
+    for (int r = threadIdx.x; r < fwd_state.L.m; r += NT) {
+      const float wv = pos[r] < 0 ? ea[r] : D[pos[r]];
+      bad |= !(isfinite(wv) && wv >= 0.f);
+    }
+    trace(P, QP_STAGE_SCALING, bad);
+  }
+
+  // a factorisation failed: the predictor stage (its first use), flagged
+  static __device__ void trace_factor_failed(const FwdParams& P) {
+    if (threadIdx.x == 0) fwd_state.diag |= QP_DIAG_FACTOR_FAILED;
+    trace(P, QP_STAGE_PREDICTOR, true);
+  }
+
+  // the iterate after a step
+  static __device__ void trace_iterate(const FwdParams& P, int stage) {
+    if (!P.diag) return;
+    QP_ARR(x); QP_ARR(z); QP_ARR(s); QP_ARR(y);
+    const bool bad = any_nonfinite(x, fwd_state.L.n) || any_nonfinite(z, fwd_state.L.m) ||
+                     any_nonfinite(s, fwd_state.L.m) || any_nonfinite(y, fwd_state.L.p);
+    trace(P, stage, bad);
   }
 
   // ---- load one instance; Q's strict upper triangle goes to K's upper part ----
@@ -251,6 +324,8 @@ struct Solver {
       chk = isfinite(v) ? chk : 1.0f;
       G[r * L.ldg + c] = v;
     }
+    // the workspace copy of G is read by bulk copies (async proxy) later
+    if (kBig) tc::fence_async_global();
     for (int e = t; e < p * n; e += NT) chk = isfinite(gA[e]) ? chk : 1.0f;
     if (t == 0) fwd_state.gA = gA;  // A stays in the caller's memory
     float lq = 0.f, lb = 0.f, lh = 0.f;
@@ -286,8 +361,8 @@ struct Solver {
     // one warp: tau = 1 unless more than amax rows have W > tau (then tau
     // grows tenfold until they fit), and the ordered compaction of the rows
     if (w == 0) {
-      float tau = 1.0f;
-      for (int round = 0; round < 40; ++round) {
+      float tau = fwd_state.all_inactive ? INFINITY : 1.0f;
+      for (int round = 0; round < 40 && tau < INFINITY; ++round) {
         int cnt = 0;
         for (int r0 = 0; r0 < m; r0 += 32) {
           const int r = r0 + lane;
@@ -322,7 +397,18 @@ struct Solver {
     for (int k = w; k < nf; k += NT / 32) {
       const float* src = k < a ? G + act[k] * L.ldg : A + (k - a) * n;
       const float dk = k < a ? bs[act[k]] / bz[act[k]] : 0.f;
-      for (int c = lane; c < n; c += 32) Y[k * L.ldk + c] = src[c];
+      if constexpr (kBig) {
+        // the whole row is loaded before it is stored (src may alias Y as
+        // far as the compiler knows, which would serialise the round trips)
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = lane + 32 * j < n ? src[lane + 32 * j] : 0.f;
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (lane + 32 * j < n) Y[k * L.ldk + lane + 32 * j] = v[j];
+      } else {
+        for (int c = lane; c < n; c += 32) Y[k * L.ldk + c] = src[c];
+      }
       for (int c = lane; c <= k; c += 32) C[k * L.ldc + c] = c == k ? dk : 0.f;
       if (lane == 0) D[k] = dk;
     }
@@ -338,6 +424,20 @@ struct Solver {
     const FLayout& L = fwd_state.L;
     QP_ARR(R); QP_BIG(Y); QP_BIG(C); QP_ARR(ua); QP_ARR(ub);
     const int n = L.n, nf = fwd_state.nf, t = threadIdx.x;
+    if (kBig && fwd_state.refine > 0) {
+      // keep both columns' right-hand sides for the refinement sweeps
+      QP_ARR(rf);
+      float* const r1s = rf + 4 * L.nv + 2 * L.fv;
+      float* const r2s = r1s + 2 * L.nv;
+      for (int e = t; e < 2 * n; e += NT) {
+        const int c = e / n, i = e - c * n;
+        r1s[c * L.nv + i] = R[c * L.ldx + i];
+      }
+      for (int e = t; e < 2 * nf; e += NT) {
+        const int c = e / nf, k = e - c * nf;
+        r2s[c * L.fv + k] = (c == 0 ? ua : ub)[k];
+      }
+    }
     for (int e = t; e < 2 * n; e += NT) {
       const int c = e / n, i = e - c * n;
       Y[(nf + c) * L.ldk + i] = R[c * L.ldx + i];
@@ -365,10 +465,24 @@ struct Solver {
         const uint32_t tm = fwd_state.tmem;
         tc_done = fwd_state.gwg == 2
                       ? tc::syrk_gwg_tc<NT, true>(K, L.ldk, qd, G, L.ldg, ea, ina, ni, L.n, stage,
-                                                  fwd_state.mbar, tm, &fwd_state.tc_flag)
+                                                  fwd_state.mbar, &fwd_state.tc_chunks, tm,
+                                                  &fwd_state.tc_flag)
                       : tc::syrk_gwg_tc<NT, false>(K, L.ldk, qd, G, L.ldg, ea, ina, ni, L.n,
-                                                   stage, fwd_state.mbar, tm, &fwd_state.tc_flag);
-        if (!tc_done && threadIdx.x == 0) fwd_state.tc_bad = 1;
+                                                   stage, fwd_state.mbar, &fwd_state.tc_chunks,
+                                                   tm, &fwd_state.tc_flag);
+        if (!tc_done && threadIdx.x == 0) {
+          fwd_state.tc_bad = 1;
+          fwd_state.diag |= QP_DIAG_TC_FALLBACK;
+        }
+      }
+      if (!tc_done && !fwd_state.async_lost) {
+        // FP32 products from rows staged in shared memory by bulk copies
+        float* stage = fwd_dyn + L.o_Pb;  // dead during the factorisation
+        tc_done = tc::syrk_gwg_staged<NT>(K, L.ldk, qd, G, L.ldg, ea, ina, fwd_state.ni, L.n,
+                                          stage, fwd_state.mbar_g, &fwd_state.g_chunks,
+                                          &fwd_state.tc_flag, &fwd_state.async_lost);
+        if (!tc_done && threadIdx.x == 0) fwd_state.diag |= QP_DIAG_STAGE_FALLBACK;
+        __syncthreads();
       }
     }
     if (!tc_done) syrk_gwg<NT>(K, L.ldk, qd, G, L.ldg, ea, ina, fwd_state.ni, L.n);
@@ -398,6 +512,8 @@ struct Solver {
   // factor; if FP32 Cholesky of C meets a non-positive pivot (rank-deficient
   // F), redo the partition and factorisation with a 100x, then 10^4x larger shift.
   static __device__ bool factor(int nfold = 0) {
+    // eq. 8 as it stands: one attempt, no shift of the equality block
+    if (fwd_state.all_inactive) return factor_once(0.0f, nfold);
     float creg = kCReg;
     for (int attempt = 0; attempt < 3; ++attempt, creg *= 100.0f) {
       if (attempt > 0) {
@@ -416,42 +532,55 @@ struct Solver {
     QP_BIG(K); QP_ARR(dinv); QP_ARR(R); QP_BIG(Y); QP_BIG(C); QP_ARR(ua); QP_ARR(ub);
     const int n = L.n, t = threadIdx.x, w = t >> 5, nf = fwd_state.nf;
     if (nf > 0) {
-      // one warp per column (both columns in turn with a single warp)
-      for (int c = w; c < 2; c += NT / 32) {
-        float* u = c == 0 ? ua : ub;
-        const float* wrow = C + (nf + c) * L.ldc;
-        for (int k = t & 31; k < nf; k += 32) u[k] = wrow[k];
-        __syncwarp();
-        c_solve_n(u, nf, true);
+      if constexpr (kBig) {
+        // L_C in global memory: blocked solve with every warp
+        QP_ARR(cdinv);
+        for (int e = t; e < 2 * nf; e += NT) {
+          const int c = e / nf, k = e - c * nf;
+          (c == 0 ? ua : ub)[k] = C[(nf + c) * L.ldc + k];
+        }
+        __syncthreads();
+        block_trsv<NT, true>(C, L.ldc, cdinv, nf, ua, ub);
+      } else {
+        // one warp per column (both columns in turn with a single warp)
+        for (int c = w; c < 2; c += NT / 32) {
+          float* u = c == 0 ? ua : ub;
+          const float* wrow = C + (nf + c) * L.ldc;
+          for (int k = t & 31; k < nf; k += 32) u[k] = wrow[k];
+          __syncwarp();
+          c_solve_n(u, nf, true);
+        }
+        __syncthreads();
       }
-      __syncthreads();
     }
     for (int e = t; e < 2 * n; e += NT) {
       const int c = e / n, i = e - c * n;
       const float* u = c == 0 ? ua : ub;
       float acc = Y[(nf + c) * L.ldk + i];
-      for (int k = 0; k < nf; ++k) acc = fmaf(-Y[k * L.ldk + i], u[k], acc);
+      if constexpr (kBig) {
+        // Y in global memory: several rows' loads in flight per thread
+#pragma unroll 8
+        for (int k = 0; k < nf; ++k) acc = fmaf(-Y[k * L.ldk + i], u[k], acc);
+      } else {
+        for (int k = 0; k < nf; ++k) acc = fmaf(-Y[k * L.ldk + i], u[k], acc);
+      }
       R[c * L.ldx + i] = acc;
     }
     __syncthreads();
-    solve_rows<NT, true, kBig ? 8 : 4>(K, L.ldk, dinv, n, R, L.ldx, 0, 2);
+    if constexpr (kBig)
+      block_trsv<NT, true>(K, L.ldk, dinv, n, R, R + L.ldx);
+    else
+      solve_rows<NT, true, 4>(K, L.ldk, dinv, n, R, L.ldx, 0, 2);
     QP_MARK(PH_SOLVE);
   }
 
-  // warp solve with C for nf rows (up to 128 on chip, 320 in the large variant)
+  // warp solve with C for nf rows (up to 128, on chip)
+  // (on chip only; the large variant solves with L_C by block_trsv)
   static __device__ void c_solve_n(float* u, int nf, bool upper_only) {
     if (nf <= 32) c_solve<1>(u, nf, upper_only);
     else if (nf <= 64) c_solve<2>(u, nf, upper_only);
     else if (nf <= 96) c_solve<3>(u, nf, upper_only);
-    else if (!kBig || nf <= 128) c_solve<4>(u, nf, upper_only);
-    else if constexpr (kBig) {
-      if (nf <= 160) c_solve<5>(u, nf, upper_only);
-      else if (nf <= 192) c_solve<6>(u, nf, upper_only);
-      else if (nf <= 224) c_solve<7>(u, nf, upper_only);
-      else if (nf <= 256) c_solve<8>(u, nf, upper_only);
-      else if (nf <= 288) c_solve<9>(u, nf, upper_only);
-      else c_solve<10>(u, nf, upper_only);
-    }
+    else c_solve<4>(u, nf, upper_only);
   }
 
   template <int SP>
@@ -480,7 +609,12 @@ struct Solver {
     const FLayout& L = fwd_state.L;
     QP_BIG(K); QP_ARR(dinv); QP_ARR(R); QP_BIG(Y); QP_ARR(ua); QP_ARR(ub);
     const int n = L.n, t = threadIdx.x, w = t >> 5, nf = fwd_state.nf;
-    solve_rows<NT, false, kBig ? 8 : 4>(K, L.ldk, dinv, n, R, L.ldx, slot0, nrhs);
+    float* const r0 = R + slot0 * L.ldx;
+    float* const r1 = nrhs == 2 ? R + (slot0 + 1) * L.ldx : nullptr;
+    if constexpr (kBig)
+      block_trsv<NT, false>(K, L.ldk, dinv, n, r0, r1);
+    else
+      solve_rows<NT, false, 4>(K, L.ldk, dinv, n, R, L.ldx, slot0, nrhs);
     if (nf > 0) {
       for (int e = t; e < nf * nrhs; e += NT) {
         const int k = e % nf, cc = slot0 + e / nf;
@@ -488,25 +622,46 @@ struct Solver {
         const float* yk = Y + k * L.ldk;
         const float* rr = R + cc * L.ldx;
         float acc = 0.f;
-        for (int i = 0; i < n; ++i) acc = fmaf(yk[i], rr[i], acc);
+        if constexpr (kBig) {
+#pragma unroll 8
+          for (int i = 0; i < n; ++i) acc = fmaf(yk[i], rr[i], acc);
+        } else {
+          for (int i = 0; i < n; ++i) acc = fmaf(yk[i], rr[i], acc);
+        }
         u[k] = acc - u[k];
       }
       __syncthreads();
-      for (int c = w; c < nrhs; c += NT / 32) {
-        float* u = (slot0 + c) == 0 ? ua : ub;
-        c_solve_n(u, nf, false);
+      if constexpr (kBig) {
+        QP_ARR(cdinv); QP_BIG(C);
+        float* const u0 = slot0 == 0 ? ua : ub;
+        float* const u1 = nrhs == 2 ? ub : nullptr;
+        block_trsv<NT, false>(C, L.ldc, cdinv, nf, u0, u1);
+        block_trsv<NT, true>(C, L.ldc, cdinv, nf, u0, u1);
+      } else {
+        for (int c = w; c < nrhs; c += NT / 32) {
+          float* u = (slot0 + c) == 0 ? ua : ub;
+          c_solve_n(u, nf, false);
+        }
+        __syncthreads();
       }
-      __syncthreads();
       for (int e = t; e < n * nrhs; e += NT) {
         const int i = e % n, cc = slot0 + e / n;
         const float* u = cc == 0 ? ua : ub;
         float acc = R[cc * L.ldx + i];
-        for (int k = 0; k < nf; ++k) acc = fmaf(-Y[k * L.ldk + i], u[k], acc);
+        if constexpr (kBig) {
+#pragma unroll 8
+          for (int k = 0; k < nf; ++k) acc = fmaf(-Y[k * L.ldk + i], u[k], acc);
+        } else {
+          for (int k = 0; k < nf; ++k) acc = fmaf(-Y[k * L.ldk + i], u[k], acc);
+        }
         R[cc * L.ldx + i] = acc;
       }
       __syncthreads();
     }
-    solve_rows<NT, true, kBig ? 8 : 4>(K, L.ldk, dinv, n, R, L.ldx, slot0, nrhs);
+    if constexpr (kBig)
+      block_trsv<NT, true>(K, L.ldk, dinv, n, r0, r1);
+    else
+      solve_rows<NT, true, 4>(K, L.ldk, dinv, n, R, L.ldx, slot0, nrhs);
     QP_MARK(PH_SOLVE);
   }
 
@@ -526,6 +681,90 @@ struct Solver {
     }
     __syncthreads();
     QP_MARK(PH_GDX);
+  }
+
+  // ---- one iterative-refinement sweep of a folded solve (large variant):
+  // the residual of the bounded system
+  //   r1 = rhs1 - (K_I dx + F' mu),  r2 = rhs2 - (F dx - D mu),
+  // K_I dx = Q dx + G_I' W_I (G_I dx) and F' mu = G_A' mu_A + A' mu_eq formed in
+  // FP32 from Q, G, A (not from the factorised matrix, whose G'WG may carry
+  // TF32 / BF16 products and whose C carries the small diagonal shift), then
+  // the correction from the same factors; both columns.  Needs e = G dx of
+  // the current solution in ea / eb, and leaves them updated. ----
+  static __device__ __noinline__ void refine_folded() {
+    const FLayout& L = fwd_state.L;
+    QP_BIG(K); QP_ARR(qd); QP_BIG(G); QP_ARR(R); QP_ARR(ua); QP_ARR(ub); QP_ARR(ea);
+    QP_ARR(eb); QP_ARR(bz); QP_ARR(bs); QP_ARR(D); QP_ARR(ta); QP_ARR(tb); QP_ARR(col);
+    QP_ARR(rf); QP_IARR(pos); QP_IARR(act);
+    const float* const A = fwd_state.gA;
+    const int n = L.n, m = L.m, p = L.p, t = threadIdx.x, a = fwd_state.a, nf = fwd_state.nf;
+    float* const dx = rf;                  // 2 nv: the solution's dx, both columns
+    float* const mu = rf + 2 * L.nv;       // 2 fv: its mu
+    float* const u = mu + 2 * L.fv;        // 2 nv: G't
+    const float* const r1s = u + 2 * L.nv;   // 2 nv: rhs1 (fold_rhs)
+    const float* const r2s = r1s + 2 * L.nv; // 2 fv: rhs2
+    for (int e = t; e < 2 * n; e += NT) {
+      const int c = e / n, i = e - c * n;
+      dx[c * L.nv + i] = R[c * L.ldx + i];
+    }
+    for (int e = t; e < 2 * nf; e += NT) {
+      const int c = e / nf, k = e - c * nf;
+      mu[c * L.fv + k] = (c == 0 ? ua : ub)[k];
+    }
+    // the G' coefficients: W e on inactive rows (K_I), mu on active rows (F')
+    for (int r = t; r < m; r += NT) {
+      const int k = pos[r];
+      if (k < 0) {
+        const float w = bz[r] / bs[r];
+        ta[r] = w * ea[r];
+        tb[r] = w * eb[r];
+      } else {
+        ta[r] = ua[k];
+        tb[r] = ub[k];
+      }
+    }
+    __syncthreads();
+    {
+      const float* vv[2] = {ta, tb};
+      float* oo[2] = {u, u + L.nv};
+      col_dot<NT, 2>(G, L.ldg, m, n, vv, oo, col);
+    }
+    for (int e = t; e < 2 * n; e += NT) {
+      const int c = e / n, i = e - c * n;
+      const float* x = dx + c * L.nv;
+      float qx = qd[i] * x[i];
+#pragma unroll 8
+      for (int j = 0; j < i; ++j) qx = fmaf(K[j * L.ldk + i], x[j], qx);
+#pragma unroll 8
+      for (int j = i + 1; j < n; ++j) qx = fmaf(K[i * L.ldk + j], x[j], qx);
+      float aty = 0.f;
+      for (int k = 0; k < p; ++k) aty = fmaf(__ldg(A + k * n + i), mu[c * L.fv + a + k], aty);
+      R[c * L.ldx + i] = r1s[c * L.nv + i] - qx - u[c * L.nv + i] - aty;
+    }
+    for (int e = t; e < 2 * nf; e += NT) {
+      const int c = e / nf, k = e - c * nf;
+      float fdx;
+      if (k < a) {
+        fdx = fmaf(-D[k], mu[c * L.fv + k], (c == 0 ? ea : eb)[act[k]]);
+      } else {
+        const float* x = dx + c * L.nv;
+        fdx = 0.f;
+        for (int j = 0; j < n; ++j) fdx = fmaf(__ldg(A + (k - a) * n + j), x[j], fdx);
+      }
+      (c == 0 ? ua : ub)[k] = r2s[c * L.fv + k] - fdx;
+    }
+    __syncthreads();
+    solve(0, 2);  // the correction
+    for (int e = t; e < 2 * n; e += NT) {
+      const int c = e / n, i = e - c * n;
+      R[c * L.ldx + i] += dx[c * L.nv + i];
+    }
+    for (int e = t; e < 2 * nf; e += NT) {
+      const int c = e / nf, k = e - c * nf;
+      (c == 0 ? ua : ub)[k] += mu[c * L.fv + k];
+    }
+    __syncthreads();
+    g_times_dx(0, 2);
   }
 
   // ---- residuals (eq. 4, eq. 10) and the measure ----
@@ -582,6 +821,8 @@ struct Solver {
           mx[10] = fmaxf(mx[10], fmaxf(fabsf(rzz), fabsf(rss)));
         } else {
           bz[r] = z[r]; bs[r] = s[r];
+          // relax of the standard method: distance of each z_i s_i from kappa_relax
+          if (mode == 1) mx[10] = fmaxf(mx[10], fabsf(fmaf(z[r], s[r], -P.kappa_relax)));
         }
       } else {
         const int k = u - n - m;
@@ -597,7 +838,9 @@ struct Solver {
     QP_MARK(PH_RESID);
     if (mx[12] > 0.f) return make_float2(NAN, kappa);
     float comp = mx[9];
-    if (mode == 1) comp = fabsf(kappa - P.kappa_relax) / P.kappa_relax;
+    if (mode == 1)
+      comp = (implicit ? fabsf(kappa - P.kappa_relax) : mx[10]) / P.kappa_relax;
+    if (!implicit) mx[10] = 0.f;  // (r_z, r_s) exist on the implicit manifold only
     if (P.norm_abs)
       return make_float2(fmaxf(fmaxf(fmaxf(mx[0], mx[4]), fmaxf(mx[6], comp)), mx[10]), kappa);
     const float dt = fmaxf(fmaxf(1.0f, fwd_state.qn), fmaxf(fmaxf(mx[1], mx[2]), mx[3]));
@@ -736,11 +979,27 @@ struct Solver {
   // kt_fixed >= 0).  Returns false on a factorisation failure.
   static __device__ __noinline__ bool implicit_step(const FwdParams& P, float kappa, float kt_fixed) {
     partition();
+    trace_scaling(P);
     implicit_rhs<false>();
     fold_rhs();
-    if (!factor(2)) return false;
+    if (!factor(2)) {
+      trace_factor_failed(P);
+      return false;
+    }
     solve_folded();
     g_times_dx(0, 2);
+    if constexpr (kBig) {
+      for (int k = 0; k < fwd_state.refine; ++k) refine_folded();
+    }
+    if (P.diag) {
+      // both right-hand-side columns (the affine one and d/dr_kappa)
+      QP_ARR(R); QP_ARR(ua); QP_ARR(ub); QP_ARR(ea); QP_ARR(eb);
+      const FLayout& L = fwd_state.L;
+      const bool bad = any_nonfinite(R, L.n) || any_nonfinite(R + L.ldx, L.n) ||
+                       any_nonfinite(ua, fwd_state.nf) || any_nonfinite(ub, fwd_state.nf) ||
+                       any_nonfinite(ea, L.m) || any_nonfinite(eb, L.m);
+      trace(P, QP_STAGE_PREDICTOR, bad);
+    }
     float kt;
     if (kt_fixed >= 0.f) {
       kt = kt_fixed;
@@ -752,6 +1011,7 @@ struct Solver {
         const float aa = implicit_alpha<false>(kappa, false);
         const float mua = implicit_mu_aff(kappa, aa);
         const float ratio = mua / kappa;
+        trace(P, QP_STAGE_CENTERING, !isfinite(aa) || !isfinite(ratio));
         sigma = ratio * ratio * ratio;
         if (!(sigma >= 0.f)) sigma = 0.f;
         if (sigma > 1.f) sigma = 1.f;
@@ -759,8 +1019,23 @@ struct Solver {
       kt = fmaxf(sigma * kappa, P.kappa_min);
     }
     const float rk = kappa - kt;
+    if (P.diag) {
+      // the corrector's (ds, dz, dv) on every row and its dx
+      QP_ARR(R);
+      const FLayout& L = fwd_state.L;
+      bool bad = false;
+      for (int r = threadIdx.x; r < L.m; r += NT) {
+        float dsr, dzr, dvr;
+        implicit_dir<false>(r, rk, dsr, dzr, dvr);
+        bad |= !isfinite(dsr) || !isfinite(dzr) || !isfinite(dvr);
+      }
+      for (int i = threadIdx.x; i < L.n; i += NT) bad |= !isfinite(fmaf(rk, R[L.ldx + i], R[i]));
+      trace(P, QP_STAGE_CORRECTOR, bad);
+    }
     const float alpha = P.step_frac * implicit_alpha<false>(rk, true);
+    trace(P, QP_STAGE_LINESEARCH, !isfinite(alpha));
     implicit_update(alpha, rk, kappa);
+    trace_iterate(P, QP_STAGE_LINESEARCH);
     QP_MARK(PH_STEP);
     return true;
   }
@@ -800,6 +1075,7 @@ struct Solver {
     QP_ARR(ua); QP_ARR(ub); QP_ARR(ea); QP_ARR(eb); QP_ARR(R); QP_BIG(G); QP_ARR(rt);
     QP_ARR(col); QP_ARR(red); QP_ARR(x); QP_ARR(y); QP_IARR(pos); QP_IARR(act);
     const int a = fwd_state.a, nf = fwd_state.nf;
+    trace_scaling(P);
     // predictor (slot 0): r_c = z.*s
     for (int r = t; r < m; r += NT) ta[r] = pos[r] < 0 ? -(z[r] / s[r]) * ri[r] + z[r] : 0.f;
     for (int k = t; k < nf; k += NT) ua[k] = k < a ? -(ri[act[k]] - s[act[k]]) : -re[k - a];
@@ -809,28 +1085,35 @@ struct Solver {
       float* oo[1] = {R};
       col_dot<NT, 1>(G, L.ldg, m, L.n, vv, oo, col, rt, -1.0f);
     }
-    if (!factor()) return false;
+    if (!factor()) {
+      trace_factor_failed(P);
+      return false;
+    }
     // W lives in the factors now: bz / bs serve as ds / dz scratch below
     float* const rz = fwd_dyn + fwd_state.L.o_bz;
     float* const rs = fwd_dyn + fwd_state.L.o_bs;
     solve(0, 1);
     g_times_dx(0, 1);
     float amin[1] = {1.0f};
+    bool bad = false;
     for (int r = t; r < m; r += NT) {
       const float e = ea[r];
       const float dzr = pos[r] < 0 ? (z[r] / s[r]) * (e + ri[r]) - z[r] : ua[pos[r]];
       const float dsr = -ri[r] - e;
       rz[r] = dsr;  // keep ds_aff
       rs[r] = dzr;  // keep dz_aff
+      bad |= !isfinite(dsr) || !isfinite(dzr);
       if (dsr < 0.f) amin[0] = fminf(amin[0], -s[r] / dsr);
       if (dzr < 0.f) amin[0] = fminf(amin[0], -z[r] / dzr);
     }
+    if (P.diag) trace(P, QP_STAGE_PREDICTOR, bad || any_nonfinite(R, L.n));
     reduce<1>(amin, red, OpMin());
     const float aa = amin[0];
     float acc[1] = {0.f};
     for (int r = t; r < m; r += NT) acc[0] = fmaf(fmaf(aa, rz[r], s[r]), fmaf(aa, rs[r], z[r]), acc[0]);
     reduce<1>(acc, red, OpSum());
     const float ratio = (acc[0] / (float)m) / mu;
+    trace(P, QP_STAGE_CENTERING, !isfinite(aa) || !isfinite(ratio));
     float sigma = ratio * ratio * ratio;
     if (!(sigma >= 0.f)) sigma = 0.f;
     if (sigma > 1.f) sigma = 1.f;
@@ -852,6 +1135,7 @@ struct Solver {
     solve(1, 1);
     g_times_dx(1, 1);
     float amin2[1] = {1.0f};
+    bad = false;
     for (int r = t; r < m; r += NT) {
       const float e = eb[r];
       const float dzc = pos[r] < 0 ? (z[r] / s[r]) * e - ta[r] / s[r] : ub[pos[r]];
@@ -859,11 +1143,18 @@ struct Solver {
       const float dzr = rs[r] + dzc;
       rz[r] = dsr;
       rs[r] = dzr;
+      bad |= !isfinite(dsr) || !isfinite(dzr);
       if (dsr < 0.f) amin2[0] = fminf(amin2[0], -s[r] / dsr);
       if (dzr < 0.f) amin2[0] = fminf(amin2[0], -z[r] / dzr);
     }
+    if (P.diag) {
+      for (int i = t; i < L.n; i += NT) bad |= !isfinite(R[i] + R[L.ldx + i]);
+      for (int k = t; k < p; k += NT) bad |= !isfinite(ua[a + k] + ub[a + k]);
+      trace(P, QP_STAGE_CORRECTOR, bad);
+    }
     reduce<1>(amin2, red, OpMin());
     const float alpha = fminf(1.0f, 0.99f * amin2[0]);
+    trace(P, QP_STAGE_LINESEARCH, !isfinite(alpha));
     for (int i = t; i < L.n; i += NT) x[i] = fmaf(alpha, R[i] + R[L.ldx + i], x[i]);
     for (int k = t; k < p; k += NT) y[k] = fmaf(alpha, ua[a + k] + ub[a + k], y[k]);
     for (int r = t; r < m; r += NT) {
@@ -871,6 +1162,68 @@ struct Solver {
       s[r] = fmaf(alpha, rz[r], s[r]);
     }
     __syncthreads();
+    trace_iterate(P, QP_STAGE_LINESEARCH);
+    return true;
+  }
+
+  // ---- explicit complementarity, Alg. 2 for the standard method: one
+  // Newton step on the KKT system with z .* s = target (no predictor),
+  // fraction-to-boundary 0.99.  With r_c = z .* s - target:
+  // rhs1 = -r_t + G_I'(-W r_i + r_c/s), rhs2 = (-(r_i - r_c/z)_A, -r_e);
+  // dz = W (r_i + G dx) - r_c/s on inactive rows, ds = -r_i - G dx. ----
+  static __device__ __noinline__ bool standard_fixed_step(const FwdParams& P, float target) {
+    const FLayout& L = fwd_state.L;
+    const int m = L.m, p = L.p, t = threadIdx.x;
+    partition();
+    QP_ARR(z); QP_ARR(s); QP_ARR(ri); QP_ARR(re); QP_ARR(ta); QP_ARR(ua); QP_ARR(ea);
+    QP_ARR(R); QP_BIG(G); QP_ARR(rt); QP_ARR(col); QP_ARR(red); QP_ARR(x); QP_ARR(y);
+    QP_IARR(pos); QP_IARR(act);
+    const int a = fwd_state.a, nf = fwd_state.nf;
+    trace_scaling(P);
+    for (int r = t; r < m; r += NT)
+      ta[r] = pos[r] < 0 ? -(z[r] / s[r]) * ri[r] + z[r] - target / s[r] : 0.f;
+    for (int k = t; k < nf; k += NT)
+      ua[k] = k < a ? -(ri[act[k]] - s[act[k]] + target / z[act[k]]) : -re[k - a];
+    __syncthreads();
+    {
+      const float* vv[1] = {ta};
+      float* oo[1] = {R};
+      col_dot<NT, 1>(G, L.ldg, m, L.n, vv, oo, col, rt, -1.0f);
+    }
+    if (!factor()) {
+      trace_factor_failed(P);
+      return false;
+    }
+    // W lives in the factors now: bz / bs serve as ds / dz scratch below
+    float* const rz = fwd_dyn + fwd_state.L.o_bz;
+    float* const rs = fwd_dyn + fwd_state.L.o_bs;
+    solve(0, 1);
+    g_times_dx(0, 1);
+    float amin[1] = {1.0f};
+    bool bad = false;
+    for (int r = t; r < m; r += NT) {
+      const float e = ea[r];
+      const float dzr =
+          pos[r] < 0 ? (z[r] / s[r]) * (e + ri[r]) - z[r] + target / s[r] : ua[pos[r]];
+      const float dsr = -ri[r] - e;
+      rz[r] = dsr;
+      rs[r] = dzr;
+      bad |= !isfinite(dsr) || !isfinite(dzr);
+      if (dsr < 0.f) amin[0] = fminf(amin[0], -s[r] / dsr);
+      if (dzr < 0.f) amin[0] = fminf(amin[0], -z[r] / dzr);
+    }
+    if (P.diag) trace(P, QP_STAGE_CORRECTOR, bad || any_nonfinite(R, L.n));
+    reduce<1>(amin, red, OpMin());
+    const float alpha = fminf(1.0f, 0.99f * amin[0]);
+    trace(P, QP_STAGE_LINESEARCH, !isfinite(alpha));
+    for (int i = t; i < L.n; i += NT) x[i] = fmaf(alpha, R[i], x[i]);
+    for (int k = t; k < p; k += NT) y[k] = fmaf(alpha, ua[a + k], y[k]);
+    for (int r = t; r < m; r += NT) {
+      z[r] = fmaf(alpha, rs[r], z[r]);
+      s[r] = fmaf(alpha, rz[r], s[r]);
+    }
+    __syncthreads();
+    trace_iterate(P, QP_STAGE_LINESEARCH);
     return true;
   }
 
@@ -1009,6 +1362,7 @@ struct Solver {
   static __device__ __noinline__ void run(const FwdParams& P, int bi) {
     const int n = fwd_state.L.n, m = fwd_state.L.m, p = fwd_state.L.p, t = threadIdx.x;
     const bool implicit = P.formulation == 0;
+    if (t == 0) fwd_state.all_inactive = P.formulation == 2;  // eq. 8 as it stands
     int status = ST_SOLVED, iters = 0;
     float meas = NAN;
     bool snap = false;      // a snapshot for Alg. 2 is in the cache slot
@@ -1032,6 +1386,7 @@ struct Solver {
         warm = mn[0] > 0.f;
       }
       if (!warm && !initialize()) status = ST_NUMERICAL;
+      if (!warm) trace_iterate(P, QP_STAGE_INIT);
       if (m == 0) {
         // equality-only QP: the start is the exact solve; Newton steps on the
         // linear KKT system refine it with the same factorisation
@@ -1080,9 +1435,33 @@ struct Solver {
     }
     write_solution(P, bi, good);
     // ---- Alg. 2 (relax) and the factor at the relaxed point ----
+    if (t == 0) fwd_state.in_relax = 1;
     if (P.cache && status != ST_BAD_INPUT) {
       QP_ARR(z); QP_ARR(s); QP_ARR(bz); QP_ARR(bs);
-      if (m > 0 && P.kappa_relax > 0.f && status != ST_NUMERICAL) {
+      if (m > 0 && P.kappa_relax > 0.f && status != ST_NUMERICAL && !implicit) {
+        // Alg. 2 for the standard method: Newton steps on z .* s =
+        // kappa_relax from its solution (each z_i s_i, not only their mean)
+        int rstatus = ST_MAX_ITER;
+        float rbest = INFINITY;
+        int rsince = 0;
+        for (int it = 0;; ++it) {
+          const float rm = residuals(P, false, 1).x;
+          if (!(rm == rm)) {
+            trace(P, QP_STAGE_RELAX, true);
+            rstatus = ST_NUMERICAL;
+            break;
+          }
+          if (rm < 0.9f * rbest) { rbest = rm; rsince = 0; } else { ++rsince; }
+          if (rm < P.relax_tol || (rm < P.tol && rsince >= 3)) { rstatus = ST_SOLVED; break; }
+          if (it >= P.relax_max_iter) break;
+          if (!standard_fixed_step(P, P.kappa_relax)) { rstatus = ST_NUMERICAL; break; }
+          ++iters;
+        }
+        if (status == ST_SOLVED) status = rstatus;
+        // gradients at this point: W = z ./ s
+        for (int r = t; r < m; r += NT) { bz[r] = z[r]; bs[r] = s[r]; }
+        __syncthreads();
+      } else if (m > 0 && P.kappa_relax > 0.f && status != ST_NUMERICAL) {
         // Alg. 2 targets the central-path point x(kappa_relax), which does
         // not depend on where the Newton iteration starts; from the solve's
         // last iterate with kappa >= kappa_relax it is a few steps away,
@@ -1149,7 +1528,10 @@ struct Solver {
         __syncthreads();
       } else {
         partition();
-        if (!factor() && status == ST_SOLVED) status = ST_NUMERICAL;
+        if (!factor()) {
+          trace_factor_failed(P);
+          if (status == ST_SOLVED) status = ST_NUMERICAL;
+        }
       }
       write_cache(P, bi);
       QP_MARK(PH_CACHE);
@@ -1162,10 +1544,18 @@ struct Solver {
       hdr[1] = -1;
       hdr[2] = 0;
     }
+    __syncthreads();
     if (t == 0) {
+      // bulk copies that may still have been in flight: nothing of this
+      // instance is trusted
+      if (fwd_state.async_lost) {
+        status = ST_NUMERICAL;
+        fwd_state.diag |= QP_DIAG_ASYNC_LOST;
+      }
       if (P.status) P.status[bi] = status;
       if (P.iters) P.iters[bi] = iters;
       if (P.kkt) P.kkt[bi] = meas;
+      if (P.diag) P.diag[bi] = (fwd_state.diag & ~QP_STAGE_MASK) | fwd_state.nan_stage;
     }
   }
 };
@@ -1174,16 +1564,19 @@ struct Solver {
 #undef QP_IARR
 #undef QP_BIG
 
-// minimum resident CTAs per SM the register budget is sized for
-template <int NT> struct MinBlocks { static constexpr int value = 1; };
-template <> struct MinBlocks<32> { static constexpr int value = 12; };
-template <> struct MinBlocks<128> { static constexpr int value = 3; };
-template <> struct MinBlocks<256> { static constexpr int value = 3; };
+// minimum resident CTAs per SM the register budget is sized for (128
+// registers a thread in the large variant: one 512-thread or two 256-thread
+// CTAs per SM)
+template <int NT, bool kBig> struct MinBlocks { static constexpr int value = 1; };
+template <> struct MinBlocks<32, false> { static constexpr int value = 12; };
+template <> struct MinBlocks<128, false> { static constexpr int value = 3; };
+template <> struct MinBlocks<256, false> { static constexpr int value = 3; };
+template <> struct MinBlocks<256, true> { static constexpr int value = 2; };
 
 // kBig: the large-problem variant, K, G, A, Y, C in the instance's slice of
 // the global workspace P.ws (L1/L2-cached) instead of shared memory.
 template <int NT, bool kBig>
-__global__ void __launch_bounds__(NT, MinBlocks<NT>::value) qp_forward_kernel(const FwdParams P) {
+__global__ void __launch_bounds__(NT, (MinBlocks<NT, kBig>::value)) qp_forward_kernel(const FwdParams P) {
   // the phases take the parameters by reference: keep them in shared memory
   // rather than letting each thread copy the whole block to local memory
   __shared__ FwdParams sP;
@@ -1203,7 +1596,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) qp_forward_kernel(co
   __syncthreads();
   const int bi = P.desc ? 0 : blockIdx.x;
   float* const ws = kBig ? sP.ws + (size_t)bi * (size_t)sP.ws_stride : nullptr;
-  Solver<NT, kBig>::init(sP.n, sP.m, sP.p, sP.amax, ws, sP.gwg);  // ends with a barrier
+  Solver<NT, kBig>::init(sP.n, sP.m, sP.p, sP.amax, ws, sP.gwg, sP.refine_fwd);  // ends with a barrier
 #ifdef QP_PHASE_TIMERS
   if (threadIdx.x == 0) fwd_state.timers = P.timers;
   __syncthreads();

@@ -37,6 +37,7 @@ struct FwdParams {
   int max_iter, relax_max_iter, sigma_mode, formulation, norm_abs, warm_start, refine_steps;
   int gwg;  // G'WG products: 0 FP32, 1 TF32, 2 BF16 (tensor cores, large variant only)
   int chord;  // Alg. 2 reuses the factorisation of its first iterate (chord steps)
+  int refine_fwd;  // refinement sweeps of each folded Newton solve (large variant)
   // gradient cache (nullptr: no relax, no cache)
   float* cache;
   long long cache_stride;
@@ -45,6 +46,7 @@ struct FwdParams {
   float* ws;
   long long ws_stride;
   const ReqDesc* desc;  // ragged launch: one descriptor per CTA (nullptr: uniform batch)
+  int32_t* diag;        // per-instance diagnostics word (nullptr: no stage tests)
 #ifdef QP_PHASE_TIMERS
   unsigned long long* timers;  // device counters of the phase timers (tracing build)
 #endif
@@ -59,6 +61,7 @@ struct BwdParams {
   long long cache_stride;
   float *dQ, *dq, *dA, *db, *dG, *dh;
   const ReqDesc* desc;  // ragged launch: one descriptor per CTA (nullptr: uniform batch)
+  int32_t* diag;        // per-instance diagnostics word (nullptr: not written)
 };
 
 // Per-instance layout of the gradient cache, in floats (offsets multiples of
@@ -104,8 +107,11 @@ __host__ __device__ inline CacheLayout cache_layout(int n, int m, int p, int ama
 // large-problem variant, the global workspace floats per instance (0 when
 // everything fits in shared memory).  warp_per_qp: one warp per CTA for
 // n <= 32 (throughput of large batches; the amax is the same either way).
+// large_threads: threads per CTA of the large variant, 512 (one CTA per SM)
+// or 256 (two; FP32 G'WG only).
 size_t forward_config(int n, int m, int p, int* nthreads, int* amax,
-                      long long* ws_floats = nullptr, bool warp_per_qp = false);
+                      long long* ws_floats = nullptr, bool warp_per_qp = false,
+                      int large_threads = 512);
 
 // Batches from this size up run problems with n <= 32 one warp per QP.
 constexpr int kWarpPerQpMinBatch = 2048;

@@ -90,6 +90,29 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
+// arrive on an mbarrier (count 1) announcing `bytes` of bulk-copy transactions
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// one-dimensional bulk copy (TMA engine) global -> this CTA's shared memory,
+// completing `bytes` transactions on `bar`; both addresses 16-byte aligned,
+// bytes a multiple of 16
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// order this thread's earlier generic-proxy writes to global memory before
+// later reads of the same memory by the async proxy (bulk copies)
+__device__ __forceinline__ void fence_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
 // shared-memory matrix descriptor: K-major, no swizzle; lbo / sbo in bytes
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
   uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
@@ -153,12 +176,15 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
 // K (lower triangle, stride ldk) = Q + sum over rows[0 .. nrows) of
 // W[r] G[r]' G[r], products on the tensor cores.  Q from K's strict upper
 // triangle and qd.  stage: two buffers of stage_bytes(n, esize), 128-byte
-// aligned; mbar: two mbarriers; tmem: this CTA's TMEM base (kTmemCols).
-// Returns false (K untouched) if a wait ran out.  Ends with a barrier.
+// aligned; mbar: two mbarriers initialised once per CTA (count 1) and used
+// only here; *chunks: the chunks this CTA has committed through them so far
+// (the phase parity of each barrier follows from it; updated here); tmem:
+// this CTA's TMEM base (kTmemCols).  Returns false (K untouched) if a wait
+// ran out.  Ends with a barrier.
 template <int NT, bool kBF16>
 __device__ bool syrk_gwg_tc(float* K, int ldk, const float* qd, const float* G, int ldg,
                             const float* W, const int* rows, int nrows, int n, char* stage,
-                            uint64_t* mbar, uint32_t tmem, int* flag) {
+                            uint64_t* mbar, uint32_t* chunks, uint32_t tmem, int* flag) {
   constexpr int esize = kBF16 ? 2 : 4;
   constexpr int per16 = 16 / esize;    // K values per 16-byte core-matrix row
   constexpr int kslabs = kKc / per16;  // 16-byte K slabs per chunk
@@ -169,19 +195,19 @@ __device__ bool syrk_gwg_tc(float* K, int ldk, const float* qd, const float* G, 
   const uint32_t slab = (uint32_t)NG * 128u;
   const uint32_t bufb = (uint32_t)kslabs * slab;
   const int nchunks = (nrows + kKc - 1) / kKc;
-  if (tid == 0) {
-    *flag = 0;
-    mbar_init(&mbar[0], 1);
-    mbar_init(&mbar[1], 1);
-    fence_mbar_init();
-  }
+  // chunk g (counted over the CTA's calls) uses buffer g & 1 and is that
+  // buffer's (g >> 1)-th commit, completing its barrier's phase of parity
+  // (g >> 1) & 1; every call waits for all of its commits before returning
+  const uint32_t g0 = *chunks;
+  if (tid == 0) *flag = 0;
   __syncthreads();
   int issued = 0;  // chunks whose MMAs were committed
   for (int c = 0; c < nchunks; ++c) {
-    const int b = c & 1;
+    const uint32_t g = g0 + (uint32_t)c;
+    const int b = (int)(g & 1u);
     char* buf = stage + b * bufb;
-    // buffer b is free once the MMAs of chunk c - 2 (its latest commit) are done
-    if (c >= 2 && !mbar_wait(&mbar[b], (uint32_t)(((c - 2) >> 1) & 1))) atomicOr(flag, 1);
+    // buffer b is free once the MMAs of chunk g - 2 (its latest commit) are done
+    if (g >= 2 && !mbar_wait(&mbar[b], ((g - 2) >> 1) & 1u)) atomicOr(flag, 1);
     if (__syncthreads_or(*flag)) break;
     // stage chunk c: item (i, j) = row i of G_hat' (variable i), K slab j
     for (int it = tid; it < npad * kslabs; it += NT) {
@@ -232,12 +258,13 @@ __device__ bool syrk_gwg_tc(float* K, int ldk, const float* qd, const float* G, 
     issued = c + 1;
   }
   // wait (bounded, also after a failure) for everything committed: the latest
-  // commit of each buffer, chunks issued - 1 and issued - 2
-  if (issued >= 1 && !mbar_wait(&mbar[(issued - 1) & 1], (uint32_t)(((issued - 1) >> 1) & 1)))
-    atomicOr(flag, 1);
-  if (issued >= 2 && !mbar_wait(&mbar[(issued - 2) & 1], (uint32_t)(((issued - 2) >> 1) & 1)))
-    atomicOr(flag, 1);
+  // commit of each buffer, chunks g0 + issued - 1 and g0 + issued - 2
+  for (int k = 1; k <= 2 && k <= issued; ++k) {
+    const uint32_t g = g0 + (uint32_t)(issued - k);
+    if (!mbar_wait(&mbar[g & 1u], (g >> 1) & 1u)) atomicOr(flag, 1);
+  }
   const bool ok = __syncthreads_or(*flag) == 0;
+  if (tid == 0) *chunks = g0 + (uint32_t)issued;
   fence_after_sync();
   if (ok) {
     // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 and a quarter of the columns
@@ -256,16 +283,142 @@ __device__ bool syrk_gwg_tc(float* K, int ldk, const float* qd, const float* G, 
 #pragma unroll
           for (int k = 0; k < 8; ++k) v[k] = 0.f;
         }
+        float base[8];  // read before any store (a store may alias a later load)
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
           const int j = j0 + k;
-          if (i < n && j <= i) K[i * ldk + j] = (j == i ? qd[i] : K[j * ldk + i]) + v[k];
+          base[k] = (i < n && j <= i) ? (j == i ? qd[i] : K[j * ldk + i]) : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int j = j0 + k;
+          if (i < n && j <= i) K[i * ldk + j] = base[k] + v[k];
         }
       }
     }
   }
   fence_before_sync();
   __syncthreads();
+  return ok;
+}
+
+// ---------------------------------------------------------------------------
+// K (lower triangle, stride ldk) = Q + sum over rows[0 .. nrows) of
+// W[r] G[r]' G[r] in FP32 on the CUDA cores, for G in global memory (the
+// large variant).  The listed rows are gathered kKc at a time into shared
+// memory by one-dimensional bulk copies (the TMA engine; one copy per row of
+// round4(n) floats -- G's pad columns are zero), two buffers alternating, so
+// the next chunk streams in while the current one is multiplied.  Each thread
+// keeps the same 4 x 4 tiles of K for every chunk and adds the chunk's
+// partial sums to them (the first chunk starts from Q), so K needs no
+// barrier between chunks.  stage: two buffers of kKc * round4(n) floats,
+// 16-byte aligned; mbar: two mbarriers initialised once per CTA (count 1) and
+// used only here, *chunks the copies' chunk count so far (phase parity; updated
+// here).  G must not have been written by this CTA since its last
+// fence_async_global.  Returns false if a wait ran out (K then holds a
+// partial sum; the caller recomputes it); *fail is set if copies may still be
+// in flight after the bounded final waits.  Ends with a barrier.
+// ---------------------------------------------------------------------------
+template <int NT>
+__device__ bool syrk_gwg_staged(float* K, int ldk, const float* qd, const float* G, int ldg,
+                                const float* W, const int* rows, int nrows, int n, float* stage,
+                                uint64_t* mbar, uint32_t* chunks, int* flag, int* fail) {
+  const int tid = threadIdx.x;
+  const int rowf = round4(n);
+  const uint32_t rowb = (uint32_t)rowf * 4u;
+  const int nt = (n + 3) >> 2;
+  const int T = nt * (nt + 1) / 2;
+  const int nchunks = (nrows + kKc - 1) / kKc;
+  const uint32_t g0 = *chunks;
+  if (tid == 0) *flag = 0;
+  __syncthreads();
+  // chunk g (counted over the CTA's calls) goes to buffer g & 1 and completes
+  // that buffer's barrier phase of parity (g >> 1) & 1
+  auto issue = [&](int c) {
+    const uint32_t g = g0 + (uint32_t)c;
+    float* buf = stage + (size_t)(g & 1u) * kKc * rowf;
+    const int k0 = c * kKc, kn = min(kKc, nrows - k0);
+    mbar_expect_tx(&mbar[g & 1u], (uint32_t)kn * rowb);
+    for (int k = 0; k < kn; ++k)
+      bulk_g2s(buf + k * rowf, G + (size_t)rows[k0 + k] * ldg, rowb, &mbar[g & 1u]);
+  };
+  if (tid == 0) {
+    for (int c = 0; c < 2 && c < nchunks; ++c) issue(c);
+  }
+  int done = 0;  // chunks consumed
+  for (int c = 0; c < nchunks; ++c) {
+    const uint32_t g = g0 + (uint32_t)c;
+    if (!mbar_wait(&mbar[g & 1u], (g >> 1) & 1u)) atomicOr(flag, 1);
+    if (__syncthreads_or(*flag)) break;
+    const float* buf = stage + (size_t)(g & 1u) * kKc * rowf;
+    const int k0 = c * kKc, kn = min(kKc, nrows - k0);
+    for (int t = tid; t < T; t += NT) {
+      const float x8 = 8.0f * (float)t + 1.0f;
+      int I = (int)((x8 * rsqrtf(x8) - 1.0f) * 0.5f);
+      while ((I + 1) * (I + 2) / 2 <= t) ++I;
+      while (I * (I + 1) / 2 > t) --I;
+      const int J = t - I * (I + 1) / 2;
+      // the tile's current values, read first: Q on the first chunk, else
+      // the partial sum so far (read before any store, and early, so that
+      // their latency overlaps the products)
+      float old[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int i = 4 * I + a, j = 4 * J + b;
+          old[a][b] = (i < n && j <= i)
+                          ? (c != 0 ? K[i * ldk + j] : (j == i ? qd[i] : K[j * ldk + i]))
+                          : 0.f;
+        }
+      float acc[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+#pragma unroll 2
+      for (int k = 0; k < kn; ++k) {
+        const float w = W[rows[k0 + k]];
+        const float4 u = *reinterpret_cast<const float4*>(buf + k * rowf + 4 * I);
+        const float4 v = *reinterpret_cast<const float4*>(buf + k * rowf + 4 * J);
+        const float aw[4] = {u.x * w, u.y * w, u.z * w, u.w * w};
+        const float cv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(aw[a], cv[b], acc[a][b]);
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int i = 4 * I + a, j = 4 * J + b;
+          if (i < n && j <= i) K[i * ldk + j] = old[a][b] + acc[a][b];
+        }
+    }
+    done = c + 1;
+    __syncthreads();  // every thread is done with this buffer
+    if (tid == 0 && c + 2 < nchunks) issue(c + 2);
+  }
+  if (nchunks == 0) {
+    // no inactive rows: K = Q
+    for (int e = tid; e < n * n; e += NT) {
+      const int i = e / n, j = e - i * n;
+      if (j <= i) K[i * ldk + j] = j == i ? qd[i] : K[j * ldk + i];
+    }
+  }
+  // after a failure: wait (bounded) for the copies already issued, chunks
+  // done .. min(done + 2, nchunks) - 1
+  int bad = 0;
+  if (tid == 0) {
+    for (int c = done; c < nchunks && c < done + 2; ++c) {
+      const uint32_t g = g0 + (uint32_t)c;
+      if (!mbar_wait(&mbar[g & 1u], (g >> 1) & 1u)) bad = 1;
+    }
+    if (bad) *fail = 1;
+    *chunks = g0 + (uint32_t)min(nchunks, done + 2);
+  }
+  const bool ok = __syncthreads_or(*flag) == 0;
   return ok;
 }
 

@@ -54,6 +54,18 @@ class QPSolver:
         check(_lib.lib().qp_handle_query(self._h, ctypes.byref(out)), "qp_handle_query")
         return {k: getattr(out, k) for k, _ in _lib.HandleInfo._fields_}
 
+    def set_diag(self, diag: Optional[torch.Tensor]) -> None:
+        """Register an int32 CUDA tensor of shape [batch] that later solves and
+        backward passes through this handle fill with per-instance
+        diagnostics words (qp_handle_set_diag); None turns them off."""
+        if diag is not None:
+            if diag.dtype != torch.int32 or not diag.is_cuda or not diag.is_contiguous() \
+                    or tuple(diag.shape) != (self.batch,):
+                raise QPError(f"diag must be a contiguous int32 CUDA tensor of shape ({self.batch},)")
+        self._diag = diag  # keep it alive while registered
+        check(_lib.lib().qp_handle_set_diag(self._h, ptr(diag) if diag is not None else None),
+              "qp_handle_set_diag")
+
     @property
     def grad_cache_bytes(self) -> int:
         return int(_lib.lib().qp_grad_cache_bytes(ctypes.byref(self._dims)))
