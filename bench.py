@@ -1,11 +1,15 @@
 """Throughput of the batched implicit-complementarity QP solver on one GB300.
 
 One step = the whole hot path over one batch of synthetic QPs resident in HBM:
-Alg. 1 solve (predictor-corrector, Schur-complement Cholesky, eq. 7 line
-search, retraction) + Alg. 2 relax to kappa_relax + factor cache, then the
-Alg. 3 backward pass for an upstream gradient g.  Workload (default): 4096
-degenerate dense QPs, n=50, m=100 inequalities (half active at the optimum),
-p=10 equalities, FP32.
+Alg. 1 solve (predictor-corrector, bounded two-level Cholesky of eq. 14, eq. 7
+line search, retraction) + Alg. 2 relax to kappa_relax + factor cache, then
+the Alg. 3 backward pass for an upstream gradient g.  Workload (default): the
+largest single-GPU configuration, 256 dense QPs with n = 256 variables,
+m = 512 inequalities, p = 32 equalities, cond(Q) = 1e4, all FP32.  An
+instance counts when its solution passes the FP64 KKT bar and its gradients
+pass the FP64 consistency check of Alg. 3 (every instance) and, on a fixed
+sample, the comparison with the FP64 oracle.  The 4096 x n = 50 degenerate
+and 1024 x n = 100 differentiation workloads are measured beside it.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
 oracle on a bounded sample of the same workload instead.
@@ -29,30 +33,41 @@ sys.path.insert(0, ROOT)
 METRIC = "QP solves+grads/sec on 1 GB300 at KKT res≤1e-5 (FP32); serve p50/p99 ms"
 UNIT = "QP solves+grads/s"
 L2_BYTES = 129 * 1024 * 1024
+HEADLINE = "precision"  # the largest single-GPU configuration (256 x n=256, m=512, p=32)
+EXTRA_WORKLOADS = ("degenerate", "diff")
+TOL_X, TOL_G = 1e-4, 1e-3  # x and per-block gradient bars against the FP64 oracle
+TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rates (recipe table)
 
-# DRAM bytes per launch of the forward kernel on the default workload (4096
-# instances), scaled by instance count from the ncu capture of 1024 instances
-# summarised in profiles/forward_degenerate_n50.md; None once the kernel changes.
-FORWARD_TRAFFIC_BYTES = 4 * 33063168
+# DRAM bytes (read + write) per instance of one forward launch, from an ncu
+# capture of the current kernel (per launch / instances); None until the
+# current kernel has been captured.
+FORWARD_TRAFFIC_PER_INSTANCE = {"precision": None, "degenerate": None, "diff": None}
 
 
 def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="degenerate")
+    ap.add_argument("--workload", default=HEADLINE)
     ap.add_argument("--batch", type=int, default=None)
     ap.add_argument("--kappa-relax", type=float, default=1e-4)
     # the FP32 stopping test runs at half the 1e-5 bar so that the FP64
     # evaluation of every returned point stays within it
     ap.add_argument("--tol", type=float, default=5e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--oracle-sample", type=int, default=None,
+                    help="instances checked against the FP64 oracle (default: one per host core)")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the degenerate / diff workloads measured beside the headline")
+    ap.add_argument("--no-e2e", action="store_true")
     # implicit vs standard complementarity in FP32 over a tolerance sweep
     # (one JSON line per formulation and tolerance instead of the bench line)
     ap.add_argument("--ablation", action="store_true")
+    # App. D Table 1: first non-finite stage per instance of the standard
+    # method (eq. 8 factored as it stands) on the projection kappa sweep
+    ap.add_argument("--nan-trace", action="store_true")
     # serving (continuous batching) on the uneven-size request stream: the full
     # study prints one JSON line per load; the bench line carries a short run
     ap.add_argument("--serve", action="store_true")
@@ -90,6 +105,12 @@ def forward_flops(n, m, p, iters: np.ndarray) -> float:
     return float(2.0 * np.sum((factor + rhs) + iters.astype(np.float64) * it + factor))
 
 
+def gwg_flops(n, m, iters: np.ndarray) -> float:
+    """2 x FMA of the G'WG contraction (lower triangle, all m rows) over the
+    batch: one per factorisation (start, each iteration, final)."""
+    return float(2.0 * m * n * (n + 1) / 2 * np.sum(iters.astype(np.float64) + 2))
+
+
 def backward_bytes(n, m, p, B) -> float:
     """Algorithmic HBM bytes of Alg. 3: read the cached factor, point, W, G and
     g; write dQ, dq, dA, db, dG, dh."""
@@ -99,7 +120,16 @@ def backward_bytes(n, m, p, B) -> float:
 
 
 def fp32_alu_peak_tflops(sms=152, lanes=128, mhz=2070.0):
+    """SMs x FP32 lanes per SM x 2 FLOP per FMA x clock."""
     return sms * lanes * 2 * mhz * 1e6 / 1e12
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
 
 
 # ---------------------------------------------------------------- multi-rank (replicas)
@@ -179,7 +209,42 @@ class Clocks:
                 "samples": len(rows)}
 
 
-# ---------------------------------------------------------------- CPU oracle baseline
+# ---------------------------------------------------------------- FP64 oracle: sample check and CPU rates
+def oracle_check(data, res, grads, count, cores, kappa_relax):
+    """Solve + relax + gradients of the first `count` instances with the FP64
+    oracle on `cores` host threads; returns (per-instance pass mask of x and
+    every gradient block against the bars, errors, seconds taken)."""
+    from oracle import oracle as O
+    from paper_2605_17913_gb300.metrics import rel_err_2, rel_err_inf
+
+    sl = slice(0, count)
+    t0 = time.perf_counter()
+    ref = O.solve(data.Q[sl], data.q[sl], data.A[sl], data.b[sl], data.G[sl], data.h[sl],
+                  tol=1e-12, kappa_relax=kappa_relax, g=data.g[sl], nthreads=cores)
+    dt = time.perf_counter() - t0
+    xe = rel_err_inf(res["x"][sl], ref["x"])
+    ok = (ref["status"] == 0) & (xe <= TOL_X)
+    ge = {}
+    for k in ("dQ", "dq", "dA", "db", "dG", "dh"):
+        if ref[k].size == 0:
+            continue
+        e = rel_err_2(grads[k][sl], ref[k])
+        ge[k] = float(e.max())
+        ok &= e <= TOL_G
+    return ok, {"x_err_max": float(xe.max()), "grad_err_max": ge}, dt
+
+
+def oracle_one_core(data, kappa_relax):
+    """Seconds of the FP64 oracle (solve + relax + gradients) for one instance
+    on one host thread."""
+    from oracle import oracle as O
+
+    t0 = time.perf_counter()
+    O.solve(data.Q[:1], data.q[:1], data.A[:1], data.b[:1], data.G[:1], data.h[:1], tol=1e-12,
+            kappa_relax=kappa_relax, g=data.g[:1], nthreads=1)
+    return time.perf_counter() - t0
+
+
 def cpu_oracle_rate(workload, n_target_s, seed=0, kappa_relax=1e-4):
     """Time the FP64 oracle (solve + relax + gradients) on host cores over a
     bounded sample of the workload; returns (instances/s, cores, sample)."""
@@ -187,17 +252,19 @@ def cpu_oracle_rate(workload, n_target_s, seed=0, kappa_relax=1e-4):
     from qpgen import make_batch
 
     cores = os.cpu_count() or 1
-    probe = make_batch(workload, 2 * cores, seed=seed, start=0)
+    probe = make_batch(workload, cores, seed=seed, start=0)
     t0 = time.perf_counter()
     O.solve(probe.Q, probe.q, probe.A, probe.b, probe.G, probe.h, tol=1e-12,
             kappa_relax=kappa_relax, g=probe.g, nthreads=cores)
     dt = time.perf_counter() - t0
-    count = int(min(16384, max(2 * cores, probe.batch * n_target_s / max(dt, 1e-6))))
-    smp = make_batch(workload, count, seed=seed, start=0)
-    t0 = time.perf_counter()
-    O.solve(smp.Q, smp.q, smp.A, smp.b, smp.G, smp.h, tol=1e-12, kappa_relax=kappa_relax,
-            g=smp.g, nthreads=cores)
-    dt = time.perf_counter() - t0
+    count = probe.batch
+    if dt < 0.5 * n_target_s:
+        count = int(min(16384, max(cores, probe.batch * n_target_s / max(dt, 1e-6))))
+        smp = make_batch(workload, count, seed=seed, start=0)
+        t0 = time.perf_counter()
+        O.solve(smp.Q, smp.q, smp.A, smp.b, smp.G, smp.h, tol=1e-12, kappa_relax=kappa_relax,
+                g=smp.g, nthreads=cores)
+        dt = time.perf_counter() - t0
     return count / dt, cores, f"{count} instances of '{workload}' (first {count} of the batch), " \
                               f"solve tol 1e-12 + relax + gradients, {dt:.1f} s"
 
@@ -212,16 +279,22 @@ def run_reference(args, rank, world):
     cores = os.cpu_count() or 1
     cfg = CONFIGS[args.workload]
     B = args.batch or cfg["batch"]
-    # each step is a bounded sample of the workload sized to ~2 s of host work
-    probe = make_batch(args.workload, cores, seed=0)
+    # each step is a bounded sample of the workload: one instance per core
+    # when the whole run stays within about three minutes, fewer otherwise
+    probe = make_batch(args.workload, min(B, cores), seed=0)
     t0 = time.perf_counter()
     O.solve(probe.Q, probe.q, probe.A, probe.b, probe.G, probe.h, tol=1e-12,
             kappa_relax=args.kappa_relax, g=probe.g, nthreads=cores)
-    per = (time.perf_counter() - t0) / probe.batch
-    count = int(max(cores, min(B, 2.0 / max(per, 1e-6))))
+    t_probe = time.perf_counter() - t0
+    per_step_budget = max(2.0, 180.0 / max(1, args.steps + args.warmup))
+    if t_probe <= per_step_budget:
+        per = t_probe / probe.batch
+        count = int(max(probe.batch, min(B, per_step_budget / max(per, 1e-6))))
+    else:
+        count = max(1, int(probe.batch * per_step_budget / t_probe))
     smp = make_batch(args.workload, count, seed=0)
     run = lambda: O.solve(smp.Q, smp.q, smp.A, smp.b, smp.G, smp.h, tol=1e-12,  # noqa: E731
-                          kappa_relax=args.kappa_relax, g=smp.g, nthreads=cores)
+                          kappa_relax=args.kappa_relax, g=smp.g, nthreads=min(cores, count))
     for _ in range(args.warmup):
         run()
     t0 = time.perf_counter()
@@ -235,21 +308,157 @@ def run_reference(args, rank, world):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "batch": B, "n": cfg["n"], "m": cfg["m"],
                        "p": cfg["p"], "sample_per_step": count},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{count} instances per step of '{args.workload}'"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": min(cores, count),
+                             "kind": "oracle",
+                             "sample": f"{count} instances per step of '{args.workload}' "
+                                       f"(solve tol 1e-12 + relax + gradients)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 # ---------------------------------------------------------------- our arm
+def _fma_probe(dev):
+    """FP32 FMA-loop throughput of the device in TFLOP/s (qp_fma_probe)."""
+    import torch
+
+    from paper_2605_17913_gb300 import _lib
+
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks, threads, iters = 4 * sms, 512, 1 << 14
+    out = torch.empty(blocks * threads, device=dev)
+    stream = torch.cuda.current_stream()
+    best = None
+    for _ in range(4):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _lib.check(_lib.lib().qp_fma_probe(blocks, threads, iters, out.data_ptr(),
+                                           stream.cuda_stream), "qp_fma_probe")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    return 2.0 * 8 * blocks * threads * iters / (best / 1e3) / 1e12
+
+
+class Run:
+    """One workload's device-resident solve + relax + backward steps."""
+
+    names = ("Q", "q", "A", "b", "G", "h", "g")
+
+    def __init__(self, workload, B, rank, dev, tol, kappa_relax, gwg="fp32"):
+        import torch
+
+        from paper_2605_17913_gb300 import _lib
+        from paper_2605_17913_gb300.solver import QPSolver
+        from qpgen import make_batch
+
+        self.workload, self.B, self.dev = workload, B, dev
+        self.data = make_batch(workload, B, seed=0, start=shard_start(rank, B))
+        d = self.data
+        self.n, self.m, self.p = d.n, d.m, d.p
+        self.T = {k: torch.from_numpy(getattr(d, k)).to(dev) for k in self.names}
+        self.slv = QPSolver(B, d.n, d.p, d.m)
+        self.cache = self.slv.new_grad_cache()
+        self.settings = _lib.default_settings(tol=tol, kappa_relax=kappa_relax,
+                                              gwg_precision=gwg)
+        n, m, p = d.n, d.m, d.p
+        self.out = dict(x=torch.empty(B, n, device=dev), y=torch.empty(B, p, device=dev),
+                        z=torch.empty(B, m, device=dev), s=torch.empty(B, m, device=dev),
+                        status=torch.empty(B, dtype=torch.int32, device=dev),
+                        iters=torch.empty(B, dtype=torch.int32, device=dev),
+                        kkt=torch.empty(B, device=dev))
+        self.gout = dict(dQ=torch.empty(B, n, n, device=dev), dq=torch.empty(B, n, device=dev),
+                         dA=torch.empty(B, p, n, device=dev), db=torch.empty(B, p, device=dev),
+                         dG=torch.empty(B, m, n, device=dev), dh=torch.empty(B, m, device=dev))
+        self.stream = torch.cuda.current_stream()
+
+    def step(self, ev=None):
+        T, st = self.T, self.stream
+        if ev is not None:
+            ev[0].record(st)
+        self.slv.solve(T["Q"], T["q"], T["A"], T["b"], T["G"], T["h"], settings=self.settings,
+                       grad_cache=self.cache, out=self.out)
+        if ev is not None:
+            ev[1].record(st)
+        self.slv.backward(self.cache, T["Q"], T["A"], T["G"], T["g"], out=self.gout)
+        if ev is not None:
+            ev[2].record(st)
+
+    def timed(self, steps, warmup, flush, world=1, clocks=None):
+        """W warm-up steps, then K steps bracketed by a barrier and a device
+        synchronize; the L2 is flushed between steps (outside the events)."""
+        import torch
+
+        for _ in range(max(3, warmup)):
+            flush.zero_()
+            self.step()
+        torch.cuda.synchronize()
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+        if clocks is not None:
+            clocks.start()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(steps):
+            flush.zero_()
+            self.step(evs[k])
+        torch.cuda.synchronize()
+        self.wall = time.perf_counter() - t0
+        if world > 1:
+            torch.distributed.barrier()
+        self.clk = clocks.stop() if clocks is not None else None
+        self.fwd_ms = [e[0].elapsed_time(e[1]) for e in evs]
+        self.bwd_ms = [e[1].elapsed_time(e[2]) for e in evs]
+        self.res = {k: v.cpu().numpy() for k, v in self.out.items()}
+        self.grads = {k: v.cpu().numpy() for k, v in self.gout.items()}
+        return self
+
+    def checks(self):
+        """Per instance, in FP64 on the host: status SOLVED, scaled KKT <= 1e-5,
+        (degenerate workload) x against its known optimum x0, and the gradients'
+        consistency with Alg. 3 (metrics.gradient_report)."""
+        from paper_2605_17913_gb300.metrics import (GRAD_CONSISTENCY_BAR, GRAD_POINT_BAR,
+                                                    gradient_report, kkt_report, rel_err_inf)
+
+        d, r, g = self.data, self.res, self.grads
+        rep = kkt_report(d.Q, d.q, d.A, d.b, d.G, d.h, r["x"], r["y"], r["z"], r["s"])
+        ok = (r["status"] == 0) & (rep["scaled"] <= 1e-5)
+        if self.workload == "degenerate":
+            ok &= rel_err_inf(r["x"], d.x0) <= TOL_X
+        gr = gradient_report(d.Q, d.q, d.A, d.b, d.G, d.g, g["dQ"], g["dq"], g["dA"], g["db"],
+                             g["dG"], g["dh"])
+        gok = (gr["worst"] <= GRAD_CONSISTENCY_BAR) & (gr["point"] <= GRAD_POINT_BAR)
+        self.ok = ok & gok
+        self.check_summary = {
+            "kkt_scaled_max": float(np.max(rep["scaled"])),
+            "solved": int(np.sum(r["status"] == 0)),
+            "kkt_passed": int(np.sum(ok)),
+            "grad_consistency_passed": int(np.sum(gok)),
+            "grad_consistency_max": {k: float(np.max(gr[k])) for k in
+                                     ("adjoint", "adjoint_eq", "structure_Q", "structure_A",
+                                      "structure_G", "point")},
+            "grad_consistency_bars": {"adjoint_and_structure": GRAD_CONSISTENCY_BAR,
+                                      "point": GRAD_POINT_BAR},
+        }
+        return self.ok
+
+    def summary(self, passed):
+        fwd = statistics.mean(self.fwd_ms)
+        bwd = statistics.mean(self.bwd_ms)
+        iters = self.res["iters"]
+        return {"fwd_ms": fwd, "bwd_ms": bwd, "ms": fwd + bwd,
+                "value": passed / ((fwd + bwd) / 1e3),
+                "flops": forward_flops(self.n, self.m, self.p, iters),
+                "mean_iters": float(np.mean(iters)), "max_iters": int(np.max(iters))}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
     import __graft_entry__ as ge
-    from paper_2605_17913_gb300.metrics import kkt_report, rel_err_inf
-    from paper_2605_17913_gb300.solver import QPSolver
-    from qpgen import CONFIGS, make_batch
+    from qpgen import CONFIGS
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
@@ -260,160 +469,172 @@ def run_ours(args, rank, world, local_rank):
         ge.build()
     cfg = CONFIGS[args.workload]
     B = args.batch or cfg["batch"]
-    # weak scaling: every rank solves its own shard of B instances
-    data = make_batch(args.workload, B, seed=0, start=shard_start(rank, B))
-    n, m, p = data.n, data.m, data.p
-    names = ("Q", "q", "A", "b", "G", "h", "g")
-    T = {k: torch.from_numpy(getattr(data, k)).to(dev) for k in names}
-    slv = QPSolver(B, n, p, m)
-    cache = slv.new_grad_cache()
-    st = dict(tol=args.tol, kappa_relax=args.kappa_relax)
-    out = dict(x=torch.empty(B, n, device=dev), y=torch.empty(B, p, device=dev),
-               z=torch.empty(B, m, device=dev), s=torch.empty(B, m, device=dev),
-               status=torch.empty(B, dtype=torch.int32, device=dev),
-               iters=torch.empty(B, dtype=torch.int32, device=dev), kkt=torch.empty(B, device=dev))
-    gout = dict(dQ=torch.empty(B, n, n, device=dev), dq=torch.empty(B, n, device=dev),
-                dA=torch.empty(B, p, n, device=dev), db=torch.empty(B, p, device=dev),
-                dG=torch.empty(B, m, n, device=dev), dh=torch.empty(B, m, device=dev))
-    settings = __import__("paper_2605_17913_gb300")._lib.default_settings(**st)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream()
-
-    def step(ev=None):
-        if ev is not None:
-            ev[0].record(stream)
-        slv.solve(T["Q"], T["q"], T["A"], T["b"], T["G"], T["h"], settings=settings,
-                  grad_cache=cache, out=out)
-        if ev is not None:
-            ev[1].record(stream)
-        slv.backward(cache, T["Q"], T["A"], T["G"], T["g"], out=gout)
-        if ev is not None:
-            ev[2].record(stream)
-
-    for _ in range(max(3, args.warmup)):
-        flush.zero_()
-        step()
-    torch.cuda.synchronize()
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
-    clocks = Clocks(local_rank)
-    clocks.start()
+    props = torch.cuda.get_device_properties(dev)
+    fma_tflops = _fma_probe(dev)
+    # ---- the headline workload: timed steps, then every instance checked ----
+    run = Run(args.workload, B, rank, dev, args.tol, args.kappa_relax)
+    run.timed(args.steps, args.warmup, flush, world, Clocks(local_rank))
+    ok = run.checks()
+    cores = os.cpu_count() or 1
+    sample = None
+    if rank == 0:
+        # the oracle on a fixed sample: x and every gradient block at the bars
+        count = min(B, args.oracle_sample or cores)
+        sok, errs, t_all = oracle_check(run.data, run.res, run.grads, count, cores,
+                                        args.kappa_relax)
+        ok[:count] &= sok
+        sample = {"instances": count, "passed": int(np.sum(sok)), **errs,
+                  "bars": {"x": TOL_X, "grad": TOL_G}}
+    passed = int(np.sum(ok))
+    s = run.summary(passed)
+    head_checks, head_clk, head_wall = run.check_summary, run.clk, run.wall
     if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for k in range(args.steps):
-        flush.zero_()  # L2 flush between steps (outside the per-step events)
-        step(evs[k])
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t0
-    if world > 1:
-        torch.distributed.barrier()
-    clk = clocks.stop()
-    fwd_ms = [e[0].elapsed_time(e[1]) for e in evs]
-    bwd_ms = [e[1].elapsed_time(e[2]) for e in evs]
-    step_ms = sum(fwd_ms) + sum(bwd_ms)
-    # correctness of what was timed: every instance against the FP64 KKT bar and
-    # (degenerate workload) the known optimum; only passing instances count
-    res = {k: v.cpu().numpy() for k, v in out.items()}
-    rep = kkt_report(data.Q, data.q, data.A, data.b, data.G, data.h, res["x"], res["y"],
-                     res["z"], res["s"])
-    ok = (res["status"] == 0) & (rep["scaled"] <= 1e-5)
-    if args.workload == "degenerate":
-        ok &= rel_err_inf(res["x"], data.x0) <= 1e-4
-    for k, v in gout.items():
-        arr = v.cpu().numpy().reshape(B, -1)
-        ok &= np.all(np.isfinite(arr), axis=1)
-    passed = int(ok.sum())
-    local = {"ms": step_ms / args.steps, "passed": passed}
-    if world > 1:
-        ms_max, total_passed = combine_ranks(local["ms"], passed, dev)
+        ms_max, total_passed = combine_ranks(s["ms"], passed, dev)
     else:
-        ms_max, total_passed = local["ms"], passed
+        ms_max, total_passed = s["ms"], passed
     value = total_passed / (ms_max / 1e3)
     # ---- roofline of the dominant kernel (the forward launch) ----
-    iters = res["iters"]
-    flops = forward_flops(n, m, p, iters)
-    fwd_avg = sum(fwd_ms) / len(fwd_ms)
-    achieved = flops / (fwd_avg / 1e3) / 1e12
-    peak = fp32_alu_peak_tflops()
-    # the captured figure is per 4096-instance degenerate launch; other
-    # workloads have no capture
-    traffic = (FORWARD_TRAFFIC_BYTES * B / 4096
-               if FORWARD_TRAFFIC_BYTES is not None and args.workload == "degenerate" else None)
-    bwd_avg = sum(bwd_ms) / len(bwd_ms)
-    bwd_gbs = backward_bytes(n, m, p, B) / (bwd_avg / 1e3) / 1e9
+    clk = head_clk or {}
+    sm_mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
+    peak = fp32_alu_peak_tflops(props.multi_processor_count, 128, sm_mhz)
+    achieved = s["flops"] / (s["fwd_ms"] / 1e3) / 1e12
+    tpi = FORWARD_TRAFFIC_PER_INSTANCE.get(args.workload)
+    traffic = tpi * B if tpi is not None else None
+    bwd_gbs = backward_bytes(run.n, run.m, run.p, B) / (s["bwd_ms"] / 1e3) / 1e9
     # ---- end to end: qp_solve_backward_host, the C-ABI call on host buffers
     # (page-locked): every step copies the inputs in and the solution, status
     # and gradients out, chunked on the library's two streams ----
-    H = {k: torch.from_numpy(getattr(data, k)).pin_memory() for k in names}
-    Hout = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in
-            list(out.items()) + list(gout.items())}
-    h2d = sum(v.numel() * v.element_size() for v in H.values())
-    d2h = sum(v.numel() * v.element_size() for v in Hout.values())
+    e2e = None
+    if not args.no_e2e:
+        H = {k: torch.from_numpy(getattr(run.data, k)).pin_memory() for k in Run.names}
+        Hout = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in
+                list(run.out.items()) + list(run.gout.items())}
+        h2d = sum(v.numel() * v.element_size() for v in H.values())
+        d2h = sum(v.numel() * v.element_size() for v in Hout.values())
 
-    def e2e_step():
-        slv.solve_backward_host(H["Q"], H["q"], H["A"], H["b"], H["G"], H["h"], dl_dx=H["g"],
-                                settings=settings, out=Hout)
+        def e2e_step():
+            run.slv.solve_backward_host(H["Q"], H["q"], H["A"], H["b"], H["G"], H["h"],
+                                        dl_dx=H["g"], settings=run.settings, out=Hout)
 
-    for _ in range(2):
-        e2e_step()
-    e2e_steps = max(3, args.steps // 2)
-    if world > 1:
-        torch.distributed.barrier()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        e2e_step()
-    e2e_dt = (time.perf_counter() - t0) / e2e_steps
-    # the host path's results are the device path's, bit for bit (so the same
-    # instances pass)
-    e2e_same = all(torch.equal(Hout[k], v.cpu()) for k, v in
-                   list(out.items()) + list(gout.items()))
-    e2e_value = total_passed / e2e_dt if world == 1 else None
-    if world > 1:
-        e2e_value = total_passed / max_over_ranks(e2e_dt, dev)
+        for _ in range(2):
+            e2e_step()
+        e2e_steps = max(3, args.steps // 2)
+        if world > 1:
+            torch.distributed.barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            e2e_step()
+        e2e_dt = (time.perf_counter() - t0) / e2e_steps
+        # the host path's results are the device path's, bit for bit (so the
+        # same instances pass)
+        same = all(torch.equal(Hout[k], v.cpu()) for k, v in
+                   list(run.out.items()) + list(run.gout.items()))
+        e2e_dt = max_over_ranks(e2e_dt, dev) if world > 1 else e2e_dt
+        e2e = {"value": total_passed / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "call": "qp_solve_backward_host",
+               "host_memory": "page-locked", "steps": e2e_steps,
+               "matches_device_outputs": bool(same)}
+    # ---- the TF32 arm of the headline (tensor-core G'WG), for the tensor
+    # roofline of the contraction ----
+    tf32 = None
+    if world == 1 and args.workload == HEADLINE:
+        run.settings.gwg_precision = 1
+        run.timed(max(3, args.steps // 3), 1, flush)
+        run.settings.gwg_precision = 0
+        tok = run.checks()
+        ts = run.summary(int(np.sum(tok)))
+        bf16 = measured_peaks().get("bf16_tflops")
+        tpeak = bf16 * TF32_PER_BF16 if bf16 else 1900.0 * TF32_PER_BF16
+        tach = gwg_flops(run.n, run.m, run.res["iters"]) / (ts["fwd_ms"] / 1e3) / 1e12
+        tf32 = {"forward_ms": ts["fwd_ms"], "backward_ms": ts["bwd_ms"], "value": ts["value"],
+                "passed_kkt_and_consistency": int(np.sum(tok)),
+                "tensor_roofline": {"bound": "tensor", "achieved": tach, "peak": tpeak,
+                                    "unit": "TFLOP/s", "frac": tach / tpeak,
+                                    "work": "G'WG contraction, 2 m n(n+1)/2 FLOP per "
+                                            "factorisation, over the forward launch",
+                                    "peak_note": "measured bf16 burst x nominal TF32/BF16 "
+                                                 "ratio 1.1/2.25" +
+                                                 ("" if bf16 else " (fallback bf16 1.9 PF)")}}
+    # ---- the other configurations of the metric, measured beside it ----
+    extras = {}
+    if world == 1 and not args.no_extra and args.workload == HEADLINE:
+        for wl in EXTRA_WORKLOADS:
+            xr = Run(wl, CONFIGS[wl]["batch"], 0, dev, args.tol, args.kappa_relax)
+            xr.timed(max(5, args.steps), args.warmup, flush)
+            xs = xr.summary(int(np.sum(xr.checks())))
+            xa = xs["flops"] / (xs["fwd_ms"] / 1e3) / 1e12
+            xtpi = FORWARD_TRAFFIC_PER_INSTANCE.get(wl)
+            extras[wl] = {
+                "value": xs["value"], "unit": UNIT, "batch": xr.B, "n": xr.n, "m_ineq": xr.m,
+                "p_eq": xr.p, "passed": int(np.sum(xr.ok)), "ms_per_step": xs["ms"],
+                "forward_ms": xs["fwd_ms"], "backward_ms": xs["bwd_ms"],
+                "mean_iters": xs["mean_iters"], "checks": xr.check_summary,
+                "roofline": {"bound": "alu", "achieved": xa, "peak": peak, "unit": "TFLOP/s",
+                             "frac": xa / peak,
+                             "traffic": xtpi * xr.B if xtpi is not None else None},
+                "backward_algorithmic_gbs":
+                    backward_bytes(xr.n, xr.m, xr.p, xr.B) / (xs["bwd_ms"] / 1e3) / 1e9}
+            del xr
     if rank != 0:
         return
     serve = None
-    if world == 1 and not args.no_serve and args.workload == "degenerate":
+    if world == 1 and not args.no_serve:
         # a short run of the serving study (uneven-size stream at 0.8 of the
         # padded baseline's saturated rate); `--serve` runs the full study
-        s = run_serve_study(args, lines=False, requests=3000, fracs=(0.8,))[0]
-        serve = {"requests": s["requests"], "rate_per_s": s["rate_per_s"],
-                 "load_vs_padded_saturation": s["load_vs_padded_saturation"],
-                 "p50_ms": s["latency_ms"]["p50"], "p99_ms": s["latency_ms"]["p99"],
-                 "solves_per_s": s["solves_per_s"], "solved": s["solved"],
-                 "padded_p50_ms": s["padded_baseline"]["latency_ms"]["p50"],
-                 "padded_p99_ms": s["padded_baseline"]["latency_ms"]["p99"],
+        sv = run_serve_study(args, lines=False, requests=3000, fracs=(0.8,))[0]
+        serve = {"requests": sv["requests"], "rate_per_s": sv["rate_per_s"],
+                 "load_vs_padded_saturation": sv["load_vs_padded_saturation"],
+                 "p50_ms": sv["latency_ms"]["p50"], "p99_ms": sv["latency_ms"]["p99"],
+                 "solves_per_s": sv["solves_per_s"], "solved": sv["solved"],
+                 "padded_p50_ms": sv["padded_baseline"]["latency_ms"]["p50"],
+                 "padded_p99_ms": sv["padded_baseline"]["latency_ms"]["p99"],
                  "note": "n log-uniform in [8, 256], m = 2n, p = n // 10, 30 % with "
                          "gradients; latency = poll completion - submit"}
     cpu = None
-    if world == 1 and not args.no_cpu_baseline:
-        rate, cores, sample = cpu_oracle_rate(args.workload, args.cpu_seconds,
-                                              kappa_relax=args.kappa_relax)
-        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+    if world == 1 and not args.no_cpu_baseline and sample is not None:
+        # the oracle sample above ran one instance per host thread: its time is
+        # the all-core rate; one more instance on one thread gives the 1-core rate
+        t1 = oracle_one_core(run.data, args.kappa_relax)
+        cpu = {"value": sample["instances"] / t_all, "unit": UNIT,
+               "cores": min(cores, sample["instances"]), "kind": "oracle",
+               "sample": f"instances 0-{sample['instances'] - 1} of '{args.workload}', "
+                         f"solve tol 1e-12 + relax + gradients, {t_all:.1f} s",
+               "one_core": {"value": 1.0 / t1, "unit": UNIT,
+                            "sample": f"instance 0 on one thread, {t1:.1f} s"}}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms_max, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "batch_per_gpu": B, "n": n, "m_ineq": m,
-                   "p_eq": p, "kappa_relax": args.kappa_relax, "tol_scaled_kkt": args.tol,
+        "config": {"workload": args.workload, "batch_per_gpu": B, "n": run.n, "m_ineq": run.m,
+                   "p_eq": run.p, "kappa_relax": args.kappa_relax, "tol_scaled_kkt": args.tol,
+                   "gwg_precision": "fp32",
                    "step": "solve (Alg. 1) + relax (Alg. 2) + backward (Alg. 3)",
-                   "l2": "inputs larger than L2 and L2 flushed between steps",
+                   "l2": "L2 flushed between steps (a 258 MB buffer written outside the events)",
                    "parallelism": f"replicas x{world}", "passed": total_passed,
-                   "instances": B * world},
+                   "instances": B * world,
+                   "pass_rule": "status SOLVED, FP64 scaled KKT <= 1e-5, FP64 gradient "
+                                "consistency with Alg. 3 (every instance); x <= 1e-4 and "
+                                "every gradient block <= 1e-3 against the FP64 oracle "
+                                "(oracle_sample)"},
+        "checks": head_checks,
+        "oracle_sample": sample,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "qp_forward_kernel",
-                     "peak_note": "FP32 FMA pipe: 152 SMs x 128 lanes x 2 x 2070 MHz"},
-        "kernels": {"forward_ms": fwd_avg, "backward_ms": bwd_avg,
+                     "peak_note": f"FP32 FMA pipe: {props.multi_processor_count} SMs x 128 "
+                                  f"lanes x 2 FLOP x {sm_mhz:.0f} MHz (median SM clock "
+                                  f"sampled in the timed region)",
+                     "fma_loop_tflops": fma_tflops},
+        "kernels": {"forward_ms": s["fwd_ms"], "backward_ms": s["bwd_ms"],
                     "backward_algorithmic_gbs": bwd_gbs,
-                    "mean_iters": float(np.mean(iters)), "max_iters": int(np.max(iters))},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h), "call": "qp_solve_backward_host",
-                "host_memory": "page-locked", "matches_device_outputs": bool(e2e_same)},
+                    "mean_iters": s["mean_iters"], "max_iters": s["max_iters"]},
+        "e2e": e2e,
+        "tf32_arm": tf32,
+        "other_configs": extras or None,
         "gpu_launches": 2 * args.steps,
-        "clocks": clk,
-        "wall_s_timed_region": wall,
+        "clocks": head_clk,
+        "wall_s_timed_region": head_wall,
         "cpu_baseline": cpu,
         "serve": serve,
     }
@@ -637,8 +858,10 @@ def run_serve_study(args, lines=True, requests=None, fracs=(0.5, 0.8, 0.95)):
 def run_precision(args):
     """Config 4: 256 QPs, n = 256, m = 512, p = 32, cond(Q) = 1e4; solve +
     relax + backward with G'WG in FP32, TF32 or BF16 (tensor cores, FP32
-    sums).  Errors against FP64: the KKT measure of every instance, x and the
-    gradients against the oracle on a sample."""
+    sums), each with k = 0 .. 3 refinement sweeps of every Newton solve
+    against the FP32 system (refine_forward).  Errors against FP64: the KKT
+    measure of every instance, x and the gradients against the oracle on a
+    sample."""
     import torch
 
     from oracle import oracle as O
@@ -661,14 +884,16 @@ def run_precision(args):
     sub = make_batch("precision", len(sample), seed=0)
     ref = O.solve(sub.Q, sub.q, sub.A, sub.b, sub.G, sub.h, tol=1e-12,
                   kappa_relax=args.kappa_relax, g=sub.g, nthreads=len(sample))
-    for mode in ("fp32", "tf32", "bf16"):
+    arms = [("fp32", 0), ("fp32", 1)] + [(md, k) for md in ("tf32", "bf16") for k in (0, 1, 2, 3)]
+    for mode, k_ref in arms:
         ms = []
         for rep_ in range(args.warmup + args.steps):
             flush.zero_()
             e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
             e[0].record()
             out = slv.solve(T["Q"], T["q"], T["A"], T["b"], T["G"], T["h"], grad_cache=cache,
-                            tol=args.tol, kappa_relax=args.kappa_relax, gwg_precision=mode)
+                            tol=args.tol, kappa_relax=args.kappa_relax, gwg_precision=mode,
+                            refine_forward=k_ref)
             e[1].record()
             gr = slv.backward(cache, T["Q"], T["A"], T["G"], T["g"])
             e[2].record()
@@ -683,7 +908,8 @@ def run_precision(args):
         bwd = statistics.median(m[1] for m in ms)
         ok = (r["status"] == 0) & (rep["scaled"] <= 1e-5)
         line = {
-            "precision": "G'WG products", "gwg": mode, "workload": "precision", "batch": B,
+            "precision": "G'WG products", "gwg": mode, "refine_forward": k_ref,
+            "workload": "precision", "batch": B,
             "n": data.n, "m_ineq": data.m, "p_eq": data.p, "cond_Q": 1e4,
             "forward_ms": fwd, "backward_ms": bwd,
             "solves_grads_per_s": float(ok.sum()) / ((fwd + bwd) / 1e3),
@@ -902,11 +1128,26 @@ def run_projection(args):
 
 
 # ---------------------------------------------------------------- ablation sweep
+def _stage_counts(diag):
+    """Histogram of the first non-finite stage (diagnostics bits 0-7) and of
+    failed factorisations."""
+    from paper_2605_17913_gb300 import _lib
+
+    st = diag & _lib.QP_STAGE_MASK
+    out = {name: int(np.sum(st == code)) for code, name in _lib.QP_STAGE_NAMES.items() if code}
+    out["factor_failed"] = int(np.sum((diag & _lib.QP_DIAG_FACTOR_FAILED) != 0))
+    return out
+
+
 def run_ablation(args):
-    """Implicit vs standard complementarity, both in FP32, on one batch of the
-    workload, at solve tolerances 1e-2 .. 1e-8 (forward only, no relax).
-    Below the FP32 floor (about 1e-6 here) the sweep shows how each method
-    stops: stalled, iteration cap or numerical failure."""
+    """Implicit vs standard complementarity, all in FP32, on one batch of the
+    workload, at solve tolerances 1e-2 .. 1e-8 (forward only, no relax):
+    the implicit method; the standard method through the same bounded
+    two-level factorisation; and the standard method with eq. 8's matrix
+    Q + G' diag(z/s) G Cholesky-factored as it stands (the paper's
+    comparison).  Below the FP32 floor the sweep shows how each method stops:
+    stalled, iteration cap or numerical failure, with the first non-finite
+    stage of every failed instance."""
     import torch
 
     from paper_2605_17913_gb300.metrics import kkt_report, rel_err_inf
@@ -917,45 +1158,107 @@ def run_ablation(args):
     import __graft_entry__ as ge
 
     ge.build()
-    B = args.batch or CONFIGS[args.workload]["batch"]
-    data = make_batch(args.workload, B, seed=0)
+    wl = args.workload if args.workload != HEADLINE else "degenerate"
+    B = args.batch or CONFIGS[wl]["batch"]
+    data = make_batch(wl, B, seed=0)
     names = ("Q", "q", "A", "b", "G", "h")
     T = {k: torch.from_numpy(getattr(data, k)).cuda() for k in names}
     slv = QPSolver(B, data.n, data.p, data.m)
+    diag = torch.zeros(B, dtype=torch.int32, device="cuda")
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
-    for form in ("implicit", "standard"):
+    for form in ("implicit", "standard", "standard_schur"):
         for tol in (1e-2, 1e-3, 1e-4, 1e-5, 1e-6, 1e-7, 1e-8):
             ms = []
             for rep in range(4):
+                # timed without the stage tests; the last pass records them
+                slv.set_diag(diag if rep == 3 else None)
                 flush.zero_()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record()
                 out = slv.solve(*(T[k] for k in names), tol=tol, formulation=form)
                 e1.record()
                 torch.cuda.synchronize()
-                if rep > 0:
+                if 0 < rep < 3:
                     ms.append(e0.elapsed_time(e1))
+            slv.set_diag(None)
             r = {k: v.cpu().numpy() for k, v in out.items()}
             st, it = r["status"], r["iters"]
             rep = kkt_report(data.Q, data.q, data.A, data.b, data.G, data.h, r["x"], r["y"],
                              r["z"], r["s"])
             finite = np.isfinite(r["x"]).all(axis=1)
-            xerr = rel_err_inf(r["x"][finite], data.x0[finite]) if finite.any() else np.array([])
+            ref_x = data.x0 if wl == "degenerate" else None
+            xerr = (rel_err_inf(r["x"][finite], ref_x[finite])
+                    if ref_x is not None and finite.any() else np.array([]))
             fwd = statistics.median(ms)
             line = {
-                "ablation": "complementarity", "workload": args.workload, "batch": B,
+                "ablation": "complementarity", "workload": wl, "batch": B,
                 "formulation": form, "tol": tol, "dtype": "f32",
                 "solved": float(np.mean(st == 0)), "stalled": float(np.mean(st == 2)),
                 "max_iter": float(np.mean(st == 1)), "numerical": float(np.mean(st == 3)),
                 "nan_rate": float(np.mean(~finite)),
+                "first_nonfinite_stage": _stage_counts(diag.cpu().numpy()),
                 "iters_median": float(np.median(it)), "iters_p95": float(np.percentile(it, 95)),
-                "kkt_scaled_median": float(np.median(rep["scaled"])),
-                "kkt_scaled_max": float(np.max(rep["scaled"])),
+                "kkt_scaled_median": float(np.median(rep["scaled"][finite])) if finite.any()
+                else None,
+                "kkt_scaled_max": float(np.max(rep["scaled"][finite])) if finite.any() else None,
                 "x_err_median": float(np.median(xerr)) if xerr.size else None,
                 "x_err_max": float(np.max(xerr)) if xerr.size else None,
                 "forward_ms": fwd, "solves_per_s": float(np.sum(st == 0)) / (fwd / 1e3),
             }
             print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- NaN trace (App. D, Table 1)
+def run_nan_trace(args):
+    """The first non-finite stage of each instance on App. D's kappa sweep
+    (n = 20, 25 inequalities, 10 / 12 / 15 active rows, kappa_relax = 1e-2 ..
+    1e-9, tol = min(kappa_relax, 1e-4)), 63 instances per row (seeds 0-2 x 21
+    displacements d), solve + relax + backward in FP32 with the standard
+    method (eq. 8's matrix factored as it stands) and with the implicit
+    method.  Columns follow the paper's table: scaling, predictor, centering,
+    corrector, line search, relax, backward, and instances whose gradients are
+    not finite without an attributed stage (N/A)."""
+    import torch
+
+    from paper_2605_17913_gb300 import _lib
+    from paper_2605_17913_gb300.solver import QPSolver
+
+    torch.cuda.set_device(0)
+    import __graft_entry__ as ge
+
+    ge.build()
+    ds = np.logspace(-2, 2, 21)
+    n, m = 20, 25
+    for form in ("standard_schur", "implicit"):
+        for m_act in (10, 12, 15):
+            data, _ = _projection_batch(n, m, m_act, (0, 1, 2), 1, ds)
+            B = data["Q"].shape[0]
+            T = {k: torch.from_numpy(v).cuda() for k, v in data.items()}
+            A = torch.zeros(B, 0, n, device="cuda")
+            b = torch.zeros(B, 0, device="cuda")
+            for kr in (1e-2, 1e-3, 1e-4, 1e-5, 1e-6, 1e-7, 1e-8, 1e-9):
+                slv = QPSolver(B, n, 0, m)
+                diag = torch.zeros(B, dtype=torch.int32, device="cuda")
+                slv.set_diag(diag)
+                cache = slv.new_grad_cache()
+                out = slv.solve(T["Q"], T["q"], A, b, T["G"], T["h"], grad_cache=cache,
+                                tol=min(kr, 1e-4), kappa_relax=kr, max_iter=100,
+                                formulation=form)
+                gr = slv.backward(cache, T["Q"], A, T["G"], T["g"])
+                torch.cuda.synchronize()
+                dg = diag.cpu().numpy()
+                finite = torch.isfinite(gr["dq"]).all(dim=1).cpu().numpy()
+                st = out["status"].cpu().numpy()
+                cnt = _stage_counts(dg)
+                na = int(np.sum(~finite & ((dg & _lib.QP_STAGE_MASK) == 0)))
+                print(json.dumps({
+                    "nan_trace": form, "n": n, "m_ineq": m, "active": m_act, "kappa_relax": kr,
+                    "tol": min(kr, 1e-4), "instances": B, "dtype": "f32",
+                    "first_nonfinite_stage": cnt, "no_attribution": na,
+                    "nonfinite_gradients": int(np.sum(~finite)),
+                    "numerical": int(np.sum(st == _lib.QP_NUMERICAL)),
+                    "solved": int(np.sum(st == 0))}), flush=True)
+                slv.close()
 
 
 def main():
@@ -977,6 +1280,9 @@ def main():
         return
     if args.projection:
         run_projection(args)
+        return
+    if args.nan_trace:
+        run_nan_trace(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
