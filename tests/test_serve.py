@@ -1,14 +1,19 @@
 """Serving (qp_serve_*): continuous batching of single requests of uneven
 sizes.  Each served result must equal the same request solved alone
-(qp_solve_batch / qp_backward_batch of batch 1) bit for bit; requests that
-arrive while others run must start and finish without waiting for them;
-admission must respect the device arena."""
+(qp_solve_batch / qp_backward_batch of batch 1) bit for bit and meet the
+FP64 oracle's bars (x, KKT, every gradient block); requests that arrive
+while others run must start and finish without waiting for them; admission
+must respect the device arena; a wait that runs out, a client that stops
+collecting and a request whose Q is not positive definite must leave every
+other request untouched."""
 import time
 
 import numpy as np
 import pytest
 import torch
 
+from oracle import oracle as O
+from paper_2605_17913_gb300.metrics import kkt_report, rel_err_2, rel_err_inf
 from qpgen import make_instance
 
 pytestmark = pytest.mark.gpu
@@ -53,20 +58,51 @@ def _submit(srv, d, grad):
                       dl_dx=d["g"] if grad else None)
 
 
-def test_served_results_equal_solo_bitwise():
+# every kernel class: one warp / 128 / 512 threads on chip, the large variant;
+# with and without gradients
+SIZES = [(8, 16, 0, False), (10, 20, 1, True), (33, 66, 3, True), (50, 100, 5, False),
+         (72, 144, 7, True), (90, 180, 9, False), (90, 180, 9, True), (130, 260, 13, True),
+         (200, 400, 20, False), (200, 400, 20, True), (256, 512, 25, True)]
+
+
+@pytest.fixture(scope="module")
+def served():
     from paper_2605_17913_gb300.serve import QPServer
 
-    sizes = [(8, 16, 0, False), (10, 20, 1, True), (33, 66, 3, True), (50, 100, 5, False),
-             (72, 144, 7, True), (90, 180, 9, False), (130, 260, 13, True),
-             (200, 400, 20, False), (256, 512, 25, True)]
-    inst = [_inst(i, n, m, p) for i, (n, m, p, _) in enumerate(sizes)]
+    inst = [_inst(i, n, m, p) for i, (n, m, p, _) in enumerate(SIZES)]
     srv = QPServer(hbm_budget_bytes=512 << 20, tol=SOLVER_TOL)
     try:
-        tickets = [_submit(srv, d, g) for d, (_, _, _, g) in zip(inst, sizes)]
+        tickets = [_submit(srv, d, g) for d, (_, _, _, g) in zip(inst, SIZES)]
         got = [srv.wait(t, 120000) for t in tickets]
     finally:
         srv.close()
-    for d, (n, m, p, grad), r in zip(inst, sizes, got):
+    return inst, got
+
+
+def test_served_results_match_oracle(served):
+    """Every served result against the FP64 oracle at the method's bars:
+    scaled KKT <= 1e-5, x <= 1e-4, and (requests with gradients) every
+    gradient block <= 1e-3 at the relaxed point."""
+    inst, got = served
+    for d, (n, m, p, grad), r in zip(inst, SIZES, got):
+        assert r["status"] == 0, (n, r["status"])
+        one = lambda k: d[k][None]  # noqa: E731
+        ref = O.solve(one("Q"), one("q"), one("A"), one("b"), one("G"), one("h"), tol=1e-12,
+                      kappa_relax=1e-4 if grad else None, g=one("g") if grad else None)
+        rep = kkt_report(one("Q"), one("q"), one("A"), one("b"), one("G"), one("h"),
+                         r["x"][None], r["y"][None], r["z"][None], r["s"][None])
+        assert rep["scaled"][0] <= 1e-5, (n, rep["scaled"][0])
+        assert rel_err_inf(r["x"][None], ref["x"])[0] <= 1e-4, n
+        if grad:
+            for k in GRAD_KEYS:
+                if ref[k].size:
+                    e = rel_err_2(r[k][None], ref[k])[0]
+                    assert e <= 1e-3, (n, k, e)
+
+
+def test_served_results_equal_solo_bitwise(served):
+    inst, got = served
+    for d, (n, m, p, grad), r in zip(inst, SIZES, got):
         ref = _solo(d, grad)
         assert r["status"] == 0 and ref["status"] == 0, (n, r["status"])
         assert r["iters"] == ref["iters"]
@@ -125,3 +161,73 @@ def test_admission_by_arena_memory():
     ref = _solo(inst[7], True)
     for k in ("x",) + GRAD_KEYS:
         np.testing.assert_array_equal(got[7][k], ref[k])
+
+
+def test_wait_times_out_and_the_request_survives():
+    """qp_serve_wait returns QP_ETIMEOUT when its bound runs out before the
+    request completes; the request is still collected afterwards, intact."""
+    from paper_2605_17913_gb300.serve import QPServer
+
+    d = _inst(400, 256, 512, 25)
+    srv = QPServer(hbm_budget_bytes=256 << 20, tol=SOLVER_TOL)
+    try:
+        t = _submit(srv, d, True)
+        with pytest.raises(Exception, match="not done after 0 ms"):
+            srv.wait(t, 0)
+        r = srv.wait(t, 120000)
+    finally:
+        srv.close()
+    assert r["status"] == 0
+    ref = _solo(d, True)
+    for k in ("x",) + GRAD_KEYS:
+        np.testing.assert_array_equal(r[k], ref[k])
+
+
+def test_client_that_stops_collecting_does_not_block_others():
+    """Requests a client never collects stay completed on the host side;
+    another client's requests, submitted after them, run and are collected
+    as usual (results bit for bit those of solo runs)."""
+    from paper_2605_17913_gb300.serve import QPServer
+
+    idle = [_inst(500 + i, 40, 80, 4) for i in range(24)]
+    busy = [_inst(600 + i, 40, 80, 4) for i in range(24)]
+    srv = QPServer(hbm_budget_bytes=64 << 20, max_inflight=2, tol=SOLVER_TOL)
+    try:
+        for d in idle:
+            _submit(srv, d, True)  # never collected
+        tb = [_submit(srv, d, i % 2 == 0) for i, d in enumerate(busy)]
+        rb = [srv.wait(t, 120000) for t in tb]
+    finally:
+        srv.close()  # drops the uncollected tickets
+    assert all(r["status"] == 0 for r in rb)
+    for i in (0, 1, 23):
+        ref = _solo(busy[i], i % 2 == 0)
+        for k in ("x", "z") + (GRAD_KEYS if i % 2 == 0 else ()):
+            np.testing.assert_array_equal(rb[i][k], ref[k])
+
+
+def test_non_positive_definite_request_is_isolated():
+    """A request whose Q is not positive definite (K = Q + G'G indefinite at
+    the start) ends QP_NUMERICAL; the requests around it, in the same
+    launches, are solved exactly as alone."""
+    from paper_2605_17913_gb300 import _lib
+    from paper_2605_17913_gb300.serve import QPServer
+
+    good = [_inst(700 + i, 10, 20, 1) for i in range(6)]
+    bad = dict(_inst(710, 10, 20, 1))
+    bad["Q"] = (-10.0 * np.eye(10)).astype(np.float32)
+    srv = QPServer(hbm_budget_bytes=64 << 20, max_inflight=1, tol=SOLVER_TOL)
+    try:
+        tg = [_submit(srv, d, True) for d in good[:3]]
+        tbad = _submit(srv, bad, True)
+        tg += [_submit(srv, d, True) for d in good[3:]]
+        rg = [srv.wait(t, 60000) for t in tg]
+        rbad = srv.wait(tbad, 60000)
+    finally:
+        srv.close()
+    assert rbad["status"] == _lib.QP_NUMERICAL
+    for d, r in zip(good, rg):
+        assert r["status"] == 0
+        ref = _solo(d, True)
+        for k in ("x", "y", "z", "s") + GRAD_KEYS:
+            np.testing.assert_array_equal(r[k], ref[k])
