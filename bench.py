@@ -72,7 +72,7 @@ def parse(argv=None):
     # study prints one JSON line per load; the bench line carries a short run
     ap.add_argument("--serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=None)
-    ap.add_argument("--serve-pool", type=int, default=2048)
+    ap.add_argument("--serve-pool", type=int, default=8192)
     ap.add_argument("--no-serve", action="store_true")
     # G'WG in FP32 vs TF32 / BF16 tensor cores on the n = 256 workload
     # (one JSON line per mode instead of the bench line)
@@ -827,7 +827,9 @@ def run_serve_study(args, lines=True, requests=None, fracs=(0.5, 0.8, 0.95)):
         arrivals -= arrivals[0]
         lat, slat, mk, st, res = _serve_run(srv, pool, order, arrivals, verify=256)
         plat = _padded_latency(arrivals, times, group)
-        # FP64 check of a sample of the served results
+        # FP64 check of a sample of the served results: the KKT measure of
+        # the first 256, and (full study) x and gradients of the first 24
+        # against the FP64 oracle
         kmax = 0.0
         for i, r in res.items():
             d = pool[order[i]]
@@ -835,6 +837,27 @@ def run_serve_study(args, lines=True, requests=None, fracs=(0.5, 0.8, 0.95)):
                              d["G"][None], d["h"][None], r["x"][None], r["y"][None],
                              r["z"][None], r["s"][None])
             kmax = max(kmax, float(rep["scaled"][0]))
+        oracle = None
+        if lines:
+            from oracle import oracle as O
+            from paper_2605_17913_gb300.metrics import rel_err_2, rel_err_inf
+
+            xe, ge, npass = [], [], 0
+            for i in sorted(res)[:24]:
+                r, d = res[i], pool[order[i]]
+                one = lambda k: d[k][None]  # noqa: E731
+                ref = O.solve(one("Q"), one("q"), one("A"), one("b"), one("G"), one("h"),
+                              tol=1e-12, kappa_relax=1e-4 if d["grad"] else None,
+                              g=one("g") if d["grad"] else None)
+                ex = float(rel_err_inf(r["x"][None], ref["x"])[0])
+                eg = max((float(rel_err_2(r[k][None], ref[k])[0]) for k in
+                          ("dQ", "dq", "dA", "db", "dG", "dh") if d["grad"] and ref[k].size),
+                         default=0.0)
+                xe.append(ex)
+                ge.append(eg)
+                npass += int(ex <= 1e-4 and eg <= 1e-3)
+            oracle = {"requests": len(xe), "passed_x_1e-4_grad_1e-3": npass,
+                      "x_err_max": max(xe), "grad_err_max": max(ge)}
         line = {
             "serve": "continuous batching", "requests": N, "distinct_instances": P,
             "arrival": "poisson", "rate_per_s": lam, "load_vs_padded_saturation": frac,
@@ -842,7 +865,7 @@ def run_serve_study(args, lines=True, requests=None, fracs=(0.5, 0.8, 0.95)):
                            "mean": float(lat.mean() * 1e3)},
             "server_latency_ms": {"p50": _pctl(slat, 50), "p99": _pctl(slat, 99)},
             "solves_per_s": N / mk, "solved": float(np.mean(st == 0)),
-            "kkt_scaled_max_sample": kmax,
+            "kkt_scaled_max_sample": kmax, "oracle_sample": oracle,
             "padded_baseline": {"latency_ms": {"p50": _pctl(plat, 50), "p99": _pctl(plat, 99)},
                                 "group": group, "saturated_solves_per_s": pad_sat},
             "served_saturated_solves_per_s": served_sat,

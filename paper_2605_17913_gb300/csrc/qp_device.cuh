@@ -449,6 +449,12 @@ __host__ __device__ constexpr int pbw_group(int pw) { return 4 * pw + 4; }
 __host__ __device__ inline int pbw_floats(int rows, int pw) {
   return ((rows + 3) / 4 + 1) * pbw_group(pw);
 }
+// rows of Pbw that a factorisation of n pivots bordered by nB rows stores: the
+// rows below the first diagonal block, rounded to a 4-row group, the border
+// rows and the pad rows zeroed after them
+__host__ __device__ inline int pbw_rows(int n, int nB, int pw) {
+  return (n > pw ? n - pw : 0) + nB + 8;
+}
 template <int PW>
 __device__ __forceinline__ int pbw_off(int r) {
   return (r >> 2) * pbw_group(PW) + (r & 3) * PW;
@@ -457,7 +463,8 @@ __device__ __forceinline__ int pbw_off(int r) {
 template <int NT, int PW>
 __device__ bool panel_factor_wide(float* M, int ld, int j0, int jb, float* dinv, float* A,
                                   int lda, int rowA0, int nA, float* B, int ldb, int nB,
-                                  float* Pb, float* fb) {
+                                  float* Pb, float* fb, unsigned long long* sub = nullptr) {
+  const long long tp0 = sub ? clock64() : 0;
   static_assert(PW != 32 || NT >= 64, "the staged panel needs warps beside warp 0");
   const int nA4 = (nA + 3) & ~3;
   const int N = nA + nB;
@@ -499,16 +506,34 @@ __device__ bool panel_factor_wide(float* M, int ld, int j0, int jb, float* dinv,
     }
   } else if (PW == 32) {
     // meanwhile the other warps stage the panel's rows in Pb, one row per
-    // warp and lane = column: coalesced 128-byte reads of global memory
-    // (one row per thread would touch 32 rows per warp load)
-    for (int rr = w - 1; rr < N; rr += NT / 32 - 1) {
-      const bool inA = rr < nA;
-      const float* row = inA ? A + (rowA0 + rr) * lda + j0 : B + (rr - nA) * ldb + j0;
-      Pb[pbw_off<PW>(inA ? rr : nA4 + (rr - nA)) + lane] = lane < jb ? row[lane] : 0.0f;
+    // warp instruction and lane = column: coalesced 128-byte reads of global
+    // memory (one row per thread would touch 32 rows per warp load); eight
+    // rows' loads are in flight before their stores
+    constexpr int kRows = 8;
+    for (int r0 = (w - 1) * kRows; r0 < N; r0 += (NT / 32 - 1) * kRows) {
+      float v[kRows];
+#pragma unroll
+      for (int k = 0; k < kRows; ++k) {
+        const int rr = r0 + k;
+        v[k] = 0.0f;
+        if (rr < N && lane < jb)
+          v[k] = rr < nA ? A[(rowA0 + rr) * lda + j0 + lane] : B[(rr - nA) * ldb + j0 + lane];
+      }
+#pragma unroll
+      for (int k = 0; k < kRows; ++k) {
+        const int rr = r0 + k;
+        if (rr < N) Pb[pbw_off<PW>(rr < nA ? rr : nA4 + (rr - nA)) + lane] = v[k];
+      }
     }
   }
   const bool all_ok = __syncthreads_and(okw) != 0;
-  for (int rr = tid; rr < N; rr += NT) {
+  const long long tp1 = sub ? clock64() : 0;
+  // one row per thread; within each warp's 32 rows, lane l takes row
+  // 4 (l % 8) + l / 8, so that the 8 lanes of a shared-memory phase read rows
+  // of 8 different 4-row groups of Pb (bank-conflict-free float4 accesses)
+  for (int r0 = w * 32; r0 < N; r0 += NT) {
+    const int rr = r0 + ((lane & 7) << 2) + (lane >> 3);
+    if (rr >= N) continue;
     const bool inA = rr < nA;
     float* row = inA ? A + (rowA0 + rr) * lda + j0 : B + (rr - nA) * ldb + j0;
     float4* pr = reinterpret_cast<float4*>(Pb + pbw_off<PW>(inA ? rr : nA4 + (rr - nA)));
@@ -549,6 +574,11 @@ __device__ bool panel_factor_wide(float* M, int ld, int j0, int jb, float* dinv,
     if (pad) Pb[pbw_off<PW>(r) + c] = 0.0f;
   }
   __syncthreads();
+  if (sub && threadIdx.x == 0) {
+    // tracing builds: (diagonal block || row staging), then the row solves
+    atomicAdd(&sub[0], (unsigned long long)(tp1 - tp0));
+    atomicAdd(&sub[1], (unsigned long long)(clock64() - tp1));
+  }
   if (PW == 32) {
     // write the solved rows back, one row per warp (coalesced); the trailing
     // update that follows reads Pb only and writes other columns, so no
@@ -659,14 +689,14 @@ __device__ __noinline__ bool blocked_cholesky_bordered(float* K, int ldk, int n,
                                           float* C, int ldc, float* dinv, float* Pb,
                                           unsigned long long* sub = nullptr) {
   bool ok = true;
-  float* const fb = PW > 8 ? Pb + pbw_floats(n + nB + 4, PW) : nullptr;
+  float* const fb = PW > 8 ? Pb + pbw_floats(pbw_rows(n, nB, PW), PW) : nullptr;
   for (int j0 = 0; j0 < n; j0 += PW) {
     const int jb = min(PW, n - j0);
     const int nK = n - j0 - jb;
     const long long c0 = sub ? clock64() : 0;
     if constexpr (PW > 8)
       ok = panel_factor_wide<NT, PW>(K, ldk, j0, jb, dinv, K, ldk, j0 + jb, nK, Y, ldy, nB, Pb,
-                                     fb) &&
+                                     fb, sub ? sub + 4 : nullptr) &&
            ok;
     else
       ok = panel_factor_trsm<NT>(K, ldk, j0, jb, dinv, K, ldk, j0 + jb, nK, Y, ldy, nB, Pb) &&

@@ -72,8 +72,9 @@ struct FLayout {
   int o_b, o_y, o_re;
   int o_cdinv, o_D, o_ua, o_ub, o_act;
   int o_h, o_z, o_s, o_ri, o_bz, o_bs, o_ea, o_eb, o_ta, o_tb, o_pos, o_ina;
-  int o_rf;  // refinement of the folded solves (large variant): saved right-hand
-             // sides, the solution and G't for both columns (6 nv + 4 fv floats)
+  int o_rf;   // refinement of the folded solves (large variant): the saved
+              // right-hand sides of both columns (2 nv + 2 fv floats)
+  int o_rfs;  // its per-sweep scratch in the union region (4 nv + 2 fv floats)
   int total;
 };
 
@@ -121,15 +122,18 @@ __host__ __device__ inline FLayout make_fwd_layout(int n, int m, int p, int amax
     // staging buffers of G'WG, 128-byte aligned
     if (split) o = (o + 31) & ~31;
     const int base = o;
-    const int rows = n + L.fmax + 2 + 4;
     const int pw = panel_width(nthreads, split);
-    int pb = pw > 8 ? pbw_floats(rows, pw) + pw * pw : pb_floats(rows);
+    int pb = pw > 8 ? pbw_floats(pbw_rows(n, L.fmax + 2, pw), pw) + pw * pw
+                    : pb_floats(n + L.fmax + 2 + 4);
     pb = round4(pb);
     if (split && pb < 2 * tc::stage_bytes(n, 4) / 4) pb = 2 * tc::stage_bytes(n, 4) / 4;
     L.o_Pb = base;
     L.o_col = take(2 * nthreads);
     L.o_ta = take(L.mv); L.o_tb = take(L.mv); L.o_eb = take(L.mv);
     L.o_tn = take(L.nv);
+    // (large variant) the refinement sweep's dx, mu and G't of both columns,
+    // live only within a sweep, after the factorisation
+    L.o_rfs = take(split ? 4 * L.nv + 2 * L.fv : 0);
     if (o < base + pb) o = base + pb;
   }
   L.o_q = take(L.nv); L.o_x = take(L.nv); L.o_rt = take(L.nv); L.o_dinv = take(L.nv);
@@ -141,7 +145,7 @@ __host__ __device__ inline FLayout make_fwd_layout(int n, int m, int p, int amax
   L.o_ea = take(L.mv);
   L.o_pos = take(L.mv);
   L.o_ina = take(L.mv);
-  L.o_rf = take(split ? 6 * L.nv + 4 * L.fv : 0);
+  L.o_rf = take(split ? 2 * L.nv + 2 * L.fv : 0);
   L.total = o;
   return L;
 }
@@ -427,8 +431,8 @@ struct Solver {
     if (kBig && fwd_state.refine > 0) {
       // keep both columns' right-hand sides for the refinement sweeps
       QP_ARR(rf);
-      float* const r1s = rf + 4 * L.nv + 2 * L.fv;
-      float* const r2s = r1s + 2 * L.nv;
+      float* const r1s = rf;
+      float* const r2s = rf + 2 * L.nv;
       for (int e = t; e < 2 * n; e += NT) {
         const int c = e / n, i = e - c * n;
         r1s[c * L.nv + i] = R[c * L.ldx + i];
@@ -478,9 +482,14 @@ struct Solver {
       if (!tc_done && !fwd_state.async_lost) {
         // FP32 products from rows staged in shared memory by bulk copies
         float* stage = fwd_dyn + L.o_Pb;  // dead during the factorisation
+#ifdef QP_PHASE_TIMERS
+        unsigned long long* const ssub = fwd_state.timers ? fwd_state.timers + PH_COUNT + 8 : nullptr;
+#else
+        unsigned long long* const ssub = nullptr;
+#endif
         tc_done = tc::syrk_gwg_staged<NT>(K, L.ldk, qd, G, L.ldg, ea, ina, fwd_state.ni, L.n,
                                           stage, fwd_state.mbar_g, &fwd_state.g_chunks,
-                                          &fwd_state.tc_flag, &fwd_state.async_lost);
+                                          &fwd_state.tc_flag, &fwd_state.async_lost, ssub);
         if (!tc_done && threadIdx.x == 0) fwd_state.diag |= QP_DIAG_STAGE_FALLBACK;
         __syncthreads();
       }
@@ -695,14 +704,14 @@ struct Solver {
     const FLayout& L = fwd_state.L;
     QP_BIG(K); QP_ARR(qd); QP_BIG(G); QP_ARR(R); QP_ARR(ua); QP_ARR(ub); QP_ARR(ea);
     QP_ARR(eb); QP_ARR(bz); QP_ARR(bs); QP_ARR(D); QP_ARR(ta); QP_ARR(tb); QP_ARR(col);
-    QP_ARR(rf); QP_IARR(pos); QP_IARR(act);
+    QP_ARR(rf); QP_ARR(rfs); QP_IARR(pos); QP_IARR(act);
     const float* const A = fwd_state.gA;
     const int n = L.n, m = L.m, p = L.p, t = threadIdx.x, a = fwd_state.a, nf = fwd_state.nf;
-    float* const dx = rf;                  // 2 nv: the solution's dx, both columns
-    float* const mu = rf + 2 * L.nv;       // 2 fv: its mu
-    float* const u = mu + 2 * L.fv;        // 2 nv: G't
-    const float* const r1s = u + 2 * L.nv;   // 2 nv: rhs1 (fold_rhs)
-    const float* const r2s = r1s + 2 * L.nv; // 2 fv: rhs2
+    float* const dx = rfs;                  // 2 nv: the solution's dx, both columns
+    float* const mu = rfs + 2 * L.nv;       // 2 fv: its mu
+    float* const u = mu + 2 * L.fv;         // 2 nv: G't
+    const float* const r1s = rf;            // 2 nv: rhs1 (fold_rhs)
+    const float* const r2s = rf + 2 * L.nv; // 2 fv: rhs2
     for (int e = t; e < 2 * n; e += NT) {
       const int c = e / n, i = e - c * n;
       dx[c * L.nv + i] = R[c * L.ldx + i];
@@ -795,8 +804,16 @@ struct Solver {
         const int i = u;
         // (Q x)_i from K's strict upper triangle and the diagonal qd
         float qx = qd[i] * x[i];
-        for (int j = 0; j < i; ++j) qx = fmaf(K[j * L.ldk + i], x[j], qx);
-        for (int j = i + 1; j < n; ++j) qx = fmaf(K[i * L.ldk + j], x[j], qx);
+        if constexpr (kBig) {
+          // K in global memory: sixteen loads in flight per thread
+#pragma unroll 16
+          for (int j = 0; j < i; ++j) qx = fmaf(K[j * L.ldk + i], x[j], qx);
+#pragma unroll 16
+          for (int j = i + 1; j < n; ++j) qx = fmaf(K[i * L.ldk + j], x[j], qx);
+        } else {
+          for (int j = 0; j < i; ++j) qx = fmaf(K[j * L.ldk + i], x[j], qx);
+          for (int j = i + 1; j < n; ++j) qx = fmaf(K[i * L.ldk + j], x[j], qx);
+        }
         float aty = 0.f;
         for (int k = 0; k < p; ++k) aty = fmaf(__ldg(A + k * n + i), y[k], aty);
         const float r = qx + q[i] + tn[i] + aty;
@@ -1638,9 +1655,17 @@ cudaError_t ensure_forward_smem(size_t smem) {
   std::lock_guard<std::mutex> lock(mu);
   if (configured == 0) {
     const size_t maxdyn = 227 * 1024 - fwd::kStaticSmem;
-    const cudaError_t e = cudaFuncSetAttribute(
+    cudaError_t e = cudaFuncSetAttribute(
         fwd::qp_forward_kernel<NT, kBig>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)maxdyn);
     if (e != cudaSuccess) return e;
+    if (kBig && NT == 256) {
+      // two CTAs per SM need the largest shared-memory carveout; without the
+      // preference the runtime may configure less and keep one CTA per SM
+      e = cudaFuncSetAttribute(fwd::qp_forward_kernel<NT, kBig>,
+                               cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared);
+      if (e != cudaSuccess) return e;
+    }
     configured = maxdyn;
   }
   return smem <= configured ? cudaSuccess : cudaErrorInvalidValue;

@@ -308,7 +308,8 @@ __device__ bool syrk_gwg_tc(float* K, int ldk, const float* qd, const float* G, 
 // large variant).  The listed rows are gathered kKc at a time into shared
 // memory by one-dimensional bulk copies (the TMA engine; one copy per row of
 // round4(n) floats -- G's pad columns are zero), two buffers alternating, so
-// the next chunk streams in while the current one is multiplied.  Each thread
+// the next chunk streams in while the current one is multiplied; each arrived
+// row is scaled by sqrt(W) once.  Each thread
 // keeps the same 4 x 4 tiles of K for every chunk and adds the chunk's
 // partial sums to them (the first chunk starts from Q), so K needs no
 // barrier between chunks.  stage: two buffers of kKc * round4(n) floats,
@@ -322,7 +323,8 @@ __device__ bool syrk_gwg_tc(float* K, int ldk, const float* qd, const float* G, 
 template <int NT>
 __device__ bool syrk_gwg_staged(float* K, int ldk, const float* qd, const float* G, int ldg,
                                 const float* W, const int* rows, int nrows, int n, float* stage,
-                                uint64_t* mbar, uint32_t* chunks, int* flag, int* fail) {
+                                uint64_t* mbar, uint32_t* chunks, int* flag, int* fail,
+                                unsigned long long* sub = nullptr) {
   const int tid = threadIdx.x;
   const int rowf = round4(n);
   const uint32_t rowb = (uint32_t)rowf * 4u;
@@ -348,10 +350,20 @@ __device__ bool syrk_gwg_staged(float* K, int ldk, const float* qd, const float*
   int done = 0;  // chunks consumed
   for (int c = 0; c < nchunks; ++c) {
     const uint32_t g = g0 + (uint32_t)c;
+    const long long ts0 = sub ? clock64() : 0;
     if (!mbar_wait(&mbar[g & 1u], (g >> 1) & 1u)) atomicOr(flag, 1);
     if (__syncthreads_or(*flag)) break;
-    const float* buf = stage + (size_t)(g & 1u) * kKc * rowf;
+    const long long ts1 = sub ? clock64() : 0;
+    float* const buf = stage + (size_t)(g & 1u) * kKc * rowf;
     const int k0 = c * kKc, kn = min(kKc, nrows - k0);
+    // scale the chunk's rows by sqrt(W) once (W <= tau on the inactive rows),
+    // so the products below need no per-row weight
+    for (int e = tid; e < kn * rowf; e += NT) {
+      const int k = e / rowf;
+      buf[e] *= sqrtf(W[rows[k0 + k]]);
+    }
+    __syncthreads();
+    const long long ts2 = sub ? clock64() : 0;
     for (int t = tid; t < T; t += NT) {
       const float x8 = 8.0f * (float)t + 1.0f;
       int I = (int)((x8 * rsqrtf(x8) - 1.0f) * 0.5f);
@@ -376,12 +388,11 @@ __device__ bool syrk_gwg_staged(float* K, int ldk, const float* qd, const float*
       for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-#pragma unroll 2
+#pragma unroll 4
       for (int k = 0; k < kn; ++k) {
-        const float w = W[rows[k0 + k]];
         const float4 u = *reinterpret_cast<const float4*>(buf + k * rowf + 4 * I);
         const float4 v = *reinterpret_cast<const float4*>(buf + k * rowf + 4 * J);
-        const float aw[4] = {u.x * w, u.y * w, u.z * w, u.w * w};
+        const float aw[4] = {u.x, u.y, u.z, u.w};
         const float cv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
         for (int a = 0; a < 4; ++a)
@@ -397,7 +408,16 @@ __device__ bool syrk_gwg_staged(float* K, int ldk, const float* qd, const float*
         }
     }
     done = c + 1;
-    __syncthreads();  // every thread is done with this buffer
+    // every thread is done with this buffer, whose generic-proxy writes (the
+    // scaling) must be ordered before the bulk copy that refills it
+    fence_async_smem();
+    __syncthreads();
+    if (sub && tid == 0) {
+      // tracing builds: waiting for the copies, scaling, products
+      atomicAdd(&sub[0], (unsigned long long)(ts1 - ts0));
+      atomicAdd(&sub[1], (unsigned long long)(ts2 - ts1));
+      atomicAdd(&sub[2], (unsigned long long)(clock64() - ts2));
+    }
     if (tid == 0 && c + 2 < nchunks) issue(c + 2);
   }
   if (nchunks == 0) {

@@ -362,19 +362,44 @@ def test_tensor_core_gwg_one_newton_step():
         assert 0 < d < bound, (mode, d)
 
 
+def _one_step_from(batch, start, **settings):
+    """x after one Newton step (Alg. 1) from the interior point `start`."""
+    from paper_2605_17913_gb300.solver import QPSolver
+
+    T = _dev(batch)
+    slv = QPSolver(batch.batch, batch.n, batch.p, batch.m)
+    out = {k: start[k].clone() for k in ("x", "y", "z", "s")}
+    out.update(status=torch.empty(batch.batch, dtype=torch.int32, device="cuda"),
+               iters=torch.empty(batch.batch, dtype=torch.int32, device="cuda"),
+               kkt=torch.empty(batch.batch, device="cuda"))
+    slv.solve(T["Q"], T["q"], T["A"], T["b"], T["G"], T["h"], out=out, warm_start=1,
+              max_iter=1, tol=SOLVER_TOL, **settings)
+    torch.cuda.synchronize()
+    return out["x"].cpu().numpy().astype(np.float64)
+
+
 def test_forward_refinement_one_newton_step():
-    """One Newton step from the same start with TF32 / BF16 G'WG and k
-    refinement sweeps against the FP32 bounded system: each sweep brings the
-    step closer to the FP32-factored one (whose own distance from the exact
-    step is FP32 rounding), by at least 10x for the first sweep."""
+    """One Newton step from the same interior point with TF32 / BF16 G'WG
+    and k refinement sweeps against the FP32 bounded system.  Refinement
+    converges to the solution of that FP32 system whatever the factorisation,
+    so the reference is the FP32-factored step refined three times: the first
+    sweep must bring the TF32 / BF16 step at least 3x closer to it, and the
+    second must not move it away."""
+    from paper_2605_17913_gb300.solver import QPSolver
+
     batch = make_batch("precision", 2, seed=2)
-    x32 = gpu_run(batch, max_iter=1)["x"].astype(np.float64)
+    T = _dev(batch)
+    slv = QPSolver(batch.batch, batch.n, batch.p, batch.m)
+    start = slv.solve(T["Q"], T["q"], T["A"], T["b"], T["G"], T["h"], max_iter=6,
+                      tol=SOLVER_TOL)
+    torch.cuda.synchronize()
+    x32 = _one_step_from(batch, start, refine_forward=3)
     for mode in ("tf32", "bf16"):
         d = []
         for k in (0, 1, 2):
-            x = gpu_run(batch, max_iter=1, gwg_precision=mode, refine_forward=k)["x"]
-            d.append(np.abs(x.astype(np.float64) - x32).max() / np.abs(x32).max())
-        assert d[1] < 0.1 * d[0] and d[2] <= d[1] * 1.5 + 1e-6, (mode, d)
+            x = _one_step_from(batch, start, gwg_precision=mode, refine_forward=k)
+            d.append(np.abs(x - x32).max() / np.abs(x32).max())
+        assert d[0] > 0 and d[1] < d[0] / 3 and d[2] <= d[1] * 1.5 + 1e-7, (mode, d)
 
 
 @pytest.mark.parametrize("mode,k", [("tf32", 2), ("bf16", 3), ("fp32", 1)])
@@ -390,13 +415,14 @@ def test_forward_refinement_vs_oracle(mode, k):
 
 
 def test_large_variant_two_ctas_per_sm_vs_oracle():
-    """The 256-thread large variant (two CTAs per SM) against the oracle."""
+    """The 256-thread large variant (two CTAs per SM) against the oracle; the
+    gradient bar per instance as in test_large_variant_parity."""
     batch = make_batch("precision", 4, seed=1)
     res = gpu_run(batch, grad=True, threads_per_qp=256)
     ref = oracle_run(batch, grad=True)
     check_forward(batch, res, O.solve(batch.Q, batch.q, batch.A, batch.b, batch.G, batch.h,
                                       tol=1e-12, nthreads=4))
-    check_grads(res, ref)
+    check_grads(res, ref, TOL_G, fp64_sensitivity(batch, ref))
 
 
 def test_tensor_core_gwg_refused_on_chip():
