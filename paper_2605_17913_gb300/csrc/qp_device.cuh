@@ -460,10 +460,135 @@ __device__ __forceinline__ int pbw_off(int r) {
   return (r >> 2) * pbw_group(PW) + (r & 3) * PW;
 }
 
+// Row stride of the diagonal block's factor fb (PW x fb_ld floats): padded so
+// that one row per lane is stored without bank conflicts.
+__host__ __device__ constexpr int fb_ld(int pw) { return pw + 1; }
+__host__ __device__ constexpr int fb_floats(int pw) { return pw * fb_ld(pw) + 32 * 8; }
+
+// Cholesky of the jb x jb diagonal block at (j0, j0) of M by one warp, lane i
+// holding row i, in PW / 8 sub-blocks of 8 columns: every lane factors the
+// 8 x 8 diagonal sub-block itself, in registers (no communication within its
+// 8 pivots), solves its own row against it, and takes the other rows' solved
+// 8 values from shared memory (sbuf, 32 x 8 floats) for its trailing update.
+// Four exchange rounds per 32 columns instead of a shuffle chain through
+// every pivot.  Writes the factor to fb (stride fb_ld(PW)), to M and
+// 1 / diag to dinv.  Returns 0 if a pivot is not positive and finite.
+// Warp 0 only; sbuf must not be in use by other warps.
+template <int PW>
+__device__ __noinline__ int factor_diag_block(float* M, int ld, int j0, int jb, float* dinv,
+                                             float* fb, float* sbuf) {
+  static_assert(PW % 8 == 0 && PW <= 32, "rows are lanes; 8-column sub-blocks");
+  const int lane = threadIdx.x & 31;
+  int okw = 1;
+  float a[PW];
+#pragma unroll
+  for (int c = 0; c < PW; ++c) a[c] = (lane < jb && c <= lane) ? M[(j0 + lane) * ld + j0 + c] : 0.0f;
+  float rinv = 0.0f;
+#pragma unroll
+  for (int b = 0; b < PW / 8; ++b) {
+    const int c0 = 8 * b;
+    if (c0 >= jb) break;
+    // the sub-block's rows, raw, for every lane
+    if (lane >= c0 && lane < c0 + 8) {
+      float4* dst = reinterpret_cast<float4*>(sbuf + 8 * lane);
+      dst[0] = make_float4(a[c0], a[c0 + 1], a[c0 + 2], a[c0 + 3]);
+      dst[1] = make_float4(a[c0 + 4], a[c0 + 5], a[c0 + 6], a[c0 + 7]);
+    }
+    __syncwarp();
+    // factor it in registers (rows beyond jb: identity)
+    float l[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float4 u = reinterpret_cast<const float4*>(sbuf + 8 * (c0 + i))[0];
+      const float4 v = reinterpret_cast<const float4*>(sbuf + 8 * (c0 + i))[1];
+      const float row[8] = {u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        l[i][j] = (c0 + i < jb) ? (j <= i ? row[j] : 0.0f) : (i == j ? 1.0f : 0.0f);
+    }
+    float inv[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float d = l[j][j];
+      if (!(d > 0.0f) || !(d < INFINITY)) okw = 0;
+      inv[j] = rsqrtf(d);
+      l[j][j] = d * inv[j];
+#pragma unroll
+      for (int i = j + 1; i < 8; ++i) l[i][j] *= inv[j];
+#pragma unroll
+      for (int i = j + 1; i < 8; ++i)
+#pragma unroll
+        for (int k = j + 1; k <= i; ++k) l[i][k] = fmaf(-l[i][j], l[k][j], l[i][k]);
+    }
+    // this lane's row in the sub-block's columns: its row of the factor, or
+    // (rows below) the solve against it
+    float v[8];
+    if (lane < c0 + 8) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (lane == c0 + i) {
+#pragma unroll
+          for (int t = 0; t < 8; ++t) v[t] = l[i][t];
+          rinv = inv[i];
+        }
+    } else {
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        float acc = a[c0 + t];
+#pragma unroll
+        for (int u = 0; u < t; ++u) acc = fmaf(-v[u], l[t][u], acc);
+        v[t] = acc * inv[t];
+      }
+    }
+    if (lane >= c0) {
+#pragma unroll
+      for (int t = 0; t < 8; ++t) a[c0 + t] = v[t];
+    }
+    __syncwarp();  // every lane has read the raw sub-block
+    if (lane >= c0) {
+      float4* dst = reinterpret_cast<float4*>(sbuf + 8 * lane);
+      dst[0] = make_float4(v[0], v[1], v[2], v[3]);
+      dst[1] = make_float4(v[4], v[5], v[6], v[7]);
+    }
+    __syncwarp();
+    // trailing columns of this lane's row: a[c] -= v_lane . v_c, c in
+    // (c0 + 7, lane]
+    if (lane >= c0 + 8) {
+#pragma unroll
+      for (int c = c0 + 8; c < PW; ++c) {
+        if (c <= lane) {
+          const float4 p = reinterpret_cast<const float4*>(sbuf + 8 * c)[0];
+          const float4 q = reinterpret_cast<const float4*>(sbuf + 8 * c)[1];
+          float acc = a[c];
+          acc = fmaf(-v[0], p.x, acc); acc = fmaf(-v[1], p.y, acc);
+          acc = fmaf(-v[2], p.z, acc); acc = fmaf(-v[3], p.w, acc);
+          acc = fmaf(-v[4], q.x, acc); acc = fmaf(-v[5], q.y, acc);
+          acc = fmaf(-v[6], q.z, acc); acc = fmaf(-v[7], q.w, acc);
+          a[c] = acc;
+        }
+      }
+    }
+    __syncwarp();  // sbuf is rewritten by the next sub-block
+  }
+  if (lane < jb) {
+#pragma unroll
+    for (int c = 0; c < PW; ++c) fb[lane * fb_ld(PW) + c] = c <= lane ? a[c] : 0.0f;
+    dinv[j0 + lane] = rinv;
+  }
+  __syncwarp();
+  // the block's factor back to M, one row per step of the warp (coalesced)
+  for (int r = 0; r < jb; ++r)
+    if (lane <= r) M[(j0 + r) * ld + j0 + lane] = fb[r * fb_ld(PW) + lane];
+  return okw;
+}
+
+// diag_done: the diagonal block was factored ahead, during the previous
+// panel's trailing update (look-ahead): fb, dinv and M already hold it.
 template <int NT, int PW>
 __device__ bool panel_factor_wide(float* M, int ld, int j0, int jb, float* dinv, float* A,
                                   int lda, int rowA0, int nA, float* B, int ldb, int nB,
-                                  float* Pb, float* fb, unsigned long long* sub = nullptr) {
+                                  float* Pb, float* fb, unsigned long long* sub = nullptr,
+                                  bool diag_done = false) {
   const long long tp0 = sub ? clock64() : 0;
   static_assert(PW != 32 || NT >= 64, "the staged panel needs warps beside warp 0");
   const int nA4 = (nA + 3) & ~3;
@@ -471,39 +596,8 @@ __device__ bool panel_factor_wide(float* M, int ld, int j0, int jb, float* dinv,
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   int okw = 1;
   if (tid < 32) {
-    float a[PW];
-#pragma unroll
-    for (int c = 0; c < PW; ++c)
-      a[c] = (lane < jb && c <= lane) ? M[(j0 + lane) * ld + j0 + c] : 0.0f;
-    float rinv = 0.0f;
-#pragma unroll
-    for (int k = 0; k < PW; ++k) {
-      if (k < jb) {
-        const float d = __shfl_sync(kFull, a[k], k);
-        if (!(d > 0.0f) || !(d < INFINITY)) okw = 0;
-        const float r = rsqrtf(d);
-        if (lane == k) {
-          a[k] = d * r;
-          rinv = r;
-        } else if (lane > k) {
-          a[k] *= r;
-        }
-#pragma unroll
-        for (int c = k + 1; c < PW; ++c) {
-          const float lck = __shfl_sync(kFull, a[k], c);  // L[c][k], held by lane c
-          if (c < jb && lane >= c) a[c] = fmaf(-a[k], lck, a[c]);
-        }
-      }
-    }
-    if (lane < jb) {
-#pragma unroll
-      for (int c = 0; c < PW; ++c) {
-        const float v = c <= lane ? a[c] : 0.0f;
-        fb[lane * PW + c] = v;
-        if (c <= lane) M[(j0 + lane) * ld + j0 + c] = v;
-      }
-      dinv[j0 + lane] = rinv;
-    }
+    if (!diag_done) okw = factor_diag_block<PW>(M, ld, j0, jb, dinv, fb, fb + PW * fb_ld(PW));
+    if (sub && tid == 0) atomicAdd(&sub[2], (unsigned long long)(clock64() - tp0));
   } else if (PW == 32) {
     // meanwhile the other warps stage the panel's rows in Pb, one row per
     // warp instruction and lane = column: coalesced 128-byte reads of global
@@ -525,6 +619,7 @@ __device__ bool panel_factor_wide(float* M, int ld, int j0, int jb, float* dinv,
         if (rr < N) Pb[pbw_off<PW>(rr < nA ? rr : nA4 + (rr - nA)) + lane] = v[k];
       }
     }
+    if (sub && tid == 32) atomicAdd(&sub[3], (unsigned long long)(clock64() - tp0));
   }
   const bool all_ok = __syncthreads_and(okw) != 0;
   const long long tp1 = sub ? clock64() : 0;
@@ -553,7 +648,7 @@ __device__ bool panel_factor_wide(float* M, int ld, int j0, int jb, float* dinv,
       if (t < jb) {
         float acc = v[t];
 #pragma unroll
-        for (int u = 0; u < t; ++u) acc = fmaf(-v[u], fb[t * PW + u], acc);
+        for (int u = 0; u < t; ++u) acc = fmaf(-v[u], fb[t * fb_ld(PW) + u], acc);
         v[t] = acc * dinv[j0 + t];
       }
     }
@@ -594,83 +689,117 @@ __device__ bool panel_factor_wide(float* M, int ld, int j0, int jb, float* dinv,
 
 // Rank-PW trailing update with the panel in Pbw (same row sets and rules as
 // panel_syrk).
-template <int NT, int PW>
-__device__ void panel_syrk_wide(const float* Pb, float* A, int lda, int rowA0, int nA, float* B,
-                                int ldb, int nB, float* C, int ldc) {
+// One 4 x 4 tile t (row-major lower-triangular numbering over the combined
+// row set) of the rank-PW trailing update with the panel in Pbw.
+template <int PW>
+__device__ __forceinline__ void trailing_tile(int t, const float* Pb, float* A, int lda, int rowA0,
+                                              int nA, float* B, int ldb, int nB, float* C,
+                                              int ldc) {
   constexpr int GS = pbw_group(PW);
+  const int nA4 = (nA + 3) & ~3;
+  const int ntA = nA4 >> 2;
+  const float x8 = 8.0f * (float)t + 1.0f;
+  int I = (int)((x8 * rsqrtf(x8) - 1.0f) * 0.5f);
+  while ((I + 1) * (I + 2) / 2 <= t) ++I;
+  while (I * (I + 1) / 2 > t) --I;
+  const int J = t - I * (I + 1) / 2;
+  const bool rowA = I < ntA, colA = J < ntA;
+  if (!rowA && !colA && C == nullptr) return;
+  float* dst;
+  int ld, rmax, cmax;
+  float sgn = -1.0f;
+  if (rowA) {
+    dst = A + (rowA0 + 4 * I) * lda + rowA0 + 4 * J;
+    ld = lda;
+    rmax = nA - 4 * I;
+    cmax = nA - 4 * J;
+  } else if (colA) {
+    dst = B + (4 * I - nA4) * ldb + rowA0 + 4 * J;
+    ld = ldb;
+    rmax = nB - (4 * I - nA4);
+    cmax = nA - 4 * J;
+  } else {
+    dst = C + (4 * I - nA4) * ldc + (4 * J - nA4);
+    ld = ldc;
+    rmax = nB - (4 * I - nA4);
+    cmax = nB - (4 * J - nA4);
+    sgn = 1.0f;
+  }
+  const bool diag = I == J;
+  // the tile's current values, read before the product and before any
+  // store: a store through dst may alias a later load of dst, so loads
+  // interleaved with the stores would each wait for the one before (16
+  // serial round trips per tile to L2)
+  float old[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+      old[a][b] = (a < rmax && b < cmax && (!diag || b <= a)) ? dst[a * ld + b] : 0.f;
+  float acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+#pragma unroll
+  for (int h = 0; h < PW / 4; ++h) {
+    float4 ra[4], cb[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) ra[a] = reinterpret_cast<const float4*>(Pb + I * GS + a * PW)[h];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) cb[b] = reinterpret_cast<const float4*>(Pb + J * GS + b * PW)[h];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        acc[a][b] = fmaf(ra[a].x, cb[b].x, acc[a][b]);
+        acc[a][b] = fmaf(ra[a].y, cb[b].y, acc[a][b]);
+        acc[a][b] = fmaf(ra[a].z, cb[b].z, acc[a][b]);
+        acc[a][b] = fmaf(ra[a].w, cb[b].w, acc[a][b]);
+      }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+      if (a < rmax && b < cmax && (!diag || b <= a))
+        dst[a * ld + b] = fmaf(sgn, acc[a][b], old[a][b]);
+}
+
+// Rank-PW trailing update with the panel in Pbw (same row sets and rules as
+// panel_syrk).  Look-ahead (jb2 > 0, PW = 32 only): the next panel's
+// diagonal block -- the first jb2 rows and columns of the trailing matrix,
+// tiles 0 .. T2-1 in this numbering -- is updated by warp 0, which then
+// factors it (factor_diag_block: into fb, dinv and M at pivot column
+// rowA0) while the other warps update the remaining tiles; the next
+// panel_factor_wide is then called with diag_done.  Returns the
+// factorisation's pivot check (1 without look-ahead).  Ends with a barrier.
+template <int NT, int PW>
+__device__ int panel_syrk_wide(const float* Pb, float* A, int lda, int rowA0, int nA, float* B,
+                               int ldb, int nB, float* C, int ldc, int jb2 = 0,
+                               float* dinv = nullptr, float* fb = nullptr) {
   const int nA4 = (nA + 3) & ~3;
   const int ntA = nA4 >> 2;
   const int nt = ntA + ((nB + 3) >> 2);
   const int T = nt * (nt + 1) / 2;
-  for (int t = threadIdx.x; t < T; t += NT) {
-    const float x8 = 8.0f * (float)t + 1.0f;
-    int I = (int)((x8 * rsqrtf(x8) - 1.0f) * 0.5f);
-    while ((I + 1) * (I + 2) / 2 <= t) ++I;
-    while (I * (I + 1) / 2 > t) --I;
-    const int J = t - I * (I + 1) / 2;
-    const bool rowA = I < ntA, colA = J < ntA;
-    if (!rowA && !colA && C == nullptr) continue;
-    float* dst;
-    int ld, rmax, cmax;
-    float sgn = -1.0f;
-    if (rowA) {
-      dst = A + (rowA0 + 4 * I) * lda + rowA0 + 4 * J;
-      ld = lda;
-      rmax = nA - 4 * I;
-      cmax = nA - 4 * J;
-    } else if (colA) {
-      dst = B + (4 * I - nA4) * ldb + rowA0 + 4 * J;
-      ld = ldb;
-      rmax = nB - (4 * I - nA4);
-      cmax = nA - 4 * J;
+  int okw = 1;
+  if (jb2 > 0) {
+    const int nt2 = (jb2 + 3) >> 2;
+    const int T2 = nt2 * (nt2 + 1) / 2;
+    if (threadIdx.x < 32) {
+      for (int t = threadIdx.x; t < T2; t += 32)
+        trailing_tile<PW>(t, Pb, A, lda, rowA0, nA, B, ldb, nB, C, ldc);
+      __syncwarp();  // the block's updated values, visible to the whole warp
+      okw = factor_diag_block<PW>(A, lda, rowA0, jb2, dinv, fb, fb + PW * fb_ld(PW));
     } else {
-      dst = C + (4 * I - nA4) * ldc + (4 * J - nA4);
-      ld = ldc;
-      rmax = nB - (4 * I - nA4);
-      cmax = nB - (4 * J - nA4);
-      sgn = 1.0f;
+      for (int t = T2 + (int)threadIdx.x - 32; t < T; t += NT - 32)
+        trailing_tile<PW>(t, Pb, A, lda, rowA0, nA, B, ldb, nB, C, ldc);
     }
-    const bool diag = I == J;
-    // the tile's current values, read before the product and before any
-    // store: a store through dst may alias a later load of dst, so loads
-    // interleaved with the stores would each wait for the one before (16
-    // serial round trips per tile, to L2 in the large variant)
-    float old[4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b)
-        old[a][b] = (a < rmax && b < cmax && (!diag || b <= a)) ? dst[a * ld + b] : 0.f;
-    float acc[4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-#pragma unroll
-    for (int h = 0; h < PW / 4; ++h) {
-      float4 ra[4], cb[4];
-#pragma unroll
-      for (int a = 0; a < 4; ++a) ra[a] = reinterpret_cast<const float4*>(Pb + I * GS + a * PW)[h];
-#pragma unroll
-      for (int b = 0; b < 4; ++b) cb[b] = reinterpret_cast<const float4*>(Pb + J * GS + b * PW)[h];
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          acc[a][b] = fmaf(ra[a].x, cb[b].x, acc[a][b]);
-          acc[a][b] = fmaf(ra[a].y, cb[b].y, acc[a][b]);
-          acc[a][b] = fmaf(ra[a].z, cb[b].z, acc[a][b]);
-          acc[a][b] = fmaf(ra[a].w, cb[b].w, acc[a][b]);
-        }
-    }
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b)
-        if (a < rmax && b < cmax && (!diag || b <= a))
-          dst[a * ld + b] = fmaf(sgn, acc[a][b], old[a][b]);
+  } else {
+    for (int t = threadIdx.x; t < T; t += NT)
+      trailing_tile<PW>(t, Pb, A, lda, rowA0, nA, B, ldb, nB, C, ldc);
   }
-  __syncthreads();
+  return __syncthreads_and(okw);
 }
 
 // Eliminate the n pivots of K (n x n lower, stride ldk) bordered by nB rows
@@ -680,33 +809,45 @@ __device__ void panel_syrk_wide(const float* Pb, float* A, int lda, int rowA0, i
 // sub (tracing builds only, may be null): cycles of the factor+TRSM stage and
 // of the trailing updates are added to sub[0] and sub[1] by thread 0.
 // PW: panel width, 8 (Pb of pb_floats rows) or 16 / 32 (Pb of pbw_floats
-// rows followed by the PW x PW block scratch).
+// rows followed by the diagonal block's factor, PW x fb_ld(PW) floats, and
+// a 32 x 8 exchange buffer: fb_floats(PW)).
 // Not inlined: the forward factors K_I and C with it, and one shared copy
 // of the unrolled panel code keeps the hot loop within the instruction cache
 // (two inlined copies made the forward 11 % slower).
 template <int NT, int PW = 8>
 __device__ __noinline__ bool blocked_cholesky_bordered(float* K, int ldk, int n, float* Y, int ldy, int nB,
                                           float* C, int ldc, float* dinv, float* Pb,
-                                          unsigned long long* sub = nullptr) {
+                                          unsigned long long* sub = nullptr,
+                                          unsigned long long* psub = nullptr) {
   bool ok = true;
   float* const fb = PW > 8 ? Pb + pbw_floats(pbw_rows(n, nB, PW), PW) : nullptr;
+  bool ahead = false;  // this panel's diagonal block was factored ahead
   for (int j0 = 0; j0 < n; j0 += PW) {
     const int jb = min(PW, n - j0);
     const int nK = n - j0 - jb;
     const long long c0 = sub ? clock64() : 0;
     if constexpr (PW > 8)
       ok = panel_factor_wide<NT, PW>(K, ldk, j0, jb, dinv, K, ldk, j0 + jb, nK, Y, ldy, nB, Pb,
-                                     fb, sub ? sub + 4 : nullptr) &&
+                                     fb, psub, ahead) &&
            ok;
     else
       ok = panel_factor_trsm<NT>(K, ldk, j0, jb, dinv, K, ldk, j0 + jb, nK, Y, ldy, nB, Pb) &&
            ok;
     const long long c1 = sub ? clock64() : 0;
+    ahead = false;
     if (nK + nB > 0) {
-      if constexpr (PW > 8)
+      if constexpr (PW == 32) {
+        // look-ahead: warp 0 updates and factors the next diagonal block
+        // while the other warps finish the trailing update
+        const int jb2 = min(PW, nK);
+        ok = panel_syrk_wide<NT, PW>(Pb, K, ldk, j0 + jb, nK, Y, ldy, nB, C, ldc, jb2, dinv, fb) &&
+             ok;
+        ahead = jb2 > 0;
+      } else if constexpr (PW > 8) {
         panel_syrk_wide<NT, PW>(Pb, K, ldk, j0 + jb, nK, Y, ldy, nB, C, ldc);
-      else
+      } else {
         panel_syrk<NT>(Pb, K, ldk, j0 + jb, nK, Y, ldy, nB, C, ldc);
+      }
     }
     if (sub && threadIdx.x == 0) {
       const long long c2 = clock64();

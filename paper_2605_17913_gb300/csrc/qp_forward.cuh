@@ -123,7 +123,7 @@ __host__ __device__ inline FLayout make_fwd_layout(int n, int m, int p, int amax
     if (split) o = (o + 31) & ~31;
     const int base = o;
     const int pw = panel_width(nthreads, split);
-    int pb = pw > 8 ? pbw_floats(pbw_rows(n, L.fmax + 2, pw), pw) + pw * pw
+    int pb = pw > 8 ? pbw_floats(pbw_rows(n, L.fmax + 2, pw), pw) + fb_floats(pw)
                     : pb_floats(n + L.fmax + 2 + 4);
     pb = round4(pb);
     if (split && pb < 2 * tc::stage_bytes(n, 4) / 4) pb = 2 * tc::stage_bytes(n, 4) / 4;
@@ -501,8 +501,10 @@ struct Solver {
 #else
     unsigned long long* const sub = nullptr;
 #endif
+    // tracing builds: counters 11-14 (K, C: panel / trailing), 24-27 and
+    // 28-31 (K, C: inside the wide panel), 19-21 (staged G'WG)
     bool ok = blocked_cholesky_bordered<NT, kPW>(K, L.ldk, L.n, Y, L.ldk, nf + nfold, C, L.ldc, dinv,
-                                            Pb, sub);
+                                            Pb, sub, sub ? sub + 13 : nullptr);
     QP_MARK(PH_BORDER);
     if (nf > 0) {
       float dm[1] = {1.0f};
@@ -512,7 +514,8 @@ struct Solver {
       for (int k = threadIdx.x; k < nf; k += NT) C[k * L.ldc + k] += shift;
       __syncthreads();
       ok = blocked_cholesky_bordered<NT, kPW>(C, L.ldc, nf, C + nf * L.ldc, L.ldc, nfold, nullptr, 0,
-                                         cdinv, Pb, sub ? sub + 2 : nullptr) && ok;
+                                         cdinv, Pb, sub ? sub + 2 : nullptr,
+                                         sub ? sub + 17 : nullptr) && ok;
       QP_MARK(PH_CCHOL);
     }
     return ok;
