@@ -476,13 +476,36 @@ __host__ __device__ constexpr int fb_floats(int pw) { return pw * fb_ld(pw) + 32
 // Warp 0 only; sbuf must not be in use by other warps.
 template <int PW>
 __device__ __noinline__ int factor_diag_block(float* M, int ld, int j0, int jb, float* dinv,
-                                             float* fb, float* sbuf) {
+                                             float* fb, float* sbuf,
+                                             unsigned long long* ft = nullptr) {
   static_assert(PW % 8 == 0 && PW <= 32, "rows are lanes; 8-column sub-blocks");
   const int lane = threadIdx.x & 31;
+  const long long tf0 = ft ? clock64() : 0;
   int okw = 1;
   float a[PW];
+  {
+    // the block, one row per warp instruction (coalesced, all loads in
+    // flight), transposed through fb (padded rows: no bank conflicts) so
+    // that lane i holds row i
+    float col[PW];
 #pragma unroll
-  for (int c = 0; c < PW; ++c) a[c] = (lane < jb && c <= lane) ? M[(j0 + lane) * ld + j0 + c] : 0.0f;
+    for (int r = 0; r < PW; ++r)
+      col[r] = (r < jb && lane <= r) ? M[(j0 + r) * ld + j0 + lane] : 0.0f;
+#pragma unroll
+    for (int r = 0; r < PW; ++r) fb[r * fb_ld(PW) + lane] = col[r];
+    __syncwarp();
+#pragma unroll
+    for (int c = 0; c < PW; ++c) a[c] = (lane < jb && c <= lane) ? fb[lane * fb_ld(PW) + c] : 0.0f;
+    __syncwarp();
+  }
+  long long tf1 = 0;
+  if (ft) {
+    // tracing builds: the clock is read after every load has returned
+    float sum = 0.0f;
+#pragma unroll
+    for (int c = 0; c < PW; ++c) sum += a[c];
+    tf1 = clock64() + (long long)(sum * 0.0f);
+  }
   float rinv = 0.0f;
 #pragma unroll
   for (int b = 0; b < PW / 8; ++b) {
@@ -570,6 +593,7 @@ __device__ __noinline__ int factor_diag_block(float* M, int ld, int j0, int jb, 
     }
     __syncwarp();  // sbuf is rewritten by the next sub-block
   }
+  const long long tf2 = ft ? clock64() : 0;
   if (lane < jb) {
 #pragma unroll
     for (int c = 0; c < PW; ++c) fb[lane * fb_ld(PW) + c] = c <= lane ? a[c] : 0.0f;
@@ -579,6 +603,11 @@ __device__ __noinline__ int factor_diag_block(float* M, int ld, int j0, int jb, 
   // the block's factor back to M, one row per step of the warp (coalesced)
   for (int r = 0; r < jb; ++r)
     if (lane <= r) M[(j0 + r) * ld + j0 + lane] = fb[r * fb_ld(PW) + lane];
+  if (ft && lane == 0) {
+    atomicAdd(&ft[0], (unsigned long long)(tf1 - tf0));
+    atomicAdd(&ft[1], (unsigned long long)(tf2 - tf1));
+    atomicAdd(&ft[2], (unsigned long long)(clock64() - tf2));
+  }
   return okw;
 }
 
@@ -769,15 +798,18 @@ __device__ __forceinline__ void trailing_tile(int t, const float* Pb, float* A, 
 // Rank-PW trailing update with the panel in Pbw (same row sets and rules as
 // panel_syrk).  Look-ahead (jb2 > 0, PW = 32 only): the next panel's
 // diagonal block -- the first jb2 rows and columns of the trailing matrix,
-// tiles 0 .. T2-1 in this numbering -- is updated by warp 0, which then
+// tiles 0 .. T2-1 in this numbering -- is updated by warps 0-3, then warp 0
 // factors it (factor_diag_block: into fb, dinv and M at pivot column
 // rowA0) while the other warps update the remaining tiles; the next
-// panel_factor_wide is then called with diag_done.  Returns the
+// panel_factor_wide is then called with diag_done.  Needs NT >= 128 and
+// uses named barrier 1.  Returns the
 // factorisation's pivot check (1 without look-ahead).  Ends with a barrier.
 template <int NT, int PW>
 __device__ int panel_syrk_wide(const float* Pb, float* A, int lda, int rowA0, int nA, float* B,
                                int ldb, int nB, float* C, int ldc, int jb2 = 0,
-                               float* dinv = nullptr, float* fb = nullptr) {
+                               float* dinv = nullptr, float* fb = nullptr,
+                               unsigned long long* ft = nullptr) {
+  static_assert(NT >= 128, "the look-ahead uses warps 0-3");
   const int nA4 = (nA + 3) & ~3;
   const int ntA = nA4 >> 2;
   const int nt = ntA + ((nB + 3) >> 2);
@@ -786,11 +818,19 @@ __device__ int panel_syrk_wide(const float* Pb, float* A, int lda, int rowA0, in
   if (jb2 > 0) {
     const int nt2 = (jb2 + 3) >> 2;
     const int T2 = nt2 * (nt2 + 1) / 2;
-    if (threadIdx.x < 32) {
-      for (int t = threadIdx.x; t < T2; t += 32)
+    const long long tlt = ft ? clock64() : 0;
+    if (threadIdx.x < 128) {
+      // warps 0-3, one per scheduler: the block's tiles, then (named
+      // barrier 1, these 128 threads only: the updated values visible to warp 0)
+      for (int t = threadIdx.x; t < T2; t += 128)
         trailing_tile<PW>(t, Pb, A, lda, rowA0, nA, B, ldb, nB, C, ldc);
-      __syncwarp();  // the block's updated values, visible to the whole warp
-      okw = factor_diag_block<PW>(A, lda, rowA0, jb2, dinv, fb, fb + PW * fb_ld(PW));
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+    }
+    if (threadIdx.x < 32) {
+      const long long tl0 = ft ? clock64() : 0;
+      okw = factor_diag_block<PW>(A, lda, rowA0, jb2, dinv, fb, fb + PW * fb_ld(PW), ft);
+      // tracing builds: the look-ahead's tile updates, before the factorisation
+      if (ft && threadIdx.x == 0) atomicAdd(&ft[3], (unsigned long long)(tl0 - tlt));
     } else {
       for (int t = T2 + (int)threadIdx.x - 32; t < T; t += NT - 32)
         trailing_tile<PW>(t, Pb, A, lda, rowA0, nA, B, ldb, nB, C, ldc);
@@ -840,7 +880,8 @@ __device__ __noinline__ bool blocked_cholesky_bordered(float* K, int ldk, int n,
         // look-ahead: warp 0 updates and factors the next diagonal block
         // while the other warps finish the trailing update
         const int jb2 = min(PW, nK);
-        ok = panel_syrk_wide<NT, PW>(Pb, K, ldk, j0 + jb, nK, Y, ldy, nB, C, ldc, jb2, dinv, fb) &&
+        ok = panel_syrk_wide<NT, PW>(Pb, K, ldk, j0 + jb, nK, Y, ldy, nB, C, ldc, jb2, dinv, fb,
+                                     psub ? psub + 4 : nullptr) &&
              ok;
         ahead = jb2 > 0;
       } else if constexpr (PW > 8) {

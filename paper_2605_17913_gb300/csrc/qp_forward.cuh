@@ -502,7 +502,8 @@ struct Solver {
     unsigned long long* const sub = nullptr;
 #endif
     // tracing builds: counters 11-14 (K, C: panel / trailing), 24-27 and
-    // 28-31 (K, C: inside the wide panel), 19-21 (staged G'WG)
+    // 40-43 (K, C: inside the wide panel), 28-31 and 44-47 (K, C: the
+    // look-ahead), 19-21 (staged G'WG); 48 counters
     bool ok = blocked_cholesky_bordered<NT, kPW>(K, L.ldk, L.n, Y, L.ldk, nf + nfold, C, L.ldc, dinv,
                                             Pb, sub, sub ? sub + 13 : nullptr);
     QP_MARK(PH_BORDER);
@@ -515,7 +516,7 @@ struct Solver {
       __syncthreads();
       ok = blocked_cholesky_bordered<NT, kPW>(C, L.ldc, nf, C + nf * L.ldc, L.ldc, nfold, nullptr, 0,
                                          cdinv, Pb, sub ? sub + 2 : nullptr,
-                                         sub ? sub + 17 : nullptr) && ok;
+                                         sub ? sub + 29 : nullptr) && ok;
       QP_MARK(PH_CCHOL);
     }
     return ok;
