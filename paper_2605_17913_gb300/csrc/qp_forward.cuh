@@ -274,9 +274,10 @@ struct Solver {
   }
 
   // trace the Newton matrix's diagonal (W of the inactive rows, 1/W of the
-  // active ones) right after partition()
-  static __device__ void trace_scaling(const FwdParams& P) {
-    if (!P.diag) return;
+  // active ones) right after partition().  The checks are out of line so that
+  // the solve's hot loop (instruction-cache bound on chip) only carries a
+  // branch and a call.
+  static __device__ __noinline__ void trace_scaling_nl(const FwdParams& P) {
     QP_ARR(ea); QP_ARR(D); QP_IARR(pos);
     bool bad = false;
     for (int r = threadIdx.x; r < fwd_state.L.m; r += NT) {
@@ -284,6 +285,9 @@ struct Solver {
       bad |= !(isfinite(wv) && wv >= 0.f);
     }
     trace(P, QP_STAGE_SCALING, bad);
+  }
+  static __device__ __forceinline__ void trace_scaling(const FwdParams& P) {
+    if (P.diag) trace_scaling_nl(P);
   }
 
   // a factorisation failed: the predictor stage (its first use), flagged
@@ -293,12 +297,38 @@ struct Solver {
   }
 
   // the iterate after a step
-  static __device__ void trace_iterate(const FwdParams& P, int stage) {
-    if (!P.diag) return;
+  static __device__ __noinline__ void trace_iterate_nl(const FwdParams& P, int stage) {
     QP_ARR(x); QP_ARR(z); QP_ARR(s); QP_ARR(y);
     const bool bad = any_nonfinite(x, fwd_state.L.n) || any_nonfinite(z, fwd_state.L.m) ||
                      any_nonfinite(s, fwd_state.L.m) || any_nonfinite(y, fwd_state.L.p);
     trace(P, stage, bad);
+  }
+  static __device__ __forceinline__ void trace_iterate(const FwdParams& P, int stage) {
+    if (P.diag) trace_iterate_nl(P, stage);
+  }
+
+  // the implicit step's two solved columns (predictor stage)
+  static __device__ __noinline__ void trace_folded_solve(const FwdParams& P) {
+    QP_ARR(R); QP_ARR(ua); QP_ARR(ub); QP_ARR(ea); QP_ARR(eb);
+    const FLayout& L = fwd_state.L;
+    const bool bad = any_nonfinite(R, L.n) || any_nonfinite(R + L.ldx, L.n) ||
+                     any_nonfinite(ua, fwd_state.nf) || any_nonfinite(ub, fwd_state.nf) ||
+                     any_nonfinite(ea, L.m) || any_nonfinite(eb, L.m);
+    trace(P, QP_STAGE_PREDICTOR, bad);
+  }
+
+  // the implicit step's corrector direction (ds, dz, dv on every row, dx)
+  static __device__ __noinline__ void trace_corrector(const FwdParams& P, float rk) {
+    QP_ARR(R);
+    const FLayout& L = fwd_state.L;
+    bool bad = false;
+    for (int r = threadIdx.x; r < L.m; r += NT) {
+      float dsr, dzr, dvr;
+      implicit_dir<false>(r, rk, dsr, dzr, dvr);
+      bad |= !isfinite(dsr) || !isfinite(dzr) || !isfinite(dvr);
+    }
+    for (int i = threadIdx.x; i < L.n; i += NT) bad |= !isfinite(fmaf(rk, R[L.ldx + i], R[i]));
+    trace(P, QP_STAGE_CORRECTOR, bad);
   }
 
   // ---- load one instance; Q's strict upper triangle goes to K's upper part ----
@@ -1012,15 +1042,7 @@ struct Solver {
     if constexpr (kBig) {
       for (int k = 0; k < fwd_state.refine; ++k) refine_folded();
     }
-    if (P.diag) {
-      // both right-hand-side columns (the affine one and d/dr_kappa)
-      QP_ARR(R); QP_ARR(ua); QP_ARR(ub); QP_ARR(ea); QP_ARR(eb);
-      const FLayout& L = fwd_state.L;
-      const bool bad = any_nonfinite(R, L.n) || any_nonfinite(R + L.ldx, L.n) ||
-                       any_nonfinite(ua, fwd_state.nf) || any_nonfinite(ub, fwd_state.nf) ||
-                       any_nonfinite(ea, L.m) || any_nonfinite(eb, L.m);
-      trace(P, QP_STAGE_PREDICTOR, bad);
-    }
+    if (P.diag) trace_folded_solve(P);
     float kt;
     if (kt_fixed >= 0.f) {
       kt = kt_fixed;
@@ -1040,19 +1062,7 @@ struct Solver {
       kt = fmaxf(sigma * kappa, P.kappa_min);
     }
     const float rk = kappa - kt;
-    if (P.diag) {
-      // the corrector's (ds, dz, dv) on every row and its dx
-      QP_ARR(R);
-      const FLayout& L = fwd_state.L;
-      bool bad = false;
-      for (int r = threadIdx.x; r < L.m; r += NT) {
-        float dsr, dzr, dvr;
-        implicit_dir<false>(r, rk, dsr, dzr, dvr);
-        bad |= !isfinite(dsr) || !isfinite(dzr) || !isfinite(dvr);
-      }
-      for (int i = threadIdx.x; i < L.n; i += NT) bad |= !isfinite(fmaf(rk, R[L.ldx + i], R[i]));
-      trace(P, QP_STAGE_CORRECTOR, bad);
-    }
+    if (P.diag) trace_corrector(P, rk);
     const float alpha = P.step_frac * implicit_alpha<false>(rk, true);
     trace(P, QP_STAGE_LINESEARCH, !isfinite(alpha));
     implicit_update(alpha, rk, kappa);
