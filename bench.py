@@ -74,6 +74,8 @@ def parse(argv=None):
     ap.add_argument("--serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=None)
     ap.add_argument("--serve-pool", type=int, default=8192)
+    ap.add_argument("--serve-modes", default="launches,persistent",
+                    help="server modes the study runs, comma separated")
     ap.add_argument("--no-serve", action="store_true")
     # G'WG in FP32 vs TF32 / BF16 tensor cores on the n = 256 workload
     # (one JSON line per mode instead of the bench line)
@@ -606,11 +608,22 @@ def run_ours(args, rank, world, local_rank):
     if world == 1 and not args.no_serve:
         # a short run of the serving study (uneven-size stream at 0.8 of the
         # padded baseline's saturated rate); `--serve` runs the full study
-        sv = run_serve_study(args, lines=False, requests=3000, fracs=(0.8,))[0]
+        svs = run_serve_study(args, lines=False, requests=3000, fracs=(0.8,))
+        by_mode = {sv["mode"]: {"p50_ms": sv["latency_ms"]["p50"],
+                                "p99_ms": sv["latency_ms"]["p99"],
+                                "solves_per_s": sv["solves_per_s"], "solved": sv["solved"],
+                                "by_size": sv["latency_ms_by_size"],
+                                "saturated_solves_per_s": sv["served_saturated_solves_per_s"]}
+                   for sv in svs}
+        main_mode = "persistent" if "persistent" in by_mode else svs[0]["mode"]
+        sv = svs[0]
         serve = {"requests": sv["requests"], "rate_per_s": sv["rate_per_s"],
                  "load_vs_padded_saturation": sv["load_vs_padded_saturation"],
-                 "p50_ms": sv["latency_ms"]["p50"], "p99_ms": sv["latency_ms"]["p99"],
-                 "solves_per_s": sv["solves_per_s"], "solved": sv["solved"],
+                 "mode": main_mode,
+                 "p50_ms": by_mode[main_mode]["p50_ms"], "p99_ms": by_mode[main_mode]["p99_ms"],
+                 "solves_per_s": by_mode[main_mode]["solves_per_s"],
+                 "solved": by_mode[main_mode]["solved"],
+                 "by_mode": by_mode,
                  "padded_p50_ms": sv["padded_baseline"]["latency_ms"]["p50"],
                  "padded_p99_ms": sv["padded_baseline"]["latency_ms"]["p99"],
                  "note": "n log-uniform in [8, 256], m = 2n, p = n // 10, 30 % with "
@@ -748,6 +761,21 @@ def _padded_latency(arrivals, times, group):
     return np.array(lat)
 
 
+SERVE_CLASSES = (("n<=72", 1, 72), ("72<n<=128", 73, 128), ("n>128", 129, 256))
+
+
+def _class_latency(pool, order, lat):
+    """p50 / p99 latency (ms) of the requests of each size class."""
+    ns = np.array([pool[i]["q"].size for i in order])
+    out = {}
+    for name, lo, hi in SERVE_CLASSES:
+        sel = (ns >= lo) & (ns <= hi)
+        if sel.any():
+            out[name] = {"requests": int(sel.sum()), "p50": _pctl(lat[sel], 50),
+                         "p99": _pctl(lat[sel], 99)}
+    return out
+
+
 def _serve_run(srv, pool, order, arrivals, verify=0):
     """Submit request order[i] at arrivals[i] (seconds from start, host clock);
     collect with poll_any.  Returns per-request latency (poll completion -
@@ -812,17 +840,14 @@ def _pctl(a, q):
     return float(np.percentile(a, q) * 1e3)
 
 
-def run_serve_study(args, lines=True, requests=None, fracs=(0.5, 0.8, 0.95)):
+def run_serve_study(args, lines=True, requests=None, fracs=(0.5, 0.8, 0.95), modes=None):
     """Config 5: Poisson stream of uneven QPs (n log-uniform in [8, 256],
-    m = 2n, p = n // 10, 30 % with gradients) through the continuous-batching
-    server vs the padded-batch baseline (groups of 256 in arrival order,
-    padded to the group's largest n)."""
+    m = 2n, p = n // 10, 30 % with gradients) through the server, in each of
+    its modes (ragged launches; resident CTAs), vs the padded-batch baseline
+    (groups of 256 in arrival order, padded to the group's largest n)."""
     import sys as _sys
 
     import torch
-
-    from paper_2605_17913_gb300.metrics import kkt_report
-    from paper_2605_17913_gb300.serve import QPServer
 
     _sys.setswitchinterval(1e-4)
     torch.cuda.set_device(0)
@@ -833,17 +858,30 @@ def run_serve_study(args, lines=True, requests=None, fracs=(0.5, 0.8, 0.95)):
     P = min(args.serve_pool, N)
     pool = _serve_pool(P)
     order = np.arange(N) % P
-    rng = np.random.default_rng(12345)
-    srv = QPServer(hbm_budget_bytes=4 << 30, max_inflight=8, tol=args.tol)
+    # padded baseline: device time of each batch of 256 in arrival order
+    # (measured while no server holds the GPU)
+    group = 256
+    times = _padded_group_times(pool, order, group, args.tol)
+    pad_sat = N / sum(times)
+    modes = modes or [m for m in args.serve_modes.split(",") if m]
+    out = []
+    for mode in modes:
+        out.extend(_serve_mode_study(args, lines, mode, pool, order, times, group, pad_sat,
+                                     fracs, N, P))
+    return out
+
+
+def _serve_mode_study(args, lines, mode, pool, order, times, group, pad_sat, fracs, N, P):
+    from paper_2605_17913_gb300.metrics import kkt_report
+    from paper_2605_17913_gb300.serve import QPServer
+
+    rng = np.random.default_rng(12345)  # the same arrivals for every mode
+    srv = QPServer(hbm_budget_bytes=4 << 30, max_inflight=8, tol=args.tol, mode=mode)
     # warm the kernels and the arena with one pass over a few requests
     _serve_run(srv, pool, order[:64], np.zeros(64))
     # saturated throughput of the server: everything submitted at once
     lat0, slat0, mk0, st0, _ = _serve_run(srv, pool, order, np.zeros(N))
     served_sat = N / mk0
-    # padded baseline: device time of each batch of 256 in arrival order
-    group = 256
-    times = _padded_group_times(pool, order, group, args.tol)
-    pad_sat = N / sum(times)
     out = []
     for frac in fracs:
         lam = frac * pad_sat
@@ -883,10 +921,12 @@ def run_serve_study(args, lines=True, requests=None, fracs=(0.5, 0.8, 0.95)):
             oracle = {"requests": len(xe), "passed_x_1e-4_grad_1e-3": npass,
                       "x_err_max": max(xe), "grad_err_max": max(ge)}
         line = {
-            "serve": "continuous batching", "requests": N, "distinct_instances": P,
+            "serve": "continuous batching", "mode": mode, "requests": N,
+            "distinct_instances": P,
             "arrival": "poisson", "rate_per_s": lam, "load_vs_padded_saturation": frac,
             "latency_ms": {"p50": _pctl(lat, 50), "p99": _pctl(lat, 99),
                            "mean": float(lat.mean() * 1e3)},
+            "latency_ms_by_size": _class_latency(pool, order, lat),
             "server_latency_ms": {"p50": _pctl(slat, 50), "p99": _pctl(slat, 99)},
             "solves_per_s": N / mk, "solved": float(np.mean(st == 0)),
             "kkt_scaled_max_sample": kmax, "oracle_sample": oracle,

@@ -171,9 +171,12 @@ int qp_handle_create(const qp_dims* dims, qp_handle** out);
 /* As qp_handle_create, with the threads per QP of the forward kernel chosen
  * by the caller: 0 automatic (as qp_handle_create: one warp per QP for
  * n <= 32 in batches of 2048 or more, else 128 up to n = 72, else 512), 32
- * (one warp per QP; n <= 32) or 128 (n <= 72).  Sizes whose data do not fit
- * one SM's shared memory at the requested width, and other widths, return
- * QP_ENOTSUP.  Results are the same up to FP32 rounding order. */
+ * (one warp per QP; n <= 32), 128 (n <= 72), 256 (n > 128: two CTAs of the
+ * large-problem variant per SM) or 512 (any n: the width the persistent
+ * server of qp_serve_create runs every size at, so that a served request
+ * equals a batch-1 solve of this width bit for bit).  Sizes whose data do
+ * not fit one SM's shared memory at the requested width, and other widths,
+ * return QP_ENOTSUP.  Results are the same up to FP32 rounding order. */
 int qp_handle_create_threads(const qp_dims* dims, int32_t threads_per_qp, qp_handle** out);
 
 /* Free the handle and its workspace, if any. */
@@ -310,26 +313,50 @@ int qp_solve_backward_static(qp_handle* h, const qp_settings* settings, const fl
 
 /* ---- serving: continuous batching of single requests ------------------- */
 
-/* A server owns a device arena, a pinned host mirror of it, max_inflight
- * CUDA streams and a scheduler thread.  Requests of any supported size are
- * submitted one at a time; the scheduler groups waiting requests into
- * launches (the oldest request first, requests of its kernel class in
- * arrival order, up to max_batch and up to the free arena memory) and keeps
- * up to max_inflight launches on the GPU at once, so requests that arrive
- * while others run start as soon as a stream and memory free up; a kernel
- * class takes the last free stream only while it has fewer than
- * max(1, max_inflight / 3) launches in flight.  Each
- * request is solved (Alg. 1; with want_grad also relaxed and differentiated,
- * Alg. 2-3) by one CTA with the same arithmetic as qp_solve_batch of its
- * size: results equal solo results bit for bit.  Every wait is bounded. */
+/* A server owns a device arena, a pinned host mirror of it and a scheduler
+ * thread; requests of any supported size are submitted one at a time and
+ * admitted while their footprint (qp_serve_footprint_bytes) fits the arena.
+ * Each request is solved (Alg. 1; with want_grad also relaxed and
+ * differentiated, Alg. 2-3) by one CTA.  Two modes:
+ *
+ * QP_SERVE_LAUNCHES: the scheduler groups waiting requests into launches (the
+ * oldest request first, requests of its kernel class in arrival order, up to
+ * max_batch and up to the free arena memory) and keeps up to max_inflight
+ * launches on the GPU at once, one stream each, so requests that arrive while
+ * others run start as soon as a stream and memory free up; a kernel class
+ * takes the last free stream only while it has fewer than
+ * max(1, max_inflight / 3) launches in flight.  A request's arithmetic is
+ * that of qp_solve_batch of its size: results equal solo results bit for bit.
+ *
+ * QP_SERVE_PERSISTENT: one resident 512-thread CTA per SM loops over a ring of
+ * request descriptors that the scheduler publishes in mapped host memory as
+ * soon as a request's data are on the device; a free CTA claims the next
+ * request while the others are in the middle of theirs, keeps its iterate
+ * and factors on the device, runs Alg. 3 for it on 128 or 256 of its threads
+ * and writes the outputs straight to mapped host memory.  Every size runs at
+ * 512 threads (qp_handle_create_threads(dims, 512)): results equal those of a
+ * batch-1 solve of that width and qp_backward_batch bit for bit.  A CTA with
+ * no request for idle_ms leaves (the scheduler starts CTAs again when work
+ * arrives); while CTAs are resident they hold every SM, so no other kernel of
+ * the process runs beside them.  Needs host-native atomics (NVLink-C2C
+ * systems); QP_ENOTSUP otherwise.
+ *
+ * Every wait, on the host and on the device, is bounded. */
 typedef struct qp_server qp_server;
+
+#define QP_SERVE_LAUNCHES 0
+#define QP_SERVE_PERSISTENT 1
 
 typedef struct {
   size_t hbm_budget_bytes; /* device arena for resident requests (>= 1 MiB)     */
-  int32_t max_inflight;    /* launches on the GPU at once, one stream each (1-64) */
-  int32_t max_batch;       /* requests per launch                                */
+  int32_t max_inflight;    /* launches: launches on the GPU at once, one stream
+                              each (1-64)                                         */
+  int32_t max_batch;       /* launches: requests per launch                       */
   int32_t max_queue;       /* requests waiting on the host before QP_EAGAIN       */
   qp_settings settings;    /* solver settings of every request (no warm start)    */
+  int32_t mode;            /* QP_SERVE_LAUNCHES or QP_SERVE_PERSISTENT            */
+  int32_t idle_ms;         /* persistent: a CTA with no request for this long
+                              leaves its loop (1-10000)                           */
 } qp_serve_config;
 
 typedef struct {
@@ -350,12 +377,14 @@ typedef struct {
   int32_t iters;
   float kkt_res;
   double t_submit_ms;      /* server clock (ms since qp_serve_create): submitted */
-  double t_launch_ms;      /* its launch was issued                              */
-  double t_done_ms;        /* its launch's results reached host memory           */
+  double t_launch_ms;      /* its launch was issued (persistent: its descriptor
+                              was published to the resident CTAs)               */
+  double t_done_ms;        /* its results reached host memory (as the scheduler
+                              saw them)                                          */
 } qp_result;
 
 /* Defaults: 1 GiB arena, 8 launches in flight, 1024 requests per launch,
- * 2^20 queued requests, qp_settings_default. */
+ * 2^20 queued requests, qp_settings_default, QP_SERVE_PERSISTENT, idle 50 ms. */
 void qp_serve_config_default(qp_serve_config* c);
 
 /* Arena bytes one request occupies while resident (data, outputs, gradient

@@ -25,6 +25,8 @@ QP_SIGMA_MEHROTRA, QP_SIGMA_CONSTANT = 0, 1
 QP_NORM_SCALED, QP_NORM_ABS = 0, 1
 QP_GWG_FP32, QP_GWG_TF32, QP_GWG_BF16 = 0, 1, 2
 QP_STATIC_CACHE_BYTES = 16 * 1024 * 1024
+QP_SERVE_LAUNCHES, QP_SERVE_PERSISTENT = 0, 1
+SERVE_MODES = {"launches": QP_SERVE_LAUNCHES, "persistent": QP_SERVE_PERSISTENT}
 # per-instance diagnostics word (qp_handle_set_diag)
 QP_STAGE_MASK = 0xFF
 QP_STAGE_NAMES = {0: "none", 1: "scaling", 2: "predictor", 3: "centering", 4: "corrector",
@@ -71,7 +73,7 @@ class Settings(ctypes.Structure):
 class ServeConfig(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int32),
                 ("max_batch", ctypes.c_int32), ("max_queue", ctypes.c_int32),
-                ("settings", Settings)]
+                ("settings", Settings), ("mode", ctypes.c_int32), ("idle_ms", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):

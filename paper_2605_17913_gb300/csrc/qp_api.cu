@@ -152,7 +152,7 @@ int qp_handle_create_threads(const qp_dims* dims, int32_t threads_per_qp, qp_han
   const bool warp = threads_per_qp == 32 ||
                     (threads_per_qp == 0 && dims->batch >= kWarpPerQpMinBatch);
   h->fwd_smem = forward_config(n, m, p, &h->fwd_threads, &h->amax, &h->ws_stride, warp,
-                               threads_per_qp == 256 ? 256 : 512);
+                               threads_per_qp == 256 ? 256 : 512, threads_per_qp == 512);
   if (threads_per_qp != 0 && h->fwd_threads != threads_per_qp) {
     free(h);
     return QP_ENOTSUP;

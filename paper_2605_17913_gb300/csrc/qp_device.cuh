@@ -15,6 +15,33 @@
 
 namespace qpgpu {
 
+// Barrier policies of code that a whole CTA or a subset of a larger CTA runs.
+// CtaBar: every thread of the CTA.
+struct CtaBar {
+  static __device__ __forceinline__ void sync() { __syncthreads(); }
+  static __device__ __forceinline__ int sync_or(int v) { return __syncthreads_or(v); }
+};
+// GroupBar<N>: the CTA's first N threads (whole warps) on named barrier 2,
+// while the CTA's other threads wait elsewhere (barrier 0 is the CTA's own,
+// barrier 1 the factorisation's look-ahead).
+template <int N>
+struct GroupBar {
+  static_assert(N % 32 == 0, "a group is whole warps");
+  static __device__ __forceinline__ void sync() {
+    asm volatile("bar.sync 2, %0;" ::"n"(N) : "memory");
+  }
+  static __device__ __forceinline__ int sync_or(int v) {
+    int r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.s32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, 2, %2, p;\n\tselp.s32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"(v), "n"(N)
+        : "memory");
+    return r;
+  }
+};
+
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kRedK = 16;  // maximum quantities reduced by one block_reduce call
 
@@ -1101,8 +1128,8 @@ __device__ void solve_rows_S(const float* L, int ldk, const float* dinv, int n, 
 }
 
 // kMaxS: 4 (n <= 128) or 8 (n <= 256; only the large-problem variant
-// instantiates the longer register arrays).
-template <int NT, bool kUpper, int kMaxS = 4>
+// instantiates the longer register arrays).  Bar: the barrier it ends with.
+template <int NT, bool kUpper, int kMaxS = 4, class Bar = CtaBar>
 __device__ void solve_rows(const float* L, int ldk, const float* dinv, int n, float* X, int ldx,
                            int row0, int nrows) {
   if (n <= 32)
@@ -1123,7 +1150,7 @@ __device__ void solve_rows(const float* L, int ldk, const float* dinv, int n, fl
     else
       solve_rows_S<NT, 8, kUpper>(L, ldk, dinv, n, X, ldx, row0, nrows);
   }
-  __syncthreads();
+  Bar::sync();
 }
 
 }  // namespace qpgpu

@@ -16,10 +16,12 @@ int forward_blocks_per_sm_nt(size_t smem);
 // (fewer warps per barrier, no register cap; 5 % faster than 256 threads at
 // n = 50), else 512; amax lowered to fit shared memory but not below
 // min(m, n - p), and amax + p <= 126 (warp solves hold at most 128 rows, two
-// of them folded right-hand sides).  Otherwise the large variant (n <= 256):
+// of them folded right-hand sides); onchip512 asks for 512 threads at every
+// n <= 128 (one kernel for every size, as a persistent server runs it).
+// Otherwise the large variant (n <= 256):
 // 512 threads, K, G, A, Y, C in a global workspace, amax + p <= 318.
 size_t forward_config(int n, int m, int p, int* nthreads, int* amax_out, long long* ws_floats,
-                      bool warp_per_qp, int large_threads) {
+                      bool warp_per_qp, int large_threads, bool onchip512) {
   if (nthreads) *nthreads = 0;
   if (amax_out) *amax_out = 0;
   if (ws_floats) *ws_floats = 0;
@@ -41,6 +43,12 @@ size_t forward_config(int n, int m, int p, int* nthreads, int* amax_out, long lo
         if (warp_per_qp && n <= 32) {
           nt_used = 32;
           bytes = (size_t)fwd::make_fwd_layout(n, m, p, amax, 32).total * sizeof(float);
+        } else if (onchip512 && nt_used != 512) {
+          // 512 threads at the same amax (the cache layout is unchanged), if
+          // its layout fits
+          bytes = (size_t)fwd::make_fwd_layout(n, m, p, amax, 512).total * sizeof(float);
+          if (bytes > budget) return 0;
+          nt_used = 512;
         }
         if (nthreads) *nthreads = nt_used;
         if (amax_out) *amax_out = amax;

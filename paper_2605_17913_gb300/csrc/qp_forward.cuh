@@ -209,11 +209,39 @@ static __shared__ unsigned char fwd_parity[512];   // block_reduce buffer parity
 #define QP_BIG(name) float* const name = (kBig ? fwd_state.gbase : fwd_dyn) + fwd_state.L.o_##name
 #define QP_IARR(name) int* const name = reinterpret_cast<int*>(fwd_dyn + fwd_state.L.o_##name)
 
-template <int NT, bool kBig>
+// kCoh: the instance's data may sit in memory that other requests used
+// earlier in the same kernel's lifetime (a persistent serving loop), which the
+// read-only cache path does not see as changed: read it through L2 instead.
+template <int NT, bool kBig, bool kCoh = false>
 struct Solver {
   static constexpr int kPW = panel_width(NT, kBig);
 
-  static __device__ void init(int n, int m, int p, int amax, float* ws, int gwg, int refine) {
+  static __device__ __forceinline__ float ld_ro(const float* ptr) {
+    if constexpr (kCoh) return __ldcg(ptr);
+    else return __ldg(ptr);
+  }
+
+  // The bulk-copy and tensor-core barriers and their chunk counters, once per
+  // CTA (their phases follow from the counts); ends with a barrier.
+  static __device__ void init_async() {
+    if (threadIdx.x == 0) {
+      fwd_state.tc_chunks = 0;
+      fwd_state.g_chunks = 0;
+      fwd_state.tmem = 0;
+      tc::mbar_init(&fwd_state.mbar[0], 1);
+      tc::mbar_init(&fwd_state.mbar[1], 1);
+      tc::mbar_init(&fwd_state.mbar_g[0], 1);
+      tc::mbar_init(&fwd_state.mbar_g[1], 1);
+      tc::fence_mbar_init();
+    }
+    __syncthreads();
+  }
+
+  // keep_async: a CTA that solves several instances in turn keeps the
+  // barriers, chunk counters and TMEM of init_async (never re-initialised
+  // while valid).
+  static __device__ void init(int n, int m, int p, int amax, float* ws, int gwg, int refine,
+                              bool keep_async = false) {
     if (threadIdx.x == 0) {
       fwd_state.L = make_fwd_layout(n, m, p, amax, NT, kBig);
       fwd_state.gbase = kBig ? ws : fwd_dyn;
@@ -226,17 +254,19 @@ struct Solver {
       fwd_state.in_relax = 0;
       fwd_state.all_inactive = 0;
       fwd_state.refine = kBig ? refine : 0;
-      fwd_state.tc_chunks = 0;
-      fwd_state.g_chunks = 0;
-      fwd_state.tmem = 0;
-      if (kBig) {
-        // the bulk-copy and tensor-core barriers, once per CTA (their phases
-        // follow from the chunk counts above)
-        tc::mbar_init(&fwd_state.mbar[0], 1);
-        tc::mbar_init(&fwd_state.mbar[1], 1);
-        tc::mbar_init(&fwd_state.mbar_g[0], 1);
-        tc::mbar_init(&fwd_state.mbar_g[1], 1);
-        tc::fence_mbar_init();
+      if (!keep_async) {
+        fwd_state.tc_chunks = 0;
+        fwd_state.g_chunks = 0;
+        fwd_state.tmem = 0;
+        if (kBig) {
+          // the bulk-copy and tensor-core barriers, once per CTA (their phases
+          // follow from the chunk counts above)
+          tc::mbar_init(&fwd_state.mbar[0], 1);
+          tc::mbar_init(&fwd_state.mbar[1], 1);
+          tc::mbar_init(&fwd_state.mbar_g[0], 1);
+          tc::mbar_init(&fwd_state.mbar_g[1], 1);
+          tc::fence_mbar_init();
+        }
       }
       fwd_state.a = 0;
       fwd_state.nf = p;
@@ -517,9 +547,15 @@ struct Solver {
 #else
         unsigned long long* const ssub = nullptr;
 #endif
-        tc_done = tc::syrk_gwg_staged<NT>(K, L.ldk, qd, G, L.ldg, ea, ina, fwd_state.ni, L.n,
-                                          stage, fwd_state.mbar_g, &fwd_state.g_chunks,
-                                          &fwd_state.tc_flag, &fwd_state.async_lost, ssub);
+        if constexpr (NT == 512)
+          tc_done = tc::syrk_gwg_staged_blocks<NT>(K, L.ldk, qd, G, L.ldg, ea, ina, fwd_state.ni,
+                                                   L.n, stage, fwd_state.mbar_g,
+                                                   &fwd_state.g_chunks, &fwd_state.tc_flag,
+                                                   &fwd_state.async_lost, ssub);
+        else
+          tc_done = tc::syrk_gwg_staged<NT>(K, L.ldk, qd, G, L.ldg, ea, ina, fwd_state.ni, L.n,
+                                            stage, fwd_state.mbar_g, &fwd_state.g_chunks,
+                                            &fwd_state.tc_flag, &fwd_state.async_lost, ssub);
         if (!tc_done && threadIdx.x == 0) fwd_state.diag |= QP_DIAG_STAGE_FALLBACK;
         __syncthreads();
       }
@@ -781,7 +817,7 @@ struct Solver {
 #pragma unroll 8
       for (int j = i + 1; j < n; ++j) qx = fmaf(K[i * L.ldk + j], x[j], qx);
       float aty = 0.f;
-      for (int k = 0; k < p; ++k) aty = fmaf(__ldg(A + k * n + i), mu[c * L.fv + a + k], aty);
+      for (int k = 0; k < p; ++k) aty = fmaf(ld_ro(A + k * n + i), mu[c * L.fv + a + k], aty);
       R[c * L.ldx + i] = r1s[c * L.nv + i] - qx - u[c * L.nv + i] - aty;
     }
     for (int e = t; e < 2 * nf; e += NT) {
@@ -792,7 +828,7 @@ struct Solver {
       } else {
         const float* x = dx + c * L.nv;
         fdx = 0.f;
-        for (int j = 0; j < n; ++j) fdx = fmaf(__ldg(A + (k - a) * n + j), x[j], fdx);
+        for (int j = 0; j < n; ++j) fdx = fmaf(ld_ro(A + (k - a) * n + j), x[j], fdx);
       }
       (c == 0 ? ua : ub)[k] = r2s[c * L.fv + k] - fdx;
     }
@@ -849,7 +885,7 @@ struct Solver {
           for (int j = i + 1; j < n; ++j) qx = fmaf(K[i * L.ldk + j], x[j], qx);
         }
         float aty = 0.f;
-        for (int k = 0; k < p; ++k) aty = fmaf(__ldg(A + k * n + i), y[k], aty);
+        for (int k = 0; k < p; ++k) aty = fmaf(ld_ro(A + k * n + i), y[k], aty);
         const float r = qx + q[i] + tn[i] + aty;
         rt[i] = r;
         mx[12] += isfinite(r) ? 0.f : 1.f;
@@ -878,7 +914,7 @@ struct Solver {
       } else {
         const int k = u - n - m;
         float ax = 0.f;
-        for (int j = 0; j < n; ++j) ax = fmaf(__ldg(A + k * n + j), x[j], ax);
+        for (int j = 0; j < n; ++j) ax = fmaf(ld_ro(A + k * n + j), x[j], ax);
         const float r = ax - b[k];
         re[k] = r;
         mx[12] += isfinite(r) ? 0.f : 1.f;

@@ -22,6 +22,8 @@ struct ReqDesc {
   float* ws;        // workspace of the large-problem variant
   const float* g;   // dl/dx for the backward pass
   float *dQ, *dq, *dA, *db, *dG, *dh;
+  int bnt;          // threads of the backward pass (persistent serving kernel)
+  int pad_;
 };
 
 // Parameters of one forward launch (all device pointers).
@@ -108,10 +110,11 @@ __host__ __device__ inline CacheLayout cache_layout(int n, int m, int p, int ama
 // everything fits in shared memory).  warp_per_qp: one warp per CTA for
 // n <= 32 (throughput of large batches; the amax is the same either way).
 // large_threads: threads per CTA of the large variant, 512 (one CTA per SM)
-// or 256 (two; FP32 G'WG only).
+// or 256 (two; FP32 G'WG only).  onchip512: 512 threads for every n <= 128
+// at the amax of the default (0 if that layout does not fit).
 size_t forward_config(int n, int m, int p, int* nthreads, int* amax,
                       long long* ws_floats = nullptr, bool warp_per_qp = false,
-                      int large_threads = 512);
+                      int large_threads = 512, bool onchip512 = false);
 
 // Batches from this size up run problems with n <= 32 one warp per QP.
 constexpr int kWarpPerQpMinBatch = 2048;
@@ -130,6 +133,34 @@ int backward_threads(int n, bool split);
 
 // Load the kernels' modules ahead of their first launch (the runtime loads
 // lazily); for callers whose launches must not pay for loading.
+// Persistent serving kernel (qp_serve_persist.cu).  The ring, its
+// completion words and the control block live in mapped host memory; head is
+// a device counter of claimed requests.
+struct ServeCtl {
+  uint32_t tail;    // requests published (host: release store)
+  uint32_t stop;    // host: CTAs leave their loop after the request they hold
+  uint32_t exited;  // CTAs that left their loop (device: system-scope atomic)
+  uint32_t pad_;
+};
+struct ServeParams {
+  FwdParams base;          // solver settings of every request
+  const ReqDesc* ring;     // cap descriptors; request s at s % cap
+  uint32_t* done;          // done[s % cap] = s + 1 once request s is complete
+  ServeCtl* ctl;
+  uint32_t* head;          // device: next request to claim
+  uint32_t cap;
+  uint32_t pad_;
+  unsigned long long idle_ns;  // a CTA with no request for this long leaves
+  unsigned long long life_ns;  // a CTA takes no new request after this long
+};
+// Threads per CTA of the persistent kernel, and the dynamic shared memory it
+// is launched with (every supported size's forward and backward fit).
+constexpr int kServeThreads = 512;
+size_t serve_kernel_smem();
+cudaError_t launch_serve_kernel(const ServeParams& S, int grid, cudaStream_t stream);
+// CTAs of the persistent kernel that fit one SM (0 on error).
+int serve_kernel_blocks_per_sm();
+
 void preload_forward_kernels();
 void preload_backward_kernels();
 

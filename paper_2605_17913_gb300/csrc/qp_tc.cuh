@@ -442,5 +442,171 @@ __device__ bool syrk_gwg_staged(float* K, int ldk, const float* qd, const float*
   return ok;
 }
 
+// ---------------------------------------------------------------------------
+// The same sum with each thread's share of K held in registers across all
+// chunks (NT = 512): thread t owns the 8 x 8 block t of K's lower triangle
+// (blocks numbered row by row; diagonal blocks computed whole and stored
+// below the diagonal), starts it from Q, adds every chunk's rows to it and
+// stores it once.  Per row of a chunk that is 4 shared-memory vector loads
+// per 64 FMAs, and K is read and written once per call instead of once per
+// chunk.  Up to n = 248 there are at most 496 blocks (one per thread, the
+// rest idle); at n = 256 (528 blocks) the last 16 blocks are dealt out as 512
+// pairs of adjacent elements, one more per thread.  Stage rows have stride
+// round8(n) (the bulk copy fills round4(n) floats; the columns beyond n only
+// feed sums that are never stored).  Same contract as syrk_gwg_staged.
+// ---------------------------------------------------------------------------
+template <int NT>
+__device__ __noinline__ bool syrk_gwg_staged_blocks(float* K, int ldk, const float* qd,
+                                                    const float* G, int ldg, const float* W,
+                                                    const int* rows, int nrows, int n,
+                                                    float* stage, uint64_t* mbar,
+                                                    uint32_t* chunks, int* flag, int* fail,
+                                                    unsigned long long* sub = nullptr) {
+  static_assert(NT == 512, "one 8 x 8 block per thread needs 512 threads up to n = 256");
+  const int tid = threadIdx.x;
+  const int rowf = round4(n);          // floats copied per row
+  const int rs = (n + 7) & ~7;         // row stride of the stage buffers
+  const uint32_t rowb = (uint32_t)rowf * 4u;
+  const int n8 = rs >> 3;
+  const int U = n8 * (n8 + 1) / 2;     // 8 x 8 blocks of the lower triangle
+  const int E2 = U > NT ? (U - NT) * 32 : 0;  // element pairs of the blocks beyond NT
+  const int nchunks = (nrows + kKc - 1) / kKc;
+  const uint32_t g0 = *chunks;
+  // this thread's block (I, J), J <= I
+  const bool has_blk = tid < U && tid < NT;
+  int I = 0, J = 0;
+  if (has_blk) {
+    const float x8 = 8.0f * (float)tid + 1.0f;
+    I = (int)((x8 * rsqrtf(x8) - 1.0f) * 0.5f);
+    while ((I + 1) * (I + 2) / 2 <= tid) ++I;
+    while (I * (I + 1) / 2 > tid) --I;
+    J = tid - I * (I + 1) / 2;
+  }
+  // this thread's extra element pair (i, j), (i, j + 1) of a block beyond NT
+  const bool has_pair = tid < E2;
+  int ie = 0, je = 0;
+  if (has_pair) {
+    const int u = NT + tid / 32, loc = tid & 31;
+    const float x8 = 8.0f * (float)u + 1.0f;
+    int Iu = (int)((x8 * rsqrtf(x8) - 1.0f) * 0.5f);
+    while ((Iu + 1) * (Iu + 2) / 2 <= u) ++Iu;
+    while (Iu * (Iu + 1) / 2 > u) --Iu;
+    const int Ju = u - Iu * (Iu + 1) / 2;
+    ie = 8 * Iu + (loc >> 2);
+    je = 8 * Ju + ((loc & 3) << 1);
+  }
+  if (tid == 0) *flag = 0;
+  __syncthreads();
+  auto issue = [&](int c) {
+    const uint32_t g = g0 + (uint32_t)c;
+    float* buf = stage + (size_t)(g & 1u) * kKc * rs;
+    const int k0 = c * kKc, kn = min(kKc, nrows - k0);
+    mbar_expect_tx(&mbar[g & 1u], (uint32_t)kn * rowb);
+    for (int k = 0; k < kn; ++k)
+      bulk_g2s(buf + k * rs, G + (size_t)rows[k0 + k] * ldg, rowb, &mbar[g & 1u]);
+  };
+  if (tid == 0) {
+    for (int c = 0; c < 2 && c < nchunks; ++c) issue(c);
+  }
+  // the running sums start from Q: its strict lower triangle is K's upper
+  // triangle (read transposed), its diagonal qd
+  float acc[8][8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const int i = 8 * I + a, j = 8 * J + b;
+      acc[a][b] = (has_blk && i < n && j <= i) ? (j == i ? qd[i] : K[j * ldk + i]) : 0.f;
+    }
+  float ex0 = 0.f, ex1 = 0.f;
+  if (has_pair) {
+    if (ie < n && je <= ie) ex0 = je == ie ? qd[ie] : K[je * ldk + ie];
+    if (ie < n && je + 1 <= ie) ex1 = je + 1 == ie ? qd[ie] : K[(je + 1) * ldk + ie];
+  }
+  int done = 0;  // chunks consumed
+  for (int c = 0; c < nchunks; ++c) {
+    const uint32_t g = g0 + (uint32_t)c;
+    const long long ts0 = sub ? clock64() : 0;
+    if (!mbar_wait(&mbar[g & 1u], (g >> 1) & 1u)) atomicOr(flag, 1);
+    if (__syncthreads_or(*flag)) break;
+    const long long ts1 = sub ? clock64() : 0;
+    float* const buf = stage + (size_t)(g & 1u) * kKc * rs;
+    const int k0 = c * kKc, kn = min(kKc, nrows - k0);
+    // scale the chunk's rows by sqrt(W) once (W <= tau on the inactive rows)
+    for (int e = tid; e < kn * rowf; e += NT) {
+      const int k = e / rowf, col = e - k * rowf;
+      buf[k * rs + col] *= sqrtf(W[rows[k0 + k]]);
+    }
+    __syncthreads();
+    const long long ts2 = sub ? clock64() : 0;
+    if (has_blk) {
+      const float* pu = buf + 8 * I;
+      const float* pv = buf + 8 * J;
+#pragma unroll 1
+      for (int k = 0; k < kn; ++k) {
+        const float4 u0 = *reinterpret_cast<const float4*>(pu + k * rs);
+        const float4 u1 = *reinterpret_cast<const float4*>(pu + k * rs + 4);
+        const float4 v0 = *reinterpret_cast<const float4*>(pv + k * rs);
+        const float4 v1 = *reinterpret_cast<const float4*>(pv + k * rs + 4);
+        const float uu[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+        const float vv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+          for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(uu[a], vv[b], acc[a][b]);
+      }
+    }
+    if (has_pair) {
+      for (int k = 0; k < kn; ++k) {
+        const float ue = buf[k * rs + ie];
+        const float2 ve = *reinterpret_cast<const float2*>(buf + k * rs + je);
+        ex0 = fmaf(ue, ve.x, ex0);
+        ex1 = fmaf(ue, ve.y, ex1);
+      }
+    }
+    done = c + 1;
+    // every thread is done with this buffer, whose generic-proxy writes (the
+    // scaling) must be ordered before the bulk copy that refills it
+    fence_async_smem();
+    __syncthreads();
+    if (sub && tid == 0) {
+      atomicAdd(&sub[0], (unsigned long long)(ts1 - ts0));
+      atomicAdd(&sub[1], (unsigned long long)(ts2 - ts1));
+      atomicAdd(&sub[2], (unsigned long long)(clock64() - ts2));
+    }
+    if (tid == 0 && c + 2 < nchunks) issue(c + 2);
+  }
+  const bool ok = __syncthreads_or(*flag) == 0;
+  if (ok) {
+    // K's lower triangle (its upper triangle, Q, is read above and kept)
+    if (has_blk) {
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+          const int i = 8 * I + a, j = 8 * J + b;
+          if (i < n && j <= i) K[i * ldk + j] = acc[a][b];
+        }
+    }
+    if (has_pair) {
+      if (ie < n && je <= ie) K[ie * ldk + je] = ex0;
+      if (ie < n && je + 1 <= ie) K[ie * ldk + je + 1] = ex1;
+    }
+  }
+  // after a failure: wait (bounded) for the copies already issued, chunks
+  // done .. min(done + 2, nchunks) - 1
+  int bad = 0;
+  if (tid == 0) {
+    for (int c = done; c < nchunks && c < done + 2; ++c) {
+      const uint32_t g = g0 + (uint32_t)c;
+      if (!mbar_wait(&mbar[g & 1u], (g >> 1) & 1u)) bad = 1;
+    }
+    if (bad) *fail = 1;
+    *chunks = g0 + (uint32_t)min(nchunks, done + 2);
+  }
+  __syncthreads();
+  return ok;
+}
+
 }  // namespace tc
 }  // namespace qpgpu

@@ -33,15 +33,23 @@ def _p(a: Optional[np.ndarray]):
 
 class QPServer:
     """One server per device: ``submit`` single QPs, collect them with
-    ``poll``, ``poll_any`` or ``wait``."""
+    ``poll``, ``poll_any`` or ``wait``.  ``mode``: "launches" (ragged launches
+    per kernel class) or "persistent" (resident CTAs that claim requests as
+    they arrive; every size at 512 threads per QP)."""
 
     def __init__(self, hbm_budget_bytes: int = 1 << 30, max_inflight: int = 8,
-                 max_batch: int = 1024, max_queue: int = 1 << 20, **settings):
+                 max_batch: int = 1024, max_queue: int = 1 << 20, mode: str = "persistent",
+                 idle_ms: int = 50, **settings):
         L = _lib.lib()
         cfg = _lib.ServeConfig()
         L.qp_serve_config_default(ctypes.byref(cfg))
         cfg.hbm_budget_bytes = int(hbm_budget_bytes)
         cfg.max_inflight, cfg.max_batch, cfg.max_queue = max_inflight, max_batch, max_queue
+        if mode not in _lib.SERVE_MODES:
+            raise QPError(f"unknown serving mode {mode!r}")
+        cfg.mode = _lib.SERVE_MODES[mode]
+        cfg.idle_ms = int(idle_ms)
+        self.mode = mode
         cfg.settings = _lib.default_settings(**settings)
         h = ctypes.c_void_p()
         check(L.qp_serve_create(ctypes.byref(cfg), ctypes.byref(h)), "qp_serve_create")

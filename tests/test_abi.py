@@ -97,7 +97,14 @@ def test_serve_footprint_and_config_validation(L):
     cfg = _lib.ServeConfig()
     L.qp_serve_config_default(ctypes.byref(cfg))
     assert cfg.hbm_budget_bytes == 1 << 30 and cfg.max_inflight == 8
+    assert cfg.mode == _lib.QP_SERVE_PERSISTENT and cfg.idle_ms == 50
     h = ctypes.c_void_p()
+    # bad modes and idle limits are refused before any device call
+    for mode, idle in ((2, 50), (-1, 50), (_lib.QP_SERVE_PERSISTENT, 0),
+                       (_lib.QP_SERVE_PERSISTENT, 10001)):
+        cfg.mode, cfg.idle_ms = mode, idle
+        assert L.qp_serve_create(ctypes.byref(cfg), ctypes.byref(h)) == _lib.QP_EINVAL
+    cfg.mode, cfg.idle_ms = _lib.QP_SERVE_LAUNCHES, 50
     cfg.max_inflight = 0
     assert L.qp_serve_create(ctypes.byref(cfg), ctypes.byref(h)) == _lib.QP_EINVAL
     assert L.qp_serve_submit(None, None, None) == _lib.QP_EINVAL

@@ -178,6 +178,24 @@ def test_ragged_and_edge_sizes(n, m, p):
     check_grads(res, ref)
 
 
+@pytest.mark.parametrize("n,m,p", [(1, 3, 0), (5, 0, 2), (10, 20, 1), (37, 53, 3), (72, 144, 7)])
+def test_width_512_small_sizes(n, m, p):
+    """The 512-thread on-chip forward at sizes whose default is 128 threads
+    (the width the persistent server runs every size at): the same bars
+    against the oracle, and the same cache layout as the default width."""
+    from paper_2605_17913_gb300.solver import QPSolver
+
+    batch = make_batch("small", 9, seed=6, n=n, m=m, p=p)
+    res = gpu_run(batch, grad=True, threads_per_qp=512)
+    ref = oracle_run(batch, grad=True)
+    check_forward(batch, res, O.solve(batch.Q, batch.q, batch.A, batch.b, batch.G, batch.h,
+                                      tol=1e-12, nthreads=8))
+    check_grads(res, ref)
+    a, b = QPSolver(9, n, p, m, 512).info(), QPSolver(9, n, p, m).info()
+    assert a["fwd_threads"] == 512 and b["fwd_threads"] != 512
+    assert a["max_active"] == b["max_active"] and a["bwd_threads"] == b["bwd_threads"]
+
+
 @pytest.mark.parametrize("workload,B,sizes", [
     ("small", 5, dict(n=130, m=200, p=10)),   # beyond the on-chip n limit
     ("small", 5, dict(n=100, m=400, p=8)),    # n fits, shared memory does not

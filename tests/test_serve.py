@@ -35,13 +35,15 @@ def _inst(i, n, m, p, seed=3):
     return {k: np.asarray(v, dtype=np.float32) for k, v in d.items()}
 
 
-def _solo(d, grad):
+def _solo(d, grad, threads=0):
+    """The request solved alone: a batch-1 qp_solve_batch (forward width
+    `threads`, 0 = the size's default) and qp_backward_batch."""
     from paper_2605_17913_gb300.solver import QPSolver
 
     n, p, m = d["q"].size, d["b"].size, d["h"].size
     T = {k: torch.from_numpy(d[k].reshape((1,) + d[k].shape)).cuda() for k in
          ("Q", "q", "A", "b", "G", "h", "g")}
-    slv = QPSolver(1, n, p, m)
+    slv = QPSolver(1, n, p, m, threads_per_qp=threads)
     cache = slv.new_grad_cache() if grad else None
     out = slv.solve(T["Q"], T["q"], T["A"], T["b"], T["G"], T["h"], grad_cache=cache,
                     tol=SOLVER_TOL)
@@ -65,25 +67,31 @@ SIZES = [(8, 16, 0, False), (10, 20, 1, True), (33, 66, 3, True), (50, 100, 5, F
          (200, 400, 20, False), (200, 400, 20, True), (256, 512, 25, True)]
 
 
-@pytest.fixture(scope="module")
-def served():
+MODES = ["launches", "persistent"]
+# the forward width a served request runs at: the size's default in launches,
+# 512 for every size in the persistent loop
+SOLO_THREADS = {"launches": 0, "persistent": 512}
+
+
+@pytest.fixture(scope="module", params=MODES)
+def served(request):
     from paper_2605_17913_gb300.serve import QPServer
 
     inst = [_inst(i, n, m, p) for i, (n, m, p, _) in enumerate(SIZES)]
-    srv = QPServer(hbm_budget_bytes=512 << 20, tol=SOLVER_TOL)
+    srv = QPServer(hbm_budget_bytes=512 << 20, tol=SOLVER_TOL, mode=request.param)
     try:
         tickets = [_submit(srv, d, g) for d, (_, _, _, g) in zip(inst, SIZES)]
         got = [srv.wait(t, 120000) for t in tickets]
     finally:
         srv.close()
-    return inst, got
+    return inst, got, request.param
 
 
 def test_served_results_match_oracle(served):
     """Every served result against the FP64 oracle at the method's bars:
     scaled KKT <= 1e-5, x <= 1e-4, and (requests with gradients) every
     gradient block <= 1e-3 at the relaxed point."""
-    inst, got = served
+    inst, got, _ = served
     for d, (n, m, p, grad), r in zip(inst, SIZES, got):
         assert r["status"] == 0, (n, r["status"])
         one = lambda k: d[k][None]  # noqa: E731
@@ -101,24 +109,27 @@ def test_served_results_match_oracle(served):
 
 
 def test_served_results_equal_solo_bitwise(served):
-    inst, got = served
+    inst, got, mode = served
     for d, (n, m, p, grad), r in zip(inst, SIZES, got):
-        ref = _solo(d, grad)
+        ref = _solo(d, grad, SOLO_THREADS[mode])
         assert r["status"] == 0 and ref["status"] == 0, (n, r["status"])
         assert r["iters"] == ref["iters"]
         for k in ("x", "y", "z", "s") + (GRAD_KEYS if grad else ()):
             np.testing.assert_array_equal(r[k], ref[k], err_msg=f"{k} at n={n}")
 
 
-def test_requests_arriving_later_start_while_others_run():
+@pytest.mark.parametrize("mode", MODES)
+def test_requests_arriving_later_start_while_others_run(mode):
     from paper_2605_17913_gb300.serve import QPServer
 
-    big = [_inst(100 + i, 256, 512, 25) for i in range(4)]
+    big = [_inst(100 + i, 256, 512, 25) for i in range(8)]
     small = [_inst(200 + i, 10, 20, 1) for i in range(24)]
-    srv = QPServer(hbm_budget_bytes=512 << 20, max_inflight=4, tol=SOLVER_TOL)
+    srv = QPServer(hbm_budget_bytes=512 << 20, max_inflight=4, tol=SOLVER_TOL, mode=mode)
     try:
         tb = [_submit(srv, d, True) for d in big]
-        time.sleep(0.02)
+        # the large requests take ~20 ms on the GPU: the small ones arrive
+        # well within that
+        time.sleep(0.003)
         ts = [_submit(srv, d, i % 3 == 0) for i, d in enumerate(small)]
         rs = [srv.wait(t, 120000) for t in ts]
         rb = [srv.wait(t, 120000) for t in tb]
@@ -133,7 +144,8 @@ def test_requests_arriving_later_start_while_others_run():
     assert sum(r["t_done_ms"] < big_done for r in rs) >= 18
 
 
-def test_admission_by_arena_memory():
+@pytest.mark.parametrize("mode", MODES)
+def test_admission_by_arena_memory(mode):
     from paper_2605_17913_gb300 import _lib
     from paper_2605_17913_gb300.serve import QPServer, footprint_bytes
 
@@ -142,7 +154,7 @@ def test_admission_by_arena_memory():
     each = footprint_bytes(n, p, m, True)
     count = 40
     assert count * each > 2 * budget  # needs several rounds of admission
-    srv = QPServer(hbm_budget_bytes=budget, max_inflight=2, tol=SOLVER_TOL)
+    srv = QPServer(hbm_budget_bytes=budget, max_inflight=2, tol=SOLVER_TOL, mode=mode)
     try:
         inst = [_inst(300 + i, n, m, p) for i in range(count)]
         tickets = [_submit(srv, d, True) for d in inst]
@@ -151,25 +163,26 @@ def test_admission_by_arena_memory():
         srv.close()
     assert all(r["status"] == 0 for r in got)
     # a request larger than the whole arena is refused at submit
-    tiny = QPServer(hbm_budget_bytes=1 << 20, tol=SOLVER_TOL)
+    tiny = QPServer(hbm_budget_bytes=1 << 20, tol=SOLVER_TOL, mode=mode)
     try:
         assert each > 1 << 20
         with pytest.raises(_lib.QPError, match="QP_ENOTSUP"):
             _submit(tiny, inst[0], True)
     finally:
         tiny.close()
-    ref = _solo(inst[7], True)
+    ref = _solo(inst[7], True, SOLO_THREADS[mode])
     for k in ("x",) + GRAD_KEYS:
         np.testing.assert_array_equal(got[7][k], ref[k])
 
 
-def test_wait_times_out_and_the_request_survives():
+@pytest.mark.parametrize("mode", MODES)
+def test_wait_times_out_and_the_request_survives(mode):
     """qp_serve_wait returns QP_ETIMEOUT when its bound runs out before the
     request completes; the request is still collected afterwards, intact."""
     from paper_2605_17913_gb300.serve import QPServer
 
     d = _inst(400, 256, 512, 25)
-    srv = QPServer(hbm_budget_bytes=256 << 20, tol=SOLVER_TOL)
+    srv = QPServer(hbm_budget_bytes=256 << 20, tol=SOLVER_TOL, mode=mode)
     try:
         t = _submit(srv, d, True)
         with pytest.raises(Exception, match="not done after 0 ms"):
@@ -178,12 +191,13 @@ def test_wait_times_out_and_the_request_survives():
     finally:
         srv.close()
     assert r["status"] == 0
-    ref = _solo(d, True)
+    ref = _solo(d, True, SOLO_THREADS[mode])
     for k in ("x",) + GRAD_KEYS:
         np.testing.assert_array_equal(r[k], ref[k])
 
 
-def test_client_that_stops_collecting_does_not_block_others():
+@pytest.mark.parametrize("mode", MODES)
+def test_client_that_stops_collecting_does_not_block_others(mode):
     """Requests a client never collects stay completed on the host side;
     another client's requests, submitted after them, run and are collected
     as usual (results bit for bit those of solo runs)."""
@@ -191,7 +205,7 @@ def test_client_that_stops_collecting_does_not_block_others():
 
     idle = [_inst(500 + i, 40, 80, 4) for i in range(24)]
     busy = [_inst(600 + i, 40, 80, 4) for i in range(24)]
-    srv = QPServer(hbm_budget_bytes=64 << 20, max_inflight=2, tol=SOLVER_TOL)
+    srv = QPServer(hbm_budget_bytes=64 << 20, max_inflight=2, tol=SOLVER_TOL, mode=mode)
     try:
         for d in idle:
             _submit(srv, d, True)  # never collected
@@ -201,12 +215,13 @@ def test_client_that_stops_collecting_does_not_block_others():
         srv.close()  # drops the uncollected tickets
     assert all(r["status"] == 0 for r in rb)
     for i in (0, 1, 23):
-        ref = _solo(busy[i], i % 2 == 0)
+        ref = _solo(busy[i], i % 2 == 0, SOLO_THREADS[mode])
         for k in ("x", "z") + (GRAD_KEYS if i % 2 == 0 else ()):
             np.testing.assert_array_equal(rb[i][k], ref[k])
 
 
-def test_non_positive_definite_request_is_isolated():
+@pytest.mark.parametrize("mode", MODES)
+def test_non_positive_definite_request_is_isolated(mode):
     """A request whose Q is not positive definite (K = Q + G'G indefinite at
     the start) ends QP_NUMERICAL; the requests around it, in the same
     launches, are solved exactly as alone."""
@@ -216,7 +231,7 @@ def test_non_positive_definite_request_is_isolated():
     good = [_inst(700 + i, 10, 20, 1) for i in range(6)]
     bad = dict(_inst(710, 10, 20, 1))
     bad["Q"] = (-10.0 * np.eye(10)).astype(np.float32)
-    srv = QPServer(hbm_budget_bytes=64 << 20, max_inflight=1, tol=SOLVER_TOL)
+    srv = QPServer(hbm_budget_bytes=64 << 20, max_inflight=1, tol=SOLVER_TOL, mode=mode)
     try:
         tg = [_submit(srv, d, True) for d in good[:3]]
         tbad = _submit(srv, bad, True)
@@ -228,6 +243,26 @@ def test_non_positive_definite_request_is_isolated():
     assert rbad["status"] == _lib.QP_NUMERICAL
     for d, r in zip(good, rg):
         assert r["status"] == 0
-        ref = _solo(d, True)
+        ref = _solo(d, True, SOLO_THREADS[mode])
+        for k in ("x", "y", "z", "s") + GRAD_KEYS:
+            np.testing.assert_array_equal(r[k], ref[k])
+
+
+def test_persistent_ctas_leave_when_idle_and_come_back():
+    """Resident CTAs that find no request for idle_ms leave their loop; a
+    request submitted afterwards starts new ones and is solved as alone."""
+    from paper_2605_17913_gb300.serve import QPServer
+
+    a, b = _inst(800, 40, 80, 4), _inst(801, 150, 300, 15)
+    srv = QPServer(hbm_budget_bytes=64 << 20, tol=SOLVER_TOL, mode="persistent", idle_ms=5)
+    try:
+        ra = srv.wait(_submit(srv, a, True), 60000)
+        time.sleep(0.2)  # every CTA has left by now
+        rb = srv.wait(_submit(srv, b, True), 60000)
+    finally:
+        srv.close()
+    for d, r in ((a, ra), (b, rb)):
+        assert r["status"] == 0
+        ref = _solo(d, True, 512)
         for k in ("x", "y", "z", "s") + GRAD_KEYS:
             np.testing.assert_array_equal(r[k], ref[k])
