@@ -123,6 +123,113 @@ __device__ __forceinline__ float row_dot(const float* M, int ld, int r, const fl
   return s0 + s1;
 }
 
+// One sweep over the rows of M (rows x n, row stride ld) in global memory,
+// for matrices too large to stage: a warp takes U rows at a time with lanes
+// over the columns (lane owns columns lane + 32 s, s < S), so every load is
+// a coalesced segment of a row and U x S loads are in flight per lane.  For
+// each row r it forms, in the same pass,
+//   the ND row dots  dout[k][r] = M[r] . xv[k]          (butterfly sums), and
+//   the NC column sums of cw[k][r] M[r][.]   into this warp's partials
+//     part[(k * nw + w) * ldp + c]                        (nw = NT / 32),
+// which the caller adds over the warps in a fixed order.  kUpper: row r
+// counts only its columns c > r (a symmetric matrix kept as its strict upper
+// triangle).  kL2: read through L2 (memory that a persistent CTA may have
+// seen hold other data).  No barrier.
+template <int NT, int S, int U, int ND, int NC, bool kUpper, bool kL2>
+__device__ __forceinline__ void warp_rows(const float* M, int ld, int rows, int n,
+                                          const float* const* xv, float* const* dout,
+                                          const float* const* cw, float* part, int ldp) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int nw = NT / 32;
+  float xr[ND > 0 ? ND : 1][S], acc[NC > 0 ? NC : 1][S];
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int c = lane + 32 * s;
+#pragma unroll
+    for (int k = 0; k < ND; ++k) xr[k][s] = c < n ? xv[k][c] : 0.f;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) acc[k][s] = 0.f;
+  }
+  for (int r0 = w * U; r0 < rows; r0 += nw * U) {
+    float v[U][S];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int r = r0 + u;
+      const float* row = M + (size_t)r * ld;
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        const int c = lane + 32 * s;
+        const bool in = r < rows && c < n && (!kUpper || c > r);
+        v[u][s] = in ? (kL2 ? __ldcg(row + c) : row[c]) : 0.f;
+      }
+    }
+    if constexpr (ND > 0) {
+      float d[U][ND];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int k = 0; k < ND; ++k) {
+          d[u][k] = 0.f;
+#pragma unroll
+          for (int s = 0; s < S; ++s) d[u][k] = fmaf(v[u][s], xr[k][s], d[u][k]);
+        }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+          for (int k = 0; k < ND; ++k) d[u][k] += __shfl_xor_sync(kFull, d[u][k], o);
+      if (lane == 0) {
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (r0 + u < rows) {
+#pragma unroll
+            for (int k = 0; k < ND; ++k) dout[k][r0 + u] = d[u][k];
+          }
+      }
+    }
+    if constexpr (NC > 0) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int r = r0 + u;
+        if (r < rows) {
+#pragma unroll
+          for (int k = 0; k < NC; ++k) {
+            const float wr = cw[k][r];
+#pragma unroll
+            for (int s = 0; s < S; ++s) acc[k][s] = fmaf(wr, v[u][s], acc[k][s]);
+          }
+        }
+      }
+    }
+  }
+  if constexpr (NC > 0) {
+#pragma unroll
+    for (int k = 0; k < NC; ++k)
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        const int c = lane + 32 * s;
+        if (c < n) part[(k * nw + w) * ldp + c] = acc[k][s];
+      }
+  }
+}
+
+// warp_rows for the column count n: S = ceil(n / 32) register slots per lane
+// (n <= 256, the large variant's range).
+template <int NT, int U, int ND, int NC, bool kUpper, bool kL2>
+__device__ __forceinline__ void warp_rows_n(const float* M, int ld, int rows, int n,
+                                            const float* const* xv, float* const* dout,
+                                            const float* const* cw, float* part, int ldp) {
+  if (n <= 160)
+    warp_rows<NT, 5, U, ND, NC, kUpper, kL2>(M, ld, rows, n, xv, dout, cw, part, ldp);
+  else if (n <= 192)
+    warp_rows<NT, 6, U, ND, NC, kUpper, kL2>(M, ld, rows, n, xv, dout, cw, part, ldp);
+  else if (n <= 224)
+    warp_rows<NT, 7, U, ND, NC, kUpper, kL2>(M, ld, rows, n, xv, dout, cw, part, ldp);
+  else
+    warp_rows<NT, 8, U, ND, NC, kUpper, kL2>(M, ld, rows, n, xv, dout, cw, part, ldp);
+}
+
 // Two vectors at once.
 __device__ __forceinline__ void row_dot2(const float* M, int ld, int r, const float* x,
                                          const float* y, int nv, float& ox, float& oy) {
@@ -488,9 +595,14 @@ __device__ __forceinline__ int pbw_off(int r) {
 }
 
 // Row stride of the diagonal block's factor fb (PW x fb_ld floats): padded so
-// that one row per lane is stored without bank conflicts.
+// that one row per lane is stored without bank conflicts.  After fb: the
+// 32 x 8 exchange buffer of factor_diag_block, then the factor's transpose
+// below the diagonal (fbt: row k holds L[t][k] for t > k, zeros elsewhere;
+// 16-byte aligned rows of fbt_ld floats) for the column-ordered panel solve.
 __host__ __device__ constexpr int fb_ld(int pw) { return pw + 1; }
-__host__ __device__ constexpr int fb_floats(int pw) { return pw * fb_ld(pw) + 32 * 8; }
+__host__ __device__ constexpr int fbt_ld(int pw) { return pw + 4; }
+__host__ __device__ constexpr int fbt_off(int pw) { return pw * fb_ld(pw) + 32 * 8; }
+__host__ __device__ constexpr int fb_floats(int pw) { return fbt_off(pw) + pw * fbt_ld(pw); }
 
 // Cholesky of the jb x jb diagonal block at (j0, j0) of M by one warp, lane i
 // holding row i, in PW / 8 sub-blocks of 8 columns: every lane factors the
@@ -626,6 +738,12 @@ __device__ __noinline__ int factor_diag_block(float* M, int ld, int j0, int jb, 
     for (int c = 0; c < PW; ++c) fb[lane * fb_ld(PW) + c] = c <= lane ? a[c] : 0.0f;
     dinv[j0 + lane] = rinv;
   }
+  {
+    // the transpose below the diagonal: lane t writes column t of fbt
+    float* const fbt = fb + fbt_off(PW);
+#pragma unroll
+    for (int c = 0; c < PW; ++c) fbt[c * fbt_ld(PW) + lane] = (c < lane && lane < jb) ? a[c] : 0.0f;
+  }
   __syncwarp();
   // the block's factor back to M, one row per step of the warp (coalesced)
   for (int r = 0; r < jb; ++r)
@@ -699,13 +817,37 @@ __device__ bool panel_factor_wide(float* M, int ld, int j0, int jb, float* dinv,
 #pragma unroll
       for (int t = 0; t < PW; ++t) v[t] = t < jb ? row[t] : 0.0f;
     }
+    if (PW == 32) {
+      // column order: step k finishes v[k] and takes its multiple off every
+      // later entry, with column k of the factor read as 16-byte rows of fbt
+      // (the same operations in the same order as the row-ordered solve)
+      const float* const fbt = fb + fbt_off(PW);
 #pragma unroll
-    for (int t = 0; t < PW; ++t) {
-      if (t < jb) {
-        float acc = v[t];
+      for (int k = 0; k < PW; ++k) {
+        if (k < jb) {
+          v[k] *= dinv[j0 + k];
+          const float4* lt = reinterpret_cast<const float4*>(fbt + k * fbt_ld(PW));
 #pragma unroll
-        for (int u = 0; u < t; ++u) acc = fmaf(-v[u], fb[t * fb_ld(PW) + u], acc);
-        v[t] = acc * dinv[j0 + t];
+          for (int g = (k + 1) >> 2; g < PW / 4; ++g) {
+            const float4 l4 = lt[g];
+            const float lv[4] = {l4.x, l4.y, l4.z, l4.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int t = 4 * g + q;
+              if (t > k && t < jb) v[t] = fmaf(-v[k], lv[q], v[t]);
+            }
+          }
+        }
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < PW; ++t) {
+        if (t < jb) {
+          float acc = v[t];
+#pragma unroll
+          for (int u = 0; u < t; ++u) acc = fmaf(-v[u], fb[t * fb_ld(PW) + u], acc);
+          v[t] = acc * dinv[j0 + t];
+        }
       }
     }
 #pragma unroll
@@ -782,16 +924,27 @@ __device__ __forceinline__ void trailing_tile(int t, const float* Pb, float* A, 
     sgn = 1.0f;
   }
   const bool diag = I == J;
+  // whole off-diagonal tiles of 16-byte aligned rows move as float4 rows
+  const bool vec = !diag && rmax >= 4 && cmax >= 4 && (ld & 3) == 0 &&
+                   (reinterpret_cast<uintptr_t>(dst) & 15) == 0;
   // the tile's current values, read before the product and before any
   // store: a store through dst may alias a later load of dst, so loads
   // interleaved with the stores would each wait for the one before (16
   // serial round trips per tile to L2)
   float old[4][4];
+  if (vec) {
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < 4; ++a) {
+      const float4 o4 = *reinterpret_cast<const float4*>(dst + a * ld);
+      old[a][0] = o4.x; old[a][1] = o4.y; old[a][2] = o4.z; old[a][3] = o4.w;
+    }
+  } else {
 #pragma unroll
-    for (int b = 0; b < 4; ++b)
-      old[a][b] = (a < rmax && b < cmax && (!diag || b <= a)) ? dst[a * ld + b] : 0.f;
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+        old[a][b] = (a < rmax && b < cmax && (!diag || b <= a)) ? dst[a * ld + b] : 0.f;
+  }
   float acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
@@ -814,12 +967,20 @@ __device__ __forceinline__ void trailing_tile(int t, const float* Pb, float* A, 
         acc[a][b] = fmaf(ra[a].w, cb[b].w, acc[a][b]);
       }
   }
+  if (vec) {
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < 4; ++a)
+      *reinterpret_cast<float4*>(dst + a * ld) =
+          make_float4(fmaf(sgn, acc[a][0], old[a][0]), fmaf(sgn, acc[a][1], old[a][1]),
+                      fmaf(sgn, acc[a][2], old[a][2]), fmaf(sgn, acc[a][3], old[a][3]));
+  } else {
 #pragma unroll
-    for (int b = 0; b < 4; ++b)
-      if (a < rmax && b < cmax && (!diag || b <= a))
-        dst[a * ld + b] = fmaf(sgn, acc[a][b], old[a][b]);
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+        if (a < rmax && b < cmax && (!diag || b <= a))
+          dst[a * ld + b] = fmaf(sgn, acc[a][b], old[a][b]);
+  }
 }
 
 // Rank-PW trailing update with the panel in Pbw (same row sets and rules as
@@ -1027,29 +1188,48 @@ __device__ __forceinline__ void warp_upper_solve(const float* L, int ldk, const 
 // Blocked triangular solves for factors in global memory (large variant):
 // x_v <- L^-1 x_v (lower) or L^-T x_v (upper) for one or two vectors x0, x1
 // (x1 may be null) of length n in shared memory; L lower, stride ld;
-// dinv = 1 / diag(L).  32 indices per block: warp 0 loads the block's 32x32
-// diagonal part into registers (all 32 loads of a lane in flight at once) and
-// solves it with shuffles; then every thread applies the block to one of the
-// remaining entries (32 independent loads each).  Two barriers per block,
-// instead of n dependent round trips to L2 on a single warp.
+// dinv = 1 / diag(L).  32 indices per block: warp 0 holds the block's 32x32
+// diagonal part in registers and solves it with shuffles; threads 32 .. NT-1
+// then apply the block to the remaining entries, one row each (32
+// independent loads).  The loads never wait on the solve: the rows' entries
+// of a block are loaded before the barrier, while warp 0 solves its
+// diagonal part, and warp 0 loads the next diagonal part while the others
+// apply the current block.  Two barriers per block.
 // ---------------------------------------------------------------------------
 template <int NT, bool kUpper>
-__device__ void block_trsv(const float* L, int ld, const float* dinv, int n, float* x0,
-                           float* x1) {
+__device__ __noinline__ void block_trsv(const float* L, int ld, const float* dinv, int n,
+                                        float* x0, float* x1) {
+  static_assert(NT >= 64, "warp 0 solves, the other warps apply");
+  constexpr int NR = NT - 32;
   const int t = threadIdx.x, lane = t & 31;
   const int nblk = (n + 31) >> 5;
+  // r: in warp 0 the block's diagonal part -- lower: lane l holds row l,
+  // r[k] = L[j0+l][j0+k] (k <= l); upper: lane l holds column l,
+  // r[k] = L[j0+k][j0+l] (k >= l) --, in the other threads the entries of
+  // the row they apply the block to
+  float r[32];
+  auto load_diag = [&](int bk) {
+    const int j0 = 32 * (kUpper ? nblk - 1 - bk : bk);
+    const int jb = min(32, n - j0);
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      const bool in = lane < jb && k < jb && (kUpper ? k >= lane : k <= lane);
+      r[k] = in ? (kUpper ? L[(j0 + k) * ld + j0 + lane] : L[(j0 + lane) * ld + j0 + k]) : 0.f;
+    }
+  };
+  auto load_row = [&](int i, int j0, int jb) {
+#pragma unroll
+    for (int k = 0; k < 32; ++k)
+      r[k] = k < jb ? (kUpper ? L[(j0 + k) * ld + i] : L[i * ld + j0 + k]) : 0.f;
+  };
+  if (t < 32 && nblk > 0) load_diag(0);
   for (int bk = 0; bk < nblk; ++bk) {
     const int j0 = 32 * (kUpper ? nblk - 1 - bk : bk);
     const int jb = min(32, n - j0);
+    // the rest: lower -> entries i >= j0 + jb, upper -> entries i < j0
+    const int r0 = kUpper ? 0 : j0 + jb, r1 = kUpper ? j0 : n;
+    const int i0 = r0 + t - 32;
     if (t < 32) {
-      // lower: lane l holds row l of the block, a[k] = L[j0+l][j0+k] (k <= l);
-      // upper: lane l holds column l, a[k] = L[j0+k][j0+l] (k >= l)
-      float a[32];
-#pragma unroll
-      for (int k = 0; k < 32; ++k) {
-        const bool in = lane < jb && k < jb && (kUpper ? k >= lane : k <= lane);
-        a[k] = in ? (kUpper ? L[(j0 + k) * ld + j0 + lane] : L[(j0 + lane) * ld + j0 + k]) : 0.f;
-      }
       float v0 = lane < jb ? x0[j0 + lane] : 0.f;
       float v1 = (x1 && lane < jb) ? x1[j0 + lane] : 0.f;
 #pragma unroll
@@ -1061,8 +1241,8 @@ __device__ void block_trsv(const float* L, int ld, const float* dinv, int n, flo
           const float s1 = __shfl_sync(kFull, v1 * dk, k);
           if (lane == k) { v0 = s0; v1 = s1; }
           if (kUpper ? lane < k : lane > k) {
-            v0 = fmaf(-a[k], s0, v0);
-            v1 = fmaf(-a[k], s1, v1);
+            v0 = fmaf(-r[k], s0, v0);
+            v1 = fmaf(-r[k], s1, v1);
           }
         }
       }
@@ -1070,25 +1250,25 @@ __device__ void block_trsv(const float* L, int ld, const float* dinv, int n, flo
         x0[j0 + lane] = v0;
         if (x1) x1[j0 + lane] = v1;
       }
+      if (bk + 1 < nblk) load_diag(bk + 1);
+    } else if (i0 < r1) {
+      load_row(i0, j0, jb);
     }
     __syncthreads();
-    // the rest: lower -> entries i >= j0 + jb, upper -> entries i < j0
-    const int r0 = kUpper ? 0 : j0 + jb, r1 = kUpper ? j0 : n;
-    for (int i = r0 + t; i < r1; i += NT) {
-      float l[32];
+    if (t >= 32) {
+      for (int i = i0; i < r1; i += NR) {
+        if (i != i0) load_row(i, j0, jb);
+        float acc0 = x0[i], acc1 = x1 ? x1[i] : 0.f;
 #pragma unroll
-      for (int k = 0; k < 32; ++k)
-        l[k] = k < jb ? (kUpper ? L[(j0 + k) * ld + i] : L[i * ld + j0 + k]) : 0.f;
-      float acc0 = x0[i], acc1 = x1 ? x1[i] : 0.f;
-#pragma unroll
-      for (int k = 0; k < 32; ++k) {
-        if (k < jb) {
-          acc0 = fmaf(-l[k], x0[j0 + k], acc0);
-          if (x1) acc1 = fmaf(-l[k], x1[j0 + k], acc1);
+        for (int k = 0; k < 32; ++k) {
+          if (k < jb) {
+            acc0 = fmaf(-r[k], x0[j0 + k], acc0);
+            if (x1) acc1 = fmaf(-r[k], x1[j0 + k], acc1);
+          }
         }
+        x0[i] = acc0;
+        if (x1) x1[i] = acc1;
       }
-      x0[i] = acc0;
-      if (x1) x1[i] = acc1;
     }
     __syncthreads();
   }

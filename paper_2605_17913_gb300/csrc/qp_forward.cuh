@@ -75,6 +75,8 @@ struct FLayout {
   int o_rf;   // refinement of the folded solves (large variant): the saved
               // right-hand sides of both columns (2 nv + 2 fv floats)
   int o_rfs;  // its per-sweep scratch in the union region (4 nv + 2 fv floats)
+  int o_wp;   // (large variant) per-warp column sums of the row sweeps over K,
+              // G, A, in the union region (3 (NT / 32) nv floats)
   int total;
 };
 
@@ -96,10 +98,13 @@ __host__ __device__ inline FLayout make_fwd_layout(int n, int m, int p, int amax
                                                    bool split = false) {
   FLayout L;
   L.n = n; L.m = m; L.p = p; L.amax = amax; L.fmax = amax + p;
-  L.ldk = ld_odd(n);
+  // odd strides keep shared-memory rows and columns free of bank conflicts;
+  // the large variant's K, Y, C live in global memory, where 16-byte aligned
+  // rows (a multiple of 4 floats, odd in quarters) allow vector accesses
+  L.ldk = split ? ld_vec(n) : ld_odd(n);
   L.ldg = ld_vec(n);
   L.ldx = round4(n);
-  L.ldc = ld_odd(L.fmax + 2);
+  L.ldc = split ? ld_vec(L.fmax + 2) : ld_odd(L.fmax + 2);
   L.nv = round4(n); L.mv = round4(m > 0 ? m : 1); L.pv = round4(p > 0 ? p : 1);
   L.fv = round4(L.fmax > 0 ? L.fmax : 1);
   int o = 0;
@@ -134,6 +139,7 @@ __host__ __device__ inline FLayout make_fwd_layout(int n, int m, int p, int amax
     // (large variant) the refinement sweep's dx, mu and G't of both columns,
     // live only within a sweep, after the factorisation
     L.o_rfs = take(split ? 4 * L.nv + 2 * L.fv : 0);
+    L.o_wp = take(split ? 3 * (nthreads / 32) * L.nv : 0);
     if (o < base + pb) o = base + pb;
   }
   L.o_q = take(L.nv); L.o_x = take(L.nv); L.o_rt = take(L.nv); L.o_dinv = take(L.nv);
@@ -748,14 +754,27 @@ struct Solver {
   static __device__ __noinline__ void g_times_dx(int slot0, int nrhs) {
     const FLayout& L = fwd_state.L;
     QP_BIG(G); QP_ARR(R); QP_ARR(ea); QP_ARR(eb);
-    for (int r = threadIdx.x; r < L.m; r += NT) {
+    if constexpr (kBig) {
+      // G in global memory: coalesced row sweep, a warp per four rows
       if (nrhs == 2) {
-        float u, v;
-        row_dot2(G, L.ldg, r, R, R + L.ldx, L.nv, u, v);
-        ea[r] = u;
-        eb[r] = v;
+        const float* xv[2] = {R, R + L.ldx};
+        float* dv[2] = {ea, eb};
+        warp_rows_n<NT, 4, 2, 0, false, false>(G, L.ldg, L.m, L.n, xv, dv, nullptr, nullptr, 0);
       } else {
-        (slot0 == 0 ? ea : eb)[r] = row_dot(G, L.ldg, r, R + slot0 * L.ldx, L.nv);
+        const float* xv[1] = {R + slot0 * L.ldx};
+        float* dv[1] = {slot0 == 0 ? ea : eb};
+        warp_rows_n<NT, 4, 1, 0, false, false>(G, L.ldg, L.m, L.n, xv, dv, nullptr, nullptr, 0);
+      }
+    } else {
+      for (int r = threadIdx.x; r < L.m; r += NT) {
+        if (nrhs == 2) {
+          float u, v;
+          row_dot2(G, L.ldg, r, R, R + L.ldx, L.nv, u, v);
+          ea[r] = u;
+          eb[r] = v;
+        } else {
+          (slot0 == 0 ? ea : eb)[r] = row_dot(G, L.ldg, r, R + slot0 * L.ldx, L.nv);
+        }
       }
     }
     __syncthreads();
@@ -860,7 +879,39 @@ struct Solver {
     for (int r = t; r < m; r += NT) ks[0] = fmaf(z[r], s[r], ks[0]);
     reduce<1>(ks, red, OpSum());
     const float kappa = m > 0 ? ks[0] / (float)m : 0.f;
-    {
+    // the large variant: one coalesced sweep over the rows of K's upper
+    // triangle (Q), G and A gives Q x (row dots into rt, column sums), G x
+    // (into ri), G'z, A x (into re) and A'y; qcol / acol hold the Q and A
+    // column sums afterwards
+    float* qcol = nullptr;
+    float* acol = nullptr;
+    if constexpr (kBig) {
+      QP_ARR(wp);
+      constexpr int nw = NT / 32;
+      const float* xq[1] = {x};
+      float* dq[1] = {rt};
+      warp_rows_n<NT, 4, 1, 1, true, false>(K, L.ldk, n, n, xq, dq, xq, wp, L.nv);
+      float* dg[1] = {ri};
+      const float* cz[1] = {z};
+      warp_rows_n<NT, 4, 1, 1, false, false>(G, L.ldg, m, n, xq, dg, cz, wp + nw * L.nv, L.nv);
+      float* da[1] = {re};
+      const float* cy[1] = {y};
+      warp_rows_n<NT, 4, 1, 1, false, kCoh>(A, n, p, n, xq, da, cy, wp + 2 * nw * L.nv, L.nv);
+      __syncthreads();
+      // column sums over the warps, in warp order, into each matrix's first
+      // partial row (column c is summed and written by one thread)
+      for (int e = t; e < 3 * n; e += NT) {
+        const int k = e / n, c = e - k * n;
+        float* pk = wp + k * nw * L.nv;
+        float acc = 0.f;
+        for (int w2 = 0; w2 < nw; ++w2) acc += pk[w2 * L.nv + c];
+        if (k == 1) tn[c] = acc;
+        else pk[c] = acc;
+      }
+      __syncthreads();
+      qcol = wp;
+      acol = wp + 2 * nw * L.nv;
+    } else {
       const float* vv[1] = {z};
       float* oo[1] = {tn};
       col_dot<NT, 1>(G, L.ldg, m, n, vv, oo, col);
@@ -874,18 +925,16 @@ struct Solver {
         const int i = u;
         // (Q x)_i from K's strict upper triangle and the diagonal qd
         float qx = qd[i] * x[i];
+        float aty = 0.f;
         if constexpr (kBig) {
-          // K in global memory: sixteen loads in flight per thread
-#pragma unroll 16
-          for (int j = 0; j < i; ++j) qx = fmaf(K[j * L.ldk + i], x[j], qx);
-#pragma unroll 16
-          for (int j = i + 1; j < n; ++j) qx = fmaf(K[i * L.ldk + j], x[j], qx);
+          // the sweep's parts: row i's upper entries (rt), column i above it
+          qx += rt[i] + qcol[i];
+          aty = acol[i];
         } else {
           for (int j = 0; j < i; ++j) qx = fmaf(K[j * L.ldk + i], x[j], qx);
           for (int j = i + 1; j < n; ++j) qx = fmaf(K[i * L.ldk + j], x[j], qx);
+          for (int k = 0; k < p; ++k) aty = fmaf(ld_ro(A + k * n + i), y[k], aty);
         }
-        float aty = 0.f;
-        for (int k = 0; k < p; ++k) aty = fmaf(ld_ro(A + k * n + i), y[k], aty);
         const float r = qx + q[i] + tn[i] + aty;
         rt[i] = r;
         mx[12] += isfinite(r) ? 0.f : 1.f;
@@ -893,7 +942,7 @@ struct Solver {
         mx[2] = fmaxf(mx[2], fabsf(aty)); mx[3] = fmaxf(mx[3], fabsf(tn[i]));
       } else if (u < n + m) {
         const int r = u - n;
-        const float gx = row_dot(G, L.ldg, r, x, L.nv);
+        const float gx = kBig ? ri[r] : row_dot(G, L.ldg, r, x, L.nv);
         const float rii = gx + s[r] - h[r];
         ri[r] = rii;
         mx[12] += (isfinite(rii) && isfinite(z[r]) && isfinite(s[r])) ? 0.f : 1.f;
@@ -914,7 +963,11 @@ struct Solver {
       } else {
         const int k = u - n - m;
         float ax = 0.f;
-        for (int j = 0; j < n; ++j) ax = fmaf(ld_ro(A + k * n + j), x[j], ax);
+        if constexpr (kBig) {
+          ax = re[k];
+        } else {
+          for (int j = 0; j < n; ++j) ax = fmaf(ld_ro(A + k * n + j), x[j], ax);
+        }
         const float r = ax - b[k];
         re[k] = r;
         mx[12] += isfinite(r) ? 0.f : 1.f;
@@ -991,7 +1044,24 @@ struct Solver {
     __syncthreads();
     const float* vv[2] = {ta, tb};
     float* oo[2] = {R, R + L.ldx};
-    col_dot<NT, 2>(G, L.ldg, m, L.n, vv, oo, col, rt, -1.0f);
+    if constexpr (kBig) {
+      // G in global memory: coalesced row sweep, per-warp column sums added
+      // in warp order
+      QP_ARR(wp);
+      constexpr int nw = NT / 32;
+      warp_rows_n<NT, 4, 0, 2, false, false>(G, L.ldg, m, L.n, nullptr, nullptr, vv, wp, L.nv);
+      __syncthreads();
+      for (int e = t; e < 2 * L.n; e += NT) {
+        const int k = e / L.n, c = e - k * L.n;
+        const float* pk = wp + k * nw * L.nv;
+        float acc = 0.f;
+        for (int w2 = 0; w2 < nw; ++w2) acc += pk[w2 * L.nv + c];
+        oo[k][c] = k == 0 ? acc - rt[c] : acc;
+      }
+      __syncthreads();
+    } else {
+      col_dot<NT, 2>(G, L.ldg, m, L.n, vv, oo, col, rt, -1.0f);
+    }
     QP_MARK(PH_RHS);
   }
 

@@ -75,8 +75,9 @@ struct BwdParams {
 // (int32, -1 for inactive rows) and the point (x, y, z); s completes the
 // solve's snapshot (x, y, z, s) that the relax starts from.
 // Large-problem variant (split): L, Y and L_C are stored unpacked with the
-// forward kernel's strides ldk = n | 1 (L, Y) and ldc = (amax + p + 2) | 1
-// (L_C), so that the backward pass reads them in place.
+// forward kernel's workspace strides (ldk for L and Y, ldc for L_C: multiples
+// of 4 floats whose quarter is odd), so that the backward pass reads them in
+// place.
 struct CacheLayout {
   int oHdr, oL, oY, oLC, oW, oPos, ox, oy, oz, os, stride;
   int ldk, ldc;  // strides of L / Y and of L_C (split layout; 0 when packed)
@@ -88,8 +89,13 @@ __host__ __device__ inline CacheLayout cache_layout(int n, int m, int p, int ama
   const long long f = (long long)amax + p;
   CacheLayout c;
   int o = 0;
-  c.ldk = split ? (n | 1) : 0;
-  c.ldc = split ? (int)((f + 2) | 1) : 0;
+  // the forward's workspace strides: a multiple of 4 floats whose quarter is odd
+  auto ldv = [](long long v) -> int {
+    int l = (int)((v < 1 ? 1 : v) + 3) & ~3;
+    return ((l >> 2) & 1) ? l : l + 4;
+  };
+  c.ldk = split ? ldv(n) : 0;
+  c.ldc = split ? ldv(f + 2) : 0;
   c.oHdr = o; o += 4;
   c.oL = o; o += r4(split ? (long long)n * c.ldk : (long long)n * (n + 1) / 2);
   c.oY = o; o += r4(split ? f * c.ldk : f * n);

@@ -452,8 +452,12 @@ __device__ bool syrk_gwg_staged(float* K, int ldk, const float* qd, const float*
 // chunk.  Up to n = 248 there are at most 496 blocks (one per thread, the
 // rest idle); at n = 256 (528 blocks) the last 16 blocks are dealt out as 512
 // pairs of adjacent elements, one more per thread.  Stage rows have stride
-// round8(n) (the bulk copy fills round4(n) floats; the columns beyond n only
-// feed sums that are never stored).  Same contract as syrk_gwg_staged.
+// rs = round8(n) (the bulk copy fills round4(n) floats; the columns beyond n
+// only feed sums that are never stored).  When a chunk has landed, the
+// scaling pass also reorders each row in place so that columns 8J..8J+3 sit
+// at 4J and 8J+4..8J+7 at rs/2 + 4J: consecutive blocks then read
+// consecutive 16-byte words (no bank conflicts).  Same contract as
+// syrk_gwg_staged.
 // ---------------------------------------------------------------------------
 template <int NT>
 __device__ __noinline__ bool syrk_gwg_staged_blocks(float* K, int ldk, const float* qd,
@@ -495,6 +499,7 @@ __device__ __noinline__ bool syrk_gwg_staged_blocks(float* K, int ldk, const flo
     ie = 8 * Iu + (loc >> 2);
     je = 8 * Ju + ((loc & 3) << 1);
   }
+  const long long tp0 = sub ? clock64() : 0;
   if (tid == 0) *flag = 0;
   __syncthreads();
   auto issue = [&](int c) {
@@ -511,19 +516,34 @@ __device__ __noinline__ bool syrk_gwg_staged_blocks(float* K, int ldk, const flo
   // the running sums start from Q: its strict lower triangle is K's upper
   // triangle (read transposed), its diagonal qd
   float acc[8][8];
-#pragma unroll
-  for (int a = 0; a < 8; ++a)
+  // whole off-diagonal blocks of 16-byte aligned rows move as float4 rows
+  const bool vec = has_blk && J < I && 8 * I + 8 <= n && (ldk & 3) == 0 &&
+                   (reinterpret_cast<uintptr_t>(K) & 15) == 0;
+  if (vec) {
 #pragma unroll
     for (int b = 0; b < 8; ++b) {
-      const int i = 8 * I + a, j = 8 * J + b;
-      acc[a][b] = (has_blk && i < n && j <= i) ? (j == i ? qd[i] : K[j * ldk + i]) : 0.f;
+      const float* q = K + (8 * J + b) * ldk + 8 * I;
+      const float4 q0 = *reinterpret_cast<const float4*>(q);
+      const float4 q1 = *reinterpret_cast<const float4*>(q + 4);
+      acc[0][b] = q0.x; acc[1][b] = q0.y; acc[2][b] = q0.z; acc[3][b] = q0.w;
+      acc[4][b] = q1.x; acc[5][b] = q1.y; acc[6][b] = q1.z; acc[7][b] = q1.w;
     }
+  } else {
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        const int i = 8 * I + a, j = 8 * J + b;
+        acc[a][b] = (has_blk && i < n && j <= i) ? (j == i ? qd[i] : K[j * ldk + i]) : 0.f;
+      }
+  }
   float ex0 = 0.f, ex1 = 0.f;
   if (has_pair) {
     if (ie < n && je <= ie) ex0 = je == ie ? qd[ie] : K[je * ldk + ie];
     if (ie < n && je + 1 <= ie) ex1 = je + 1 == ie ? qd[ie] : K[(je + 1) * ldk + ie];
   }
   int done = 0;  // chunks consumed
+  if (sub && tid == 0) atomicAdd(&sub[3], (unsigned long long)(clock64() - tp0));
   for (int c = 0; c < nchunks; ++c) {
     const uint32_t g = g0 + (uint32_t)c;
     const long long ts0 = sub ? clock64() : 0;
@@ -533,21 +553,49 @@ __device__ __noinline__ bool syrk_gwg_staged_blocks(float* K, int ldk, const flo
     float* const buf = stage + (size_t)(g & 1u) * kKc * rs;
     const int k0 = c * kKc, kn = min(kKc, nrows - k0);
     // scale the chunk's rows by sqrt(W) once (W <= tau on the inactive rows)
-    for (int e = tid; e < kn * rowf; e += NT) {
-      const int k = e / rowf, col = e - k * rowf;
-      buf[k * rs + col] *= sqrtf(W[rows[k0 + k]]);
+    // and reorder them: read every 8-column group, then (after the barrier)
+    // write its halves to 4J and rs/2 + 4J.  At most kKc * 32 groups: two per
+    // thread.
+    {
+      float4 ga[2], gb[2];
+      int gk[2], gJ[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int e = tid + q * NT;
+        gk[q] = -1;
+        if (e < kn * n8) {
+          const int k = e / n8, Jg = e - k * n8;
+          const float sw = sqrtf(W[rows[k0 + k]]);
+          const float4 x0 = *reinterpret_cast<const float4*>(buf + k * rs + 8 * Jg);
+          const float4 x1 = *reinterpret_cast<const float4*>(buf + k * rs + 8 * Jg + 4);
+          ga[q] = make_float4(x0.x * sw, x0.y * sw, x0.z * sw, x0.w * sw);
+          gb[q] = make_float4(x1.x * sw, x1.y * sw, x1.z * sw, x1.w * sw);
+          gk[q] = k;
+          gJ[q] = Jg;
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        if (gk[q] >= 0) {
+          float* row = buf + gk[q] * rs;
+          *reinterpret_cast<float4*>(row + 4 * gJ[q]) = ga[q];
+          *reinterpret_cast<float4*>(row + (rs >> 1) + 4 * gJ[q]) = gb[q];
+        }
+      }
     }
     __syncthreads();
     const long long ts2 = sub ? clock64() : 0;
     if (has_blk) {
-      const float* pu = buf + 8 * I;
-      const float* pv = buf + 8 * J;
+      const float* pu = buf + 4 * I;
+      const float* pv = buf + 4 * J;
+      const int h2 = rs >> 1;
 #pragma unroll 1
       for (int k = 0; k < kn; ++k) {
         const float4 u0 = *reinterpret_cast<const float4*>(pu + k * rs);
-        const float4 u1 = *reinterpret_cast<const float4*>(pu + k * rs + 4);
+        const float4 u1 = *reinterpret_cast<const float4*>(pu + k * rs + h2);
         const float4 v0 = *reinterpret_cast<const float4*>(pv + k * rs);
-        const float4 v1 = *reinterpret_cast<const float4*>(pv + k * rs + 4);
+        const float4 v1 = *reinterpret_cast<const float4*>(pv + k * rs + h2);
         const float uu[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
         const float vv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
 #pragma unroll
@@ -557,9 +605,12 @@ __device__ __noinline__ bool syrk_gwg_staged_blocks(float* K, int ldk, const flo
       }
     }
     if (has_pair) {
+      // positions of columns ie and je, je + 1 in the reordered rows
+      const int pi = ((ie & 4) ? (rs >> 1) : 0) + 4 * (ie >> 3) + (ie & 3);
+      const int pj = ((je & 4) ? (rs >> 1) : 0) + 4 * (je >> 3) + (je & 3);
       for (int k = 0; k < kn; ++k) {
-        const float ue = buf[k * rs + ie];
-        const float2 ve = *reinterpret_cast<const float2*>(buf + k * rs + je);
+        const float ue = buf[k * rs + pi];
+        const float2 ve = *reinterpret_cast<const float2*>(buf + k * rs + pj);
         ex0 = fmaf(ue, ve.x, ex0);
         ex1 = fmaf(ue, ve.y, ex1);
       }
@@ -576,10 +627,19 @@ __device__ __noinline__ bool syrk_gwg_staged_blocks(float* K, int ldk, const flo
     }
     if (tid == 0 && c + 2 < nchunks) issue(c + 2);
   }
+  const long long te0 = sub ? clock64() : 0;
   const bool ok = __syncthreads_or(*flag) == 0;
   if (ok) {
     // K's lower triangle (its upper triangle, Q, is read above and kept)
-    if (has_blk) {
+    if (vec) {
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        float* k = K + (8 * I + a) * ldk + 8 * J;
+        *reinterpret_cast<float4*>(k) = make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+        *reinterpret_cast<float4*>(k + 4) =
+            make_float4(acc[a][4], acc[a][5], acc[a][6], acc[a][7]);
+      }
+    } else if (has_blk) {
 #pragma unroll
       for (int a = 0; a < 8; ++a)
 #pragma unroll
@@ -605,6 +665,7 @@ __device__ __noinline__ bool syrk_gwg_staged_blocks(float* K, int ldk, const flo
     *chunks = g0 + (uint32_t)min(nchunks, done + 2);
   }
   __syncthreads();
+  if (sub && tid == 0) atomicAdd(&sub[4], (unsigned long long)(clock64() - te0));
   return ok;
 }
 
