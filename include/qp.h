@@ -105,8 +105,9 @@ extern "C" {
 #define QP_DIAG_FACTOR_FAILED 0x100  /* a Cholesky pivot was not positive              */
 #define QP_DIAG_TC_FALLBACK 0x200    /* tensor-core G'WG ran out of a bounded wait and
                                         the solve continued with FP32 products          */
-#define QP_DIAG_STAGE_FALLBACK 0x400 /* bulk-copy staging of G'WG ran out of a bounded
-                                        wait; the products were redone from global memory */
+#define QP_DIAG_STAGE_FALLBACK 0x400 /* bulk-copy staging (of G'WG, or of a back
+                                        substitution's factor blocks) ran out of a bounded
+                                        wait; that step was finished from global memory   */
 #define QP_DIAG_ASYNC_LOST 0x800     /* copies may have been in flight after a bounded
                                         wait: the instance is reported QP_NUMERICAL     */
 

@@ -132,6 +132,8 @@ __host__ __device__ inline FLayout make_fwd_layout(int n, int m, int p, int amax
                     : pb_floats(n + L.fmax + 2 + 4);
     pb = round4(pb);
     if (split && pb < 2 * tc::stage_bytes(n, 4) / 4) pb = 2 * tc::stage_bytes(n, 4) / 4;
+    // (large variant) the two 32-row buffers of the staged back substitutions
+    if (split && pb < 64 * round4(n > L.fmax ? n : L.fmax)) pb = 64 * round4(n > L.fmax ? n : L.fmax);
     L.o_Pb = base;
     L.o_col = take(2 * nthreads);
     L.o_ta = take(L.mv); L.o_tb = take(L.mv); L.o_eb = take(L.mv);
@@ -625,7 +627,7 @@ struct Solver {
           (c == 0 ? ua : ub)[k] = C[(nf + c) * L.ldc + k];
         }
         __syncthreads();
-        block_trsv<NT, true>(C, L.ldc, cdinv, nf, ua, ub);
+        upper_solve_big(C, L.ldc, cdinv, nf, ua, ub);
       } else {
         // one warp per column (both columns in turn with a single warp)
         for (int c = w; c < 2; c += NT / 32) {
@@ -638,25 +640,52 @@ struct Solver {
         __syncthreads();
       }
     }
-    for (int e = t; e < 2 * n; e += NT) {
-      const int c = e / n, i = e - c * n;
-      const float* u = c == 0 ? ua : ub;
-      float acc = Y[(nf + c) * L.ldk + i];
-      if constexpr (kBig) {
-        // Y in global memory: several rows' loads in flight per thread
-#pragma unroll 8
-        for (int k = 0; k < nf; ++k) acc = fmaf(-Y[k * L.ldk + i], u[k], acc);
-      } else {
-        for (int k = 0; k < nf; ++k) acc = fmaf(-Y[k * L.ldk + i], u[k], acc);
+    if constexpr (kBig) {
+      // Y in global memory: Y'u for both columns in one coalesced sweep over
+      // Y's rows (per-warp column sums, added in warp order)
+      QP_ARR(wp);
+      constexpr int nw = NT / 32;
+      const float* cw[2] = {ua, ub};
+      warp_rows_n<NT, 4, 0, 2, false, false>(Y, L.ldk, nf, n, nullptr, nullptr, cw, wp, L.nv);
+      __syncthreads();
+      for (int e = t; e < 2 * n; e += NT) {
+        const int c = e / n, i = e - c * n;
+        const float* pk = wp + c * nw * L.nv;
+        float acc = 0.f;
+        for (int w2 = 0; w2 < nw; ++w2) acc += pk[w2 * L.nv + i];
+        R[c * L.ldx + i] = Y[(nf + c) * L.ldk + i] - acc;
       }
-      R[c * L.ldx + i] = acc;
+    } else {
+      for (int e = t; e < 2 * n; e += NT) {
+        const int c = e / n, i = e - c * n;
+        const float* u = c == 0 ? ua : ub;
+        float acc = Y[(nf + c) * L.ldk + i];
+        for (int k = 0; k < nf; ++k) acc = fmaf(-Y[k * L.ldk + i], u[k], acc);
+        R[c * L.ldx + i] = acc;
+      }
     }
     __syncthreads();
     if constexpr (kBig)
-      block_trsv<NT, true>(K, L.ldk, dinv, n, R, R + L.ldx);
+      upper_solve_big(K, L.ldk, dinv, n, R, R + L.ldx);
     else
       solve_rows<NT, true, 4>(K, L.ldk, dinv, n, R, L.ldx, 0, 2);
     QP_MARK(PH_SOLVE);
+  }
+
+  // (large variant) back substitution with a factor in the workspace: its
+  // 32-row blocks staged in shared memory by bulk copies (the union region is
+  // dead here), or read in place once bulk copies are no longer trusted
+  static __device__ void upper_solve_big(const float* Lf, int ld, const float* di, int nn,
+                                         float* x0, float* x1) {
+    if (!fwd_state.async_lost) {
+      float* const stage = fwd_dyn + fwd_state.L.o_Pb;
+      const bool all = tc::block_trsv_upper_staged<NT>(Lf, ld, di, nn, x0, x1, stage, round4(nn),
+                                                       fwd_state.mbar_g, &fwd_state.g_chunks,
+                                                       &fwd_state.tc_flag, &fwd_state.async_lost);
+      if (!all && threadIdx.x == 0) fwd_state.diag |= QP_DIAG_STAGE_FALLBACK;
+    } else {
+      block_trsv<NT, true>(Lf, ld, di, nn, x0, x1);
+    }
   }
 
   // warp solve with C for nf rows (up to 128, on chip)

@@ -669,5 +669,120 @@ __device__ __noinline__ bool syrk_gwg_staged_blocks(float* K, int ldk, const flo
   return ok;
 }
 
+// ---------------------------------------------------------------------------
+// Back substitution L' x_v = x_v (block_trsv's upper solve) for L in global
+// memory (n x n lower, row stride ld: a multiple of 4 floats, rows 16-byte
+// aligned) with each 32-row block staged in shared memory by bulk copies:
+// block bk (rows j0 .. j0+jb) needs those rows' columns 0 .. j0+jb, one copy
+// per row, issued two blocks ahead into two buffers (stage: 2 x 32 x sld
+// floats, sld >= round4(n) a multiple of 4, 16-byte aligned) on the mbarriers
+// mbar with the chunk count *chunks (shared with syrk_gwg_staged*).  Warp 0
+// solves the block's diagonal part from shared memory, then every thread
+// applies the block to one remaining entry.  L must not have been written by
+// this CTA since its last fence_async_global, except by the calling threads
+// just before the call (the call fences first).  A wait that runs out sets
+// *flag and the rest of the solve reads L in global memory (same
+// arithmetic); *fail is set if copies may still be in flight after the
+// bounded final waits.  Returns whether every block was staged.  Ends with a
+// barrier.
+// ---------------------------------------------------------------------------
+template <int NT>
+__device__ __noinline__ bool block_trsv_upper_staged(const float* L, int ld, const float* dinv,
+                                                     int n, float* x0, float* x1, float* stage,
+                                                     int sld, uint64_t* mbar, uint32_t* chunks,
+                                                     int* flag, int* fail) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int nblk = (n + 31) >> 5;
+  const uint32_t g0 = *chunks;
+  if (tid == 0) *flag = 0;
+  // the factor was stored through the generic proxy, and so were the stage
+  // buffers' earlier contents: order both before the bulk copies
+  fence_async_global();
+  fence_async_smem();
+  __syncthreads();
+  auto issue = [&](int bk) {
+    const uint32_t g = g0 + (uint32_t)bk;
+    float* buf = stage + (size_t)(g & 1u) * 32 * sld;
+    const int j0 = 32 * (nblk - 1 - bk), jb = min(32, n - j0);
+    const uint32_t bytes = (uint32_t)round4(j0 + jb) * 4u;
+    mbar_expect_tx(&mbar[g & 1u], (uint32_t)jb * bytes);
+    for (int k = 0; k < jb; ++k) bulk_g2s(buf + k * sld, L + (size_t)(j0 + k) * ld, bytes, &mbar[g & 1u]);
+  };
+  if (tid == 0) {
+    for (int bk = 0; bk < 2 && bk < nblk; ++bk) issue(bk);
+  }
+  int issued = min(2, nblk), done = 0;
+  bool staged = true;
+  for (int bk = 0; bk < nblk; ++bk) {
+    const uint32_t g = g0 + (uint32_t)bk;
+    const int j0 = 32 * (nblk - 1 - bk), jb = min(32, n - j0);
+    if (staged) {
+      if (!mbar_wait(&mbar[g & 1u], (g >> 1) & 1u)) atomicOr(flag, 1);
+      staged = __syncthreads_or(*flag) == 0;
+      if (staged) done = bk + 1;
+    }
+    // row k of the block: src[k * sst + column]
+    const float* src = staged ? stage + (size_t)(g & 1u) * 32 * sld : L + (size_t)j0 * ld;
+    const int sst = staged ? sld : ld;
+    if (tid < 32) {
+      // lane l holds column l of the diagonal part: r[k] = L[j0+k][j0+l], k >= l
+      float r[32];
+#pragma unroll
+      for (int k = 0; k < 32; ++k)
+        r[k] = (lane < jb && k < jb && k >= lane) ? src[k * sst + j0 + lane] : 0.f;
+      float v0 = lane < jb ? x0[j0 + lane] : 0.f;
+      float v1 = (x1 && lane < jb) ? x1[j0 + lane] : 0.f;
+#pragma unroll
+      for (int kk = 0; kk < 32; ++kk) {
+        const int k = 31 - kk;
+        if (k < jb) {
+          const float dk = dinv[j0 + k];
+          const float s0 = __shfl_sync(kFull, v0 * dk, k);
+          const float s1 = __shfl_sync(kFull, v1 * dk, k);
+          if (lane == k) { v0 = s0; v1 = s1; }
+          if (lane < k) {
+            v0 = fmaf(-r[k], s0, v0);
+            v1 = fmaf(-r[k], s1, v1);
+          }
+        }
+      }
+      if (lane < jb) {
+        x0[j0 + lane] = v0;
+        if (x1) x1[j0 + lane] = v1;
+      }
+    }
+    __syncthreads();
+    // the entries above the block: x_i -= sum_k L[j0+k][i] x_{j0+k}
+    for (int i = tid; i < j0; i += NT) {
+      float acc0 = x0[i], acc1 = x1 ? x1[i] : 0.f;
+#pragma unroll 8
+      for (int k = 0; k < jb; ++k) {
+        const float l = src[k * sst + i];
+        acc0 = fmaf(-l, x0[j0 + k], acc0);
+        if (x1) acc1 = fmaf(-l, x1[j0 + k], acc1);
+      }
+      x0[i] = acc0;
+      if (x1) x1[i] = acc1;
+    }
+    // this buffer is read (generic proxy) before the copy that refills it
+    fence_async_smem();
+    __syncthreads();
+    if (staged && tid == 0 && bk + 2 < nblk) issue(bk + 2);
+    if (staged && bk + 2 < nblk) issued = bk + 3;
+  }
+  // copies issued but not waited for (after a wait ran out): wait, bounded
+  if (tid == 0) {
+    int bad = 0;
+    for (int bk = done; bk < issued; ++bk) {
+      const uint32_t g = g0 + (uint32_t)bk;
+      if (!mbar_wait(&mbar[g & 1u], (g >> 1) & 1u)) bad = 1;
+    }
+    if (bad) *fail = 1;
+    *chunks = g0 + (uint32_t)issued;
+  }
+  __syncthreads();
+  return done == nblk;
+}
+
 }  // namespace tc
 }  // namespace qpgpu
