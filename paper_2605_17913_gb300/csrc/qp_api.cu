@@ -80,7 +80,7 @@ int settings_to_params(const qp_settings* st, FwdParams* P) {
 extern "C" {
 
 #ifdef QP_PHASE_TIMERS
-// Tracing build only: device array of 48 phase-cycle counters the forward
+// Tracing build only: device array of 64 phase-cycle counters the forward
 // kernel adds to (NULL turns the timers off).
 void qp_debug_set_phase_counters(unsigned long long* dev) { g_phase_counters = dev; }
 #endif

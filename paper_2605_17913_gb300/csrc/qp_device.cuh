@@ -800,6 +800,7 @@ __device__ bool panel_factor_wide(float* M, int ld, int j0, int jb, float* dinv,
   // one row per thread; within each warp's 32 rows, lane l takes row
   // 4 (l % 8) + l / 8, so that the 8 lanes of a shared-memory phase read rows
   // of 8 different 4-row groups of Pb (bank-conflict-free float4 accesses)
+  long long tq1 = 0, tq2 = 0;  // tracing builds: thread 0's row solved / stored
   for (int r0 = w * 32; r0 < N; r0 += NT) {
     const int rr = r0 + ((lane & 7) << 2) + (lane >> 3);
     if (rr >= N) continue;
@@ -850,9 +851,16 @@ __device__ bool panel_factor_wide(float* M, int ld, int j0, int jb, float* dinv,
         }
       }
     }
+    if (sub && tid == 0) {
+      float sum = 0.0f;
+#pragma unroll
+      for (int q = 0; q < PW; ++q) sum += v[q];
+      tq1 = clock64() + (long long)(sum * 0.0f);
+    }
 #pragma unroll
     for (int q = 0; q < PW / 4; ++q)
       pr[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    if (sub && tid == 0) tq2 = clock64();
     if (PW != 32) {
 #pragma unroll
       for (int t = 0; t < PW; ++t)
@@ -868,9 +876,17 @@ __device__ bool panel_factor_wide(float* M, int ld, int j0, int jb, float* dinv,
   }
   __syncthreads();
   if (sub && threadIdx.x == 0) {
-    // tracing builds: (diagonal block || row staging), then the row solves
+    // tracing builds: (diagonal block || row staging), then the row solves;
+    // within them thread 0's own row (solved, stored) and the wait for the
+    // other rows
+    const long long tq3 = clock64();
     atomicAdd(&sub[0], (unsigned long long)(tp1 - tp0));
-    atomicAdd(&sub[1], (unsigned long long)(clock64() - tp1));
+    atomicAdd(&sub[1], (unsigned long long)(tq3 - tp1));
+    if (tq1) {
+      atomicAdd(&sub[8], (unsigned long long)(tq1 - tp1));
+      atomicAdd(&sub[9], (unsigned long long)(tq2 - tq1));
+      atomicAdd(&sub[10], (unsigned long long)(tq3 - tq2));
+    }
   }
   if (PW == 32) {
     // write the solved rows back, one row per warp (coalesced); the trailing

@@ -576,8 +576,9 @@ struct Solver {
     unsigned long long* const sub = nullptr;
 #endif
     // tracing builds: counters 11-14 (K, C: panel / trailing), 24-27 and
-    // 40-43 (K, C: inside the wide panel), 28-31 and 44-47 (K, C: the
-    // look-ahead), 19-21 (staged G'WG); 48 counters
+    // 40-43 (K, C: inside the wide panel), 32-34 and 48-50 (K, C: the panel
+    // solve's own row / store / wait), 28-31 and 44-47 (K, C: the
+    // look-ahead), 19-23 (staged G'WG); 64 counters
     bool ok = blocked_cholesky_bordered<NT, kPW>(K, L.ldk, L.n, Y, L.ldk, nf + nfold, C, L.ldc, dinv,
                                             Pb, sub, sub ? sub + 13 : nullptr);
     QP_MARK(PH_BORDER);
