@@ -248,11 +248,45 @@ __device__ __forceinline__ void rows_pass(const float* G, const float* Q, const 
 // (row 0), r2 in t; the solution overwrites both.  kMaxS: warp-solve length
 // bound of the K part in units of 32 rows (4 on chip, 8 for the large
 // variant, whose C part goes to 320 rows).
-template <int NT, int kMaxS, class Bar>
+template <int NT, int kMaxS, class Bar, bool kCoh = false>
 __device__ void two_level_solve(const float* K, int ldk, const float* dinv, const float* Y,
                                 const float* C, int ldc, const float* cdinv, int n, int nf,
-                                float* R, int ldx, float* t) {
+                                float* R, int ldx, float* t, float* part = nullptr) {
   const int tid = threadIdx.x;
+  if constexpr (kMaxS > 4) {
+    // the large variant: factors in global memory.  Blocked triangular solves
+    // with every warp, and the products with Y as coalesced row sweeps
+    // (per-warp column sums in part, nw x round4(n) floats, added in warp
+    // order); part[0 .. nf) first holds Y R.
+    constexpr int nw = NT / 32;
+    const int nv = (n + 3) & ~3;
+    block_trsv<NT, false, Bar>(K, ldk, dinv, n, R, nullptr);
+    if (nf > 0) {
+      {
+        const float* xv[1] = {R};
+        float* dv[1] = {part};
+        warp_rows_n<NT, 4, 1, 0, false, kCoh>(Y, ldk, nf, n, xv, dv, nullptr, nullptr, 0);
+      }
+      Bar::sync();
+      for (int k = tid; k < nf; k += NT) t[k] = part[k] - t[k];
+      Bar::sync();
+      block_trsv<NT, false, Bar>(C, ldc, cdinv, nf, t, nullptr);
+      block_trsv<NT, true, Bar>(C, ldc, cdinv, nf, t, nullptr);
+      {
+        const float* cw[1] = {t};
+        warp_rows_n<NT, 4, 0, 1, false, kCoh>(Y, ldk, nf, n, nullptr, nullptr, cw, part, nv);
+      }
+      Bar::sync();
+      for (int i = tid; i < n; i += NT) {
+        float acc = 0.f;
+        for (int w2 = 0; w2 < nw; ++w2) acc += part[w2 * nv + i];
+        R[i] -= acc;
+      }
+      Bar::sync();
+    }
+    block_trsv<NT, true, Bar>(K, ldk, dinv, n, R, nullptr);
+    return;
+  }
   solve_rows<NT, false, kMaxS, Bar>(K, ldk, dinv, n, R, ldx, 0, 1);
   if (nf > 0) {
     for (int k = tid; k < nf; k += NT) {
@@ -388,7 +422,8 @@ __device__ __forceinline__ void backward_body(const BwdParams& P, int bi) {
     return;
   }
   // ---- adjoint solve, then refinement against the bounded system ----
-  two_level_solve<NT, kGlobal ? 8 : 4, Bar>(K, ldk, dinv, Y, C, ldc, cdinv, n, nf, R, B.ldx, mu);
+  two_level_solve<NT, kGlobal ? 8 : 4, Bar, kCoh>(K, ldk, dinv, Y, C, ldc, cdinv, n, nf, R, B.ldx, mu,
+                                                 part);
   float* dx = R + B.ldx;  // accumulated solution; R row 0 is the work row
   for (int i = t; i < n; i += NT) dx[i] = R[i];
   Bar::sync();
@@ -415,7 +450,8 @@ __device__ __forceinline__ void backward_body(const BwdParams& P, int bi) {
       }
     }
     Bar::sync();
-    two_level_solve<NT, kGlobal ? 8 : 4, Bar>(K, ldk, dinv, Y, C, ldc, cdinv, n, nf, R, B.ldx, dmu);
+    two_level_solve<NT, kGlobal ? 8 : 4, Bar, kCoh>(K, ldk, dinv, Y, C, ldc, cdinv, n, nf, R, B.ldx,
+                                                   dmu, part);
     for (int i = t; i < n; i += NT) dx[i] += R[i];
     for (int k = t; k < nf; k += NT) mu[k] += dmu[k];
     Bar::sync();

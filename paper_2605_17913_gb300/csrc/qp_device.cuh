@@ -1212,7 +1212,7 @@ __device__ __forceinline__ void warp_upper_solve(const float* L, int ldk, const 
 // diagonal part, and warp 0 loads the next diagonal part while the others
 // apply the current block.  Two barriers per block.
 // ---------------------------------------------------------------------------
-template <int NT, bool kUpper>
+template <int NT, bool kUpper, class Bar = CtaBar>
 __device__ __noinline__ void block_trsv(const float* L, int ld, const float* dinv, int n,
                                         float* x0, float* x1) {
   static_assert(NT >= 64, "warp 0 solves, the other warps apply");
@@ -1270,7 +1270,7 @@ __device__ __noinline__ void block_trsv(const float* L, int ld, const float* din
     } else if (i0 < r1) {
       load_row(i0, j0, jb);
     }
-    __syncthreads();
+    Bar::sync();
     if (t >= 32) {
       for (int i = i0; i < r1; i += NR) {
         if (i != i0) load_row(i, j0, jb);
@@ -1286,7 +1286,7 @@ __device__ __noinline__ void block_trsv(const float* L, int ld, const float* din
         if (x1) x1[i] = acc1;
       }
     }
-    __syncthreads();
+    Bar::sync();
   }
 }
 
