@@ -822,22 +822,40 @@ __device__ bool panel_factor_wide(float* M, int ld, int j0, int jb, float* dinv,
       // column order: step k finishes v[k] and takes its multiple off every
       // later entry, with column k of the factor read as 16-byte rows of fbt
       // (the same operations in the same order as the row-ordered solve)
+      // the next step's column and pivot reciprocal are loaded while this
+      // step computes, so the shared-memory round trips overlap the FMAs
+      // instead of forming a chain of one per 16-byte word
       const float* const fbt = fb + fbt_off(PW);
+      float4 lc[PW / 4];
+      float dc = jb > 0 ? dinv[j0] : 0.0f;
+#pragma unroll
+      for (int g = 0; g < PW / 4; ++g) lc[g] = reinterpret_cast<const float4*>(fbt)[g];
 #pragma unroll
       for (int k = 0; k < PW; ++k) {
+        float4 ln[PW / 4];
+        float dn = 0.0f;
+        if (k + 1 < PW) {
+          const float4* lt = reinterpret_cast<const float4*>(fbt + (k + 1) * fbt_ld(PW));
+#pragma unroll
+          for (int g = (k + 2) >> 2; g < PW / 4; ++g) ln[g] = lt[g];
+          if (k + 1 < jb) dn = dinv[j0 + k + 1];
+        }
         if (k < jb) {
-          v[k] *= dinv[j0 + k];
-          const float4* lt = reinterpret_cast<const float4*>(fbt + k * fbt_ld(PW));
+          v[k] *= dc;
 #pragma unroll
           for (int g = (k + 1) >> 2; g < PW / 4; ++g) {
-            const float4 l4 = lt[g];
-            const float lv[4] = {l4.x, l4.y, l4.z, l4.w};
+            const float lv[4] = {lc[g].x, lc[g].y, lc[g].z, lc[g].w};
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
               const int t = 4 * g + q;
               if (t > k && t < jb) v[t] = fmaf(-v[k], lv[q], v[t]);
             }
           }
+        }
+        if (k + 1 < PW) {
+#pragma unroll
+          for (int g = (k + 2) >> 2; g < PW / 4; ++g) lc[g] = ln[g];
+          dc = dn;
         }
       }
     } else {
@@ -966,13 +984,25 @@ __device__ __forceinline__ void trailing_tile(int t, const float* Pb, float* A, 
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+  // the operands of step h + 1 are loaded while step h's products run
+  float4 rn[4], cn[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) rn[a] = reinterpret_cast<const float4*>(Pb + I * GS + a * PW)[0];
+#pragma unroll
+  for (int b = 0; b < 4; ++b) cn[b] = reinterpret_cast<const float4*>(Pb + J * GS + b * PW)[0];
 #pragma unroll
   for (int h = 0; h < PW / 4; ++h) {
     float4 ra[4], cb[4];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) ra[a] = reinterpret_cast<const float4*>(Pb + I * GS + a * PW)[h];
+    for (int a = 0; a < 4; ++a) ra[a] = rn[a];
 #pragma unroll
-    for (int b = 0; b < 4; ++b) cb[b] = reinterpret_cast<const float4*>(Pb + J * GS + b * PW)[h];
+    for (int b = 0; b < 4; ++b) cb[b] = cn[b];
+    if (h + 1 < PW / 4) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a) rn[a] = reinterpret_cast<const float4*>(Pb + I * GS + a * PW)[h + 1];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) cn[b] = reinterpret_cast<const float4*>(Pb + J * GS + b * PW)[h + 1];
+    }
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
