@@ -984,25 +984,13 @@ __device__ __forceinline__ void trailing_tile(int t, const float* Pb, float* A, 
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-  // the operands of step h + 1 are loaded while step h's products run
-  float4 rn[4], cn[4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a) rn[a] = reinterpret_cast<const float4*>(Pb + I * GS + a * PW)[0];
-#pragma unroll
-  for (int b = 0; b < 4; ++b) cn[b] = reinterpret_cast<const float4*>(Pb + J * GS + b * PW)[0];
 #pragma unroll
   for (int h = 0; h < PW / 4; ++h) {
     float4 ra[4], cb[4];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) ra[a] = rn[a];
+    for (int a = 0; a < 4; ++a) ra[a] = reinterpret_cast<const float4*>(Pb + I * GS + a * PW)[h];
 #pragma unroll
-    for (int b = 0; b < 4; ++b) cb[b] = cn[b];
-    if (h + 1 < PW / 4) {
-#pragma unroll
-      for (int a = 0; a < 4; ++a) rn[a] = reinterpret_cast<const float4*>(Pb + I * GS + a * PW)[h + 1];
-#pragma unroll
-      for (int b = 0; b < 4; ++b) cn[b] = reinterpret_cast<const float4*>(Pb + J * GS + b * PW)[h + 1];
-    }
+    for (int b = 0; b < 4; ++b) cb[b] = reinterpret_cast<const float4*>(Pb + J * GS + b * PW)[h];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
