@@ -215,12 +215,20 @@ __device__ __forceinline__ void warp_rows(const float* M, int ld, int rows, int 
 }
 
 // warp_rows for the column count n: S = ceil(n / 32) register slots per lane
-// (n <= 256, the large variant's range).
+// (n <= 256).
 template <int NT, int U, int ND, int NC, bool kUpper, bool kL2>
 __device__ __forceinline__ void warp_rows_n(const float* M, int ld, int rows, int n,
                                             const float* const* xv, float* const* dout,
                                             const float* const* cw, float* part, int ldp) {
-  if (n <= 160)
+  if (n <= 32)
+    warp_rows<NT, 1, U, ND, NC, kUpper, kL2>(M, ld, rows, n, xv, dout, cw, part, ldp);
+  else if (n <= 64)
+    warp_rows<NT, 2, U, ND, NC, kUpper, kL2>(M, ld, rows, n, xv, dout, cw, part, ldp);
+  else if (n <= 96)
+    warp_rows<NT, 3, U, ND, NC, kUpper, kL2>(M, ld, rows, n, xv, dout, cw, part, ldp);
+  else if (n <= 128)
+    warp_rows<NT, 4, U, ND, NC, kUpper, kL2>(M, ld, rows, n, xv, dout, cw, part, ldp);
+  else if (n <= 160)
     warp_rows<NT, 5, U, ND, NC, kUpper, kL2>(M, ld, rows, n, xv, dout, cw, part, ldp);
   else if (n <= 192)
     warp_rows<NT, 6, U, ND, NC, kUpper, kL2>(M, ld, rows, n, xv, dout, cw, part, ldp);

@@ -479,7 +479,14 @@ struct Solver {
         for (int j = 0; j < 8; ++j)
           if (lane + 32 * j < n) Y[k * L.ldk + lane + 32 * j] = v[j];
       } else {
-        for (int c = lane; c < n; c += 32) Y[k * L.ldk + c] = src[c];
+        // likewise on chip (n <= 128): an equality row comes from the caller's
+        // A in global memory, whose round trips would otherwise be serialised
+        float v[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[j] = lane + 32 * j < n ? src[lane + 32 * j] : 0.f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (lane + 32 * j < n) Y[k * L.ldk + lane + 32 * j] = v[j];
       }
       for (int c = lane; c <= k; c += 32) C[k * L.ldc + c] = c == k ? dk : 0.f;
       if (lane == 0) D[k] = dk;
@@ -945,6 +952,14 @@ struct Solver {
       const float* vv[1] = {z};
       float* oo[1] = {tn};
       col_dot<NT, 1>(G, L.ldg, m, n, vv, oo, col);
+      // A x: A is the caller's, in global memory: a warp per row (coalesced,
+      // the row's loads in flight together) instead of a thread walking it
+      if (p > 0) {
+        const float* xq[1] = {x};
+        float* da[1] = {re};
+        warp_rows_n<NT, 2, 1, 0, false, kCoh>(A, n, p, n, xq, da, nullptr, nullptr, 0);
+        __syncthreads();
+      }
     }
     // 0 |rt| 1 |Qx| 2 |A'y| 3 |G'z| 4 |re| 5 |Ax| 6 |ri| 7 |Gx| 8 |s| 9 zs 10 |rz,rs| 11 |z| 12 nonfinite
     float mx[13];
@@ -992,12 +1007,7 @@ struct Solver {
         }
       } else {
         const int k = u - n - m;
-        float ax = 0.f;
-        if constexpr (kBig) {
-          ax = re[k];
-        } else {
-          for (int j = 0; j < n; ++j) ax = fmaf(ld_ro(A + k * n + j), x[j], ax);
-        }
+        const float ax = re[k];  // from the row sweep above
         const float r = ax - b[k];
         re[k] = r;
         mx[12] += isfinite(r) ? 0.f : 1.f;
