@@ -266,3 +266,40 @@ def test_persistent_ctas_leave_when_idle_and_come_back():
         ref = _solo(d, True, 512)
         for k in ("x", "y", "z", "s") + GRAD_KEYS:
             np.testing.assert_array_equal(r[k], ref[k])
+
+
+def test_persistent_server_tensor_core_gwg():
+    """Resident CTAs with TF32 G'WG on the tensor cores (TMEM held for the
+    CTA's life): large requests equal batch-1 solves of width 512 with the
+    same setting bit for bit, and meet the oracle's bars."""
+    from paper_2605_17913_gb300.serve import QPServer
+    from paper_2605_17913_gb300.solver import QPSolver
+
+    inst = [_inst(900 + i, 200, 400, 20) for i in range(2)]
+    srv = QPServer(hbm_budget_bytes=256 << 20, tol=SOLVER_TOL, mode="persistent",
+                   gwg_precision="tf32")
+    try:
+        got = [srv.wait(_submit(srv, d, True), 60000) for d in inst]
+    finally:
+        srv.close()
+    for d, r in zip(inst, got):
+        assert r["status"] == 0
+        n, p, m = d["q"].size, d["b"].size, d["h"].size
+        T = {k: torch.from_numpy(d[k].reshape((1,) + d[k].shape)).cuda() for k in
+             ("Q", "q", "A", "b", "G", "h", "g")}
+        slv = QPSolver(1, n, p, m, threads_per_qp=512)
+        cache = slv.new_grad_cache()
+        out = slv.solve(T["Q"], T["q"], T["A"], T["b"], T["G"], T["h"], grad_cache=cache,
+                        tol=SOLVER_TOL, gwg_precision="tf32")
+        g = slv.backward(cache, T["Q"], T["A"], T["G"], T["g"])
+        torch.cuda.synchronize()
+        ref = {k: v.cpu().numpy()[0] for k, v in list(out.items()) + list(g.items())}
+        for k in ("x", "y", "z", "s") + GRAD_KEYS:
+            np.testing.assert_array_equal(r[k], ref[k], err_msg=k)
+        one = lambda k: d[k][None]  # noqa: E731
+        orc = O.solve(one("Q"), one("q"), one("A"), one("b"), one("G"), one("h"), tol=1e-12,
+                      kappa_relax=1e-4, g=one("g"))
+        assert rel_err_inf(r["x"][None], orc["x"])[0] <= 1e-4
+        for k in GRAD_KEYS:
+            if orc[k].size:
+                assert rel_err_2(r[k][None], orc[k])[0] <= 1e-3, k
