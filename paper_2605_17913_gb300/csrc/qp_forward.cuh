@@ -1,5 +1,11 @@
-// qp_forward.cuh -- batched implicit-complementarity IPM (Alg. 1, Alg. 2) for
-// QPs whose data fit in one SM's shared memory.  One CTA solves one QP.
+// qp_forward.cuh -- batched implicit-complementarity IPM (Alg. 1, Alg. 2).
+// One CTA solves one QP.  On chip (kBig = false) every per-instance array
+// lives in shared memory; the large-problem variant (kBig) keeps K, G, Y, C
+// in a per-instance global workspace with 16-byte aligned rows, stages G'WG's
+// rows and the back substitutions' factor blocks in shared memory by bulk
+// copies, and reads the matrices in its residuals and products by coalesced
+// warp row sweeps.  kCoh: the same solver run by the persistent serving
+// kernel, which reads memory reused across requests through L2.
 //
 // Newton system.  eq. 14 (symmetric, every block bounded):
 //   [ Q - G'G   G'     A' ] [dx]     [ rho1 ]   rho1 = r_t - G'(r_i + r_z - r_s)
@@ -36,9 +42,11 @@
 // system is factored once more at the relaxed point and the factors, W, the
 // active-row map and the relaxed (x, y, z) go to the gradient cache (Alg. 3).
 //
-// The explicit-complementarity ablation (eq. 6 / eq. 8) uses the same
-// two-level factorisation with W = z ./ s, a Mehrotra predictor-corrector
-// (second solve for the corrector) and fraction-to-boundary 0.99.
+// The explicit-complementarity ablation (eq. 6 / eq. 8) uses W = z ./ s, a
+// Mehrotra predictor-corrector (second solve for the corrector) and
+// fraction-to-boundary 0.99, either through the same two-level factorisation
+// (QP_STANDARD) or with eq. 8's Q + G' diag(z/s) G factored as it stands
+// (QP_STANDARD_SCHUR: every row eliminated, no shift, no retry).
 //
 // Register budget: the layout lives in shared memory and each method forms
 // only the addresses it uses, so that no pointer stays live across phases.
