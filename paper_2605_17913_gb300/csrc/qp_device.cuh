@@ -1,7 +1,9 @@
-// qp_device.cuh -- shared-memory building blocks of the batched IPM kernels.
+// qp_device.cuh -- building blocks of the batched IPM kernels: retraction,
+// reductions, G'WG, the blocked bordered Cholesky and triangular solves, and
+// (for matrices in global memory) warp row sweeps and blocked solves.
 //
-// One CTA owns one QP at a time.  Every per-instance array lives in shared
-// memory with strides chosen for the two access patterns used:
+// One CTA owns one QP at a time.  On chip every per-instance array lives in
+// shared memory with strides chosen for the two access patterns used:
 //   * "vector" strides (ldg): a multiple of 4 floats whose quarter is odd, so
 //     thread-per-row float4 dot products and column reads are both free of
 //     bank conflicts; pad columns are zero, so float4 reads past n add 0;
