@@ -590,7 +590,7 @@ __device__ __noinline__ bool syrk_gwg_staged_blocks(float* K, int ldk, const flo
       const float* pu = buf + 4 * I;
       const float* pv = buf + 4 * J;
       const int h2 = rs >> 1;
-#pragma unroll 1
+#pragma unroll 2
       for (int k = 0; k < kn; ++k) {
         const float4 u0 = *reinterpret_cast<const float4*>(pu + k * rs);
         const float4 u1 = *reinterpret_cast<const float4*>(pu + k * rs + h2);
