@@ -41,7 +41,7 @@ TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rates (recipe tab
 # DRAM bytes (read + write) per instance of one forward launch, from an ncu
 # capture of the current kernel (per launch / instances); None until the
 # current kernel has been captured.
-FORWARD_TRAFFIC_PER_INSTANCE = {"precision": (10841303552 + 8032653056) / 256,
+FORWARD_TRAFFIC_PER_INSTANCE = {"precision": (10593364224 + 7565090048) / 256,
                                 "degenerate": None, "diff": None}
 
 
