@@ -9,7 +9,9 @@ predictor-corrector sigma), optionally Alg. 2 (relax to kappa_relax) and
 Alg. 3 (gradients at the relaxed point); ``formulation="standard"`` runs the
 explicit-complementarity ablation (eq. 6 / eq. 8, Mehrotra).
 Parity status: pinned (closed forms, brute-force active sets, known optima,
-central-path invariants and central finite differences in tests/).
+central-path invariants, the linearisation that one direction solves and
+central finite differences in tests/; mistakes planted in copies of the C
+source fail those pins).
 """
 from __future__ import annotations
 
@@ -62,9 +64,14 @@ _lib = None
 
 
 def lib():
+    """The oracle library: ``liboracle.so`` (built on first use), or the build
+    that ``QP_ORACLE_LIB`` names -- a separately compiled copy of
+    ``qp_oracle.c``, used by the test that plants mistakes in the oracle and
+    checks that its pins catch them."""
     global _lib
     if _lib is None:
-        L = ctypes.CDLL(build())
+        other = os.environ.get("QP_ORACLE_LIB")
+        L = ctypes.CDLL(other if other else build())
         d, vp, i = ctypes.c_double, ctypes.c_void_p, ctypes.c_int
         L.oqp_retract.restype = d
         L.oqp_retract.argtypes = [d, d]
@@ -74,6 +81,8 @@ def lib():
         L.oqp_retract_dk.argtypes = [d, d]
         L.oqp_kkt_measure.restype = d
         L.oqp_kkt_measure.argtypes = [ctypes.POINTER(_Problem), vp, vp, vp, vp, i]
+        L.oqp_newton_direction.restype = i
+        L.oqp_newton_direction.argtypes = [ctypes.POINTER(_Problem)] + [vp] * 4 + [d] + [vp] * 6
         L.oqp_batch.restype = i
         L.oqp_batch.argtypes = ([i, i, i, i, i] + [vp] * 7 + [ctypes.POINTER(_Settings), d]
                                 + [vp] * 8 + [vp] * 4 + [vp] * 6 + [i])
@@ -126,6 +135,25 @@ def kkt_measure(Q, q, A, b, G, h, x, y, z, s, scaled: bool = True) -> float:
     P = _Problem(n, p, m, *[_ptr(a) for a in arrs])
     xs = [_f64(v) for v in (x, y, z, s)]
     return lib().oqp_kkt_measure(ctypes.byref(P), *[_ptr(v) for v in xs], int(scaled))
+
+
+def newton_direction(Q, q, A, b, G, h, x, y, z, s, kappa_target: float) -> dict:
+    """One Alg. 1 direction at (x, y, z, s) toward ``kappa_target``: eq. 14
+    solved at v = z - s, kappa = s'z/m, then dz, ds, dkappa from eq. 13.
+    Returns dx, dy, dv, dz, ds, dkappa and the status."""
+    _, Qb, qb, Ab, bb, Gb, hb = _as_batch(Q, q, A, b, G, h)
+    n, p, m = Qb.shape[1], Ab.shape[1], Gb.shape[1]
+    arrs = [Qb[0], qb[0], Ab[0], bb[0], Gb[0], hb[0]]
+    P = _Problem(n, p, m, *[_ptr(a) for a in arrs])
+    xs = [_f64(v) for v in (x, y, z, s)]
+    out = dict(dx=np.zeros(n), dy=np.zeros(p), dv=np.zeros(m), dz=np.zeros(m), ds=np.zeros(m))
+    dk = ctypes.c_double(0.0)
+    st = lib().oqp_newton_direction(ctypes.byref(P), *[_ptr(v) for v in xs], float(kappa_target),
+                                    *[_ptr(out[k]) for k in ("dx", "dy", "dv", "dz", "ds")],
+                                    ctypes.byref(dk))
+    out["dkappa"] = dk.value
+    out["status"] = st
+    return out
 
 
 def solve(Q, q, A, b, G, h, *, tol: float = 1e-12, max_iter: int = 100, sigma_mode: int = 0,

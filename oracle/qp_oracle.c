@@ -507,6 +507,37 @@ int oqp_solve(const oqp_problem* P, const oqp_settings* S, double* x, double* y,
 }
 
 /* ---------------------------------------------------------------------------
+ * One direction of Alg. 1 at (x, y, z, s), on its own: v = z - s and
+ * kappa = s'z/m as the iteration forms them, eq. 14 factored and solved for
+ * r_kappa = kappa - kappa_target, and (dz, ds, dkappa) recovered from eq. 13.
+ * The tests hold it to the linearisation of eq. 4 and eq. 11 that it solves.
+ * ------------------------------------------------------------------------- */
+int oqp_newton_direction(const oqp_problem* P, const double* x, const double* y,
+                         const double* z, const double* s, double kappa_target, double* dx,
+                         double* dy, double* dv, double* dz, double* ds, double* dkappa) {
+  int n = P->n, p = P->p, m = P->m;
+  if (n < 1 || p < 0 || m < 1 || p > n) return OQP_BAD_INPUT;
+  oqp_work w;
+  if (work_alloc(P, &w) != 0) return OQP_NUMERICAL;
+  double kappa = 0.0;
+  for (int k = 0; k < m; ++k) { w.v[k] = z[k] - s[k]; kappa += s[k] * z[k]; }
+  kappa /= (double)m; /* R1 */
+  residuals(P, x, y, z, s, &w.R);
+  for (int k = 0; k < m; ++k) {
+    w.rz[k] = z[k] - oqp_retract(w.v[k], kappa);
+    w.rs[k] = s[k] - oqp_retract(-w.v[k], kappa);
+  }
+  int status = OQP_SOLVED;
+  if (newton_factor(P, w.v, kappa, &w.W) != 0)
+    status = OQP_NUMERICAL;
+  else
+    newton_solve(P, &w.W, w.R.rt, w.R.re, w.R.ri, w.rz, w.rs, kappa - kappa_target, dx, dv, dy,
+                 dz, ds, dkappa);
+  work_free(&w);
+  return status;
+}
+
+/* ---------------------------------------------------------------------------
  * Alg. 2 (relax_qp): warm start from (x, y, z, s), Newton steps with
  * kappa_target = kappa_relax, refactoring every iteration (exact Newton).
  * Converged when the residual measure of (r_t, r_e, r_i) is below tol and

@@ -301,3 +301,71 @@ def test_gradient_equality_constrained_closed_form():
     np.testing.assert_allclose(r["dq"], dx, atol=1e-11)
     np.testing.assert_allclose(r["db"], -dy, atol=1e-11)
     np.testing.assert_allclose(r["dA"], np.outer(dy, x) + np.outer(y, dx), atol=1e-10)
+
+
+def test_absolute_kkt_measure_at_arbitrary_points():
+    """The absolute measure is the largest infinity norm among eq. 4's r_t, r_e,
+    r_i and the complementarity z.*s, at any point, not only near a solution
+    (where every term is tiny)."""
+    rng = np.random.default_rng(12)
+    for trial in range(20):
+        n, m, p = 6, 9, 2
+        d = _rand_qp(rng, n, m, p)
+        x, y = rng.standard_normal(n), rng.standard_normal(p)
+        z, s = rng.uniform(0.01, 3.0, m), rng.uniform(0.01, 3.0, m)
+        if trial % 2:
+            z *= 10.0  # complementarity the largest term
+        Q, q, A, b, G, h = (d[k] for k in ("Q", "q", "A", "b", "G", "h"))
+        want = max(np.abs(Q @ x + q + G.T @ z + A.T @ y).max(), np.abs(A @ x - b).max(),
+                   np.abs(G @ x + s - h).max(), (z * s).max())
+        got = O.kkt_measure(Q, q, A, b, G, h, x, y, z, s, scaled=False)
+        assert abs(got - want) <= 1e-13 * want, (trial, got, want)
+
+
+# ---------------------------------------------------------------- Newton direction
+def _b_directional(v, k, dv, dk):
+    """d/dt b_{k + t dk}(v + t dv) at t = 0 (eq. 11), by 60-digit central
+    differences of the exact formula."""
+    t = mpmath.mpf("1e-25")
+    v, k, dv, dk = (mpmath.mpf(a) for a in (v, k, dv, dk))
+    return (_b_exact(v + t * dv, k + t * dk) - _b_exact(v - t * dv, k - t * dk)) / (2 * t)
+
+
+@pytest.mark.parametrize("on_manifold", [True, False])
+@pytest.mark.parametrize("target", [0.0, 0.2])
+def test_newton_direction_solves_the_linearised_conditions(on_manifold, target):
+    """One Alg. 1 direction is Newton's step for eq. 4 with z = b_k(v),
+    s = b_k(-v) (eq. 11) in the coordinates (x, y, v, kappa):
+      Q dx + G'dz + A'dy = -r_t,  A dx = -r_e,  G dx + ds = -r_i,
+      dkappa = kappa_target - kappa,
+      dz = b_k(v) - z + Db_k(v)[dv, dkappa],  ds = b_k(-v) - s + Db_k(-v)[-dv, dkappa].
+    Residuals in numpy, the retraction's derivative by 60-digit differences:
+    this fixes eq. 13 and eq. 14 (matrix, right-hand side and recovery)."""
+    rng = np.random.default_rng(21 + int(on_manifold) + int(10 * target))
+    n, m, p = 5, 8, 2
+    for _ in range(4):
+        d = _rand_qp(rng, n, m, p)
+        Q, q, A, b, G, h = (d[k] for k in ("Q", "q", "A", "b", "G", "h"))
+        x, y = rng.standard_normal(n), rng.standard_normal(p)
+        if on_manifold:
+            kap, v = 0.3, rng.standard_normal(m)
+            z = np.array([float(_b_exact(a, kap)) for a in v])
+            s = np.array([float(_b_exact(-a, kap)) for a in v])
+        else:
+            z, s = rng.uniform(0.05, 2.0, m), rng.uniform(0.05, 2.0, m)
+        v, kap = z - s, float(s @ z) / m
+        kt = target * kap
+        r = O.newton_direction(Q, q, A, b, G, h, x, y, z, s, kt)
+        assert r["status"] == O.SOLVED
+        dx, dy, dv, dz, ds, dk = (r[k] for k in ("dx", "dy", "dv", "dz", "ds", "dkappa"))
+        rt, re, ri = Q @ x + q + G.T @ z + A.T @ y, A @ x - b, G @ x + s - h
+        scale = max(1.0, np.abs(rt).max(), np.abs(ri).max(), np.abs(dx).max(), np.abs(dz).max())
+        assert np.abs(Q @ dx + G.T @ dz + A.T @ dy + rt).max() <= 1e-11 * scale
+        assert np.abs(A @ dx + re).max() <= 1e-11 * scale
+        assert np.abs(G @ dx + ds + ri).max() <= 1e-11 * scale
+        assert abs(dk - (kt - kap)) <= 1e-15 * kap
+        for i in range(m):
+            want_z = _b_exact(v[i], kap) - z[i] + _b_directional(v[i], kap, dv[i], dk)
+            want_s = _b_exact(-v[i], kap) - s[i] + _b_directional(-v[i], kap, -dv[i], dk)
+            assert abs(dz[i] - float(want_z)) <= 1e-12 * scale, (i, dz[i], want_z)
+            assert abs(ds[i] - float(want_s)) <= 1e-12 * scale, (i, ds[i], want_s)
