@@ -404,8 +404,10 @@ int qp_serve_create(const qp_serve_config* cfg, qp_server** out);
 int qp_serve_submit(qp_server* s, const qp_request* r, uint64_t* ticket);
 
 /* QP_PENDING while the request is queued or running; otherwise writes its
- * outputs, fills *res, retires the ticket and returns QP_OK (or the error
- * code of a failed launch).  QP_EINVAL for an unknown ticket. */
+ * outputs, fills *res, retires the ticket and returns QP_OK, or QP_ECUDA when
+ * a device error failed its launch (after such an error every request still
+ * queued fails the same way, and new submissions return QP_ECUDA).
+ * QP_EINVAL for an unknown ticket. */
 int qp_serve_poll(qp_server* s, uint64_t ticket, qp_result* res);
 
 /* As qp_serve_poll for the earliest completed request not yet collected;

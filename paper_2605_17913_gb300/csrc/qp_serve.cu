@@ -246,6 +246,7 @@ struct qp_server {
   cudaError_t issue(Launch& L);
   void finish_launch(Launch& L);
   void fail_launch(Launch& L);
+  void fail_pending();
   // persistent mode
   void run_persistent();
   void fail_all_persistent();
@@ -399,6 +400,20 @@ cudaError_t qp_server::issue(Launch& L) {
   return e;
 }
 
+// After a device error no request is admitted any more: the ones still
+// queued fail too (they hold no arena block yet), so that their callers get
+// QP_ECUDA instead of waiting out their timeouts (called with mu held).
+void qp_server::fail_pending() {
+  const double t = now_ms();
+  for (Req* r : pending) {
+    r->state = kFailed;
+    r->err = QP_ECUDA;
+    r->t_done = t;
+    done_fifo.push_back(r->ticket);
+  }
+  pending.clear();
+}
+
 // A launch whose issue or execution failed: drain its stream (without mu),
 // then fail its requests and release its block (with mu).
 void qp_server::fail_launch(Launch& L) {
@@ -413,6 +428,7 @@ void qp_server::fail_launch(Launch& L) {
   L.reqs.clear();
   L.busy = false;
   fatal = QP_ECUDA;
+  fail_pending();
   cv_done.notify_all();
 }
 
@@ -542,6 +558,7 @@ void qp_server::fail_all_persistent() {
   published.clear();
   inflight_reqs = 0;
   fatal = QP_ECUDA;
+  fail_pending();
   cv_done.notify_all();
 }
 
