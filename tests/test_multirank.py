@@ -63,3 +63,26 @@ def test_reference_arm_other_ranks_do_no_work(capsys):
 
     bench.run_reference(A(), rank=1, world=2)
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_rank0_prints_one_line(capsys):
+    """Rank 0 of the reference arm (the FP64 oracle on the host cores) prints
+    one JSON line with the main arm's metric and unit, and its CPU-baseline
+    and e2e records (no host-device copies)."""
+    import json
+
+    class A:
+        workload, batch, steps, warmup, gpus, kappa_relax = "small", 8, 1, 0, 1, 1e-4
+
+    bench.run_reference(A(), rank=0, world=1)
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    rec = json.loads(lines[0])
+    assert rec["impl"] == "reference"
+    assert rec["metric"] == bench.METRIC and rec["unit"] == bench.UNIT
+    assert rec["higher_is_better"] is True and rec["value"] > 0
+    assert rec["config"]["workload"] == "small" and rec["config"]["sample_per_step"] >= 1
+    assert rec["cpu_baseline"]["kind"] == "oracle" and rec["cpu_baseline"]["cores"] >= 1
+    assert rec["cpu_baseline"]["value"] == rec["value"]
+    assert rec["e2e"] == {"value": rec["value"], "unit": rec["unit"],
+                          "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
