@@ -115,3 +115,29 @@ def test_serve_footprint_and_config_validation(L):
     for tpq, dims in ((64, (8, 10, 0, 20)), (32, (8, 40, 0, 20)), (128, (8, 100, 0, 20))):
         d = _lib.Dims(*dims)
         assert L.qp_handle_create_threads(ctypes.byref(d), tpq, ctypes.byref(h2)) == _lib.QP_ENOTSUP
+
+
+def test_no_fallback_when_the_library_is_missing(monkeypatch, tmp_path):
+    """Without libqpgpu.so every call raises: there is no CPU path."""
+    from paper_2605_17913_gb300 import _lib
+
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "libqpgpu.so"))
+    with pytest.raises(_lib.QPError, match="not built"):
+        _lib.lib()
+
+
+def test_solver_takes_device_tensors_only(L):
+    """Host tensors are refused by the device-array API rather than solved on
+    the CPU; without a GPU, creating a solver fails with the CUDA error."""
+    import torch
+
+    from paper_2605_17913_gb300 import _lib
+    from paper_2605_17913_gb300.solver import QPSolver
+
+    s = QPSolver.__new__(QPSolver)
+    with pytest.raises(_lib.QPError, match="CUDA tensor"):
+        s._check("Q", torch.zeros(2, 3, 3), (2, 3, 3))
+    if not torch.cuda.is_available():
+        with pytest.raises(_lib.QPError, match="QP_ECUDA"):
+            QPSolver(2, 3, 0, 2)
