@@ -14,7 +14,8 @@ C mu = Y u - rhs2, dx = L^-T (u - Y' mu).  Every pivot of that route is
 bounded: B_- >= 1 / (1 + tau) on the eliminated rows (1/2 at the default
 tau = 1), D < 1 / tau on the kept ones.
 The right-hand sides are affine in r_kappa, so the two columns r_kappa = 0
-and d/dr_kappa give every kappa_target.
+and d/dr_kappa give every kappa_target.  The adjoint solve of Alg. 3 takes
+the same route (eq. 14 is symmetric) and gives the oracle's gradients.
 """
 import numpy as np
 import pytest
@@ -126,3 +127,31 @@ def test_two_columns_give_every_kappa_target():
         for key in ("dx", "dv", "dz", "ds"):
             np.testing.assert_allclose(col0[key] + rk * col1[key], ref[key], rtol=0,
                                        atol=1e-9 * max(1.0, np.abs(ref[key]).max()))
+
+
+@pytest.mark.parametrize("workload", ["small", "degenerate"])
+def test_two_level_adjoint_gives_the_oracle_gradients(workload):
+    """Alg. 3 through the same route: eq. 14 is symmetric, so the adjoint is
+    the route with right-hand side (-g, 0, 0) (rho1 = g, everything else 0) at
+    the relaxed point, dz = B_k(v) dv, and the gradient blocks of Alg. 3
+    follow; they equal the oracle's, which solves the full system."""
+    from qpgen import make_instance
+
+    kr = 1e-4
+    for i in range(3):
+        d = make_instance(workload, i)
+        Q, q, A, b, G, h, g = (d[k] for k in ("Q", "q", "A", "b", "G", "h", "g"))
+        r = O.solve(Q, q, A, b, G, h, tol=1e-12, kappa_relax=kr, g=g)
+        assert r["status"] == O.SOLVED
+        x, y, z, s = r["xr"], r["yr"], r["zr"], r["sr"]
+        v = z - s
+        n, m, p = Q.shape[0], G.shape[0], A.shape[0]
+        adj = _two_level(Q, G, A, v, kr, g, np.zeros(p), np.zeros(m), np.zeros(m),
+                         np.zeros(m), 0.0, 1.0)
+        dx, dy, dz = adj["dx"], adj["dy"], _db(v, kr) * adj["dv"]
+        got = dict(dq=dx, db=-dy, dh=-dz, dQ=0.5 * (np.outer(dx, x) + np.outer(x, dx)),
+                   dA=np.outer(dy, x) + np.outer(y, dx), dG=np.outer(dz, x) + np.outer(z, dx))
+        for key, val in got.items():
+            ref = r[key]
+            err = np.abs(val - ref).max() / max(1.0, np.abs(ref).max())
+            assert err <= 1e-7, (workload, i, key, err)
